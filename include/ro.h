@@ -1,0 +1,268 @@
+/*
+ * ro.h — C ABI of the residency-octree ray caster (GB300, sm_103a).
+ *
+ * The library implements the per-frame path of the Residency Octree method
+ * (Herzberger et al., arXiv 2309.04393): a multi-channel multi-resolution
+ * page-table hierarchy over one brick cache (Sec. 5.1), a residency octree
+ * whose nodes hold per-channel partial-residency bitmasks and min/max
+ * metadata (Sec. 5.2, Sec. 7), its incremental update (Sec. 5.3), and the
+ * mixed-resolution multi-volume ray caster with empty-space skipping,
+ * coarser-level substitution and ray-guided request emission (Sec. 6.1,
+ * Algorithm 1; Sec. 6.2).
+ *
+ * Conventions for every call:
+ *  - Every call returns an ro_status and never aborts.  A CUDA error is
+ *    latched in the context: later calls return RO_ERR_CUDA until the
+ *    context is destroyed.  ro_last_error() gives a one-line message.
+ *  - Device memory is owned by the caller.  ro_query_sizes() says how many
+ *    bytes one device arena needs; the caller allocates it (e.g. a torch
+ *    uint8 tensor) and passes its pointer to ro_create().  The library never
+ *    calls cudaMalloc.  Host buffers passed in are owned by the caller.
+ *  - All device work is enqueued on the stream given to ro_create().  Calls
+ *    that return host data (ro_read_requests, ro_upload_bricks when it must
+ *    evict, ro_get_stats, ro_debug_read) wait for that stream by polling an
+ *    event against a deadline (ro_set_timeout, default 30 s) and return
+ *    RO_ERR_TIMEOUT when it passes.
+ *  - Arrays are C order with x fastest ([z][y][x]).  Sizes are in voxels
+ *    unless stated.  Positions are physical: the volume occupies
+ *    [0, dims[a] * spacing[a]) on each axis.
+ *  - Not thread-safe: one host thread per context.
+ */
+#ifndef RO_H
+#define RO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RO_MAX_CHANNELS 16
+#define RO_MAX_LEVELS 16
+#define RO_NONE 0xFFFFFFFFu
+
+typedef enum {
+  RO_OK = 0,
+  RO_ERR_INVALID_ARG = 1, /* a size, pointer or id outside what the call accepts */
+  RO_ERR_CUDA = 2,        /* a CUDA runtime error (latched) */
+  RO_ERR_CAPACITY = 3,    /* arena too small, or more items than the descriptor allows */
+  RO_ERR_TIMEOUT = 4,     /* the stream did not reach the call's event before the deadline */
+  RO_ERR_INTERNAL = 5     /* a device-side index guard fired (latched) */
+} ro_status;
+
+/* Volume, cache and octree parameters, fixed at creation (Sec. 5.1: brick
+ * size, cache size and channel count; Sec. 5.2: octree depth via the leaf
+ * extent; Sec. 7: m, k chosen at initialisation).
+ *  dims          level-0 voxels per axis, each >= 1
+ *  spacing       physical size of a level-0 voxel per axis, > 0
+ *  channels      m, 1..16
+ *  value_bits    8 (u8) or 16 (u16) per voxel
+ *  brick         B, brick edge in voxels: 8, 16, 32 or 64
+ *  levels        k, 1..16, with m*k <= 256 (the 8-bit page-table id)
+ *  leaf_extent   octree leaf extent in level-0 voxels per axis: a power of
+ *                two <= B (so a leaf lies inside one brick of every level)
+ *  cache_slots   brick cache capacity in bricks, >= 1
+ *  max_requests  request-list limit per frame (Sec. 4), >= 1
+ *  max_upload    bricks per ro_upload_bricks call, >= 1
+ *  max_meta      leaf metadata entries per ro_update_residency_octree chunk
+ * Bricks per axis at every level must be <= 256 (the 8-bit offsets of the
+ * brick ID, Sec. 7). */
+typedef struct {
+  uint32_t dims[3];
+  float spacing[3];
+  uint32_t channels;
+  uint32_t value_bits;
+  uint32_t brick;
+  uint32_t levels;
+  uint32_t leaf_extent[3];
+  uint32_t cache_slots;
+  uint32_t max_requests;
+  uint32_t max_upload;
+  uint32_t max_meta;
+} ro_desc;
+
+/* Byte sizes of the parts of the device arena (all 256-byte aligned inside
+ * it, in this order) and their sum. */
+typedef struct {
+  uint64_t cache;        /* cache_slots * slot_pitch voxels bytes */
+  uint64_t page_table;   /* one u32 per brick of the virtual hierarchy: slot + 1, 0 = absent */
+  uint64_t octree;       /* n_nodes * channel_stride u32 node words */
+  uint64_t req_flags;    /* one byte per brick */
+  uint64_t node_req_flags;/* one byte per (node, channel) */
+  uint64_t used_flags;   /* one byte per slot */
+  uint64_t last_used;    /* one u32 frame stamp per slot */
+  uint64_t staging;      /* max_upload bricks, host-to-device landing area */
+  uint64_t frame;        /* per-frame constants: LUTs, bucket prefix sums */
+  uint64_t lists;        /* request / node-request output lists + counts */
+  uint64_t scratch;      /* compaction partial counts, update item lists, stats */
+  uint64_t total;
+  uint64_t slot_pitch;   /* bytes per cache slot ((B+2)^3 voxels, padded) */
+  uint64_t n_bricks;     /* bricks of the virtual hierarchy, all channels and levels */
+  uint64_t n_nodes;      /* octree nodes, all depths */
+  uint32_t depth;        /* octree depth D (leaves at depth D) */
+  uint32_t channel_stride;/* u32 words per node: channels rounded up to a power of two */
+} ro_buffer_sizes;
+
+typedef struct ro_ctx ro_ctx;
+
+/* Fills *out for desc.  Returns RO_ERR_INVALID_ARG for a descriptor that
+ * breaks any rule above. */
+ro_status ro_query_sizes(const ro_desc* desc, ro_buffer_sizes* out);
+
+/* Creates a context over the caller's device arena (arena_bytes >=
+ * sizes.total, 256-byte aligned) on the CUDA stream `stream` (a
+ * cudaStream_t; NULL = legacy default stream) of the current device.
+ * Enqueues the initialisation: empty page tables, every node INVALID with an
+ * empty mask for every channel (Sec. 5.2), cleared flags.  The arena must
+ * stay allocated until ro_destroy. */
+ro_status ro_create(const ro_desc* desc, void* arena_device, uint64_t arena_bytes, void* stream, ro_ctx** out);
+
+/* Waits for the context's stream and frees the host-side context.  The
+ * arena is the caller's to free afterwards. */
+ro_status ro_destroy(ro_ctx* ctx);
+
+/* Makes n bricks resident (Sec. 5.3, "Updating residency information" and
+ * "LRU cache eviction").
+ *  brick_ids  n IDs in the 32-bit format of Sec. 7: page-table id c*k + l in
+ *             bits 31:24, then z, y, x brick offsets (8 bits each); no
+ *             duplicates within one call.
+ *  voxels     host pointer to n bricks of (B+2)^3 voxels each (u8 or u16 per
+ *             value_bits), x fastest, holding level-l voxels b*B-1 .. (b+1)*B
+ *             per axis clamped to the level (a one-voxel border).  Copied
+ *             before the call returns; pinned memory makes the copy faster.
+ *  out_slots  n slots chosen (host), may be NULL.
+ *  out_evicted n IDs evicted to make room, RO_NONE where a free slot was
+ *             used (host), may be NULL.
+ * A brick already resident keeps its slot and gets its data rewritten.
+ * Free slots are used first, in ascending order; then the least recently
+ * used slots (stamped by ro_read_requests), never one chosen earlier in the
+ * same call.  The page table is updated on the device; the octree masks
+ * change at the next ro_update_residency_octree.  n <= max_upload and
+ * n <= cache_slots, else RO_ERR_CAPACITY. */
+ro_status ro_upload_bricks(ro_ctx* ctx, uint32_t n, const uint32_t* brick_ids, const void* voxels,
+                           uint32_t* out_slots, uint32_t* out_evicted);
+
+/* Leaf metadata entry: raw value range of channel `channel` over leaf
+ * `leaf` (x fastest over ceil(dims / leaf_extent) leaves per axis).  The
+ * range must cover every level-0 voxel whose trilinear support reaches the
+ * leaf.  vmin > vmax marks the leaf's channel INVALID again. */
+typedef struct {
+  uint32_t leaf;
+  uint32_t channel;
+  uint32_t vmin;
+  uint32_t vmax;
+} ro_leaf_meta;
+
+/* Brings the residency octree up to date (Sec. 5.3): writes the n_meta leaf
+ * ranges (quantised to the 8-bit node format of Sec. 7: u16 values >> 8),
+ * recomputes the partial-residency masks of every leaf that overlaps a brick
+ * uploaded or evicted since the previous call, and recomputes every
+ * ancestor of a changed leaf as the bitwise OR of its children's masks and
+ * the hull of their ranges (INVALID if any child is).  No atomics.
+ * meta is a host pointer (NULL if n_meta = 0). */
+ro_status ro_update_residency_octree(ro_ctx* ctx, uint32_t n_meta, const ro_leaf_meta* meta);
+
+/* Camera (physical units).  ortho (perspective = 0): pixel (i, j) starts at
+ * eye + a*right + b*up, a = (i + 0.5 - W/2)*pixel, b = (H/2 - j - 0.5)*pixel,
+ * and travels along forward.  perspective: rays start at eye along
+ * normalize(forward + a*right + b*up), a = (2(i + 0.5)/W - 1)*tan_x,
+ * b = (1 - 2(j + 0.5)/H)*tan_y.  forward/right/up are unit vectors. */
+typedef struct {
+  float eye[3];
+  float forward[3];
+  float right[3];
+  float up[3];
+  uint32_t perspective;
+  float tan_x, tan_y;
+  float pixel;
+} ro_camera;
+
+/* Transfer function of one channel: a raw value v maps to the LUT
+ * coordinate clamp((v - lo) * scale, 0, 255) and to the RGBA interpolated
+ * linearly between the 256 knots of lut (host pointer, 256*4 floats). */
+typedef struct {
+  float lo;
+  float scale;
+  const float* lut;
+} ro_tf;
+
+/* Per-frame rendering parameters.
+ *  dt          lattice spacing along the ray, physical units, > 0
+ *  lod_t       desired-level thresholds: lod(t) = #{l in 1..k-1 : t >= lod_t[l]}
+ *              (t = physical distance from the ray origin); index 0 unused
+ *  lmin, lmax  per-channel level range, 0 <= lmin <= lmax < k (Sec. 6.2)
+ *  start_depth octree depth at which traversal starts (Sec. 7), <= depth
+ *  skip        1 = empty-space skipping on
+ *  ert         early ray termination once transmittance < ert; 0 = off
+ *  debug_*     optional device pointers (W*H u32 each) for the per-pixel
+ *              selection hash, evaluated samples, final lattice index and
+ *              brick samples; NULL to skip. */
+typedef struct {
+  float dt;
+  float lod_t[RO_MAX_LEVELS];
+  uint32_t lmin[RO_MAX_CHANNELS];
+  uint32_t lmax[RO_MAX_CHANNELS];
+  uint32_t start_depth;
+  uint32_t skip;
+  float ert;
+  uint32_t* debug_hash;
+  uint32_t* debug_n_eval;
+  uint32_t* debug_i_end;
+  uint32_t* debug_n_bs;
+} ro_render_params;
+
+/* Renders one frame (Sec. 6): one thread per pixel marches its ray through
+ * the residency octree, skips empty nodes, picks each channel's brick
+ * (substituting coarser resident levels on a miss), samples it trilinearly,
+ * applies the channel's TF with opacity correction for the adaptive step,
+ * composites additively front to back with early termination, and flags
+ * requested bricks, requested nodes and used slots with plain stores.
+ *  tfs       host array of m transfer functions
+ *  image     device pointer, W*H RGBA float32 (16 bytes per pixel), row j
+ *            at image + 4*W*j; written for every pixel
+ * 1 <= W, H <= 16384.  Enqueued on the stream; returns without waiting. */
+ro_status ro_render(ro_ctx* ctx, const ro_camera* camera, const ro_tf* tfs, const ro_render_params* params,
+                    float* image, uint32_t W, uint32_t H);
+
+/* Compacts the flags of the frames rendered since the previous call
+ * (Sec. 4: a global request limit keeps the copy small): brick requests as
+ * sorted IDs, node requests as node*m + channel, usage as
+ * last_used[slot] = frame counter; clears every flag.  Waits for the stream.
+ *  ids       host, capacity cap; receives min(total, cap, max_requests) IDs
+ *            in ascending order
+ *  n         number written; overflow = total - n
+ *  node_ids  host, capacity node_cap (may be NULL with node_cap = 0) */
+ro_status ro_read_requests(ro_ctx* ctx, uint32_t* ids, uint32_t cap, uint32_t* n, uint32_t* overflow,
+                           uint32_t* node_ids, uint32_t node_cap, uint32_t* n_node);
+
+/* Per-frame counters of the last ro_render, summed over its blocks:
+ * [0] pixels whose ray hit the volume, [1] evaluated lattice samples,
+ * [2] channel samples read from bricks, [3] samples rendered from
+ * homogeneous nodes, [4] skips, [5] lattice samples skipped over.
+ * Waits for the stream. */
+ro_status ro_get_stats(ro_ctx* ctx, uint64_t out[8]);
+
+/* Copies one internal array to the host (waits for the stream):
+ * what = 0 octree words (n_nodes * channel_stride u32), 1 page table
+ * (n_bricks u32), 2 last_used (cache_slots u32), 3 request flags (n_bricks
+ * bytes), 4 used flags (cache_slots bytes).  bytes must equal the array's
+ * size. */
+ro_status ro_debug_read(ro_ctx* ctx, uint32_t what, void* host, uint64_t bytes);
+
+/* Linear index of a brick ID in the page table (c*k + l table, then z, y,
+ * x), or RO_NONE for an ID outside the hierarchy. */
+uint32_t ro_brick_index(const ro_ctx* ctx, uint32_t brick_id);
+
+/* Deadline for the waits above, in milliseconds (default 30000). */
+ro_status ro_set_timeout(ro_ctx* ctx, uint32_t ms);
+
+/* Message of the last error of this context (static storage while the
+ * context lives); "ok" if none.  A NULL ctx gives the last ro_create error. */
+const char* ro_last_error(const ro_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RO_H */

@@ -1,0 +1,760 @@
+// Host side of the C ABI (include/ro.h): descriptor validation, device-arena
+// layout, the LRU slot policy (Sec. 5.3), update item lists, frame constants,
+// and the bounded waits on the context's stream.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/ro.h"
+#include "ro_internal.h"
+
+using ro::Geometry;
+
+namespace {
+
+constexpr uint64_t kAlign = 256;
+constexpr uint32_t kMaxItems = 65536;           // update items per chunk
+constexpr uint32_t kMaxStatBlocks = 65536;      // render blocks whose counters are kept
+constexpr uint32_t kItemLeaves = 4096;          // leaves per update item (boxes are split)
+
+uint64_t align_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
+
+bool is_pow2(uint32_t v) { return v && !(v & (v - 1)); }
+
+int ilog2(uint32_t v) {
+  int r = 0;
+  while ((1u << r) < v) ++r;
+  return r;
+}
+
+struct Layout {
+  uint64_t off[11];
+  ro_buffer_sizes sz;
+  uint64_t req_pad, node_req_pad, used_pad;
+  uint64_t sc_counts, sc_totals, sc_items, sc_meta, sc_ins_index, sc_ins_slot, sc_ev_index, sc_stats, sc_err;
+  uint64_t fr_lut, fr_prefix, li_req, li_node;
+  uint32_t max_tiles;
+};
+
+std::string g_create_error = "ok";
+
+ro_status make_geometry(const ro_desc* d, Geometry* g, std::string* why) {
+  auto fail = [&](const char* m) {
+    *why = m;
+    return RO_ERR_INVALID_ARG;
+  };
+  if (!d) return fail("null descriptor");
+  std::memset(g, 0, sizeof(*g));
+  for (int a = 0; a < 3; ++a) {
+    if (d->dims[a] < 1 || d->dims[a] > (1u << 24)) return fail("dims must be in [1, 2^24]");
+    if (!(d->spacing[a] > 0.0f) || !std::isfinite(d->spacing[a])) return fail("spacing must be positive and finite");
+  }
+  if (d->channels < 1 || d->channels > RO_MAX_CHANNELS) return fail("channels must be in [1, 16]");
+  if (d->value_bits != 8 && d->value_bits != 16) return fail("value_bits must be 8 or 16");
+  if (d->brick != 8 && d->brick != 16 && d->brick != 32 && d->brick != 64) return fail("brick must be 8, 16, 32 or 64");
+  if (d->levels < 1 || d->levels > RO_MAX_LEVELS) return fail("levels must be in [1, 16]");
+  if (d->channels * d->levels > 256) return fail("channels * levels must be <= 256 (8-bit page-table id)");
+  for (int a = 0; a < 3; ++a)
+    if (!is_pow2(d->leaf_extent[a]) || d->leaf_extent[a] > d->brick) return fail("leaf_extent must be powers of two <= brick");
+  if (d->cache_slots < 1) return fail("cache_slots must be >= 1");
+  if (d->max_requests < 1 || d->max_upload < 1 || d->max_meta < 1) return fail("max_requests/max_upload/max_meta must be >= 1");
+  g->m = (int)d->channels;
+  g->mp = 1;
+  while (g->mp < g->m) g->mp <<= 1;
+  g->k = (int)d->levels;
+  g->B = (int)d->brick;
+  g->blog2 = ilog2(d->brick);
+  g->bpv = d->value_bits / 8;
+  g->edge = d->brick + 2;
+  g->cache_slots = d->cache_slots;
+  for (int a = 0; a < 3; ++a) {
+    g->dims0[a] = (int)d->dims[a];
+    g->spacing[a] = d->spacing[a];
+    g->dimm[a] = std::nextafter((float)d->dims[a], 0.0f);
+    g->leaf_log2[a] = ilog2(d->leaf_extent[a]);
+  }
+  for (int l = 0; l < g->k; ++l)
+    for (int a = 0; a < 3; ++a) {
+      int v = g->dims0[a];
+      for (int q = 0; q < l; ++q) v = (v + 1) / 2;
+      g->ldims[l][a] = v;
+      g->nb[l][a] = (v + g->B - 1) / g->B;
+      if (g->nb[l][a] > 256) return fail("more than 256 bricks per axis (8-bit brick offsets)");
+    }
+  uint64_t off = 0;
+  for (int c = 0; c < g->m; ++c)
+    for (int l = 0; l < g->k; ++l) {
+      g->pt_off[c * g->k + l] = (uint32_t)off;
+      off += (uint64_t)g->nb[l][0] * g->nb[l][1] * g->nb[l][2];
+      if (off >= 0xFFFFFFFFull) return fail("too many bricks");
+    }
+  g->pt_off[g->m * g->k] = (uint32_t)off;
+  g->n_bricks = off;
+  int D = 0;
+  for (int a = 0; a < 3; ++a) {
+    const int nl = (g->dims0[a] + (int)d->leaf_extent[a] - 1) / (int)d->leaf_extent[a];
+    g->nleaf[a] = nl;
+    D = std::max(D, ilog2((uint32_t)nl));
+  }
+  if (D > ro::kMaxDepth) return fail("octree too deep");
+  g->D = D;
+  uint64_t noff = 0;
+  for (int dd = 0; dd <= D; ++dd) {
+    g->node_off[dd] = noff;
+    uint64_t cnt = 1;
+    for (int a = 0; a < 3; ++a) {
+      const uint64_t e = (uint64_t)d->leaf_extent[a] << (D - dd);
+      g->nn[dd][a] = (int)((g->dims0[a] + e - 1) / e);
+      cnt *= (uint64_t)g->nn[dd][a];
+    }
+    noff += cnt;
+  }
+  g->node_off[D + 1] = noff;
+  g->n_nodes = noff;
+  const uint64_t slot_bytes = (uint64_t)g->edge * g->edge * g->edge * g->bpv;
+  g->slot_pitch = (uint32_t)align_up(slot_bytes, kAlign);
+  return RO_OK;
+}
+
+void make_layout(const ro_desc* d, const Geometry& g, Layout* L) {
+  std::memset(L, 0, sizeof(*L));
+  ro_buffer_sizes& s = L->sz;
+  s.slot_pitch = g.slot_pitch;
+  s.n_bricks = g.n_bricks;
+  s.n_nodes = g.n_nodes;
+  s.depth = (uint32_t)g.D;
+  s.channel_stride = (uint32_t)g.mp;
+  L->req_pad = align_up(g.n_bricks, ro::kCompactTile);
+  L->node_req_pad = align_up(g.n_nodes * (uint64_t)g.m, ro::kCompactTile);
+  L->used_pad = align_up(d->cache_slots, ro::kCompactTile);
+  s.cache = (uint64_t)d->cache_slots * g.slot_pitch;
+  s.page_table = align_up(g.n_bricks * 4, kAlign);
+  s.octree = align_up(g.n_nodes * (uint64_t)g.mp * 4, kAlign);
+  s.req_flags = L->req_pad;
+  s.node_req_flags = L->node_req_pad;
+  s.used_flags = L->used_pad;
+  s.last_used = align_up((uint64_t)d->cache_slots * 4, kAlign);
+  s.staging = (uint64_t)d->max_upload * g.slot_pitch;
+  L->fr_lut = 0;
+  L->fr_prefix = (uint64_t)ro::kMaxC * 256 * 16;
+  s.frame = align_up(L->fr_prefix + (uint64_t)ro::kMaxC * 257 * 2, kAlign);
+  L->li_req = 0;
+  L->li_node = align_up((uint64_t)d->max_requests * 4, kAlign);
+  s.lists = L->li_node + align_up((uint64_t)d->max_requests * 4, kAlign);
+  L->max_tiles = (uint32_t)(std::max(L->req_pad, L->node_req_pad) / ro::kCompactTile);
+  uint64_t o = 0;
+  L->sc_counts = o; o = align_up(o + (uint64_t)L->max_tiles * 4, kAlign);
+  L->sc_totals = o; o = align_up(o + 64, kAlign);
+  L->sc_items = o; o = align_up(o + (uint64_t)kMaxItems * sizeof(ro::UpdateItem), kAlign);
+  L->sc_meta = o; o = align_up(o + (uint64_t)d->max_meta * sizeof(ro::MetaItem), kAlign);
+  L->sc_ins_index = o; o = align_up(o + (uint64_t)d->max_upload * 4, kAlign);
+  L->sc_ins_slot = o; o = align_up(o + (uint64_t)d->max_upload * 4, kAlign);
+  L->sc_ev_index = o; o = align_up(o + (uint64_t)d->max_upload * 4, kAlign);
+  L->sc_stats = o; o = align_up(o + (uint64_t)kMaxStatBlocks * ro::kStats * 8, kAlign);
+  L->sc_err = o; o = align_up(o + 64, kAlign);
+  s.scratch = o;
+  const uint64_t parts[11] = {s.cache, s.page_table, s.octree, s.req_flags, s.node_req_flags, s.used_flags,
+                              s.last_used, s.staging, s.frame, s.lists, s.scratch};
+  uint64_t tot = 0;
+  for (int i = 0; i < 11; ++i) {
+    L->off[i] = tot;
+    tot = align_up(tot + parts[i], kAlign);
+  }
+  s.total = tot;
+}
+
+}  // namespace
+
+struct ro_ctx {
+  ro_desc desc;
+  Geometry g;
+  Layout L;
+  uint8_t* arena = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  uint8_t *cache, *req, *node_req, *used, *staging, *scratch;
+  uint32_t *pt, *octree, *last_used, *req_out, *node_out, *err;
+  float4* lut;
+  uint16_t* prefix;
+  std::vector<uint32_t> slot_of_brick;   // page-table index -> slot or RO_NONE
+  std::vector<uint32_t> brick_of_slot;   // slot -> page-table index or RO_NONE
+  std::vector<uint32_t> free_slots;      // descending, pop_back gives the lowest
+  std::vector<uint32_t> pending;         // page-table indices changed since the last update
+  std::vector<float4> host_lut;
+  uint32_t frame = 0;
+  uint32_t timeout_ms = 30000;
+  uint32_t last_blocks = 0;
+  ro_status latched = RO_OK;
+  std::string err_msg = "ok";
+};
+
+namespace {
+
+ro_status set_err(ro_ctx* c, ro_status s, const std::string& m) {
+  c->err_msg = m;
+  if (s == RO_ERR_CUDA || s == RO_ERR_INTERNAL) c->latched = s;
+  return s;
+}
+
+ro_status cuda_check(ro_ctx* c, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return RO_OK;
+  return set_err(c, RO_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define RO_TRY(expr)                 \
+  do {                               \
+    ro_status _s = (expr);           \
+    if (_s != RO_OK) return _s;      \
+  } while (0)
+
+ro_status wait_stream(ro_ctx* c, const char* where) {
+  RO_TRY(cuda_check(c, cudaEventRecord(c->ev, c->stream), where));
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(c->ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return cuda_check(c, e, where);
+    const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+    if (ms > (long long)c->timeout_ms) return set_err(c, RO_ERR_TIMEOUT, std::string(where) + ": stream wait timed out");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  uint32_t e = 0;
+  RO_TRY(cuda_check(c, cudaMemcpy(&e, c->err, 4, cudaMemcpyDeviceToHost), where));
+  if (e != 0) return set_err(c, RO_ERR_INTERNAL, std::string(where) + ": device index guard fired (code " + std::to_string(e) + ")");
+  return RO_OK;
+}
+
+bool decode_id(const ro_ctx* c, uint32_t id, int* ch, int* l, uint32_t* pi) {
+  const Geometry& g = c->g;
+  const uint32_t p = id >> 24;
+  if (p >= (uint32_t)(g.m * g.k)) return false;
+  const int lv = (int)(p % (uint32_t)g.k);
+  const uint32_t bz = (id >> 16) & 0xFF, by = (id >> 8) & 0xFF, bx = id & 0xFF;
+  if (bx >= (uint32_t)g.nb[lv][0] || by >= (uint32_t)g.nb[lv][1] || bz >= (uint32_t)g.nb[lv][2]) return false;
+  *ch = (int)(p / (uint32_t)g.k);
+  *l = lv;
+  *pi = g.pt_off[p] + (bz * (uint32_t)g.nb[lv][1] + by) * (uint32_t)g.nb[lv][0] + bx;
+  return true;
+}
+
+// page-table index -> (channel, level, brick coords)
+void index_to_brick(const Geometry& g, uint32_t pi, int* ch, int* l, uint32_t b[3]) {
+  int p = 0;
+  while (p + 1 < g.m * g.k && g.pt_off[p + 1] <= pi) ++p;
+  *ch = p / g.k;
+  *l = p % g.k;
+  const uint32_t local = pi - g.pt_off[p];
+  const uint32_t nx = (uint32_t)g.nb[*l][0], ny = (uint32_t)g.nb[*l][1];
+  b[0] = local % nx;
+  b[1] = (local / nx) % ny;
+  b[2] = local / (nx * ny);
+}
+
+// Leaf boxes of one channel, split into items of at most kItemLeaves leaves.
+void push_box(std::vector<ro::UpdateItem>& items, uint32_t ch, const uint32_t lo[3], const uint32_t hi[3]) {
+  const uint32_t nx = hi[0] - lo[0], ny = hi[1] - lo[1];
+  uint32_t sx = nx, sy = ny, sz;
+  if (sx > kItemLeaves) sx = kItemLeaves;
+  if ((uint64_t)sx * sy > kItemLeaves) sy = std::max(1u, kItemLeaves / sx);
+  sz = std::max(1u, kItemLeaves / (sx * sy));
+  for (uint32_t z = lo[2]; z < hi[2]; z += sz)
+    for (uint32_t y = lo[1]; y < hi[1]; y += sy)
+      for (uint32_t x = lo[0]; x < hi[0]; x += sx) {
+        ro::UpdateItem it{};
+        it.lo[0] = x; it.lo[1] = y; it.lo[2] = z;
+        it.hi[0] = std::min(x + sx, hi[0]); it.hi[1] = std::min(y + sy, hi[1]); it.hi[2] = std::min(z + sz, hi[2]);
+        it.channel = ch;
+        items.push_back(it);
+      }
+}
+
+}  // namespace
+
+extern "C" {
+
+ro_status ro_query_sizes(const ro_desc* desc, ro_buffer_sizes* out) {
+  if (!out) return RO_ERR_INVALID_ARG;
+  Geometry g;
+  std::string why;
+  ro_status s = make_geometry(desc, &g, &why);
+  if (s != RO_OK) {
+    g_create_error = why;
+    return s;
+  }
+  Layout L;
+  make_layout(desc, g, &L);
+  *out = L.sz;
+  return RO_OK;
+}
+
+ro_status ro_create(const ro_desc* desc, void* arena_device, uint64_t arena_bytes, void* stream, ro_ctx** out) {
+  if (!out) return RO_ERR_INVALID_ARG;
+  *out = nullptr;
+  ro_ctx* c = new (std::nothrow) ro_ctx();
+  if (!c) return RO_ERR_CAPACITY;
+  std::string why;
+  ro_status s = make_geometry(desc, &c->g, &why);
+  if (s != RO_OK) {
+    g_create_error = why;
+    delete c;
+    return s;
+  }
+  c->desc = *desc;
+  make_layout(desc, c->g, &c->L);
+  if (!arena_device || (reinterpret_cast<uintptr_t>(arena_device) % kAlign) != 0) {
+    g_create_error = "arena must be a 256-byte aligned device pointer";
+    delete c;
+    return RO_ERR_INVALID_ARG;
+  }
+  if (arena_bytes < c->L.sz.total) {
+    g_create_error = "arena smaller than ro_query_sizes().total";
+    delete c;
+    return RO_ERR_CAPACITY;
+  }
+  c->arena = static_cast<uint8_t*>(arena_device);
+  c->stream = static_cast<cudaStream_t>(stream);
+  const uint64_t* o = c->L.off;
+  c->cache = c->arena + o[0];
+  c->pt = reinterpret_cast<uint32_t*>(c->arena + o[1]);
+  c->octree = reinterpret_cast<uint32_t*>(c->arena + o[2]);
+  c->req = c->arena + o[3];
+  c->node_req = c->arena + o[4];
+  c->used = c->arena + o[5];
+  c->last_used = reinterpret_cast<uint32_t*>(c->arena + o[6]);
+  c->staging = c->arena + o[7];
+  c->lut = reinterpret_cast<float4*>(c->arena + o[8] + c->L.fr_lut);
+  c->prefix = reinterpret_cast<uint16_t*>(c->arena + o[8] + c->L.fr_prefix);
+  c->req_out = reinterpret_cast<uint32_t*>(c->arena + o[9] + c->L.li_req);
+  c->node_out = reinterpret_cast<uint32_t*>(c->arena + o[9] + c->L.li_node);
+  c->scratch = c->arena + o[10];
+  c->err = reinterpret_cast<uint32_t*>(c->scratch + c->L.sc_err);
+  c->slot_of_brick.assign(c->g.n_bricks, RO_NONE);
+  c->brick_of_slot.assign(desc->cache_slots, RO_NONE);
+  c->free_slots.resize(desc->cache_slots);
+  for (uint32_t i = 0; i < desc->cache_slots; ++i) c->free_slots[i] = desc->cache_slots - 1 - i;
+  c->host_lut.resize((size_t)ro::kMaxC * 256);
+  cudaError_t e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("cudaEventCreate: ") + cudaGetErrorString(e);
+    delete c;
+    return RO_ERR_CUDA;
+  }
+  const ro_buffer_sizes& z = c->L.sz;
+  cudaStream_t st = c->stream;
+  e = cudaMemsetAsync(c->pt, 0, z.page_table, st);
+  if (e == cudaSuccess) e = ro::launch_fill_words(c->octree, z.octree / 4, 0x00FF0000u, st);  // INVALID, empty mask
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->req, 0, z.req_flags, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->node_req, 0, z.node_req_flags, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->used, 0, z.used_flags, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->last_used, 0, z.last_used, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->scratch, 0, z.scratch, st);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("initialisation: ") + cudaGetErrorString(e);
+    cudaEventDestroy(c->ev);
+    delete c;
+    return RO_ERR_CUDA;
+  }
+  *out = c;
+  return RO_OK;
+}
+
+ro_status ro_destroy(ro_ctx* c) {
+  if (!c) return RO_ERR_INVALID_ARG;
+  ro_status s = RO_OK;
+  if (c->latched == RO_OK) s = wait_stream(c, "ro_destroy");
+  if (c->ev) cudaEventDestroy(c->ev);
+  delete c;
+  return s == RO_ERR_INTERNAL ? RO_OK : s;
+}
+
+ro_status ro_set_timeout(ro_ctx* c, uint32_t ms) {
+  if (!c || ms == 0) return RO_ERR_INVALID_ARG;
+  c->timeout_ms = ms;
+  return RO_OK;
+}
+
+const char* ro_last_error(const ro_ctx* c) { return c ? c->err_msg.c_str() : g_create_error.c_str(); }
+
+uint32_t ro_brick_index(const ro_ctx* c, uint32_t id) {
+  if (!c) return RO_NONE;
+  int ch, l;
+  uint32_t pi;
+  return decode_id(c, id, &ch, &l, &pi) ? pi : RO_NONE;
+}
+
+ro_status ro_upload_bricks(ro_ctx* c, uint32_t n, const uint32_t* ids, const void* voxels, uint32_t* out_slots,
+                           uint32_t* out_evicted) {
+  if (!c) return RO_ERR_INVALID_ARG;
+  if (c->latched != RO_OK) return c->latched;
+  if (n == 0) return RO_OK;
+  if (!ids || !voxels) return set_err(c, RO_ERR_INVALID_ARG, "ro_upload_bricks: null pointer");
+  if (n > c->desc.max_upload || n > c->desc.cache_slots)
+    return set_err(c, RO_ERR_CAPACITY, "ro_upload_bricks: n exceeds max_upload or cache_slots");
+  std::vector<uint32_t> pis(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    int ch, l;
+    if (!decode_id(c, ids[i], &ch, &l, &pis[i]))
+      return set_err(c, RO_ERR_INVALID_ARG, "ro_upload_bricks: brick id outside the hierarchy");
+  }
+  {
+    std::vector<uint32_t> s(pis);
+    std::sort(s.begin(), s.end());
+    if (std::adjacent_find(s.begin(), s.end()) != s.end())
+      return set_err(c, RO_ERR_INVALID_ARG, "ro_upload_bricks: duplicate brick id");
+  }
+  // slot choice: keep resident bricks' slots, then free slots, then LRU
+  std::vector<uint32_t> slots(n, RO_NONE), evicted(n, RO_NONE);
+  std::vector<uint8_t> taken;  // slots assigned in this call
+  uint32_t need = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    if (c->slot_of_brick[pis[i]] != RO_NONE) slots[i] = c->slot_of_brick[pis[i]];
+    else ++need;
+  }
+  const uint32_t from_free = std::min<uint32_t>(need, (uint32_t)c->free_slots.size());
+  std::vector<uint32_t> lru;
+  if (need > from_free) {
+    std::vector<uint32_t> stamps(c->desc.cache_slots);
+    RO_TRY(wait_stream(c, "ro_upload_bricks"));
+    RO_TRY(cuda_check(c, cudaMemcpy(stamps.data(), c->last_used, 4ull * c->desc.cache_slots, cudaMemcpyDeviceToHost),
+                      "ro_upload_bricks: last_used"));
+    std::vector<uint8_t> keep(c->desc.cache_slots, 0);
+    for (uint32_t i = 0; i < n; ++i)
+      if (slots[i] != RO_NONE) keep[slots[i]] = 1;
+    std::vector<uint32_t> cand;
+    cand.reserve(c->desc.cache_slots);
+    for (uint32_t sl = 0; sl < c->desc.cache_slots; ++sl)
+      if (c->brick_of_slot[sl] != RO_NONE && !keep[sl]) cand.push_back(sl);
+    const uint32_t want = need - from_free;
+    if (cand.size() < want) return set_err(c, RO_ERR_CAPACITY, "ro_upload_bricks: not enough evictable slots");
+    std::partial_sort(cand.begin(), cand.begin() + want, cand.end(), [&](uint32_t a, uint32_t b) {
+      return stamps[a] != stamps[b] ? stamps[a] < stamps[b] : a < b;
+    });
+    lru.assign(cand.begin(), cand.begin() + want);
+  }
+  uint32_t used_free = 0, used_lru = 0;
+  std::vector<uint32_t> ev_index;
+  for (uint32_t i = 0; i < n; ++i) {
+    if (slots[i] != RO_NONE) continue;
+    uint32_t sl;
+    if (used_free < from_free) {
+      sl = c->free_slots.back();
+      c->free_slots.pop_back();
+      ++used_free;
+    } else {
+      sl = lru[used_lru++];
+      const uint32_t old = c->brick_of_slot[sl];
+      c->slot_of_brick[old] = RO_NONE;
+      ev_index.push_back(old);
+      c->pending.push_back(old);
+      int ch, l;
+      uint32_t b[3];
+      index_to_brick(c->g, old, &ch, &l, b);
+      evicted[i] = ((uint32_t)(ch * c->g.k + l) << 24) | (b[2] << 16) | (b[1] << 8) | b[0];
+    }
+    slots[i] = sl;
+    c->brick_of_slot[sl] = pis[i];
+    c->slot_of_brick[pis[i]] = sl;
+    c->pending.push_back(pis[i]);
+  }
+  const uint64_t bytes = (uint64_t)c->g.edge * c->g.edge * c->g.edge * c->g.bpv;
+  cudaStream_t st = c->stream;
+  RO_TRY(cuda_check(c, cudaMemcpy2DAsync(c->staging, c->g.slot_pitch, voxels, bytes, bytes, n, cudaMemcpyHostToDevice, st),
+                    "ro_upload_bricks: voxels"));
+  uint32_t* d_ins_index = reinterpret_cast<uint32_t*>(c->scratch + c->L.sc_ins_index);
+  uint32_t* d_ins_slot = reinterpret_cast<uint32_t*>(c->scratch + c->L.sc_ins_slot);
+  uint32_t* d_ev_index = reinterpret_cast<uint32_t*>(c->scratch + c->L.sc_ev_index);
+  RO_TRY(cuda_check(c, cudaMemcpyAsync(d_ins_index, pis.data(), 4ull * n, cudaMemcpyHostToDevice, st), "ro_upload_bricks"));
+  RO_TRY(cuda_check(c, cudaMemcpyAsync(d_ins_slot, slots.data(), 4ull * n, cudaMemcpyHostToDevice, st), "ro_upload_bricks"));
+  if (!ev_index.empty())
+    RO_TRY(cuda_check(c, cudaMemcpyAsync(d_ev_index, ev_index.data(), 4ull * ev_index.size(), cudaMemcpyHostToDevice, st),
+                      "ro_upload_bricks"));
+  ro::ScatterArgs a{};
+  a.staging = c->staging;
+  a.cache = c->cache;
+  a.pt = c->pt;
+  a.ins_index = d_ins_index;
+  a.ins_slot = d_ins_slot;
+  a.n_ins = n;
+  a.ev_index = d_ev_index;
+  a.n_ev = (uint32_t)ev_index.size();
+  a.slot_pitch = c->g.slot_pitch;
+  a.cache_slots = c->desc.cache_slots;
+  a.n_bricks = c->g.n_bricks;
+  a.err = c->err;
+  RO_TRY(cuda_check(c, ro::launch_scatter(a, st), "ro_upload_bricks: scatter"));
+  // the caller's host buffers may be reused once the copies have landed
+  RO_TRY(wait_stream(c, "ro_upload_bricks"));
+  if (out_slots) std::memcpy(out_slots, slots.data(), 4ull * n);
+  if (out_evicted) std::memcpy(out_evicted, evicted.data(), 4ull * n);
+  return RO_OK;
+}
+
+ro_status ro_update_residency_octree(ro_ctx* c, uint32_t n_meta, const ro_leaf_meta* meta) {
+  if (!c) return RO_ERR_INVALID_ARG;
+  if (c->latched != RO_OK) return c->latched;
+  if (n_meta && !meta) return set_err(c, RO_ERR_INVALID_ARG, "ro_update_residency_octree: null meta");
+  const Geometry& g = c->g;
+  const uint64_t n_leaves = (uint64_t)g.nleaf[0] * g.nleaf[1] * g.nleaf[2];
+  for (uint32_t i = 0; i < n_meta; ++i)
+    if (meta[i].leaf >= n_leaves || meta[i].channel >= (uint32_t)g.m)
+      return set_err(c, RO_ERR_INVALID_ARG, "ro_update_residency_octree: leaf or channel out of range");
+  // last entry wins for a repeated (leaf, channel)
+  std::vector<ro::MetaItem> mi;
+  mi.reserve(n_meta);
+  {
+    std::vector<uint32_t> order(n_meta);
+    for (uint32_t i = 0; i < n_meta; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+      const uint64_t ka = (uint64_t)meta[a].leaf * g.m + meta[a].channel, kb = (uint64_t)meta[b].leaf * g.m + meta[b].channel;
+      return ka < kb;
+    });
+    for (uint32_t q = 0; q < n_meta; ++q) {
+      const uint32_t i = order[q];
+      const bool last = q + 1 == n_meta || meta[order[q + 1]].leaf != meta[i].leaf || meta[order[q + 1]].channel != meta[i].channel;
+      if (last) mi.push_back({meta[i].leaf, meta[i].channel, meta[i].vmin, meta[i].vmax});
+    }
+  }
+  // items: leaf boxes of changed bricks (masks recomputed), then metadata leaves
+  std::vector<ro::UpdateItem> brick_items, meta_items;
+  std::sort(c->pending.begin(), c->pending.end());
+  c->pending.erase(std::unique(c->pending.begin(), c->pending.end()), c->pending.end());
+  for (uint32_t pi : c->pending) {
+    int ch, l;
+    uint32_t b[3], lo[3], hi[3];
+    index_to_brick(g, pi, &ch, &l, b);
+    for (int a = 0; a < 3; ++a) {
+      const uint64_t v0 = (uint64_t)b[a] << (g.blog2 + l);
+      uint64_t v1 = (uint64_t)(b[a] + 1) << (g.blog2 + l);
+      if (v1 > (uint64_t)g.dims0[a]) v1 = (uint64_t)g.dims0[a];
+      lo[a] = (uint32_t)(v0 >> g.leaf_log2[a]);
+      hi[a] = (uint32_t)((v1 + (1ull << g.leaf_log2[a]) - 1) >> g.leaf_log2[a]);
+    }
+    push_box(brick_items, (uint32_t)ch, lo, hi);
+  }
+  for (const ro::MetaItem& m : mi) {
+    uint32_t lo[3], hi[3];
+    lo[0] = m.leaf % g.nleaf[0];
+    lo[1] = (m.leaf / g.nleaf[0]) % g.nleaf[1];
+    lo[2] = (uint32_t)(m.leaf / ((uint64_t)g.nleaf[0] * g.nleaf[1]));
+    for (int a = 0; a < 3; ++a) hi[a] = lo[a] + 1;
+    push_box(meta_items, m.channel, lo, hi);
+  }
+  cudaStream_t st = c->stream;
+  ro::UpdateArgs a{};
+  a.g = g;
+  a.pt = c->pt;
+  a.octree = c->octree;
+  a.err = c->err;
+  ro::UpdateItem* d_items = reinterpret_cast<ro::UpdateItem*>(c->scratch + c->L.sc_items);
+  ro::MetaItem* d_meta = reinterpret_cast<ro::MetaItem*>(c->scratch + c->L.sc_meta);
+  // metadata in chunks of max_meta
+  for (size_t q = 0; q < mi.size(); q += c->desc.max_meta) {
+    const uint32_t nm = (uint32_t)std::min<size_t>(c->desc.max_meta, mi.size() - q);
+    RO_TRY(cuda_check(c, cudaMemcpyAsync(d_meta, mi.data() + q, nm * sizeof(ro::MetaItem), cudaMemcpyHostToDevice, st),
+                      "ro_update_residency_octree: meta"));
+    a.meta = d_meta;
+    a.n_meta = nm;
+    RO_TRY(cuda_check(c, ro::launch_write_meta(a, st), "ro_update_residency_octree: write_meta"));
+    // the copy source is pageable host memory: the next chunk may reuse d_meta
+    // only after this launch; stream order guarantees it
+  }
+  a.n_meta = 0;
+  // leaf masks + bottom-up passes, chunk by chunk
+  std::vector<ro::UpdateItem> all(brick_items);
+  const size_t n_brick_items = brick_items.size();
+  all.insert(all.end(), meta_items.begin(), meta_items.end());
+  for (size_t q = 0; q < all.size(); q += kMaxItems) {
+    const uint32_t ni = (uint32_t)std::min<size_t>(kMaxItems, all.size() - q);
+    RO_TRY(cuda_check(c, cudaMemcpyAsync(d_items, all.data() + q, ni * sizeof(ro::UpdateItem), cudaMemcpyHostToDevice, st),
+                      "ro_update_residency_octree: items"));
+    a.items = d_items;
+    a.n_items = q < n_brick_items ? (uint32_t)std::min<size_t>(ni, n_brick_items - q) : 0;
+    RO_TRY(cuda_check(c, ro::launch_leaf_masks(a, st), "ro_update_residency_octree: leaf masks"));
+    a.n_items = ni;
+    for (int d = g.D - 1; d >= 0; --d) {
+      a.depth = d;
+      RO_TRY(cuda_check(c, ro::launch_reduce_depth(a, st), "ro_update_residency_octree: reduce"));
+    }
+    // d_items is rewritten by the next chunk's copy, which stream order puts
+    // after these launches
+  }
+  c->pending.clear();
+  return RO_OK;
+}
+
+ro_status ro_render(ro_ctx* c, const ro_camera* cam, const ro_tf* tfs, const ro_render_params* p, float* image,
+                    uint32_t W, uint32_t H) {
+  if (!c) return RO_ERR_INVALID_ARG;
+  if (c->latched != RO_OK) return c->latched;
+  if (!cam || !tfs || !p || !image) return set_err(c, RO_ERR_INVALID_ARG, "ro_render: null pointer");
+  if (W < 1 || H < 1 || W > 16384 || H > 16384) return set_err(c, RO_ERR_INVALID_ARG, "ro_render: W and H must be in [1, 16384]");
+  const uint64_t blocks = (uint64_t)((W + 15) / 16) * ((H + 15) / 16);
+  if (blocks > kMaxStatBlocks) return set_err(c, RO_ERR_CAPACITY, "ro_render: image larger than 65536 blocks of 16x16");
+  const Geometry& g = c->g;
+  if (!(p->dt > 0.0f) || !std::isfinite(p->dt)) return set_err(c, RO_ERR_INVALID_ARG, "ro_render: dt must be positive");
+  if (p->start_depth > (uint32_t)g.D) return set_err(c, RO_ERR_INVALID_ARG, "ro_render: start_depth beyond the octree depth");
+  for (int ch = 0; ch < g.m; ++ch) {
+    if (p->lmin[ch] > p->lmax[ch] || p->lmax[ch] >= (uint32_t)g.k)
+      return set_err(c, RO_ERR_INVALID_ARG, "ro_render: need lmin <= lmax < levels");
+    if (!tfs[ch].lut) return set_err(c, RO_ERR_INVALID_ARG, "ro_render: null LUT");
+  }
+  ro::RenderArgs a{};
+  a.g = g;
+  for (int q = 0; q < 3; ++q) {
+    a.eye[q] = cam->eye[q];
+    a.fwd[q] = cam->forward[q];
+    a.right[q] = cam->right[q];
+    a.up[q] = cam->up[q];
+  }
+  a.persp = cam->perspective ? 1 : 0;
+  a.tan_x = cam->tan_x;
+  a.tan_y = cam->tan_y;
+  a.pixel = cam->pixel;
+  a.W = (int)W;
+  a.H = (int)H;
+  a.dt = p->dt;
+  for (int l = 0; l < ro::kMaxL; ++l) a.lod_t[l] = p->lod_t[l];
+  for (int ch = 0; ch < ro::kMaxC; ++ch) {
+    a.lmin[ch] = ch < g.m ? (int)p->lmin[ch] : 0;
+    a.lmax[ch] = ch < g.m ? (int)p->lmax[ch] : 0;
+    a.tf_lo[ch] = ch < g.m ? tfs[ch].lo : 0.0f;
+    a.tf_scale[ch] = ch < g.m ? tfs[ch].scale : 0.0f;
+  }
+  // traversal depth per level (R8): deepest depth whose nodes are at least
+  // one step long along every axis, physically
+  for (int l = 0; l < ro::kMaxL; ++l) {
+    const double step = (double)p->dt * std::ldexp(1.0, l);
+    int best = 0;
+    for (int d = 0; d <= g.D; ++d) {
+      double mn = INFINITY;
+      for (int q = 0; q < 3; ++q) mn = std::min(mn, std::ldexp(1.0, g.leaf_log2[q] + g.D - d) * (double)g.spacing[q]);
+      if (mn >= step) best = d;
+    }
+    a.sdepth[l] = best;
+  }
+  a.start_depth = (int)p->start_depth;
+  a.skip = p->skip ? 1 : 0;
+  a.ert = p->ert;
+  a.cache = c->cache;
+  a.pt = c->pt;
+  a.octree = c->octree;
+  a.req = c->req;
+  a.node_req = c->node_req;
+  a.used = c->used;
+  a.lut = c->lut;
+  a.prefix = c->prefix;
+  a.image = reinterpret_cast<float4*>(image);
+  a.dbg_hash = p->debug_hash;
+  a.dbg_n_eval = p->debug_n_eval;
+  a.dbg_i_end = p->debug_i_end;
+  a.dbg_n_bs = p->debug_n_bs;
+  a.block_stats = reinterpret_cast<unsigned long long*>(c->scratch + c->L.sc_stats);
+  a.err = c->err;
+  for (int ch = 0; ch < g.m; ++ch)
+    std::memcpy(&c->host_lut[(size_t)ch * 256], tfs[ch].lut, 256 * sizeof(float4));
+  cudaStream_t st = c->stream;
+  RO_TRY(cuda_check(c, cudaMemcpyAsync(c->lut, c->host_lut.data(), (size_t)g.m * 256 * sizeof(float4), cudaMemcpyHostToDevice, st),
+                    "ro_render: LUT upload"));
+  ro::PrefixArgs pa{};
+  pa.m = g.m;
+  pa.bpv = g.bpv;
+  for (int ch = 0; ch < ro::kMaxC; ++ch) {
+    pa.tf_lo[ch] = a.tf_lo[ch];
+    pa.tf_scale[ch] = a.tf_scale[ch];
+  }
+  pa.lut = c->lut;
+  pa.prefix = c->prefix;
+  RO_TRY(cuda_check(c, ro::launch_prefix(pa, st), "ro_render: prefix"));
+  const bool debug = p->debug_hash || p->debug_n_eval || p->debug_i_end || p->debug_n_bs;
+  RO_TRY(cuda_check(c, ro::launch_render(a, debug, st), "ro_render: render"));
+  c->last_blocks = (uint32_t)blocks;
+  ++c->frame;
+  return RO_OK;
+}
+
+ro_status ro_read_requests(ro_ctx* c, uint32_t* ids, uint32_t cap, uint32_t* n, uint32_t* overflow, uint32_t* node_ids,
+                           uint32_t node_cap, uint32_t* n_node) {
+  if (!c) return RO_ERR_INVALID_ARG;
+  if (c->latched != RO_OK) return c->latched;
+  if ((cap && !ids) || (node_cap && !node_ids)) return set_err(c, RO_ERR_INVALID_ARG, "ro_read_requests: null list");
+  const Geometry& g = c->g;
+  cudaStream_t st = c->stream;
+  uint32_t* counts = reinterpret_cast<uint32_t*>(c->scratch + c->L.sc_counts);
+  uint32_t* totals = reinterpret_cast<uint32_t*>(c->scratch + c->L.sc_totals);
+  ro::CompactArgs a{};
+  a.g = g;
+  a.block_counts = counts;
+  a.flags = c->req;
+  a.n = c->L.req_pad;
+  a.n_tiles = (uint32_t)(c->L.req_pad / ro::kCompactTile);
+  a.out = c->req_out;
+  a.cap = c->desc.max_requests;
+  a.total = totals;
+  a.id_mode = 0;
+  RO_TRY(cuda_check(c, ro::launch_compact(a, st), "ro_read_requests: compact"));
+  a.flags = c->node_req;
+  a.n = c->L.node_req_pad;
+  a.n_tiles = (uint32_t)(c->L.node_req_pad / ro::kCompactTile);
+  a.out = c->node_out;
+  a.total = totals + 1;
+  a.id_mode = 1;
+  RO_TRY(cuda_check(c, ro::launch_compact(a, st), "ro_read_requests: compact nodes"));
+  ro::UsageArgs u{};
+  u.used = c->used;
+  u.last_used = c->last_used;
+  u.n = c->desc.cache_slots;
+  u.frame = c->frame;
+  RO_TRY(cuda_check(c, ro::launch_usage(u, st), "ro_read_requests: usage"));
+  uint32_t tot[2] = {0, 0};
+  RO_TRY(cuda_check(c, cudaMemcpyAsync(tot, totals, 8, cudaMemcpyDeviceToHost, st), "ro_read_requests: totals"));
+  RO_TRY(wait_stream(c, "ro_read_requests"));
+  const uint32_t nr = std::min({tot[0], cap, c->desc.max_requests});
+  const uint32_t nn = std::min({tot[1], node_cap, c->desc.max_requests});
+  if (nr) RO_TRY(cuda_check(c, cudaMemcpyAsync(ids, c->req_out, 4ull * nr, cudaMemcpyDeviceToHost, st), "ro_read_requests: ids"));
+  if (nn)
+    RO_TRY(cuda_check(c, cudaMemcpyAsync(node_ids, c->node_out, 4ull * nn, cudaMemcpyDeviceToHost, st), "ro_read_requests: nodes"));
+  if (nr || nn) RO_TRY(wait_stream(c, "ro_read_requests"));
+  if (n) *n = nr;
+  if (overflow) *overflow = tot[0] - nr;
+  if (n_node) *n_node = nn;
+  return RO_OK;
+}
+
+ro_status ro_get_stats(ro_ctx* c, uint64_t out[8]) {
+  if (!c || !out) return RO_ERR_INVALID_ARG;
+  if (c->latched != RO_OK) return c->latched;
+  std::vector<unsigned long long> v((size_t)c->last_blocks * ro::kStats);
+  if (!v.empty())
+    RO_TRY(cuda_check(c, cudaMemcpyAsync(v.data(), c->scratch + c->L.sc_stats, v.size() * 8, cudaMemcpyDeviceToHost, c->stream),
+                      "ro_get_stats"));
+  RO_TRY(wait_stream(c, "ro_get_stats"));
+  for (int q = 0; q < 8; ++q) out[q] = 0;
+  for (size_t b = 0; b < c->last_blocks; ++b)
+    for (int q = 0; q < ro::kStats; ++q) out[q] += v[b * ro::kStats + q];
+  return RO_OK;
+}
+
+ro_status ro_debug_read(ro_ctx* c, uint32_t what, void* host, uint64_t bytes) {
+  if (!c || !host) return RO_ERR_INVALID_ARG;
+  if (c->latched != RO_OK) return c->latched;
+  const void* src = nullptr;
+  uint64_t size = 0;
+  switch (what) {
+    case 0: src = c->octree; size = c->g.n_nodes * (uint64_t)c->g.mp * 4; break;
+    case 1: src = c->pt; size = c->g.n_bricks * 4; break;
+    case 2: src = c->last_used; size = 4ull * c->desc.cache_slots; break;
+    case 3: src = c->req; size = c->g.n_bricks; break;
+    case 4: src = c->used; size = c->desc.cache_slots; break;
+    default: return set_err(c, RO_ERR_INVALID_ARG, "ro_debug_read: unknown array");
+  }
+  if (bytes != size) return set_err(c, RO_ERR_INVALID_ARG, "ro_debug_read: size mismatch");
+  RO_TRY(cuda_check(c, cudaMemcpyAsync(host, src, size, cudaMemcpyDeviceToHost, c->stream), "ro_debug_read"));
+  return wait_stream(c, "ro_debug_read");
+}
+
+}  // extern "C"

@@ -1,0 +1,151 @@
+// Internal declarations shared by the library's translation units (host
+// runtime and kernels).  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ro {
+
+constexpr int kMaxC = 16;       // channels per context (RO_MAX_CHANNELS)
+constexpr int kMaxL = 16;       // levels per context (RO_MAX_LEVELS)
+constexpr int kMaxDepth = 24;   // octree depth bound (2^24 leaves per axis)
+constexpr int kMaxSamples = 1 << 24;  // lattice indices stay exact in binary32
+constexpr int kRenderThreads = 256;   // 16 x 16 pixels per block, 8 x 4 per warp
+constexpr int kStats = 8;             // per-block counters of the render kernel
+
+// Geometry derived once from the descriptor; copied by value into kernels.
+struct Geometry {
+  int dims0[3];
+  float spacing[3];
+  float dimm[3];              // largest binary32 value below dims0 (position clamp)
+  int m, mp, k, B, blog2, bpv;
+  int leaf_log2[3];
+  int D;                      // octree depth (leaves at depth D)
+  int ldims[kMaxL][3];        // level dims
+  int nb[kMaxL][3];           // bricks per axis per level
+  uint32_t pt_off[kMaxC * kMaxL + 1];  // page-table offset of table c*k + l; [m*k] = n_bricks
+  uint64_t node_off[kMaxDepth + 2];    // first node of each depth; [D+1] = n_nodes
+  int nn[kMaxDepth + 1][3];   // nodes per axis per depth
+  int nleaf[3];               // leaves per axis (= nn[D])
+  uint64_t n_nodes, n_bricks;
+  uint32_t cache_slots;
+  uint32_t slot_pitch;        // bytes per cache slot
+  uint32_t edge;              // B + 2 (apron slot edge)
+};
+
+// Everything one render launch needs; passed as a __grid_constant__ parameter.
+struct RenderArgs {
+  Geometry g;
+  float eye[3], fwd[3], right[3], up[3];
+  int persp;
+  float tan_x, tan_y, pixel;
+  int W, H;
+  float dt;
+  float lod_t[kMaxL];
+  int lmin[kMaxC], lmax[kMaxC];
+  int sdepth[kMaxL];
+  int start_depth, skip;
+  float ert;
+  float tf_lo[kMaxC], tf_scale[kMaxC];
+  const uint8_t* cache;
+  const uint32_t* pt;
+  const uint32_t* octree;
+  uint8_t* req;
+  uint8_t* node_req;
+  uint8_t* used;
+  const float4* lut;          // m * 256 knots
+  const uint16_t* prefix;     // m * 257 bucket-occupancy prefix sums
+  float4* image;
+  uint32_t *dbg_hash, *dbg_n_eval, *dbg_i_end, *dbg_n_bs;
+  unsigned long long* block_stats;  // kStats per block
+  uint32_t* err;
+};
+
+struct PrefixArgs {
+  int m, bpv;
+  float tf_lo[kMaxC], tf_scale[kMaxC];
+  const float4* lut;
+  uint16_t* prefix;
+};
+
+// One residency-octree update item: a box of leaves [lo, hi) of one channel
+// whose words must be recomputed (leaf masks from the page table, then every
+// ancestor by gathering its children).
+struct UpdateItem {
+  uint32_t lo[3], hi[3];
+  uint32_t channel;
+  uint32_t pad;
+};
+
+struct MetaItem {
+  uint32_t leaf, channel, vmin, vmax;
+};
+
+struct UpdateArgs {
+  Geometry g;
+  const uint32_t* pt;
+  uint32_t* octree;
+  const UpdateItem* items;
+  uint32_t n_items;
+  const MetaItem* meta;
+  uint32_t n_meta;
+  int depth;                 // depth being recomputed (reduce pass)
+  uint32_t* err;
+};
+
+struct ScatterArgs {
+  const uint8_t* staging;    // n bricks at slot_pitch
+  uint8_t* cache;
+  uint32_t* pt;
+  const uint32_t* ins_index; // page-table index per inserted brick
+  const uint32_t* ins_slot;
+  uint32_t n_ins;
+  const uint32_t* ev_index;  // page-table index per evicted brick
+  uint32_t n_ev;
+  uint32_t slot_pitch;
+  uint32_t cache_slots;
+  uint64_t n_bricks;
+  uint32_t* err;
+};
+
+struct CompactArgs {
+  uint8_t* flags;            // n flags, cleared by the write pass
+  uint64_t n;
+  uint32_t* block_counts;    // scratch: one count per tile, then exclusive offsets
+  uint32_t n_tiles;
+  uint32_t* out;             // ids, capacity cap
+  uint32_t cap;
+  uint32_t* total;           // flags set
+  int id_mode;               // 0: brick ids via page-table offsets, 1: the flag index itself
+  Geometry g;
+};
+
+constexpr int kCompactThreads = 256;
+constexpr int kCompactPerThread = 16;                         // one uint4 of flags
+constexpr int kCompactTile = kCompactThreads * kCompactPerThread;
+
+struct UsageArgs {
+  uint8_t* used;
+  uint32_t* last_used;
+  uint32_t n;
+  uint32_t frame;
+};
+
+// Error codes a kernel may store into the context's error word.
+enum : uint32_t { kErrNone = 0, kErrNodeIndex = 1, kErrPageIndex = 2, kErrSlot = 3, kErrUpdate = 4 };
+
+// Launchers (each returns the launch status).
+cudaError_t launch_prefix(const PrefixArgs& a, cudaStream_t s);
+cudaError_t launch_render(const RenderArgs& a, bool debug, cudaStream_t s);
+cudaError_t launch_fill_words(uint32_t* words, uint64_t n, uint32_t value, cudaStream_t s);
+cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s);
+cudaError_t launch_write_meta(const UpdateArgs& a, cudaStream_t s);
+cudaError_t launch_leaf_masks(const UpdateArgs& a, cudaStream_t s);
+cudaError_t launch_reduce_depth(const UpdateArgs& a, cudaStream_t s);
+cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
+cudaError_t launch_usage(const UsageArgs& a, cudaStream_t s);
+
+size_t render_smem_bytes(int mp);
+
+}  // namespace ro

@@ -1,0 +1,164 @@
+// Residency-octree and page-table updates (Sec. 5.3) and the brick-cache
+// slot scatter.
+//
+// Leaf masks are recomputed from the page table: a leaf (extent a power of
+// two <= B) lies inside exactly one brick of every level, so bit l of a leaf
+// is "the owner brick of level l is resident".  Inner nodes are recomputed as
+// the bitwise OR of their children's masks and the hull of their ranges
+// (INVALID if any child is), depth by depth from the leaves up.  Every write
+// recomputes a word from the final page table / children, so concurrent
+// writers of the same word store the same value: no atomics are needed.
+#include "ro_internal.h"
+
+namespace ro {
+namespace {
+
+__global__ void fill_words_kernel(uint32_t* __restrict__ w, uint64_t n, uint32_t value) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    w[i] = value;
+}
+
+// Copy each staged brick into its slot (16-byte vectors; slot_pitch is a
+// multiple of 256) and write the page-table entries of inserted (slot + 1)
+// and evicted (0) bricks.
+__global__ void __launch_bounds__(256) scatter_kernel(const __grid_constant__ ScatterArgs a) {
+  const uint32_t b = blockIdx.x;
+  if (b < a.n_ins) {
+    const uint32_t slot = a.ins_slot[b];
+    if (slot >= a.cache_slots) { if (threadIdx.x == 0) *a.err = kErrSlot; return; }
+    const uint4* src = reinterpret_cast<const uint4*>(a.staging + (size_t)b * a.slot_pitch);
+    uint4* dst = reinterpret_cast<uint4*>(a.cache + (size_t)slot * a.slot_pitch);
+    for (uint32_t i = threadIdx.x; i < a.slot_pitch / 16; i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x == 0) {
+      const uint32_t pi = a.ins_index[b];
+      if (pi >= a.n_bricks) *a.err = kErrPageIndex;
+      else a.pt[pi] = slot + 1;
+    }
+  } else {
+    const uint32_t e = b - a.n_ins;
+    if (e < a.n_ev && threadIdx.x == 0) {
+      const uint32_t pi = a.ev_index[e];
+      if (pi >= a.n_bricks) *a.err = kErrPageIndex;
+      else a.pt[pi] = 0;
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t quant(uint32_t v, int bpv) { return bpv == 1 ? (v > 255 ? 255 : v) : (v >> 8); }
+
+// Leaf metadata writes: keep the mask, replace min8/max8 (Sec. 7 layout).
+__global__ void write_meta_kernel(const __grid_constant__ UpdateArgs a) {
+  const Geometry& g = a.g;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_meta; i += gridDim.x * blockDim.x) {
+    const MetaItem it = a.meta[i];
+    const uint64_t nl = (uint64_t)g.nleaf[0] * g.nleaf[1] * g.nleaf[2];
+    if (it.leaf >= nl || it.channel >= (uint32_t)g.m) { *a.err = kErrUpdate; continue; }
+    uint32_t* p = a.octree + (g.node_off[g.D] + it.leaf) * g.mp + it.channel;
+    uint32_t mn8, mx8;
+    if (it.vmin > it.vmax) { mn8 = 255; mx8 = 0; }
+    else { mn8 = quant(it.vmin, g.bpv); mx8 = quant(it.vmax, g.bpv); }
+    *p = (*p & 0xFFFFu) | (mn8 << 16) | (mx8 << 24);
+  }
+}
+
+// One block per item: recompute the channel's mask of every leaf in the box.
+__global__ void __launch_bounds__(256) leaf_masks_kernel(const __grid_constant__ UpdateArgs a) {
+  const Geometry& g = a.g;
+  const UpdateItem it = a.items[blockIdx.x];
+  const uint32_t nx = it.hi[0] - it.lo[0], ny = it.hi[1] - it.lo[1], nz = it.hi[2] - it.lo[2];
+  const uint64_t total = (uint64_t)nx * ny * nz;
+  const int c = (int)it.channel;
+  for (uint64_t q = threadIdx.x; q < total; q += blockDim.x) {
+    const uint32_t lx = it.lo[0] + (uint32_t)(q % nx), ly = it.lo[1] + (uint32_t)((q / nx) % ny),
+                   lz = it.lo[2] + (uint32_t)(q / ((uint64_t)nx * ny));
+    if (lx >= (uint32_t)g.nleaf[0] || ly >= (uint32_t)g.nleaf[1] || lz >= (uint32_t)g.nleaf[2]) continue;
+    uint32_t mask = 0;
+    for (int l = 0; l < g.k; ++l) {
+      // leaf origin in level-0 voxels, divided by the level-l brick extent
+      const int sh = g.blog2 + l;
+      const uint32_t bx = (lx << g.leaf_log2[0]) >> sh, by = (ly << g.leaf_log2[1]) >> sh,
+                     bz = (lz << g.leaf_log2[2]) >> sh;
+      const uint64_t pi = g.pt_off[c * g.k + l] + ((uint64_t)bz * g.nb[l][1] + by) * g.nb[l][0] + bx;
+      if (a.pt[pi] != 0) mask |= 1u << l;
+    }
+    uint32_t* p = a.octree + (g.node_off[g.D] + ((uint64_t)lz * g.nleaf[1] + ly) * g.nleaf[0] + lx) * g.mp + c;
+    *p = (*p & 0xFFFF0000u) | mask;
+  }
+}
+
+// One block per item: recompute every depth-d node above the item's leaf box
+// from its (up to 8) children at depth d + 1.
+__global__ void __launch_bounds__(256) reduce_depth_kernel(const __grid_constant__ UpdateArgs a) {
+  const Geometry& g = a.g;
+  const int d = a.depth;
+  const int sh = g.D - d;
+  const UpdateItem it = a.items[blockIdx.x];
+  uint32_t lo[3], hi[3];
+  for (int q = 0; q < 3; ++q) {
+    lo[q] = it.lo[q] >> sh;
+    hi[q] = ((it.hi[q] - 1) >> sh) + 1;
+    if (hi[q] > (uint32_t)g.nn[d][q]) hi[q] = (uint32_t)g.nn[d][q];
+  }
+  const uint32_t nx = hi[0] - lo[0], ny = hi[1] - lo[1], nz = hi[2] - lo[2];
+  const uint64_t total = (uint64_t)nx * ny * nz;
+  const int c = (int)it.channel;
+  for (uint64_t q = threadIdx.x; q < total; q += blockDim.x) {
+    const uint32_t jx = lo[0] + (uint32_t)(q % nx), jy = lo[1] + (uint32_t)((q / nx) % ny),
+                   jz = lo[2] + (uint32_t)(q / ((uint64_t)nx * ny));
+    uint32_t mask = 0, mn = 255, mx = 0;
+    bool invalid = false;
+    for (int cz = 0; cz < 2; ++cz)
+      for (int cy = 0; cy < 2; ++cy)
+        for (int cx = 0; cx < 2; ++cx) {
+          const uint32_t kx = 2 * jx + cx, ky = 2 * jy + cy, kz = 2 * jz + cz;
+          if (kx >= (uint32_t)g.nn[d + 1][0] || ky >= (uint32_t)g.nn[d + 1][1] || kz >= (uint32_t)g.nn[d + 1][2]) continue;
+          const uint32_t w =
+              a.octree[(g.node_off[d + 1] + ((uint64_t)kz * g.nn[d + 1][1] + ky) * g.nn[d + 1][0] + kx) * g.mp + c];
+          mask |= w & 0xFFFFu;
+          const uint32_t wmn = (w >> 16) & 0xFFu, wmx = w >> 24;
+          if (wmn > wmx) invalid = true;
+          mn = wmn < mn ? wmn : mn;
+          mx = wmx > mx ? wmx : mx;
+        }
+    if (invalid) { mn = 255; mx = 0; }
+    a.octree[(g.node_off[d] + ((uint64_t)jz * g.nn[d][1] + jy) * g.nn[d][0] + jx) * g.mp + c] = mask | (mn << 16) | (mx << 24);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_fill_words(uint32_t* words, uint64_t n, uint32_t value, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  uint64_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  fill_words_kernel<<<(unsigned)blocks, 256, 0, s>>>(words, n, value);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s) {
+  if (a.n_ins + a.n_ev == 0) return cudaSuccess;
+  scatter_kernel<<<a.n_ins + a.n_ev, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_write_meta(const UpdateArgs& a, cudaStream_t s) {
+  if (a.n_meta == 0) return cudaSuccess;
+  uint32_t blocks = (a.n_meta + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  write_meta_kernel<<<blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_masks(const UpdateArgs& a, cudaStream_t s) {
+  if (a.n_items == 0) return cudaSuccess;
+  leaf_masks_kernel<<<a.n_items, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_depth(const UpdateArgs& a, cudaStream_t s) {
+  if (a.n_items == 0) return cudaSuccess;
+  reduce_depth_kernel<<<a.n_items, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ro
