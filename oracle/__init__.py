@@ -37,7 +37,8 @@ class _Volume(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int32 * 3), ("spacing", ctypes.c_float * 3),
                 ("m", ctypes.c_int32), ("k", ctypes.c_int32), ("B", ctypes.c_int32), ("bpv", ctypes.c_int32),
                 ("leaf", ctypes.c_int32 * 3), ("levels", ctypes.POINTER(ctypes.c_void_p)),
-                ("resident", ctypes.c_void_p), ("leaf_min", ctypes.c_void_p), ("leaf_max", ctypes.c_void_p)]
+                ("resident", ctypes.c_void_p), ("leaf_min", ctypes.c_void_p), ("leaf_max", ctypes.c_void_p),
+                ("voxel_fn", ctypes.c_void_p), ("voxel_ctx", ctypes.c_void_p)]
 
 
 class _Params(ctypes.Structure):
@@ -105,26 +106,38 @@ class Volume:
     levels[c][l]: numpy array [z][y][x] (uint8 or uint16) of level l.
     resident: iterable of (c, l, bx, by, bz) bricks resident in the cache.
     leaf_min / leaf_max: arrays (m, lz, ly, lx) int64, -1 = no metadata.
+    provider: instead of levels, (m, k, dims_xyz, bytes_per_voxel, fn, ctx)
+    where fn is a C function pointer uint32_t(void*, int c, int l, int64 x,
+    int64 y, int64 z) and ctx its first argument (a voxel source for
+    volumes too large to hold densely).
     """
 
-    def __init__(self, levels, spacing, B, leaf_extent, resident=(), leaf_min=None, leaf_max=None):
-        self.m = len(levels)
-        self.k = len(levels[0])
-        self.levels = [[np.ascontiguousarray(a) for a in ch] for ch in levels]
-        nz, ny, nx = self.levels[0][0].shape
-        self.dims = (nx, ny, nz)
-        self.bpv = self.levels[0][0].dtype.itemsize
-        self._ptrs = (ctypes.c_void_p * (self.m * self.k))()
-        for c in range(self.m):
-            for l in range(self.k):
-                assert self.levels[c][l].dtype == self.levels[0][0].dtype
-                self._ptrs[c * self.k + l] = self.levels[c][l].ctypes.data
+    def __init__(self, levels, spacing, B, leaf_extent, resident=(), leaf_min=None, leaf_max=None, provider=None):
         self.s = _Volume()
+        if provider is None:
+            self.m = len(levels)
+            self.k = len(levels[0])
+            self.levels = [[np.ascontiguousarray(a) for a in ch] for ch in levels]
+            nz, ny, nx = self.levels[0][0].shape
+            self.dims = (nx, ny, nz)
+            self.bpv = self.levels[0][0].dtype.itemsize
+            self._ptrs = (ctypes.c_void_p * (self.m * self.k))()
+            for c in range(self.m):
+                for l in range(self.k):
+                    assert self.levels[c][l].dtype == self.levels[0][0].dtype
+                    self._ptrs[c * self.k + l] = self.levels[c][l].ctypes.data
+            self.s.levels = ctypes.cast(self._ptrs, ctypes.POINTER(ctypes.c_void_p))
+        else:
+            self.m, self.k, self.dims, self.bpv, fn, fctx = provider
+            nx, ny, nz = self.dims
+            self.levels = None
+            self.s.levels = None
+            self.s.voxel_fn = fn
+            self.s.voxel_ctx = fctx
         self.s.dims[:] = list(self.dims)
         self.s.spacing[:] = [float(np.float32(v)) for v in spacing]
         self.s.m, self.s.k, self.s.B, self.s.bpv = self.m, self.k, int(B), self.bpv
         self.s.leaf[:] = list(leaf_extent)
-        self.s.levels = ctypes.cast(self._ptrs, ctypes.POINTER(ctypes.c_void_p))
         self.n_bricks = int(lib().or_brick_count(ctypes.byref(self.s)))
         self.resident = np.zeros(self.n_bricks, np.uint8)
         self.s.resident = self.resident.ctypes.data

@@ -59,6 +59,11 @@ typedef struct {
   const uint8_t *resident;  /* oracle brick layout (or_brick_index): 1 = resident */
   const int64_t *leaf_min;  /* m * n_leaves raw values, -1 = no metadata */
   const int64_t *leaf_max;
+  /* voxel source used when levels is NULL (volumes too large to hold
+   * densely): value of level-l voxel (x, y, z) of channel c, coordinates
+   * already clamped to the level */
+  uint32_t (*voxel_fn)(void *ctx, int c, int l, int64_t x, int64_t y, int64_t z);
+  void *voxel_ctx;
 } or_volume;
 
 typedef struct {
@@ -96,19 +101,58 @@ static int nbricks(const or_volume *v, int l, int a) {
   return (lvl_dim(v->dims[a], l) + v->B - 1) / v->B;
 }
 
-/* oracle brick layout: (c, l) tables in order c*k + l, each [bz][by][bx] */
-OR_EXPORT int64_t or_brick_index(const or_volume *v, int c, int l, int bx, int by, int bz) {
-  int64_t off = 0;
-  for (int cc = 0; cc < v->m; ++cc)
-    for (int ll = 0; ll < v->k; ++ll) {
-      int64_t nx = nbricks(v, ll, 0), ny = nbricks(v, ll, 1), nz = nbricks(v, ll, 2);
-      if (cc == c && ll == l) {
-        if (bx < 0 || by < 0 || bz < 0 || bx >= nx || by >= ny || bz >= nz) return -1;
-        return off + ((int64_t)bz * ny + by) * nx + bx;
-      }
-      off += nx * ny * nz;
+/* Geometry tables computed once per call from the volume description:
+ * per-level dims and bricks per axis, the offset of each (c, l) brick table,
+ * the octree depth and the first node of each depth. */
+typedef struct {
+  int ld[OR_MAXL][3], nb[OR_MAXL][3];
+  int64_t pt_off[OR_MAXC * OR_MAXL + 1];
+  int D;
+  int64_t nn[32][3], node_off[33];
+} or_geom;
+
+static int geom_depth(const or_volume *v);
+
+static void make_geom(const or_volume *v, or_geom *g) {
+  memset(g, 0, sizeof(*g));
+  for (int l = 0; l < v->k; ++l)
+    for (int a = 0; a < 3; ++a) {
+      g->ld[l][a] = lvl_dim(v->dims[a], l);
+      g->nb[l][a] = (g->ld[l][a] + v->B - 1) / v->B;
     }
-  return -1;
+  int64_t off = 0;
+  for (int c = 0; c < v->m; ++c)
+    for (int l = 0; l < v->k; ++l) {
+      g->pt_off[c * v->k + l] = off;
+      off += (int64_t)g->nb[l][0] * g->nb[l][1] * g->nb[l][2];
+    }
+  g->pt_off[v->m * v->k] = off;
+  g->D = geom_depth(v);
+  int64_t noff = 0;
+  for (int d = 0; d <= g->D; ++d) {
+    g->node_off[d] = noff;
+    int64_t cnt = 1;
+    for (int a = 0; a < 3; ++a) {
+      int64_t e = (int64_t)v->leaf[a] << (g->D - d);
+      g->nn[d][a] = (v->dims[a] + e - 1) / e;
+      cnt *= g->nn[d][a];
+    }
+    noff += cnt;
+  }
+  g->node_off[g->D + 1] = noff;
+}
+
+/* oracle brick layout: (c, l) tables in order c*k + l, each [bz][by][bx] */
+static int64_t brick_index_g(const or_volume *v, const or_geom *g, int c, int l, int bx, int by, int bz) {
+  if (c < 0 || c >= v->m || l < 0 || l >= v->k) return -1;
+  if (bx < 0 || by < 0 || bz < 0 || bx >= g->nb[l][0] || by >= g->nb[l][1] || bz >= g->nb[l][2]) return -1;
+  return g->pt_off[c * v->k + l] + ((int64_t)bz * g->nb[l][1] + by) * g->nb[l][0] + bx;
+}
+
+OR_EXPORT int64_t or_brick_index(const or_volume *v, int c, int l, int bx, int by, int bz) {
+  or_geom g;
+  make_geom(v, &g);
+  return brick_index_g(v, &g, c, l, bx, by, bz);
 }
 
 OR_EXPORT int64_t or_brick_count(const or_volume *v) {
@@ -125,7 +169,7 @@ static uint32_t brick_id(const or_volume *v, int c, int l, int bx, int by, int b
 }
 
 /* Octree depth: the smallest D with 2^D leaves covering every axis. */
-OR_EXPORT int or_depth(const or_volume *v) {
+static int geom_depth(const or_volume *v) {
   int D = 0;
   for (int a = 0; a < 3; ++a) {
     int nl = (v->dims[a] + v->leaf[a] - 1) / v->leaf[a];
@@ -135,6 +179,8 @@ OR_EXPORT int or_depth(const or_volume *v) {
   }
   return D;
 }
+
+OR_EXPORT int or_depth(const or_volume *v) { return geom_depth(v); }
 
 /* node extent at depth d, per axis, in level-0 voxels */
 static int64_t node_ext(const or_volume *v, int D, int d, int a) { return (int64_t)v->leaf[a] << (D - d); }
@@ -162,6 +208,7 @@ typedef struct {
   const or_volume *v;
   int D;
   uint32_t *words;
+  or_geom g;
 } oa_ctx;
 
 static void oa_node(const oa_ctx *x, int d, int64_t jx, int64_t jy, int64_t jz) {
@@ -174,7 +221,7 @@ static void oa_node(const oa_ctx *x, int d, int64_t jx, int64_t jy, int64_t jz) 
     hi[a] = (j3[a] + 1) * e;
     if (hi[a] > v->dims[a]) hi[a] = v->dims[a];
   }
-  int64_t nidx = node_offset(v, D, d) + (jz * nodes_axis(v, D, d, 1) + jy) * nodes_axis(v, D, d, 0) + jx;
+  int64_t nidx = x->g.node_off[d] + (jz * x->g.nn[d][1] + jy) * x->g.nn[d][0] + jx;
   int64_t nl[3], llo[3], lhi[3];
   for (int a = 0; a < 3; ++a) {
     nl[a] = (v->dims[a] + v->leaf[a] - 1) / v->leaf[a];
@@ -197,7 +244,7 @@ static void oa_node(const oa_ctx *x, int d, int64_t jx, int64_t jy, int64_t jz) 
       for (int64_t bz = b0[2]; bz <= b1[2] && !found; ++bz)
         for (int64_t by = b0[1]; by <= b1[1] && !found; ++by)
           for (int64_t bx = b0[0]; bx <= b1[0] && !found; ++bx) {
-            int64_t bi = or_brick_index(v, c, l, (int)bx, (int)by, (int)bz);
+            int64_t bi = brick_index_g(v, &x->g, c, l, (int)bx, (int)by, (int)bz);
             if (bi >= 0 && v->resident[bi]) found = 1;
           }
       if (found) mask |= 1u << l;
@@ -241,7 +288,8 @@ static void oa_by_index(oa_ctx *x, int64_t g) {
   const or_volume *v = x->v;
   int D = x->D;
   for (int d = 0; d <= D; ++d) {
-    int64_t nx = nodes_axis(v, D, d, 0), ny = nodes_axis(v, D, d, 1), nz = nodes_axis(v, D, d, 2);
+    int64_t nx = x->g.nn[d][0], ny = x->g.nn[d][1], nz = x->g.nn[d][2];
+    (void)v;
     if (g < nx * ny * nz) {
       oa_node(x, d, g % nx, (g / nx) % ny, g / (nx * ny));
       return;
@@ -267,7 +315,11 @@ static void *oa_worker(void *arg) {
  * mask[15:0] | min8[23:16] | max8[31:24] (Sec. 7), INVALID = min8 > max8. */
 OR_EXPORT int or_node_words(const or_volume *v, uint32_t *words) {
   if (v->m < 1 || v->m > OR_MAXC || v->k < 1 || v->k > OR_MAXL || (v->bpv != 1 && v->bpv != 2)) return -1;
-  oa_ctx x = {v, or_depth(v), words};
+  oa_ctx x;
+  x.v = v;
+  x.D = or_depth(v);
+  x.words = words;
+  make_geom(v, &x.g);
   oa_pool p = {&x, or_node_count(v), 0};
   pthread_mutex_init(&p.mu, NULL);
   int nt = threads_to_use();
@@ -291,6 +343,7 @@ typedef struct {
   uint8_t occ[OR_MAXC][256];     /* bucket occupancy per channel */
   float dimm[3];                 /* largest float below each level-0 dim */
   int64_t nleaves;
+  or_geom g;
 } ob_frame;
 
 /* Transfer-function coordinate of a raw value, binary32:
@@ -408,8 +461,7 @@ static void node_coords(const ob_frame *f, int d, const float x[3], int64_t j[3]
 }
 
 static int64_t node_index(const ob_frame *f, int d, const int64_t j[3]) {
-  return node_offset(f->v, f->D, d) +
-         (j[2] * nodes_axis(f->v, f->D, d, 1) + j[1]) * nodes_axis(f->v, f->D, d, 0) + j[0];
+  return f->g.node_off[d] + (j[2] * f->g.nn[d][1] + j[1]) * f->g.nn[d][0] + j[0];
 }
 
 /* owner brick of a position at level l: floor(x / (B 2^l)) per axis */
@@ -444,6 +496,7 @@ static uint32_t voxel(const or_volume *v, int c, int l, int64_t x, int64_t y, in
   if (x > nx - 1) x = nx - 1;
   if (y > ny - 1) y = ny - 1;
   if (z > nz - 1) z = nz - 1;
+  if (!v->levels) return v->voxel_fn(v->voxel_ctx, c, l, x, y, z);
   int64_t idx = (z * ny + y) * nx + x;
   const void *a = v->levels[c * v->k + l];
   return v->bpv == 1 ? ((const uint8_t *)a)[idx] : ((const uint16_t *)a)[idx];
@@ -612,7 +665,7 @@ static void march_pixel(const ob_frame *f, int px, int py, int64_t n_out, const 
         if (unm) {
           int b[3];
           owner_brick(f, ld[c], x, b);
-          fl->req[or_brick_index(v, c, ld[c], b[0], b[1], b[2])] = 1;
+          fl->req[brick_index_g(v, &f->g, c, ld[c], b[0], b[1], b[2])] = 1;
         }
         if (state[c] == ST_INVALID) fl->node_req[node * m + c] = 1;   /* reportNodeRequest */
       }
@@ -673,12 +726,12 @@ static void march_pixel(const ob_frame *f, int px, int py, int64_t n_out, const 
         for (int l = ld[c]; l < k; ++l) {
           int b[3];
           owner_brick(f, l, x, b);
-          int64_t bi = or_brick_index(v, c, l, b[0], b[1], b[2]);
+          int64_t bi = brick_index_g(v, &f->g, c, l, b[0], b[1], b[2]);
           if (v->resident[bi]) { found = l; fb[0] = b[0]; fb[1] = b[1]; fb[2] = b[2]; break; }
           if (l == ld[c]) fl->req[bi] = 1;   /* the desired brick is missing */
         }
         if (found < 0) continue;            /* nothing resident: no contribution */
-        fl->used[or_brick_index(v, c, found, fb[0], fb[1], fb[2])] = 1;
+        fl->used[brick_index_g(v, &f->g, c, found, fb[0], fb[1], fb[2])] = 1;
         has[c] = 1;
         lused[c] = found;
         if (found < s_used) s_used = found;
@@ -788,6 +841,7 @@ OR_EXPORT int or_render(const or_volume *v, const uint32_t *words, const or_para
   ob_frame *f = (ob_frame *)calloc(1, sizeof(ob_frame));
   if (!f) return -4;
   f->v = v; f->words = words; f->p = p; f->D = or_depth(v);
+  make_geom(v, &f->g);
   if (p->start_depth < 0 || p->start_depth > f->D) { free(f); return -5; }
   for (int a = 0; a < 3; ++a) f->dimm[a] = nextafterf((float)v->dims[a], 0.0f);
   frame_occupancy(f);

@@ -62,6 +62,11 @@ def lib():
         L.sy_cells_count.restype = ctypes.c_int64
         L.sy_cells_count.argtypes = [c_void_p, c_int]
         L.sy_set_threads.argtypes = [c_int]
+        L.sy_vcache_create.restype = c_void_p
+        L.sy_vcache_create.argtypes = [c_void_p, c_int, ctypes.c_int64]
+        L.sy_vcache_free.argtypes = [c_void_p]
+        L.sy_vcache_bricks.restype = ctypes.c_int64
+        L.sy_vcache_bricks.argtypes = [c_void_p]
         _lib = L
     return _lib
 
@@ -180,6 +185,10 @@ class Cells:
             raise ValueError("sy_cells_bricks_mixed failed")
         return out
 
+    def voxel_source(self, B, capacity=1 << 20):
+        """A lazily filled voxel source over this field (see VoxelSource)."""
+        return VoxelSource(self, B, capacity)
+
     def leaf_bounds(self, ch, leaf_extent_xyz):
         nx, ny, nz = self.dims
         ex, ey, ez = leaf_extent_xyz
@@ -189,6 +198,31 @@ class Cells:
         if lib().sy_cells_leaf_bounds(self._h, ch, ex, ey, ez, _ptr(mn), _ptr(mx)):
             raise ValueError("sy_cells_leaf_bounds failed")
         return mn, mx
+
+
+class VoxelSource:
+    """Voxel-at-a-time access to a cell field for readers that cannot hold
+    the volume densely: bricks of B^3 level-l voxels are generated on first
+    touch and kept.  `fn` / `ctx` are the C function pointer and its context
+    for a C consumer."""
+
+    def __init__(self, cells: "Cells", B: int, capacity: int):
+        self.cells = cells          # keeps the field alive
+        L = lib()
+        self._h = L.sy_vcache_create(cells._h, int(B), int(capacity))
+        if not self._h:
+            raise ValueError("sy_vcache_create failed")
+        self.fn = ctypes.cast(L.sy_vcache_voxel, ctypes.c_void_p).value
+        self.ctx = self._h
+
+    def bricks_generated(self) -> int:
+        return int(lib().sy_vcache_bricks(self._h))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.sy_vcache_free(h)
+            self._h = None
 
 
 # ------------------------------------------------- transfer functions

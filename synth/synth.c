@@ -20,6 +20,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <sched.h>
 #include <unistd.h>
 
 #define SY_EXPORT __attribute__((visibility("default")))
@@ -532,4 +533,89 @@ SY_EXPORT int64_t sy_cells_count(const sy_cells *c, int ch) {
   int64_t n = 0;
   for (int i = 0; i < c->ncells; ++i) n += c->I[(size_t)i * c->m + ch] > 0.0f;
   return n;
+}
+
+/* ------------------------------------- lazily generated voxel source */
+
+/* Voxel access to the procedural cell field for consumers that read voxels
+ * one at a time (the CPU oracle): level-l voxels are generated a whole brick
+ * (B^3, no border) at a time on first touch and kept.  Insert-only
+ * open-addressing table; lookups take no lock. */
+typedef struct {
+  const sy_cells *c;
+  int B, blog2;
+  int64_t cap;                 /* power of two */
+  uint64_t *keys;              /* 0 = empty; key = packed (c, l, bz, by, bx) + 1 */
+  uint16_t *volatile *vals;
+  int nl[16][3];
+  int64_t n_generated;
+} sy_vcache;
+
+SY_EXPORT sy_vcache *sy_vcache_create(const sy_cells *c, int B, int64_t capacity) {
+  if (!c || B < 1 || (B & (B - 1))) return NULL;
+  sy_vcache *v = (sy_vcache *)calloc(1, sizeof(sy_vcache));
+  if (!v) return NULL;
+  v->c = c; v->B = B;
+  while ((1 << v->blog2) < B) ++v->blog2;
+  v->cap = 1;
+  while (v->cap < 2 * capacity) v->cap <<= 1;
+  v->keys = (uint64_t *)calloc((size_t)v->cap, sizeof(uint64_t));
+  v->vals = (uint16_t *volatile *)calloc((size_t)v->cap, sizeof(uint16_t *));
+  if (!v->keys || !v->vals) { free(v->keys); free((void *)v->vals); free(v); return NULL; }
+  for (int l = 0; l < 16; ++l)
+    for (int a = 0; a < 3; ++a) {
+      int d = c->dims0[a];
+      for (int q = 0; q < l; ++q) d = (d + 1) / 2;
+      v->nl[l][a] = d;
+    }
+  return v;
+}
+
+SY_EXPORT void sy_vcache_free(sy_vcache *v) {
+  if (!v) return;
+  for (int64_t i = 0; i < v->cap; ++i) free(v->vals[i]);
+  free(v->keys);
+  free((void *)v->vals);
+  free(v);
+}
+
+SY_EXPORT int64_t sy_vcache_bricks(const sy_vcache *v) { return v ? __atomic_load_n(&v->n_generated, __ATOMIC_RELAXED) : -1; }
+
+/* Value of level-l voxel (x, y, z) of channel ch (coordinates inside the
+ * level); returns 0 and leaves the table untouched if it is full. */
+SY_EXPORT uint32_t sy_vcache_voxel(void *vv, int ch, int l, int64_t x, int64_t y, int64_t z) {
+  sy_vcache *v = (sy_vcache *)vv;
+  const int sh = v->blog2;
+  const uint64_t bx = (uint64_t)x >> sh, by = (uint64_t)y >> sh, bz = (uint64_t)z >> sh;
+  const uint64_t key = (((((uint64_t)ch << 4 | (uint64_t)l) << 16 | bz) << 16 | by) << 16 | bx) + 1;
+  uint64_t h = sy_mix(key) & (uint64_t)(v->cap - 1);
+  const int B = v->B;
+  for (int64_t probe = 0; probe < v->cap; ++probe, h = (h + 1) & (uint64_t)(v->cap - 1)) {
+    uint64_t k = __atomic_load_n(&v->keys[h], __ATOMIC_ACQUIRE);
+    if (k == 0) {
+      uint64_t expect = 0;
+      if (__atomic_compare_exchange_n(&v->keys[h], &expect, key, 0, __ATOMIC_ACQ_REL, __ATOMIC_ACQUIRE)) {
+        uint16_t *blk = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)B * B * B);
+        if (!blk) return 0;
+        for (int zz = 0; zz < B; ++zz)
+          for (int yy = 0; yy < B; ++yy)
+            for (int xx = 0; xx < B; ++xx) {
+              int gx = (int)(bx * B) + xx, gy = (int)(by * B) + yy, gz = (int)(bz * B) + zz;
+              uint16_t val = 0;
+              if (gx < v->nl[l][0] && gy < v->nl[l][1] && gz < v->nl[l][2]) val = sy_cells_voxel(v->c, ch, l, gx, gy, gz);
+              blk[((size_t)zz * B + yy) * B + xx] = val;
+            }
+        __atomic_store_n(&v->vals[h], blk, __ATOMIC_RELEASE);
+        __atomic_add_fetch(&v->n_generated, 1, __ATOMIC_RELAXED);
+        return blk[(((size_t)(z & (B - 1))) * B + (size_t)(y & (B - 1))) * B + (size_t)(x & (B - 1))];
+      }
+      k = expect;
+    }
+    if (k == key) {
+      uint16_t *blk;
+      while ((blk = __atomic_load_n(&v->vals[h], __ATOMIC_ACQUIRE)) == NULL) sched_yield();
+      return blk[(((size_t)(z & (B - 1))) * B + (size_t)(y & (B - 1))) * B + (size_t)(x & (B - 1))];
+    }
+  }
+  return 0;
 }

@@ -90,3 +90,27 @@ def test_lod_thresholds_closed_form():
     # tan(45 deg) = 1: tau_l = 2^l * 1080 / 2
     assert t[1] == pytest.approx(1080.0, rel=1e-6) and t[2] == pytest.approx(2160.0, rel=1e-6)
     assert t[3] == float("inf")
+
+
+def test_voxel_source_matches_dense_field_in_the_oracle():
+    """The lazily filled voxel source gives the oracle the same voxels as the
+    dense field (level 0), so both march to identical results."""
+    import oracle
+    cells = synth.Cells(4, 60, 2, (80, 72, 20), (1.0, 1.0, 4.0))
+    dense = [[cells.dense(c)] for c in range(2)]
+    mins, maxs = zip(*[synth.leaf_ranges(d[0], (8, 8, 4)) for d in dense])
+    mn, mx = np.stack(mins).astype(np.int64), np.stack(maxs).astype(np.int64)
+    res = [(c, 0, x, y, 0) for c in range(2) for x in range(5) for y in range(5)]
+    src = cells.voxel_source(16, capacity=4096)
+    vd = oracle.Volume(dense, (1, 1, 4), 16, (8, 8, 4), res, mn, mx)
+    vp = oracle.Volume(None, (1, 1, 4), 16, (8, 8, 4), res, mn, mx,
+                       provider=(2, 1, (80, 72, 20), 2, src.fn, src.ctx))
+    cam = synth.look_at((-30.0, -40.0, 150.0), (40.0, 36.0, 40.0), (0, 0, 1), 40, 32, fovy_deg=40.0)
+    tfs = [synth.tf_ramp(400, 12000, rgb=(1, 0, 0), alpha_max=0.5), synth.tf_ramp(400, 12000, rgb=(0, 1, 0))]
+    fr = synth.Frame(40, 32, cam, tfs, 0.5, [0.0] + [float("inf")] * 15, [0, 0], [0, 0])
+    a = oracle.render(vd, vd.node_words(), fr)
+    b = oracle.render(vp, vp.node_words(), fr)
+    assert a["n_bs"].sum() > 1000
+    for key in ("rgba32", "rgba64", "hash", "n_eval"):
+        assert np.array_equal(a[key], b[key]), key
+    assert src.bricks_generated() > 0
