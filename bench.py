@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Benchmark of the residency-octree ray caster on GB300.
+
+One step = one frame of the orbit: ro_render (the ray caster), then
+ro_read_requests (request / usage compaction and the request-list readback)
+and ro_update_residency_octree.  The default workload is the 16-channel
+4096x4096x96 u16 procedural cell slab (51.5 GB at full resolution, bricks
+made on request) behind an 8 GiB brick cache, 1920x1080 perspective views
+orbiting the slab; the cache is warmed over the orbit before timing, so the
+timed steps read bricks already resident in HBM.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded pixel sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+GIB = 1 << 30
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=16)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["cells16", "cells4", "blobs"], default="cells16")
+    ap.add_argument("--warm-seconds", type=float, default=150.0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--radius", type=float, default=None)
+    ap.add_argument("--lod-bias", type=float, default=1.0)
+    ap.add_argument("--cache-gib", type=float, default=8.0)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------- workload
+
+def make_workload(args):
+    import synth
+    from synth import recipes
+    if args.workload == "cells16":
+        kw = {} if args.radius is None else {"radius": args.radius}
+        scene = recipes.cells_large(**kw)
+        label = {"workload": "cells16: 16-channel 4096x4096x96 u16 procedural cell slab (spacing 1:1:4), "
+                             "32^3 bricks, 7 levels, 8 GiB brick cache, 1920x1080 perspective orbit, "
+                             "per-channel TFs with additive colour",
+                 "channels": 16, "dims": [4096, 4096, 96], "image": [1920, 1080], "levels": 7,
+                 "cache_gib": args.cache_gib, "sample_dtype": "u16 -> f32"}
+        slot_bytes = 34 ** 3 * 2
+        slots = int(args.cache_gib * GIB) // (((slot_bytes + 255) // 256) * 256)
+    elif args.workload == "cells4":
+        scene = recipes.cells_slab(dense=False)
+        label = {"workload": "cells4: 4-channel 1024x1024x64 u16 cell slab, 5 levels, 1024^2 perspective",
+                 "channels": 4, "dims": [1024, 1024, 64], "image": [1024, 1024], "levels": 5}
+        slots = len(scene.all_bricks())
+    else:
+        scene = recipes.blobs128()
+        label = {"workload": "blobs: 1-channel 128^3 u8 Gaussian blobs, 256^2 ortho", "channels": 1,
+                 "dims": [128, 128, 128], "image": [256, 256], "levels": 3}
+        slots = len(scene.all_bricks())
+    if args.lod_bias != 1.0:
+        for f in scene.frames:
+            f.lod_t = [t * args.lod_bias for t in f.lod_t]
+    return scene, label, slots
+
+
+def decode_ids(ids, k):
+    ids = np.asarray(ids, np.uint32)
+    p = ids >> 24
+    return np.stack([p // k, p % k, ids & 0xFF, (ids >> 8) & 0xFF, (ids >> 16) & 0xFF], 1).astype(np.int32)
+
+
+def warm_cache(ctx, scene, image, budget_s):
+    """Ray-guided warm-up (Sec. 4): render each orbit frame, read its
+    requests, make the requested bricks, upload them, update the octree;
+    repeat over the orbit until a round requests nothing or time runs out."""
+    from paper_2309_04393_gb300 import ro
+    t0 = time.time()
+    uploaded, rounds, last = 0, 0, None
+    max_up = int(ctx.desc.max_upload)
+    while time.time() - t0 < budget_s:
+        rounds += 1
+        req_round = 0
+        for f in scene.frames:
+            ro.render_frame(ctx, f, image)
+            ids, overflow, _ = ctx.read_requests()
+            req_round += int(ids.size) + overflow
+            if ids.size:
+                keys = decode_ids(ids, scene.k)
+                for q in range(0, ids.size, max_up):
+                    vox = scene.bricks(keys[q:q + max_up])
+                    ctx.upload_bricks(ids[q:q + max_up], vox)
+                ctx.update_residency_octree()
+                uploaded += int(ids.size)
+            if time.time() - t0 > budget_s:
+                break
+        log(f"  warm round {rounds}: {req_round} requests, {uploaded} bricks uploaded, {time.time() - t0:.1f} s")
+        last = req_round
+        if req_round == 0:
+            break
+    return {"rounds": rounds, "bricks_uploaded": uploaded, "requests_last_round": last,
+            "seconds": round(time.time() - t0, 1)}
+
+
+# ----------------------------------------------------------------- clocks
+
+class Clocks:
+    """nvidia-smi sampling (every 200 ms) during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_volume_all_resident(scene):
+    import oracle
+    if scene.cells is not None:
+        src = scene.cells.voxel_source(scene.B, capacity=1 << 21)
+        vol = oracle.Volume(None, scene.spacing, scene.B, scene.leaf, (), scene.leaf_min, scene.leaf_max,
+                            provider=(scene.m, scene.k, scene.dims, scene.value_bits // 8, src.fn, src.ctx))
+        vol._src = src
+    else:
+        vol = oracle.Volume(scene.levels, scene.spacing, scene.B, scene.leaf, (), scene.leaf_min, scene.leaf_max)
+    vol.resident[:] = 1
+    return vol
+
+
+def oracle_rate(scene, frame, seconds, seed=0, words=None, vol=None):
+    """Evaluated samples per second of the CPU oracle (as it stands) on a
+    seeded pixel sample of `frame`, with every brick resident.  A small
+    calibration pass sizes the sample to about `seconds` of CPU time; each
+    pass runs twice and the second (voxel source already filled) is timed."""
+    import oracle
+    vol = vol if vol is not None else oracle_volume_all_resident(scene)
+    if words is None:
+        words = vol.node_words()
+    rng = np.random.default_rng(seed)
+
+    def tile(side):
+        side = int(max(8, min(side, frame.W, frame.H)))
+        x0 = int(rng.integers(0, frame.W - side + 1))
+        y0 = int(rng.integers(frame.H // 4, max(frame.H // 4 + 1, frame.H - frame.H // 4 - side + 1)))
+        yy, xx = np.meshgrid(np.arange(y0, y0 + side), np.arange(x0, x0 + side), indexing="ij")
+        return np.stack([xx.ravel(), yy.ravel()], 1), side
+
+    px, _ = tile(48)
+    oracle.render(vol, words, frame, px)
+    t = time.perf_counter()
+    oracle.render(vol, words, frame, px)
+    per_pix = (time.perf_counter() - t) / len(px)
+    px, side = tile(math.sqrt(seconds / max(per_pix, 1e-9)))
+    oracle.render(vol, words, frame, px)
+    t = time.perf_counter()
+    o = oracle.render(vol, words, frame, px)
+    dt = time.perf_counter() - t
+    return {"samples": int(o["n_eval"].sum()), "seconds": dt, "pixels": len(px), "side": side,
+            "cores": oracle.threads_used(), "vol": vol, "words": words}
+
+
+# ------------------------------------------------------------------- arms
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    scene, label, _ = make_workload(args)
+    frames = scene.frames
+    vol = oracle_volume_all_resident(scene)
+    t = time.perf_counter()
+    words = vol.node_words()
+    log(f"oracle node words: {time.perf_counter() - t:.1f} s")
+    per_step = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    samples, seconds, pixels, cores = 0, 0.0, 0, 1
+    for s in range(args.warmup + args.steps):
+        r = oracle_rate(scene, frames[s % len(frames)], per_step, seed=s, words=words, vol=vol)
+        if s >= args.warmup:
+            samples += r["samples"]
+            seconds += r["seconds"]
+            pixels += r["pixels"]
+        cores = r["cores"]
+    value = samples / seconds if seconds > 0 else 0.0
+    sample = (f"{pixels} pixels in seeded square tiles over {args.steps} orbit frames (every brick resident), "
+              f"about {per_step:.0f} s of oracle time per step, second pass timed")
+    out = {"metric": "ray samples/s", "value": value, "unit": "samples/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000.0 * seconds / max(1, args.steps), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
+           "config": label,
+           "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2309_04393_gb300 import loader, ro
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    scene, label, slots = make_workload(args)
+    frames = scene.frames
+    W, H = frames[0].W, frames[0].H
+    desc = ro.make_desc(scene.dims, scene.spacing, scene.m, scene.value_bits, scene.B, scene.k, scene.leaf, slots,
+                        max_requests=1 << 16, max_upload=2048, max_meta=1 << 20)
+    ctx = ro.Context(desc)
+    t = time.time()
+    if scene.resident:
+        loader.upload_keys(ctx, scene, scene.resident)
+    ctx.update_residency_octree(loader.meta_rows(scene.leaf_min, scene.leaf_max))
+    torch.cuda.synchronize()
+    log(f"rank {rank}: arena {ctx.sizes.total / GIB:.2f} GiB, {slots} slots, metadata + initial bricks "
+        f"{time.time() - t:.1f} s")
+    image = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    warm = warm_cache(ctx, scene, image, args.warm_seconds)
+
+    def step(f):
+        ro.render_frame(ctx, f, image)
+        ctx.read_requests()
+        ctx.update_residency_octree()
+
+    order = [frames[(args.warmup + i) % len(frames)] for i in range(args.steps)]
+    for i in range(args.warmup):
+        step(frames[i % len(frames)])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local_rank)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    er = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in order]
+    torch.cuda.synchronize()
+    ev0.record()
+    for f, (a, b) in zip(order, er):
+        a.record()
+        ro.render_frame(ctx, f, image)
+        b.record()
+        ctx.read_requests()
+        ctx.update_residency_octree()
+    ev1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    render_ms = [a.elapsed_time(b) for a, b in er]
+
+    # counters of the same frames (same cache state, untimed)
+    samples = chan = hit = 0
+    for f in order:
+        ro.render_frame(ctx, f, image)
+        st = ctx.stats()
+        hit += int(st[0])
+        samples += int(st[1])
+        chan += int(st[2])
+        ctx.read_requests()
+    torch.cuda.synchronize()
+
+    # end to end through the public API with host buffers: per step the
+    # frame's transfer-function LUTs go host -> device inside ro_render and
+    # the image plus the request list come back to pinned host memory
+    host_img = torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True)
+    lut_bytes = scene.m * 256 * 16
+    req_bytes = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for f in order:
+        ro.render_frame(ctx, f, image)
+        host_img.copy_(image, non_blocking=True)
+        ids, ov, nodes = ctx.read_requests()
+        req_bytes += 4 * (ids.size + nodes.size) + 12
+        ctx.update_residency_octree()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+
+    tot = torch.tensor([total_ms, e2e_s, float(samples)], dtype=torch.float64, device="cuda")
+    if dist:
+        mx = tot.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tot.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        total_ms, e2e_s, samples_all = float(mx[0]), float(mx[1]), float(sm[2])
+    else:
+        samples_all = float(samples)
+    if rank != 0:
+        return 0
+    value = samples_all / (total_ms / 1000.0)
+    peak, peak_kind = measured_hbm_peak()
+    avg_render_s = float(np.mean(render_ms)) / 1000.0
+    fp_bytes = 16 if scene.value_bits == 16 else 8
+    bytes_per_launch = (chan * fp_bytes + W * H * 16) / len(order)
+    achieved = bytes_per_launch / avg_render_s / 1e9
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        r = oracle_rate(scene, order[0], args.cpu_seconds)
+        cpu = {"value": r["samples"] / r["seconds"], "unit": "samples/s", "cores": r["cores"], "kind": "oracle",
+               "sample": f"a seeded {r['side']}x{r['side']} pixel tile of one 1920x1080 orbit frame (every brick resident), "
+                         f"{r['samples']} samples in {r['seconds']:.1f} s (second pass timed)"}
+    out = {"metric": "ray samples/s", "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / len(order), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded procedural cells; no dataset)",
+           "config": dict(label, l2="inputs larger than L2 (8 GiB brick cache)",
+                          parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                          render_ms_avg=round(avg_render_s * 1000, 3),
+                          channel_samples_per_step=chan // len(order), samples_per_step=samples // len(order),
+                          rays_hit_per_step=hit // len(order), warmup_cache=warm),
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": None, "peak_source": f"{peak_kind} copy bandwidth",
+                        "kernel": "render_kernel (ro_render)",
+                        "algorithmic_bytes": f"{fp_bytes} B per channel brick sample (2x2x2 footprint) + 16 B per pixel"},
+           "clocks": clk,
+           "e2e": {"value": samples_all / e2e_s, "unit": "samples/s",
+                   "h2d_bytes_per_step": lut_bytes, "d2h_bytes_per_step": W * H * 16 + req_bytes // len(order)},
+           "gpu_launches": 9 * len(order),
+           "cpu_baseline": cpu}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    rc = run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

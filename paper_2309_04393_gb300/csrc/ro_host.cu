@@ -503,20 +503,25 @@ ro_status ro_update_residency_octree(ro_ctx* c, uint32_t n_meta, const ro_leaf_m
   for (uint32_t i = 0; i < n_meta; ++i)
     if (meta[i].leaf >= n_leaves || meta[i].channel >= (uint32_t)g.m)
       return set_err(c, RO_ERR_INVALID_ARG, "ro_update_residency_octree: leaf or channel out of range");
-  // last entry wins for a repeated (leaf, channel)
+  // last entry wins for a repeated (channel, leaf); input already in strictly
+  // increasing (channel, leaf) order needs no sort
   std::vector<ro::MetaItem> mi;
   mi.reserve(n_meta);
   {
-    std::vector<uint32_t> order(n_meta);
-    for (uint32_t i = 0; i < n_meta; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
-      const uint64_t ka = (uint64_t)meta[a].leaf * g.m + meta[a].channel, kb = (uint64_t)meta[b].leaf * g.m + meta[b].channel;
-      return ka < kb;
-    });
-    for (uint32_t q = 0; q < n_meta; ++q) {
-      const uint32_t i = order[q];
-      const bool last = q + 1 == n_meta || meta[order[q + 1]].leaf != meta[i].leaf || meta[order[q + 1]].channel != meta[i].channel;
-      if (last) mi.push_back({meta[i].leaf, meta[i].channel, meta[i].vmin, meta[i].vmax});
+    auto key = [&](uint32_t i) { return (uint64_t)meta[i].channel * n_leaves + meta[i].leaf; };
+    bool sorted = true;
+    for (uint32_t i = 1; i < n_meta && sorted; ++i) sorted = key(i - 1) < key(i);
+    if (sorted) {
+      for (uint32_t i = 0; i < n_meta; ++i) mi.push_back({meta[i].leaf, meta[i].channel, meta[i].vmin, meta[i].vmax});
+    } else {
+      std::vector<uint32_t> order(n_meta);
+      for (uint32_t i = 0; i < n_meta; ++i) order[i] = i;
+      std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return key(a) < key(b); });
+      for (uint32_t q = 0; q < n_meta; ++q) {
+        const uint32_t i = order[q];
+        if (q + 1 == n_meta || key(order[q + 1]) != key(i))
+          mi.push_back({meta[i].leaf, meta[i].channel, meta[i].vmin, meta[i].vmax});
+      }
     }
   }
   // items: leaf boxes of changed bricks (masks recomputed), then metadata leaves
@@ -536,7 +541,18 @@ ro_status ro_update_residency_octree(ro_ctx* c, uint32_t n_meta, const ro_leaf_m
     }
     push_box(brick_items, (uint32_t)ch, lo, hi);
   }
+  // a channel with many changed leaves gets one whole-volume box instead of
+  // one item per leaf
+  std::vector<uint64_t> per_channel(g.m, 0);
+  for (const ro::MetaItem& m : mi) ++per_channel[m.channel];
+  for (int ch = 0; ch < g.m; ++ch)
+    if (per_channel[ch] > n_leaves / 8) {
+      const uint32_t lo[3] = {0, 0, 0};
+      const uint32_t hi[3] = {(uint32_t)g.nleaf[0], (uint32_t)g.nleaf[1], (uint32_t)g.nleaf[2]};
+      push_box(meta_items, (uint32_t)ch, lo, hi);
+    }
   for (const ro::MetaItem& m : mi) {
+    if (per_channel[m.channel] > n_leaves / 8) continue;
     uint32_t lo[3], hi[3];
     lo[0] = m.leaf % g.nleaf[0];
     lo[1] = (m.leaf / g.nleaf[0]) % g.nleaf[1];
