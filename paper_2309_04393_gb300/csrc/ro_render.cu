@@ -194,8 +194,25 @@ __device__ __forceinline__ void shade(const RenderArgs& a, const float4* __restr
   for (int e = 0; e < s; ++e) q = q * q;
 }
 
+// Per-ray cache of the last classification: the final node, the desired
+// levels it was made for, each channel's state and selected brick.  A sample
+// that lands in the same node with the same desired levels gets the same
+// decisions (the walk, the states, the selected slots and levels), provided
+// the node lies inside one brick of every level a channel may use; requests
+// and usage flags are then already set (the stores are idempotent).
+struct NodeCache {
+  int d;                 // final depth, -1 = empty
+  int jn[3];             // node coordinates at depth d
+  uint64_t ldp;          // desired levels (4 bits per channel)
+  int st;                // traversal depth
+  uint64_t node;
+  uint64_t states;       // 4 bits per channel
+  bool all_skip, one_brick;
+  int s_sel;             // finest level read from a brick, 99 = none
+};
+
 template <int MP, int BPV, bool DBG>
-__global__ void __launch_bounds__(kRenderThreads) render_kernel(const __grid_constant__ RenderArgs a) {
+__global__ void __launch_bounds__(kRenderThreads, 2) render_kernel(const __grid_constant__ RenderArgs a) {
   extern __shared__ float4 smem[];
   float4* s_lut = smem;
   uint16_t* s_pre = reinterpret_cast<uint16_t*>(s_lut + MP * 256);
@@ -217,6 +234,10 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(const __grid_con
     const Ray r = make_ray(a, px, py);
     if (r.hit) {
       hitc = 1;
+      NodeCache nc;
+      nc.d = -1;
+      uint32_t sel[MP];      // per channel: slot, or the node value of a homogeneous channel
+      uint32_t lvp[(MP + 3) / 4];  // per channel one byte: level read, 0xFE homogeneous, 0xFF nothing
       for (;;) {
         if (i >= kMaxSamples) break;
         const float t = fmaf((float)i, a.dt, r.t0);
@@ -239,60 +260,141 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(const __grid_con
           }
         }
         const int st = a.sdepth[lminu];
+        int L[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) L[q] = (int)(x[q] * pow2f(-g.leaf_log2[q]));
+        const bool same_levels = nc.d >= 0 && ldp == nc.ldp && st == nc.st;
+        bool same_node = false;
+        if (same_levels) {
+          const int sh = g.D - nc.d;
+          same_node = (L[0] >> sh) == nc.jn[0] && (L[1] >> sh) == nc.jn[1] && (L[2] >> sh) == nc.jn[2];
+        }
 
-        // descend until every channel has terminated or the traversal depth
-        // is reached (R9)
-        int d = a.start_depth < st ? a.start_depth : st;
-        uint32_t w[MP];
-        int jn[3];
-        uint64_t node;
-        int state[MP];
-        for (;;) {
-          node_coords(g, d, x, jn);
-          node = g.node_off[d] + ((uint64_t)jn[2] * g.nn[d][1] + jn[1]) * g.nn[d][0] + jn[0];
-          if (node >= g.node_off[d + 1]) { bad = true; break; }
-          load_words<MP>(a.octree, node, m, w);
-          bool all = true;
+        if (!(same_node && nc.one_brick)) {
+          // walk (R9): every depth where the previous sample's ancestors are
+          // shared and were not all terminal is skipped
+          const int d0 = a.start_depth < st ? a.start_depth : st;
+          int d = d0;
+          if (same_node) {
+            d = nc.d;
+          } else if (same_levels) {
+            int dca = -1;
+            for (int q = nc.d; q >= 0; --q) {
+              const int sh = g.D - q;
+              if ((L[0] >> sh) == (nc.jn[0] >> (nc.d - q)) && (L[1] >> sh) == (nc.jn[1] >> (nc.d - q)) &&
+                  (L[2] >> sh) == (nc.jn[2] >> (nc.d - q))) {
+                dca = q;
+                break;
+              }
+            }
+            d = dca + 1 > d0 ? dca + 1 : d0;
+          }
+          uint32_t w[MP];
+          int jn[3];
+          uint64_t node, states;
+          for (;;) {
+            const int sh = g.D - d;
+            jn[0] = L[0] >> sh; jn[1] = L[1] >> sh; jn[2] = L[2] >> sh;
+            node = g.node_off[d] + ((uint64_t)jn[2] * g.nn[d][1] + jn[1]) * g.nn[d][0] + jn[0];
+            if (node >= g.node_off[d + 1]) { bad = true; break; }
+            load_words<MP>(a.octree, node, m, w);
+            bool all = true;
+            states = 0;
+#pragma unroll
+            for (int c = 0; c < MP; ++c) {
+              if (c < m) {
+                const int sc = classify<BPV>(w[c], s_pre + c * 257, (int)((ldp >> (4 * c)) & 15), k);
+                states |= (uint64_t)sc << (4 * c);
+                all = all && terminal(sc);
+              }
+            }
+            if (all || d == st || same_node) break;
+            ++d;
+          }
+          if (bad) break;
+
+          bool all_skip = true;
+          int s_sel = 99;
 #pragma unroll
           for (int c = 0; c < MP; ++c) {
+            sel[c] = 0;
             if (c < m) {
-              state[c] = classify<BPV>(w[c], s_pre + c * 257, (int)((ldp >> (4 * c)) & 15), k);
-              all = all && terminal(state[c]);
+              const int ld = (int)((ldp >> (4 * c)) & 15);
+              const int sc = (int)((states >> (4 * c)) & 15);
+              if (sc != kEmpty && sc != kUnmapped) all_skip = false;
+              const bool no_use = ((w[c] & 0xFFFFu) & (~0u << ld) & ((1u << k) - 1u)) == 0;
+              if (sc == kUnmapped || (sc == kInvalid && no_use)) {
+                const int bsh = g.blog2 + ld;
+                const int bx = (int)(x[0] * pow2f(-bsh)), by = (int)(x[1] * pow2f(-bsh)), bz = (int)(x[2] * pow2f(-bsh));
+                const uint64_t pi = g.pt_off[c * k + ld] + ((uint64_t)bz * g.nb[ld][1] + by) * g.nb[ld][0] + bx;
+                if (pi >= g.n_bricks) bad = true;
+                else a.req[pi] = 1;
+              }
+              if (sc == kInvalid) a.node_req[node * m + c] = 1;
             }
           }
-          if (all || d == st) break;
-          ++d;
-        }
-        if (bad) break;
-
-        bool all_skip = true;
+          if (bad) break;
+          // brick selection (R11): desired level, else request it and take the
+          // next coarser resident level
 #pragma unroll
-        for (int c = 0; c < MP; ++c) {
-          if (c < m) {
-            const int ld = (int)((ldp >> (4 * c)) & 15);
-            const int sc = state[c];
-            if (sc != kEmpty && sc != kUnmapped) all_skip = false;
-            const bool no_use = ((w[c] & 0xFFFFu) & (~0u << ld) & ((1u << k) - 1u)) == 0;
-            if (sc == kUnmapped || (sc == kInvalid && no_use)) {
-              const int sh = g.blog2 + ld;
-              const int bx = (int)(x[0] * pow2f(-sh)), by = (int)(x[1] * pow2f(-sh)), bz = (int)(x[2] * pow2f(-sh));
-              const uint64_t pi = g.pt_off[c * k + ld] + ((uint64_t)bz * g.nb[ld][1] + by) * g.nb[ld][0] + bx;
-              if (pi >= g.n_bricks) { bad = true; } else { a.req[pi] = 1; }
+          for (int q = 0; q < (MP + 3) / 4; ++q) lvp[q] = 0xFFFFFFFFu;
+          if (!all_skip) {
+#pragma unroll
+            for (int c = 0; c < MP; ++c) {
+              if (c >= m) continue;
+              const int sc = (int)((states >> (4 * c)) & 15);
+              if (sc == kEmpty || sc == kUnmapped) continue;
+              if (sc == kHomog) {
+                sel[c] = (w[c] >> 16) & 0xFFu;
+                lvp[c >> 2] &= ~(0x01u << (8 * (c & 3)));  // 0xFE
+                continue;
+              }
+              const int ld = (int)((ldp >> (4 * c)) & 15);
+              if (((w[c] & 0xFFFFu) & (~0u << ld) & ((1u << k) - 1u)) == 0) continue;
+              for (int l = ld; l < k; ++l) {
+                const int bsh = g.blog2 + l;
+                const int bx = (int)(x[0] * pow2f(-bsh)), by = (int)(x[1] * pow2f(-bsh)), bz = (int)(x[2] * pow2f(-bsh));
+                const uint64_t pi = g.pt_off[c * k + l] + ((uint64_t)bz * g.nb[l][1] + by) * g.nb[l][0] + bx;
+                if (pi >= g.n_bricks) { bad = true; break; }
+                uint32_t e = 0;
+                if ((w[c] >> l) & 1u) e = __ldg(a.pt + pi);
+                if (e != 0) {
+                  if (e - 1 >= g.cache_slots) { bad = true; break; }
+                  sel[c] = e - 1;
+                  lvp[c >> 2] = (lvp[c >> 2] & ~(0xFFu << (8 * (c & 3)))) | ((uint32_t)l << (8 * (c & 3)));
+                  a.used[e - 1] = 1;
+                  s_sel = l < s_sel ? l : s_sel;
+                  break;
+                }
+                if (l == ld) a.req[pi] = 1;
+              }
+              if (bad) break;
             }
-            if (sc == kInvalid) a.node_req[node * m + c] = 1;
+            if (bad) break;
           }
+          nc.d = d;
+          nc.jn[0] = jn[0]; nc.jn[1] = jn[1]; nc.jn[2] = jn[2];
+          nc.ldp = ldp;
+          nc.st = st;
+          nc.node = node;
+          nc.states = states;
+          nc.all_skip = all_skip;
+          nc.s_sel = s_sel;
+          const int esh = g.D - d;
+          nc.one_brick = g.leaf_log2[0] + esh <= g.blog2 + lminu && g.leaf_log2[1] + esh <= g.blog2 + lminu &&
+                         g.leaf_log2[2] + esh <= g.blog2 + lminu;
         }
-        if (bad) break;
 
-        if (all_skip && a.skip) {
+        if (nc.all_skip && a.skip) {
           // first lattice index whose sample lies outside the node (R10):
           // estimate from the node box's exit distance, then correct with the
           // same position arithmetic
+          const int d = nc.d;
           float tb = r.t1;
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
             const int sh = g.leaf_log2[q] + g.D - d;
-            const float lo = (float)(jn[q] << sh), hi = (float)((jn[q] + 1) << sh);
+            const float lo = (float)(nc.jn[q] << sh), hi = (float)((nc.jn[q] + 1) << sh);
             if (r.d[q] > 0.0f) tb = fminf(tb, __fdiv_rn(hi - r.o[q], r.d[q]));
             else if (r.d[q] < 0.0f) tb = fminf(tb, __fdiv_rn(lo - r.o[q], r.d[q]));
           }
@@ -306,7 +408,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(const __grid_con
             int jc[3];
             position(a, r, tj, xj);
             node_coords(g, d, xj, jc);
-            return jc[0] == jn[0] && jc[1] == jn[1] && jc[2] == jn[2];
+            return jc[0] == nc.jn[0] && jc[1] == nc.jn[1] && jc[2] == nc.jn[2];
           };
           while (j < kMaxSamples && inside(j)) ++j;
           while (j > i + 1 && !inside(j - 1)) --j;
@@ -322,64 +424,33 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(const __grid_con
           continue;
         }
 
-        // pick each channel's brick: desired level, else request it and take
-        // the next coarser resident level (R11)
-        uint32_t slot[MP];
-        int lv[MP];
-        int s_used = 99;
+        // shade and composite (R12-R14)
+        const int s = nc.s_sel == 99 ? lminu : nc.s_sel;
+        float col0 = 0.0f, col1 = 0.0f, col2 = 0.0f, trans = 1.0f;
 #pragma unroll
         for (int c = 0; c < MP; ++c) {
-          lv[c] = -1;
-          slot[c] = 0;
           if (c >= m) continue;
-          const int sc = state[c];
-          if (sc == kEmpty || sc == kUnmapped) continue;
-          if (sc == kHomog) {
-            lv[c] = 99;
+          const uint32_t lb = (lvp[c >> 2] >> (8 * (c & 3))) & 0xFFu;
+          if (lb == 0xFFu) continue;
+          float val;
+          if (lb == 0xFEu) {
+            val = (float)sel[c];
             ++n_homog;
             if constexpr (DBG) {
               h = fnv_word(h, (uint32_t)i); h = fnv_word(h, (uint32_t)c);
               h = fnv_word(h, 0xFFu); h = fnv_word(h, 0xFFFFFFFFu);
             }
-            continue;
-          }
-          const int ld = (int)((ldp >> (4 * c)) & 15);
-          if (((w[c] & 0xFFFFu) & (~0u << ld) & ((1u << k) - 1u)) == 0) continue;  // INVALID, nothing usable
-          for (int l = ld; l < k; ++l) {
-            const int sh = g.blog2 + l;
-            const int bx = (int)(x[0] * pow2f(-sh)), by = (int)(x[1] * pow2f(-sh)), bz = (int)(x[2] * pow2f(-sh));
-            const uint64_t pi = g.pt_off[c * k + l] + ((uint64_t)bz * g.nb[l][1] + by) * g.nb[l][0] + bx;
-            if (pi >= g.n_bricks) { bad = true; break; }
-            uint32_t e = 0;
-            if ((w[c] >> l) & 1u) e = __ldg(a.pt + pi);
-            if (e != 0) {
-              if (e - 1 >= g.cache_slots) { bad = true; break; }
-              lv[c] = l;
-              slot[c] = e - 1;
-              a.used[e - 1] = 1;
-              if constexpr (DBG) {
-                h = fnv_word(h, (uint32_t)i); h = fnv_word(h, (uint32_t)c); h = fnv_word(h, (uint32_t)l);
-                h = fnv_word(h, ((uint32_t)(c * k + l) << 24) | ((uint32_t)bz << 16) | ((uint32_t)by << 8) | (uint32_t)bx);
-              }
-              s_used = l < s_used ? l : s_used;
-              ++n_bs;
-              break;
+          } else {
+            val = trilinear<BPV>(a, sel[c], (int)lb, x);
+            ++n_bs;
+            if constexpr (DBG) {
+              const int bsh = g.blog2 + (int)lb;
+              const uint32_t bx = (uint32_t)(x[0] * pow2f(-bsh)), by = (uint32_t)(x[1] * pow2f(-bsh)),
+                             bz = (uint32_t)(x[2] * pow2f(-bsh));
+              h = fnv_word(h, (uint32_t)i); h = fnv_word(h, (uint32_t)c); h = fnv_word(h, lb);
+              h = fnv_word(h, ((uint32_t)(c * k + (int)lb) << 24) | (bz << 16) | (by << 8) | bx);
             }
-            if (l == ld) a.req[pi] = 1;
           }
-          if (bad) break;
-        }
-        if (bad) break;
-        const int s = s_used == 99 ? lminu : s_used;
-
-        // shade and composite (R12-R14)
-        float col0 = 0.0f, col1 = 0.0f, col2 = 0.0f, trans = 1.0f;
-#pragma unroll
-        for (int c = 0; c < MP; ++c) {
-          if (c >= m || lv[c] < 0) continue;
-          float val;
-          if (lv[c] == 99) val = (float)((w[c] >> 16) & 0xFFu);
-          else val = trilinear<BPV>(a, slot[c], lv[c], x);
           float q, cr, cg, cb;
           shade(a, s_lut + c * 256, c, val, s, q, cr, cg, cb);
           const float ap = 1.0f - q;
