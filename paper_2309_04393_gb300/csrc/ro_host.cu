@@ -36,7 +36,7 @@ struct Layout {
   uint64_t off[11];
   ro_buffer_sizes sz;
   uint64_t req_pad, node_req_pad, used_pad;
-  uint64_t sc_counts, sc_totals, sc_items, sc_meta, sc_ins_index, sc_ins_slot, sc_ev_index, sc_stats, sc_err;
+  uint64_t sc_counts, sc_totals, sc_items, sc_meta, sc_ins_index, sc_ins_slot, sc_ev_index, sc_stats, sc_err, sc_work;
   uint64_t fr_lut, fr_prefix, li_req, li_node;
   uint32_t max_tiles;
 };
@@ -61,7 +61,7 @@ ro_status make_geometry(const ro_desc* d, Geometry* g, std::string* why) {
   if (d->channels * d->levels > 256) return fail("channels * levels must be <= 256 (8-bit page-table id)");
   for (int a = 0; a < 3; ++a)
     if (!is_pow2(d->leaf_extent[a]) || d->leaf_extent[a] > d->brick) return fail("leaf_extent must be powers of two <= brick");
-  if (d->cache_slots < 1) return fail("cache_slots must be >= 1");
+  if (d->cache_slots < 1 || d->cache_slots > (1u << 27)) return fail("cache_slots must be in [1, 2^27]");
   if (d->max_requests < 1 || d->max_upload < 1 || d->max_meta < 1) return fail("max_requests/max_upload/max_meta must be >= 1");
   g->m = (int)d->channels;
   g->mp = 1;
@@ -157,6 +157,7 @@ void make_layout(const ro_desc* d, const Geometry& g, Layout* L) {
   L->sc_ev_index = o; o = align_up(o + (uint64_t)d->max_upload * 4, kAlign);
   L->sc_stats = o; o = align_up(o + (uint64_t)kMaxStatBlocks * ro::kStats * 8, kAlign);
   L->sc_err = o; o = align_up(o + 64, kAlign);
+  L->sc_work = o; o = align_up(o + 64, kAlign);
   s.scratch = o;
   const uint64_t parts[11] = {s.cache, s.page_table, s.octree, s.req_flags, s.node_req_flags, s.used_flags,
                               s.last_used, s.staging, s.frame, s.lists, s.scratch};
@@ -671,6 +672,9 @@ ro_status ro_render(ro_ctx* c, const ro_camera* cam, const ro_tf* tfs, const ro_
   a.dbg_n_bs = p->debug_n_bs;
   a.block_stats = reinterpret_cast<unsigned long long*>(c->scratch + c->L.sc_stats);
   a.err = c->err;
+  a.work = reinterpret_cast<unsigned long long*>(c->scratch + c->L.sc_work);
+  a.tiles_x = (W + 7) / 8;
+  a.n_rays = (uint64_t)a.tiles_x * ((H + 3) / 4) * 32;
   for (int ch = 0; ch < g.m; ++ch)
     std::memcpy(&c->host_lut[(size_t)ch * 256], tfs[ch].lut, 256 * sizeof(float4));
   cudaStream_t st = c->stream;
@@ -687,8 +691,10 @@ ro_status ro_render(ro_ctx* c, const ro_camera* cam, const ro_tf* tfs, const ro_
   pa.prefix = c->prefix;
   RO_TRY(cuda_check(c, ro::launch_prefix(pa, st), "ro_render: prefix"));
   const bool debug = p->debug_hash || p->debug_n_eval || p->debug_i_end || p->debug_n_bs;
-  RO_TRY(cuda_check(c, ro::launch_render(a, debug, st), "ro_render: render"));
-  c->last_blocks = (uint32_t)blocks;
+  RO_TRY(cuda_check(c, cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), st), "ro_render: work counter"));
+  int launched = 0;
+  RO_TRY(cuda_check(c, ro::launch_render(a, debug, st, &launched), "ro_render: render"));
+  c->last_blocks = (uint32_t)launched;
   ++c->frame;
   return RO_OK;
 }

@@ -11,7 +11,7 @@ constexpr int kMaxC = 16;       // channels per context (RO_MAX_CHANNELS)
 constexpr int kMaxL = 16;       // levels per context (RO_MAX_LEVELS)
 constexpr int kMaxDepth = 24;   // octree depth bound (2^24 leaves per axis)
 constexpr int kMaxSamples = 1 << 24;  // lattice indices stay exact in binary32
-constexpr int kRenderThreads = 256;   // 16 x 16 pixels per block, 8 x 4 per warp
+constexpr int kRenderThreads = 512;   // persistent blocks; rays are taken in 8 x 4 pixel tiles
 constexpr int kStats = 8;             // per-block counters of the render kernel
 
 // Geometry derived once from the descriptor; copied by value into kernels.
@@ -60,6 +60,9 @@ struct RenderArgs {
   uint32_t *dbg_hash, *dbg_n_eval, *dbg_i_end, *dbg_n_bs;
   unsigned long long* block_stats;  // kStats per block
   uint32_t* err;
+  unsigned long long* work;         // ray counter of the persistent launch (zeroed before it)
+  uint32_t tiles_x;                 // 8 x 4 pixel tiles per image row
+  uint64_t n_rays;                  // tiles_x * tiles_y * 32
 };
 
 struct PrefixArgs {
@@ -137,7 +140,7 @@ enum : uint32_t { kErrNone = 0, kErrNodeIndex = 1, kErrPageIndex = 2, kErrSlot =
 
 // Launchers (each returns the launch status).
 cudaError_t launch_prefix(const PrefixArgs& a, cudaStream_t s);
-cudaError_t launch_render(const RenderArgs& a, bool debug, cudaStream_t s);
+cudaError_t launch_render(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out);
 cudaError_t launch_fill_words(uint32_t* words, uint64_t n, uint32_t value, cudaStream_t s);
 cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s);
 cudaError_t launch_write_meta(const UpdateArgs& a, cudaStream_t s);
