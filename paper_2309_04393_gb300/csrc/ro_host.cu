@@ -10,7 +10,7 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/ro.h"
+#include "ro.h"
 #include "ro_internal.h"
 
 using ro::Geometry;
@@ -653,6 +653,20 @@ ro_status ro_render(ro_ctx* c, const ro_camera* cam, const ro_tf* tfs, const ro_
       if (mn >= step) best = d;
     }
     a.sdepth[l] = best;
+  }
+  // desired levels of every channel for each value of lod (R7): the clamp
+  // of lod to the channel's [lmin, lmax]
+  for (int lod = 0; lod < ro::kMaxL; ++lod) {
+    uint64_t ldp = 0;
+    int lminu = 15;
+    for (int ch = 0; ch < g.m; ++ch) {
+      int l = lod < (int)p->lmin[ch] ? (int)p->lmin[ch] : lod;
+      l = l > (int)p->lmax[ch] ? (int)p->lmax[ch] : l;
+      ldp |= (uint64_t)l << (4 * ch);
+      lminu = l < lminu ? l : lminu;
+    }
+    a.ldp_tab[lod] = ldp;
+    a.lminu_tab[lod] = lminu;
   }
   a.start_depth = (int)p->start_depth;
   a.skip = p->skip ? 1 : 0;

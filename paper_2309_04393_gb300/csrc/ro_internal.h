@@ -11,7 +11,7 @@ constexpr int kMaxC = 16;       // channels per context (RO_MAX_CHANNELS)
 constexpr int kMaxL = 16;       // levels per context (RO_MAX_LEVELS)
 constexpr int kMaxDepth = 24;   // octree depth bound (2^24 leaves per axis)
 constexpr int kMaxSamples = 1 << 24;  // lattice indices stay exact in binary32
-constexpr int kRenderThreads = 512;   // persistent blocks; rays are taken in 8 x 4 pixel tiles
+constexpr int kRenderThreads = 768;   // persistent blocks, one per SM; rays are taken in 8 x 4 pixel tiles
 constexpr int kStats = 8;             // per-block counters of the render kernel
 
 // Geometry derived once from the descriptor; copied by value into kernels.
@@ -63,6 +63,8 @@ struct RenderArgs {
   unsigned long long* work;         // ray counter of the persistent launch (zeroed before it)
   uint32_t tiles_x;                 // 8 x 4 pixel tiles per image row
   uint64_t n_rays;                  // tiles_x * tiles_y * 32
+  uint64_t ldp_tab[kMaxL];          // desired levels of all channels (4 bits each) per lod value
+  int lminu_tab[kMaxL];             // finest desired level per lod value
 };
 
 struct PrefixArgs {

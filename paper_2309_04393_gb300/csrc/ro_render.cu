@@ -40,24 +40,6 @@ __device__ __forceinline__ int classify(uint32_t w, const uint16_t* pre, int ld,
 
 __device__ __forceinline__ bool terminal(int s) { return s == kEmpty || s == kHomog || s == kUnmapped; }
 
-template <int MP>
-__device__ __forceinline__ void load_words(const uint32_t* __restrict__ oct, uint64_t node, int m, uint32_t (&w)[MP]) {
-  const uint32_t* p = oct + node * MP;
-  if constexpr (MP >= 4) {
-#pragma unroll
-    for (int q = 0; q < MP / 4; ++q) {
-      const uint4 v = __ldg(reinterpret_cast<const uint4*>(p) + q);
-      w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
-    }
-  } else if constexpr (MP == 2) {
-    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
-    w[0] = v.x; w[1] = v.y;
-  } else {
-    w[0] = __ldg(p);
-  }
-  (void)m;
-}
-
 struct Ray {
   float o[3], d[3];
   float t0, t1;
@@ -141,11 +123,11 @@ __device__ __forceinline__ float trilinear(const RenderArgs& a, uint32_t slot, i
     const int b = (int)(x[k] * pow2f(-(g.blog2 + l)));
     li[k] = i0 - (b * g.B - 1);
   }
-  const size_t base = (size_t)slot * g.slot_pitch;
+  const uint8_t* base = a.cache + (size_t)slot * g.slot_pitch;
   const int idx = (li[2] * E + li[1]) * E + li[0];
   float v[8];
   if constexpr (BPV == 1) {
-    const uint8_t* p = a.cache + base + idx;
+    const uint8_t* p = base + idx;
     v[0] = (float)__ldg(p);
     v[1] = (float)__ldg(p + 1);
     v[2] = (float)__ldg(p + E);
@@ -155,7 +137,7 @@ __device__ __forceinline__ float trilinear(const RenderArgs& a, uint32_t slot, i
     v[6] = (float)__ldg(p + E * E + E);
     v[7] = (float)__ldg(p + E * E + E + 1);
   } else {
-    const uint16_t* p = reinterpret_cast<const uint16_t*>(a.cache + base) + idx;
+    const uint16_t* p = reinterpret_cast<const uint16_t*>(base) + idx;
     v[0] = (float)__ldg(p);
     v[1] = (float)__ldg(p + 1);
     v[2] = (float)__ldg(p + E);
@@ -195,11 +177,11 @@ __device__ __forceinline__ void shade(const RenderArgs& a, const float4* __restr
 }
 
 // Per-ray cache of the last classification: the final node, the desired
-// levels it was made for and each channel's state.  A sample that lands in
-// the same node with the same desired levels gets the same decisions (the
-// walk, the states, the selected slots and levels), provided the node lies
-// inside one brick of every level a channel may use; requests and usage flags
-// are then already set (the stores are idempotent).
+// levels it was made for and whether every channel may be skipped there.  A
+// sample that lands in the same node with the same desired levels gets the
+// same decisions (the walk, the states, the selected slots and levels),
+// provided the node lies inside one brick of every level a channel may use;
+// requests and usage flags are then already set (the stores are idempotent).
 struct NodeCache {
   int d;                 // final depth, -1 = empty
   int jn[3];             // node coordinates at depth d
@@ -207,6 +189,8 @@ struct NodeCache {
   int st;                // traversal depth
   bool all_skip, one_brick;
   int s_sel;             // finest level read from a brick, 99 = none
+  uint32_t act;          // channels with a value at this node (brick or node value)
+  uint32_t n_brick;      // how many of them read a brick
 };
 
 // Per-lane selection word (one per channel, in shared memory): bits 31..27
@@ -215,317 +199,367 @@ constexpr uint32_t kSelNone = 0xFFFFFFFFu;
 constexpr uint32_t kSelHomog = 30u;
 constexpr uint32_t kSelMask = (1u << 27) - 1u;
 
-struct RayState {
-  Ray r;
-  int px, py, i;
-  float C0, C1, C2, T;
-  uint32_t h, n_eval, n_bs;
-  NodeCache nc;
-};
-
 struct Counters {
   unsigned long long hit, eval, bs, homog, skip, skipped;
 };
 
-// One lattice step of one ray (one evaluated sample, or one skip).  Returns
-// true once the ray is finished (left the volume, terminated early, or hit a
-// guard).
-template <int MP, int BPV, bool DBG>
-__device__ __forceinline__ bool ray_step(const RenderArgs& a, const float4* __restrict__ s_lut,
-                                         const uint16_t* __restrict__ s_pre, uint32_t* my_sel, int stride,
-                                         RayState& R, Counters& cnt) {
-  const Geometry& g = a.g;
-  const int m = g.m, k = g.k;
-  if (R.i >= kMaxSamples) return true;
-  const float t = fmaf((float)R.i, a.dt, R.r.t0);
-  if (!(t < R.r.t1)) return true;
-  float x[3];
-  position(a, R.r, t, x);
-
-  // desired level per channel (R7), packed 4 bits per channel
-  int lod = 0;
-  for (int l = 1; l < k; ++l) lod += (t >= a.lod_t[l]);
-  uint64_t ldp = 0;
-  int lminu = 15;
-#pragma unroll 1
-  for (int c = 0; c < m; ++c) {
-    int l = lod < a.lmin[c] ? a.lmin[c] : lod;
-    l = l > a.lmax[c] ? a.lmax[c] : l;
-    ldp |= (uint64_t)l << (4 * c);
-    lminu = l < lminu ? l : lminu;
-  }
-  const int st = a.sdepth[lminu];
-  int L[3];
-#pragma unroll
-  for (int q = 0; q < 3; ++q) L[q] = (int)(x[q] * pow2f(-g.leaf_log2[q]));
-  NodeCache& nc = R.nc;
-  const bool same_levels = nc.d >= 0 && ldp == nc.ldp && st == nc.st;
-  bool same_node = false;
-  if (same_levels) {
-    const int sh = g.D - nc.d;
-    same_node = (L[0] >> sh) == nc.jn[0] && (L[1] >> sh) == nc.jn[1] && (L[2] >> sh) == nc.jn[2];
-  }
-
-  if (!(same_node && nc.one_brick)) {
-    // walk (R9); depths whose nodes the previous sample shared and found not
-    // all terminal are not visited again
-    const int d0 = a.start_depth < st ? a.start_depth : st;
-    int d = d0;
-    if (same_node) {
-      d = nc.d;
-    } else if (same_levels) {
-      int dca = 0;
-      for (int q = nc.d; q >= 0; --q) {
-        const int sh = g.D - q, up = nc.d - q;
-        if ((L[0] >> sh) == (nc.jn[0] >> up) && (L[1] >> sh) == (nc.jn[1] >> up) && (L[2] >> sh) == (nc.jn[2] >> up)) {
-          dca = q;
-          break;
-        }
-      }
-      d = dca + 1 > d0 ? dca + 1 : d0;
-    }
-    int jn[3];
-    uint64_t node, states;
-    for (;;) {
-      const int sh = g.D - d;
-      jn[0] = L[0] >> sh; jn[1] = L[1] >> sh; jn[2] = L[2] >> sh;
-      node = g.node_off[d] + ((uint64_t)jn[2] * g.nn[d][1] + jn[1]) * g.nn[d][0] + jn[0];
-      if (node >= g.node_off[d + 1]) { *a.err = kErrNodeIndex; return true; }
-      const uint32_t* wp = a.octree + node * MP;
-      bool all = true;
-      states = 0;
-#pragma unroll 1
-      for (int c = 0; c < m; ++c) {
-        const int sc = classify<BPV>(__ldg(wp + c), s_pre + c * 257, (int)((ldp >> (4 * c)) & 15), k);
-        states |= (uint64_t)sc << (4 * c);
-        all = all && terminal(sc);
-      }
-      if (all || d == st || same_node) break;
-      ++d;
-    }
-
-    // requests of channels with nothing usable here, node requests of INVALID
-    // channels, then brick selection (R11): desired level, else request it
-    // and take the next coarser resident level
-    const uint32_t* wp = a.octree + node * MP;
-    bool all_skip = true;
-    int s_sel = 99;
-#pragma unroll 1
-    for (int c = 0; c < m; ++c) {
-      const uint32_t w = __ldg(wp + c);
-      const int ld = (int)((ldp >> (4 * c)) & 15);
-      const int sc = (int)((states >> (4 * c)) & 15);
-      if (sc != kEmpty && sc != kUnmapped) all_skip = false;
-      const bool no_use = ((w & 0xFFFFu) & (~0u << ld) & ((1u << k) - 1u)) == 0;
-      if (sc == kUnmapped || (sc == kInvalid && no_use)) {
-        const int bsh = g.blog2 + ld;
-        const int bx = (int)(x[0] * pow2f(-bsh)), by = (int)(x[1] * pow2f(-bsh)), bz = (int)(x[2] * pow2f(-bsh));
-        const uint64_t pi = g.pt_off[c * k + ld] + ((uint64_t)bz * g.nb[ld][1] + by) * g.nb[ld][0] + bx;
-        if (pi >= g.n_bricks) { *a.err = kErrPageIndex; return true; }
-        a.req[pi] = 1;
-      }
-      if (sc == kInvalid) a.node_req[node * m + c] = 1;
-    }
-#pragma unroll 1
-    for (int c = 0; c < m; ++c) {
-      uint32_t sel = kSelNone;
-      const int sc = (int)((states >> (4 * c)) & 15);
-      if (!all_skip && sc != kEmpty && sc != kUnmapped) {
-        const uint32_t w = __ldg(wp + c);
-        if (sc == kHomog) {
-          sel = (kSelHomog << 27) | ((w >> 16) & 0xFFu);
-        } else {
-          const int ld = (int)((ldp >> (4 * c)) & 15);
-          if (((w & 0xFFFFu) & (~0u << ld) & ((1u << k) - 1u)) != 0) {
-            for (int l = ld; l < k; ++l) {
-              const int bsh = g.blog2 + l;
-              const int bx = (int)(x[0] * pow2f(-bsh)), by = (int)(x[1] * pow2f(-bsh)), bz = (int)(x[2] * pow2f(-bsh));
-              const uint64_t pi = g.pt_off[c * k + l] + ((uint64_t)bz * g.nb[l][1] + by) * g.nb[l][0] + bx;
-              if (pi >= g.n_bricks) { *a.err = kErrPageIndex; return true; }
-              uint32_t e = 0;
-              if ((w >> l) & 1u) e = __ldg(a.pt + pi);
-              if (e != 0) {
-                if (e - 1 >= g.cache_slots) { *a.err = kErrSlot; return true; }
-                sel = ((uint32_t)l << 27) | (e - 1);
-                a.used[e - 1] = 1;
-                s_sel = l < s_sel ? l : s_sel;
-                break;
-              }
-              if (l == ld) a.req[pi] = 1;
-            }
-          }
-        }
-      }
-      my_sel[c * stride] = sel;
-    }
-    nc.d = d;
-    nc.jn[0] = jn[0]; nc.jn[1] = jn[1]; nc.jn[2] = jn[2];
-    nc.ldp = ldp;
-    nc.st = st;
-    nc.all_skip = all_skip;
-    nc.s_sel = s_sel;
-    const int esh = g.D - d;
-    nc.one_brick = g.leaf_log2[0] + esh <= g.blog2 + lminu && g.leaf_log2[1] + esh <= g.blog2 + lminu &&
-                   g.leaf_log2[2] + esh <= g.blog2 + lminu;
-  }
-
-  if (nc.all_skip && a.skip) {
-    // first lattice index whose sample lies outside the node (R10): estimate
-    // from the node box's exit distance, then correct with the same position
-    // arithmetic
-    const int d = nc.d;
-    float tb = R.r.t1;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int sh = g.leaf_log2[q] + g.D - d;
-      const float lo = (float)(nc.jn[q] << sh), hi = (float)((nc.jn[q] + 1) << sh);
-      if (R.r.d[q] > 0.0f) tb = fminf(tb, __fdiv_rn(hi - R.r.o[q], R.r.d[q]));
-      else if (R.r.d[q] < 0.0f) tb = fminf(tb, __fdiv_rn(lo - R.r.o[q], R.r.d[q]));
-    }
-    float fj = ceilf(__fdiv_rn(tb - R.r.t0, a.dt));
-    fj = fminf(fmaxf(fj, (float)(R.i + 1)), (float)kMaxSamples);
-    int j = (int)fj;
-    auto inside = [&](int jj) -> bool {
-      const float tj = fmaf((float)jj, a.dt, R.r.t0);
-      if (!(tj < R.r.t1)) return false;
-      float xj[3];
-      int jc[3];
-      position(a, R.r, tj, xj);
-      node_coords(g, d, xj, jc);
-      return jc[0] == nc.jn[0] && jc[1] == nc.jn[1] && jc[2] == nc.jn[2];
-    };
-    while (j < kMaxSamples && inside(j)) ++j;
-    while (j > R.i + 1 && !inside(j - 1)) --j;
-    if constexpr (DBG) {
-      R.h = fnv_word(R.h, (uint32_t)R.i);
-      R.h = fnv_word(R.h, 0xFFFFFFFFu);
-      R.h = fnv_word(R.h, (uint32_t)d);
-      R.h = fnv_word(R.h, (uint32_t)j);
-    }
-    ++cnt.skip;
-    cnt.skipped += (unsigned long long)(j - R.i);
-    R.i = j;
-    return false;
-  }
-
-  // shade and composite (R12-R14)
-  const int s = nc.s_sel == 99 ? lminu : nc.s_sel;
-  float col0 = 0.0f, col1 = 0.0f, col2 = 0.0f, trans = 1.0f;
-#pragma unroll 1
-  for (int c = 0; c < m; ++c) {
-    const uint32_t sel = my_sel[c * stride];
-    if (sel == kSelNone) continue;
-    const uint32_t lb = sel >> 27;
-    float val;
-    if (lb == kSelHomog) {
-      val = (float)(sel & kSelMask);
-      ++cnt.homog;
-      if constexpr (DBG) {
-        R.h = fnv_word(R.h, (uint32_t)R.i); R.h = fnv_word(R.h, (uint32_t)c);
-        R.h = fnv_word(R.h, 0xFFu); R.h = fnv_word(R.h, 0xFFFFFFFFu);
-      }
-    } else {
-      val = trilinear<BPV>(a, sel & kSelMask, (int)lb, x);
-      ++cnt.bs;
-      ++R.n_bs;
-      if constexpr (DBG) {
-        const int bsh = g.blog2 + (int)lb;
-        const uint32_t bx = (uint32_t)(x[0] * pow2f(-bsh)), by = (uint32_t)(x[1] * pow2f(-bsh)),
-                       bz = (uint32_t)(x[2] * pow2f(-bsh));
-        R.h = fnv_word(R.h, (uint32_t)R.i); R.h = fnv_word(R.h, (uint32_t)c); R.h = fnv_word(R.h, lb);
-        R.h = fnv_word(R.h, ((uint32_t)(c * k + (int)lb) << 24) | (bz << 16) | (by << 8) | bx);
-      }
-    }
-    float q, cr, cg, cb;
-    shade(a, s_lut + c * 256, c, val, s, q, cr, cg, cb);
-    const float ap = 1.0f - q;
-    col0 = fmaf(ap, cr, col0);
-    col1 = fmaf(ap, cg, col1);
-    col2 = fmaf(ap, cb, col2);
-    trans = trans * q;
-  }
-  R.C0 = fmaf(R.T, col0, R.C0);
-  R.C1 = fmaf(R.T, col1, R.C1);
-  R.C2 = fmaf(R.T, col2, R.C2);
-  R.T = R.T * trans;
-  ++R.n_eval;
-  ++cnt.eval;
-  if (R.T < a.ert) return true;
-  R.i += 1 << s;
-  return false;
-}
-
 template <int BPV, bool DBG>
-__device__ __forceinline__ void finish_ray(const RenderArgs& a, const RayState& R) {
-  const size_t p = (size_t)R.py * a.W + R.px;
-  a.image[p] = make_float4(fminf(R.C0, 1.0f), fminf(R.C1, 1.0f), fminf(R.C2, 1.0f), 1.0f - R.T);
+__device__ __forceinline__ void write_pixel(const RenderArgs& a, int px, int py, float C0, float C1, float C2, float T,
+                                            uint32_t h, uint32_t n_eval, int i, uint32_t n_bs) {
+  const size_t p = (size_t)py * a.W + px;
+  a.image[p] = make_float4(fminf(C0, 1.0f), fminf(C1, 1.0f), fminf(C2, 1.0f), 1.0f - T);
   if constexpr (DBG) {
-    if (a.dbg_hash) a.dbg_hash[p] = R.h;
-    if (a.dbg_n_eval) a.dbg_n_eval[p] = R.n_eval;
-    if (a.dbg_i_end) a.dbg_i_end[p] = (uint32_t)R.i;
-    if (a.dbg_n_bs) a.dbg_n_bs[p] = R.n_bs;
+    if (a.dbg_hash) a.dbg_hash[p] = h;
+    if (a.dbg_n_eval) a.dbg_n_eval[p] = n_eval;
+    if (a.dbg_i_end) a.dbg_i_end[p] = (uint32_t)i;
+    if (a.dbg_n_bs) a.dbg_n_bs[p] = n_bs;
   }
 }
 
-// Persistent launch: every lane takes the next ray from a shared counter (in
-// 8 x 4 pixel tiles, warp-aggregated) whenever its previous ray is finished,
-// so lanes stay busy however long individual rays run.
+// Persistent launch.  Each lane marches one ray and takes the next ray
+// (8 x 4 pixel tiles, warp-aggregated counter) when its ray is finished.
+// One loop iteration = one lattice step of every active lane, in three
+// phases: (1) per lane, the sample position and desired levels, and whether
+// the cached node still applies; (2) for the lanes that need a new node, the
+// warp walks the octree cooperatively, one lane per channel, 32 / MP rays at
+// a time, and writes each ray's states and brick selections; (3) per lane,
+// the skip or the evaluated sample.
 template <int MP, int BPV, bool DBG>
-__global__ void __launch_bounds__(kRenderThreads, 2) render_kernel(const __grid_constant__ RenderArgs a) {
+__global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_constant__ RenderArgs a) {
   extern __shared__ float4 smem[];
   float4* s_lut = smem;
   uint16_t* s_pre = reinterpret_cast<uint16_t*>(s_lut + MP * 256);
   uint32_t* s_sel = reinterpret_cast<uint32_t*>(smem) + MP * 256 * 4 + ((MP * 257 * 2 + 15) & ~15) / 4;
-  const int m = a.g.m;
-  for (int i = threadIdx.x; i < m * 256; i += blockDim.x) s_lut[i] = a.lut[i];
-  for (int i = threadIdx.x; i < m * 257; i += blockDim.x) s_pre[i] = a.prefix[i];
+  const Geometry& g = a.g;
+  const int m = g.m, k = g.k;
+  for (int q = threadIdx.x; q < m * 256; q += blockDim.x) s_lut[q] = a.lut[q];
+  for (int q = threadIdx.x; q < m * 257; q += blockDim.x) s_pre[q] = a.prefix[q];
   __syncthreads();
 
   const unsigned FULL = 0xFFFFFFFFu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t* my_sel = s_sel + threadIdx.x;
   const int stride = blockDim.x;
+  uint32_t* my_sel = s_sel + threadIdx.x;
+  constexpr int G = 32 / MP;                       // rays walked per cooperative pass
+  const int grp = lane / MP, ch = lane % MP;
+  const unsigned gmask = (MP == 32 ? FULL : ((1u << MP) - 1u)) << (grp * MP);
+  const unsigned lt_mask = (1u << lane) - 1u;
+
   Counters cnt = {0, 0, 0, 0, 0, 0};
-  RayState R;
+  Ray r;
+  int px = 0, py = 0, i = 0;
+  float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
+  uint32_t h = 0, n_eval = 0, n_bs = 0;
+  NodeCache nc;
+  nc.d = -1;
   bool active = false, done = false;
+
   for (;;) {
-    const unsigned need = __ballot_sync(FULL, !active && !done);
-    if (need) {
-      const int leader = __ffs(need) - 1;
+    // ------------------------------------------------------------- refill
+    const unsigned want = __ballot_sync(FULL, !active && !done);
+    if (want) {
+      const int leader = __ffs(want) - 1;
       unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(a.work, (unsigned long long)__popc(need));
+      if (lane == leader) base = atomicAdd(a.work, (unsigned long long)__popc(want));
       base = __shfl_sync(FULL, base, leader);
       if (!active && !done) {
-        const unsigned long long ray = base + __popc(need & ((1u << lane) - 1u));
+        const unsigned long long ray = base + __popc(want & lt_mask);
         if (ray >= a.n_rays) {
           done = true;
         } else {
           const uint32_t tile = (uint32_t)(ray >> 5), w = (uint32_t)(ray & 31);
-          R.px = (int)((tile % a.tiles_x) * 8 + (w & 7));
-          R.py = (int)((tile / a.tiles_x) * 4 + (w >> 3));
-          if (R.px < a.W && R.py < a.H) {
-            R.r = make_ray(a, R.px, R.py);
-            R.i = 0;
-            R.C0 = R.C1 = R.C2 = 0.0f;
-            R.T = 1.0f;
-            R.h = 2166136261u;
-            R.n_eval = R.n_bs = 0;
-            R.nc.d = -1;
-            if (R.r.hit) {
+          px = (int)((tile % a.tiles_x) * 8 + (w & 7));
+          py = (int)((tile / a.tiles_x) * 4 + (w >> 3));
+          if (px < a.W && py < a.H) {
+            r = make_ray(a, px, py);
+            i = 0;
+            C0 = C1 = C2 = 0.0f;
+            T = 1.0f;
+            h = 2166136261u;
+            n_eval = n_bs = 0;
+            nc.d = -1;
+            if (r.hit) {
               active = true;
               ++cnt.hit;
             } else {
-              finish_ray<BPV, DBG>(a, R);
+              write_pixel<BPV, DBG>(a, px, py, C0, C1, C2, T, h, n_eval, i, n_bs);
             }
           }
         }
       }
     }
     if (__all_sync(FULL, done)) break;
-    if (active && ray_step<MP, BPV, DBG>(a, s_lut, s_pre, my_sel, stride, R, cnt)) {
-      finish_ray<BPV, DBG>(a, R);
-      active = false;
+
+    // ------------------------------------- phase 1: sample, levels, node?
+    float x[3] = {0.0f, 0.0f, 0.0f};
+    int L[3] = {0, 0, 0};
+    uint64_t ldp = 0;
+    int lminu = 15, st = 0, dstart = 0;
+    bool need = false, same_node = false;
+    if (active) {
+      const float t = fmaf((float)i, a.dt, r.t0);
+      if (i >= kMaxSamples || !(t < r.t1)) {
+        write_pixel<BPV, DBG>(a, px, py, C0, C1, C2, T, h, n_eval, i, n_bs);
+        active = false;
+      } else {
+        position(a, r, t, x);
+        int lod = 0;
+        for (int l = 1; l < k; ++l) lod += (t >= a.lod_t[l]);
+        ldp = a.ldp_tab[lod];
+        lminu = a.lminu_tab[lod];
+        st = a.sdepth[lminu];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) L[q] = (int)(x[q] * pow2f(-g.leaf_log2[q]));
+        const bool same_levels = nc.d >= 0 && ldp == nc.ldp && st == nc.st;
+        if (same_levels) {
+          const int sh = g.D - nc.d;
+          same_node = (L[0] >> sh) == nc.jn[0] && (L[1] >> sh) == nc.jn[1] && (L[2] >> sh) == nc.jn[2];
+        }
+        need = !(same_node && nc.one_brick);
+        // the walk (R9) resumes below the deepest ancestor shared with the
+        // previous sample: those depths were found not all terminal
+        const int d0 = a.start_depth < st ? a.start_depth : st;
+        dstart = d0;
+        if (same_node) {
+          dstart = nc.d;
+        } else if (same_levels) {
+          int dca = 0;
+          for (int q = nc.d; q >= 0; --q) {
+            const int sh = g.D - q, up = nc.d - q;
+            if ((L[0] >> sh) == (nc.jn[0] >> up) && (L[1] >> sh) == (nc.jn[1] >> up) &&
+                (L[2] >> sh) == (nc.jn[2] >> up)) {
+              dca = q;
+              break;
+            }
+          }
+          dstart = dca + 1 > d0 ? dca + 1 : d0;
+        }
+      }
     }
+
+    // ------------------------------ phase 2: cooperative walk + selection
+    unsigned pending = __ballot_sync(FULL, need);
+    while (pending) {
+      // the q-th lane of `pending` (in lane order) is walked by group q
+      unsigned rest = pending;
+#pragma unroll
+      for (int q = 0; q < G; ++q) rest &= rest - 1u;
+      const unsigned taken = pending & ~rest;
+      pending = rest;
+      unsigned pm = taken;
+      for (int q = 0; q < grp && pm; ++q) pm &= pm - 1u;
+      const int src = pm ? __ffs(pm) - 1 : lane;
+      const bool gact = pm != 0;
+      const float sx0 = __shfl_sync(FULL, x[0], src), sx1 = __shfl_sync(FULL, x[1], src),
+                  sx2 = __shfl_sync(FULL, x[2], src);
+      const int sL0 = __shfl_sync(FULL, L[0], src), sL1 = __shfl_sync(FULL, L[1], src),
+                sL2 = __shfl_sync(FULL, L[2], src);
+      const uint32_t ldp_lo = __shfl_sync(FULL, (uint32_t)ldp, src),
+                     ldp_hi = __shfl_sync(FULL, (uint32_t)(ldp >> 32), src);
+      const uint64_t sldp = ((uint64_t)ldp_hi << 32) | ldp_lo;
+      const int sst = __shfl_sync(FULL, st, src), sds = __shfl_sync(FULL, dstart, src),
+                slm = __shfl_sync(FULL, lminu, src);
+      const bool ssame = __shfl_sync(FULL, (int)same_node, src) != 0;
+      const bool cact = gact && ch < m;
+      const int ld = cact ? (int)((sldp >> (4 * ch)) & 15) : 0;
+
+      int d = sds;
+      bool gdone = !gact, bad = false;
+      int jn0 = 0, jn1 = 0, jn2 = 0;
+      uint64_t node = 0;
+      uint32_t w = 0;
+      int sc = kEmpty;
+      for (;;) {
+        if (!gdone) {
+          const int sh = g.D - d;
+          jn0 = sL0 >> sh; jn1 = sL1 >> sh; jn2 = sL2 >> sh;
+          node = g.node_off[d] + ((uint64_t)jn2 * g.nn[d][1] + jn1) * g.nn[d][0] + jn0;
+          if (node >= g.node_off[d + 1]) {
+            bad = true;
+          } else if (cact) {
+            w = __ldg(a.octree + node * MP + ch);
+            sc = classify<BPV>(w, s_pre + ch * 257, ld, k);
+          }
+        }
+        const unsigned term = __ballot_sync(FULL, gdone || !cact || bad || terminal(sc));
+        if (!gdone && ((term & gmask) == gmask || d == sst || ssame || bad)) gdone = true;
+        if (__all_sync(FULL, gdone)) break;
+        if (!gdone) ++d;
+      }
+      const bool gbad = (__ballot_sync(FULL, bad) & gmask) != 0;
+
+      // requests of channels with nothing usable here, node requests of
+      // INVALID channels
+      if (cact && !gbad) {
+        const bool no_use = ((w & 0xFFFFu) & (~0u << ld) & ((1u << k) - 1u)) == 0;
+        if (sc == kUnmapped || (sc == kInvalid && no_use)) {
+          const int bsh = g.blog2 + ld;
+          const int bx = (int)(sx0 * pow2f(-bsh)), by = (int)(sx1 * pow2f(-bsh)), bz = (int)(sx2 * pow2f(-bsh));
+          const uint64_t pi = g.pt_off[ch * k + ld] + ((uint64_t)bz * g.nb[ld][1] + by) * g.nb[ld][0] + bx;
+          if (pi >= g.n_bricks) *a.err = kErrPageIndex;
+          else a.req[pi] = 1;
+        }
+        if (sc == kInvalid) a.node_req[node * m + ch] = 1;
+      }
+      const unsigned nonskip = __ballot_sync(FULL, cact && sc != kEmpty && sc != kUnmapped);
+      const bool all_skip = (nonskip & gmask) == 0;
+
+      // brick selection (R11): desired level, else request it and take the
+      // next coarser resident level
+      uint32_t sel = kSelNone;
+      int found = 99;
+      if (cact && !gbad && !all_skip && sc != kEmpty && sc != kUnmapped) {
+        if (sc == kHomog) {
+          sel = (kSelHomog << 27) | ((w >> 16) & 0xFFu);
+        } else if (((w & 0xFFFFu) & (~0u << ld) & ((1u << k) - 1u)) != 0) {
+          for (int l = ld; l < k; ++l) {
+            const int bsh = g.blog2 + l;
+            const int bx = (int)(sx0 * pow2f(-bsh)), by = (int)(sx1 * pow2f(-bsh)), bz = (int)(sx2 * pow2f(-bsh));
+            const uint64_t pi = g.pt_off[ch * k + l] + ((uint64_t)bz * g.nb[l][1] + by) * g.nb[l][0] + bx;
+            if (pi >= g.n_bricks) { *a.err = kErrPageIndex; break; }
+            uint32_t e = 0;
+            if ((w >> l) & 1u) e = __ldg(a.pt + pi);
+            if (e != 0) {
+              if (e - 1 >= g.cache_slots) { *a.err = kErrSlot; break; }
+              sel = ((uint32_t)l << 27) | (e - 1);
+              a.used[e - 1] = 1;
+              found = l;
+              break;
+            }
+            if (l == ld) a.req[pi] = 1;
+          }
+        }
+      }
+      if (cact) s_sel[ch * stride + warp * 32 + src] = sel;
+      const unsigned chmask = MP == 32 ? FULL : ((1u << MP) - 1u);
+      const uint32_t act = (__ballot_sync(FULL, sel != kSelNone) >> (grp * MP)) & chmask;
+      const uint32_t nbrk = __popc((__ballot_sync(FULL, sel != kSelNone && (sel >> 27) != kSelHomog) >> (grp * MP)) & chmask);
+#pragma unroll
+      for (int o = 1; o < MP; o <<= 1) {
+        const int other = __shfl_xor_sync(FULL, found, o);
+        found = other < found ? other : found;
+      }
+      // hand the walk's result to the lanes it was for
+      const bool mine = (taken >> lane) & 1u;
+      const int from = mine ? __popc(taken & lt_mask) * MP : lane;
+      const int od = __shfl_sync(FULL, d, from);
+      const int oj0 = __shfl_sync(FULL, jn0, from), oj1 = __shfl_sync(FULL, jn1, from),
+                oj2 = __shfl_sync(FULL, jn2, from);
+      const bool oskip = __shfl_sync(FULL, (int)all_skip, from) != 0;
+      const int osel = __shfl_sync(FULL, found, from);
+      const bool obad = __shfl_sync(FULL, (int)gbad, from) != 0;
+      const uint32_t oact = __shfl_sync(FULL, act, from), onb = __shfl_sync(FULL, nbrk, from);
+      (void)slm;
+      if (mine) {
+        if (obad) {
+          *a.err = kErrNodeIndex;
+          write_pixel<BPV, DBG>(a, px, py, C0, C1, C2, T, h, n_eval, i, n_bs);
+          active = false;
+        } else {
+          nc.d = od;
+          nc.jn[0] = oj0; nc.jn[1] = oj1; nc.jn[2] = oj2;
+          nc.ldp = ldp;
+          nc.st = st;
+          nc.all_skip = oskip;
+          nc.s_sel = osel;
+          nc.act = oact;
+          nc.n_brick = onb;
+          const int esh = g.D - od;
+          nc.one_brick = g.leaf_log2[0] + esh <= g.blog2 + lminu && g.leaf_log2[1] + esh <= g.blog2 + lminu &&
+                         g.leaf_log2[2] + esh <= g.blog2 + lminu;
+        }
+      }
+    }
+    __syncwarp();
+
+    // ----------------------------------------- phase 3: skip or evaluate
+    if (!active) continue;
+    if (nc.all_skip && a.skip) {
+      // first lattice index whose sample lies outside the node (R10):
+      // estimate from the node box's exit distance, then correct with the
+      // same position arithmetic
+      const int d = nc.d;
+      float tb = r.t1;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int sh = g.leaf_log2[q] + g.D - d;
+        const float lo = (float)(nc.jn[q] << sh), hi = (float)((nc.jn[q] + 1) << sh);
+        if (r.d[q] > 0.0f) tb = fminf(tb, __fdiv_rn(hi - r.o[q], r.d[q]));
+        else if (r.d[q] < 0.0f) tb = fminf(tb, __fdiv_rn(lo - r.o[q], r.d[q]));
+      }
+      float fj = ceilf(__fdiv_rn(tb - r.t0, a.dt));
+      fj = fminf(fmaxf(fj, (float)(i + 1)), (float)kMaxSamples);
+      int j = (int)fj;
+      auto inside = [&](int jj) -> bool {
+        const float tj = fmaf((float)jj, a.dt, r.t0);
+        if (!(tj < r.t1)) return false;
+        float xj[3];
+        int jc[3];
+        position(a, r, tj, xj);
+        node_coords(g, d, xj, jc);
+        return jc[0] == nc.jn[0] && jc[1] == nc.jn[1] && jc[2] == nc.jn[2];
+      };
+      while (j < kMaxSamples && inside(j)) ++j;
+      while (j > i + 1 && !inside(j - 1)) --j;
+      if constexpr (DBG) {
+        h = fnv_word(h, (uint32_t)i);
+        h = fnv_word(h, 0xFFFFFFFFu);
+        h = fnv_word(h, (uint32_t)d);
+        h = fnv_word(h, (uint32_t)j);
+      }
+      ++cnt.skip;
+      cnt.skipped += (unsigned long long)(j - i);
+      i = j;
+      continue;
+    }
+
+    // shade and composite (R12-R14)
+    const int s = nc.s_sel == 99 ? lminu : nc.s_sel;
+    float col0 = 0.0f, col1 = 0.0f, col2 = 0.0f, trans = 1.0f;
+    cnt.bs += nc.n_brick;
+    cnt.homog += __popc(nc.act) - nc.n_brick;
+    n_bs += nc.n_brick;
+    for (uint32_t mm = nc.act; mm; mm &= mm - 1u) {
+      const int c = __ffs(mm) - 1;
+      const uint32_t sel = my_sel[c * stride];
+      const uint32_t lb = sel >> 27;
+      float val;
+      if (lb == kSelHomog) {
+        val = (float)(sel & kSelMask);
+        if constexpr (DBG) {
+          h = fnv_word(h, (uint32_t)i); h = fnv_word(h, (uint32_t)c);
+          h = fnv_word(h, 0xFFu); h = fnv_word(h, 0xFFFFFFFFu);
+        }
+      } else {
+        val = trilinear<BPV>(a, sel & kSelMask, (int)lb, x);
+        if constexpr (DBG) {
+          const int bsh = g.blog2 + (int)lb;
+          const uint32_t bx = (uint32_t)(x[0] * pow2f(-bsh)), by = (uint32_t)(x[1] * pow2f(-bsh)),
+                         bz = (uint32_t)(x[2] * pow2f(-bsh));
+          h = fnv_word(h, (uint32_t)i); h = fnv_word(h, (uint32_t)c); h = fnv_word(h, lb);
+          h = fnv_word(h, ((uint32_t)(c * k + (int)lb) << 24) | (bz << 16) | (by << 8) | bx);
+        }
+      }
+      float q, cr, cg, cb;
+      shade(a, s_lut + c * 256, c, val, s, q, cr, cg, cb);
+      const float ap = 1.0f - q;
+      col0 = fmaf(ap, cr, col0);
+      col1 = fmaf(ap, cg, col1);
+      col2 = fmaf(ap, cb, col2);
+      trans = trans * q;
+    }
+    C0 = fmaf(T, col0, C0);
+    C1 = fmaf(T, col1, C1);
+    C2 = fmaf(T, col2, C2);
+    T = T * trans;
+    ++n_eval;
+    ++cnt.eval;
+    if (T < a.ert) {
+      write_pixel<BPV, DBG>(a, px, py, C0, C1, C2, T, h, n_eval, i, n_bs);
+      active = false;
+      continue;
+    }
+    i += 1 << s;
   }
 
   // per-block counters, reduced without atomics
