@@ -47,7 +47,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--radius", type=float, default=None)
-    ap.add_argument("--lod-bias", type=float, default=1.0)
+    ap.add_argument("--lod-bias", type=float, default=None,
+                    help="scale of the level thresholds (default 0.5 for cells16, 1 otherwise)")
+    ap.add_argument("--arc", type=float, default=45.0, help="orbit arc of the cells16 views, degrees")
     ap.add_argument("--cache-gib", type=float, default=8.0)
     return ap.parse_args()
 
@@ -59,12 +61,14 @@ def make_workload(args):
     from synth import recipes
     if args.workload == "cells16":
         kw = {} if args.radius is None else {"radius": args.radius}
-        scene = recipes.cells_large(**kw)
+        bias = 0.5 if args.lod_bias is None else args.lod_bias
+        scene = recipes.cells_large(arc_deg=args.arc, lod_bias=bias, **kw)
         label = {"workload": "cells16: 16-channel 4096x4096x96 u16 procedural cell slab (spacing 1:1:4), "
                              "32^3 bricks, 7 levels, 8 GiB brick cache, 1920x1080 perspective orbit, "
                              "per-channel TFs with additive colour",
                  "channels": 16, "dims": [4096, 4096, 96], "image": [1920, 1080], "levels": 7,
-                 "cache_gib": args.cache_gib, "sample_dtype": "u16 -> f32"}
+                 "cache_gib": args.cache_gib, "sample_dtype": "u16 -> f32", "orbit_arc_deg": args.arc,
+                 "lod_bias": bias, "views": len(scene.frames)}
         slot_bytes = 34 ** 3 * 2
         slots = int(args.cache_gib * GIB) // (((slot_bytes + 255) // 256) * 256)
     elif args.workload == "cells4":
@@ -77,7 +81,7 @@ def make_workload(args):
         label = {"workload": "blobs: 1-channel 128^3 u8 Gaussian blobs, 256^2 ortho", "channels": 1,
                  "dims": [128, 128, 128], "image": [256, 256], "levels": 3}
         slots = len(scene.all_bricks())
-    if args.lod_bias != 1.0:
+    if args.workload != "cells16" and args.lod_bias not in (None, 1.0):
         for f in scene.frames:
             f.lod_t = [t * args.lod_bias for t in f.lod_t]
     return scene, label, slots

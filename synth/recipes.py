@@ -133,11 +133,12 @@ def cells_slab(seed=2, m=4, dims=(1024, 1024, 64), ncells=20000, k=5, resident_l
 
 
 def cells_large(seed=3, m=16, dims=(4096, 4096, 96), ncells=480000, k=7, W=1920, H=1080, n_views=16, fovy=40.0,
-                radius=1500.0, elevation=35.0, close_up=True) -> Scene:
+                radius=1500.0, elevation=35.0, close_up=True, arc_deg=360.0, lod_bias=1.0) -> Scene:
     """16-channel 4096x4096x96 u16 procedural slab (spacing 1:1:4) of the
     same cell model, bricks generated on request; 1920x1080 perspective orbit
     about the slab normal around the centre (close-up: one pixel ~ one
-    level-0 voxel at the focus)."""
+    level-0 voxel at the focus), n_views views spread over arc_deg degrees;
+    lod_bias scales the level thresholds."""
     spacing = (1.0, 1.0, 4.0)
     cells = Cells(seed, ncells, m, dims, spacing)
     leaf = (16, 16, 4)
@@ -147,8 +148,8 @@ def cells_large(seed=3, m=16, dims=(4096, 4096, 96), ncells=480000, k=7, W=1920,
     center = tuple(d * sp / 2.0 for d, sp in zip(dims, spacing))
     r = radius if close_up else 0.55 * math.hypot(dims[0], dims[1]) / math.tan(math.radians(fovy) / 2.0)
     tfs = _cell_tfs(m)
-    lod = lod_thresholds(min(spacing), H, fovy, k)
+    lod = lod_thresholds(min(spacing), H, fovy, k, bias=lod_bias)
     for v in range(n_views):
-        cam = orbit(center, r, elevation, 360.0 * v / n_views + 7.0, W, H, fovy)
+        cam = orbit(center, r, elevation, arc_deg * v / n_views + 7.0, W, H, fovy)
         s.frames.append(Frame(W, H, cam, tfs, 0.5 * min(spacing), lod, [0] * m, [k - 1] * m))
     return s
