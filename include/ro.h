@@ -261,6 +261,35 @@ ro_status ro_set_timeout(ro_ctx* ctx, uint32_t ms);
  * context lives); "ok" if none.  A NULL ctx gives the last ro_create error. */
 const char* ro_last_error(const ro_ctx* ctx);
 
+/* Flag compaction that allocates no memory.  The paper has no counterpart:
+ * this exists for callers that cannot allocate device memory, such as a
+ * plugin whose host application owns all GPU memory and gives it no
+ * allocator, or a frame loop in which a device allocation would stall or
+ * synchronise the GPU.  It runs the same compaction as the request readback
+ * of ro_read_requests, without a context:
+ *  flags    device pointer, n_flags bytes, 16-byte aligned; non-zero = set.
+ *           Every flag is cleared.
+ *  n_flags  a multiple of 16, at most 2^28 (268,435,456); larger sizes
+ *           return RO_ERR_CAPACITY, other sizes RO_ERR_INVALID_ARG.
+ *  ids      device pointer, cap u32: the indices of the set flags in
+ *           ascending order, the first min(total, cap) of them (may be NULL
+ *           when cap = 0).
+ *  total    device pointer to one u32: the number of set flags.
+ *  stream   cudaStream_t the work is enqueued on (NULL = legacy default
+ *           stream); the call returns without waiting.
+ * Its per-tile counts live in one 256 KiB array in device memory, part of the
+ * library itself, which every GPU that loads the library holds until the
+ * process exits; it never calls cudaMalloc, cudaFree or any allocating
+ * routine.  The first call on a device looks up that array's device address
+ * (with the device current), so make the first call on each device before
+ * any stream capture.  Every call overwrites the counts it uses before
+ * reading them, and all calls share the one array: calls whose work overlaps
+ * on the GPU (other streams, other threads) race and give wrong lists, so
+ * order them on one stream or with events.  Returns RO_ERR_CUDA if the
+ * lookup or the launch fails. */
+ro_status ro_compact_flags_noalloc(uint8_t* flags, uint64_t n_flags, uint32_t* ids, uint32_t cap,
+                                   uint32_t* total, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,8 @@ RO_NONE = 0xFFFFFFFF
 STATUS = {0: "RO_OK", 1: "RO_ERR_INVALID_ARG", 2: "RO_ERR_CUDA", 3: "RO_ERR_CAPACITY", 4: "RO_ERR_TIMEOUT",
           5: "RO_ERR_INTERNAL"}
 EXPORTS = ["ro_query_sizes", "ro_create", "ro_destroy", "ro_upload_bricks", "ro_update_residency_octree", "ro_render",
-           "ro_read_requests", "ro_get_stats", "ro_debug_read", "ro_brick_index", "ro_set_timeout", "ro_last_error"]
+           "ro_read_requests", "ro_get_stats", "ro_debug_read", "ro_brick_index", "ro_set_timeout", "ro_last_error",
+           "ro_compact_flags_noalloc"]
 
 
 class RoError(RuntimeError):
@@ -99,6 +100,7 @@ def load(build_if_missing: bool = True):
     L.ro_set_timeout.argtypes = [vp, u32]
     L.ro_last_error.restype = ctypes.c_char_p
     L.ro_last_error.argtypes = [vp]
+    L.ro_compact_flags_noalloc.argtypes = [vp, u64, vp, u32, vp, vp]
     for f in EXPORTS:
         getattr(L, f).restype = getattr(L, f).restype if f in ("ro_brick_index", "ro_last_error") else ctypes.c_int
     _lib = L
@@ -236,6 +238,19 @@ class Context:
 
     def brick_index(self, brick_id: int) -> int:
         return int(self.L.ro_brick_index(self.h, int(brick_id)))
+
+
+def compact_flags_noalloc(flags, ids, total, stream=None):
+    """ro_compact_flags_noalloc on torch cuda tensors: flags (uint8, length a
+    multiple of 16), ids (int32 capacity), total (int32, one element).  No
+    device memory is allocated by the call."""
+    import torch
+    L = load()
+    st = stream if stream is not None else torch.cuda.current_stream(flags.device)
+    rc = L.ro_compact_flags_noalloc(ctypes.c_void_p(flags.data_ptr()), flags.numel(), ctypes.c_void_p(ids.data_ptr()),
+                                    ids.numel(), ctypes.c_void_p(total.data_ptr()), ctypes.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise RoError(rc, "ro_compact_flags_noalloc failed")
 
 
 def brick_id(c, l, bx, by, bz, k) -> int:
