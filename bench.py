@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--radius", type=float, default=None)
     ap.add_argument("--lod-bias", type=float, default=None,
                     help="scale of the level thresholds (default 0.5 for cells16, 1 otherwise)")
-    ap.add_argument("--arc", type=float, default=45.0, help="orbit arc of the cells16 views, degrees")
+    ap.add_argument("--arc", type=float, default=30.0, help="orbit arc of the cells16 views, degrees")
     ap.add_argument("--cache-gib", type=float, default=8.0)
     return ap.parse_args()
 

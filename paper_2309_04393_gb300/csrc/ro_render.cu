@@ -216,8 +216,9 @@ __device__ __forceinline__ void write_pixel(const RenderArgs& a, int px, int py,
   }
 }
 
-// Persistent launch.  Each lane marches one ray and takes the next ray
-// (8 x 4 pixel tiles, warp-aggregated counter) when its ray is finished.
+// Persistent launch.  Each warp takes the next 8 x 4 pixel tile from a
+// counter once all its lanes are free, so the 32 rays of a warp stay
+// neighbours and their footprints share cache lines.
 // One loop iteration = one lattice step of every active lane, in three
 // phases: (1) per lane, the sample position and desired levels, and whether
 // the cached node still applies; (2) for the lanes that need a new node, the
@@ -256,34 +257,31 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
 
   for (;;) {
     // ------------------------------------------------------------- refill
-    const unsigned want = __ballot_sync(FULL, !active && !done);
-    if (want) {
-      const int leader = __ffs(want) - 1;
+    const unsigned busy = __ballot_sync(FULL, active);
+    if (!busy && !done) {
       unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(a.work, (unsigned long long)__popc(want));
-      base = __shfl_sync(FULL, base, leader);
-      if (!active && !done) {
-        const unsigned long long ray = base + __popc(want & lt_mask);
-        if (ray >= a.n_rays) {
-          done = true;
-        } else {
-          const uint32_t tile = (uint32_t)(ray >> 5), w = (uint32_t)(ray & 31);
-          px = (int)((tile % a.tiles_x) * 8 + (w & 7));
-          py = (int)((tile / a.tiles_x) * 4 + (w >> 3));
-          if (px < a.W && py < a.H) {
-            r = make_ray(a, px, py);
-            i = 0;
-            C0 = C1 = C2 = 0.0f;
-            T = 1.0f;
-            h = 2166136261u;
-            n_eval = n_bs = 0;
-            nc.d = -1;
-            if (r.hit) {
-              active = true;
-              ++cnt.hit;
-            } else {
-              write_pixel<BPV, DBG>(a, px, py, C0, C1, C2, T, h, n_eval, i, n_bs);
-            }
+      if (lane == 0) base = atomicAdd(a.work, 32ull);
+      base = __shfl_sync(FULL, base, 0);
+      const unsigned long long ray = base + lane;
+      if (base >= a.n_rays) {
+        done = true;
+      } else {
+        const uint32_t tile = (uint32_t)(ray >> 5), w = (uint32_t)(ray & 31);
+        px = (int)((tile % a.tiles_x) * 8 + (w & 7));
+        py = (int)((tile / a.tiles_x) * 4 + (w >> 3));
+        if (px < a.W && py < a.H) {
+          r = make_ray(a, px, py);
+          i = 0;
+          C0 = C1 = C2 = 0.0f;
+          T = 1.0f;
+          h = 2166136261u;
+          n_eval = n_bs = 0;
+          nc.d = -1;
+          if (r.hit) {
+            active = true;
+            ++cnt.hit;
+          } else {
+            write_pixel<BPV, DBG>(a, px, py, C0, C1, C2, T, h, n_eval, i, n_bs);
           }
         }
       }
