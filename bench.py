@@ -51,6 +51,8 @@ def parse():
                     help="scale of the level thresholds (default 0.5 for cells16, 1 otherwise)")
     ap.add_argument("--arc", type=float, default=30.0, help="orbit arc of the cells16 views, degrees")
     ap.add_argument("--cache-gib", type=float, default=8.0)
+    ap.add_argument("--image", type=str, default=None, help="override the image size, WxH")
+    ap.add_argument("--warm-rounds", type=int, default=12, help="at most this many warm-up rounds over the orbit")
     return ap.parse_args()
 
 
@@ -81,6 +83,11 @@ def make_workload(args):
         label = {"workload": "blobs: 1-channel 128^3 u8 Gaussian blobs, 256^2 ortho", "channels": 1,
                  "dims": [128, 128, 128], "image": [256, 256], "levels": 3}
         slots = len(scene.all_bricks())
+    if args.image:
+        W, H = (int(v) for v in args.image.lower().split("x"))
+        for f in scene.frames:
+            f.W, f.H = W, H
+        label["image"] = [W, H]
     if args.workload != "cells16" and args.lod_bias not in (None, 1.0):
         for f in scene.frames:
             f.lod_t = [t * args.lod_bias for t in f.lod_t]
@@ -93,7 +100,7 @@ def decode_ids(ids, k):
     return np.stack([p // k, p % k, ids & 0xFF, (ids >> 8) & 0xFF, (ids >> 16) & 0xFF], 1).astype(np.int32)
 
 
-def warm_cache(ctx, scene, image, budget_s):
+def warm_cache(ctx, scene, image, budget_s, max_rounds):
     """Ray-guided warm-up (Sec. 4): render each orbit frame, read its
     requests, make the requested bricks, upload them, update the octree;
     repeat over the orbit until a round requests nothing or time runs out."""
@@ -101,7 +108,7 @@ def warm_cache(ctx, scene, image, budget_s):
     t0 = time.time()
     uploaded, rounds, last = 0, 0, None
     max_up = int(ctx.desc.max_upload)
-    while time.time() - t0 < budget_s:
+    while time.time() - t0 < budget_s and rounds < max_rounds:
         rounds += 1
         req_round = 0
         for f in scene.frames:
@@ -166,6 +173,27 @@ class Clocks:
                     reasons.add(n)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def recorded_traffic(args):
+    """DRAM bytes per render launch from the committed ncu record, only while
+    the render kernel's source is the one that record was taken from and the
+    workload is the default one; else None."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "render_kernel_cells16_traffic.json")) as fh:
+            rec = json.load(fh)
+        h = hashlib.sha256()
+        for f in rec["source_files"]:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        default = (args.workload == "cells16" and args.image is None and args.cache_gib == 8.0 and args.arc == 30.0
+                   and args.lod_bias is None and args.radius is None)
+        if h.hexdigest() == rec["source_sha256"] and default:
+            return int(rec["dram_read_bytes_per_launch"]) + int(rec["dram_write_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
 
 
 def measured_hbm_peak():
@@ -277,7 +305,7 @@ def run_ours(args, rank, world, local_rank):
     log(f"rank {rank}: arena {ctx.sizes.total / GIB:.2f} GiB, {slots} slots, metadata + initial bricks "
         f"{time.time() - t:.1f} s")
     image = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
-    warm = warm_cache(ctx, scene, image, args.warm_seconds)
+    warm = warm_cache(ctx, scene, image, args.warm_seconds, args.warm_rounds)
 
     def step(f):
         ro.render_frame(ctx, f, image)
@@ -309,10 +337,13 @@ def run_ours(args, rank, world, local_rank):
     total_ms = ev0.elapsed_time(ev1)
     render_ms = [a.elapsed_time(b) for a, b in er]
 
-    # counters of the same frames (same cache state, untimed)
+    # counters of the same frames (same cache state, untimed); the NVTX range
+    # lets a profiler pick one steady-state render launch
     samples = chan = hit = 0
     for f in order:
+        torch.cuda.nvtx.range_push("stats_render")
         ro.render_frame(ctx, f, image)
+        torch.cuda.nvtx.range_pop()
         st = ctx.stats()
         hit += int(st[0])
         samples += int(st[1])
@@ -369,7 +400,7 @@ def run_ours(args, rank, world, local_rank):
                           channel_samples_per_step=chan // len(order), samples_per_step=samples // len(order),
                           rays_hit_per_step=hit // len(order), warmup_cache=warm),
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "traffic": None, "peak_source": f"{peak_kind} copy bandwidth",
+                        "traffic": recorded_traffic(args), "peak_source": f"{peak_kind} copy bandwidth",
                         "kernel": "render_kernel (ro_render)",
                         "algorithmic_bytes": f"{fp_bytes} B per channel brick sample (2x2x2 footprint) + 16 B per pixel"},
            "clocks": clk,
