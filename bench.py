@@ -262,7 +262,7 @@ def run_reference(args, rank, world):
     t = time.perf_counter()
     words = vol.node_words()
     log(f"oracle node words: {time.perf_counter() - t:.1f} s")
-    per_step = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     samples, seconds, pixels, cores = 0, 0.0, 0, 1
     for s in range(args.warmup + args.steps):
         r = oracle_rate(scene, frames[s % len(frames)], per_step, seed=s, words=words, vol=vol)
@@ -282,6 +282,19 @@ def run_reference(args, rank, world):
            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
+
+
+def combine_ranks(total_ms, e2e_s, samples, dist=None, device="cpu"):
+    """Whole-job numbers of a replicas run: the slowest rank's times and the
+    samples of all ranks (weak scaling: every rank renders its own frames)."""
+    import torch
+    if dist is None:
+        return float(total_ms), float(e2e_s), float(samples)
+    mx = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=device)
+    sm = torch.tensor([float(samples)], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(mx[1]), float(sm[0])
 
 
 def run_ours(args, rank, world, local_rank):
@@ -368,15 +381,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
 
-    tot = torch.tensor([total_ms, e2e_s, float(samples)], dtype=torch.float64, device="cuda")
-    if dist:
-        mx = tot.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tot.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        total_ms, e2e_s, samples_all = float(mx[0]), float(mx[1]), float(sm[2])
-    else:
-        samples_all = float(samples)
+    total_ms, e2e_s, samples_all = combine_ranks(total_ms, e2e_s, samples, dist, "cuda")
     if rank != 0:
         return 0
     value = samples_all / (total_ms / 1000.0)

@@ -746,9 +746,11 @@ ro_status ro_read_requests(ro_ctx* c, uint32_t* ids, uint32_t cap, uint32_t* n, 
   u.n = c->desc.cache_slots;
   u.frame = c->frame;
   RO_TRY(cuda_check(c, ro::launch_usage(u, st), "ro_read_requests: usage"));
+  // wait (with the deadline) before any copy into pageable host memory: such
+  // a copy would itself block until the stream reaches it
+  RO_TRY(wait_stream(c, "ro_read_requests"));
   uint32_t tot[2] = {0, 0};
   RO_TRY(cuda_check(c, cudaMemcpyAsync(tot, totals, 8, cudaMemcpyDeviceToHost, st), "ro_read_requests: totals"));
-  RO_TRY(wait_stream(c, "ro_read_requests"));
   const uint32_t nr = std::min({tot[0], cap, c->desc.max_requests});
   const uint32_t nn = std::min({tot[1], node_cap, c->desc.max_requests});
   if (nr) RO_TRY(cuda_check(c, cudaMemcpyAsync(ids, c->req_out, 4ull * nr, cudaMemcpyDeviceToHost, st), "ro_read_requests: ids"));
@@ -764,11 +766,11 @@ ro_status ro_read_requests(ro_ctx* c, uint32_t* ids, uint32_t cap, uint32_t* n, 
 ro_status ro_get_stats(ro_ctx* c, uint64_t out[8]) {
   if (!c || !out) return RO_ERR_INVALID_ARG;
   if (c->latched != RO_OK) return c->latched;
+  RO_TRY(wait_stream(c, "ro_get_stats"));
   std::vector<unsigned long long> v((size_t)c->last_blocks * ro::kStats);
   if (!v.empty())
     RO_TRY(cuda_check(c, cudaMemcpyAsync(v.data(), c->scratch + c->L.sc_stats, v.size() * 8, cudaMemcpyDeviceToHost, c->stream),
                       "ro_get_stats"));
-  RO_TRY(wait_stream(c, "ro_get_stats"));
   for (int q = 0; q < 8; ++q) out[q] = 0;
   for (size_t b = 0; b < c->last_blocks; ++b)
     for (int q = 0; q < ro::kStats; ++q) out[q] += v[b * ro::kStats + q];
@@ -789,6 +791,7 @@ ro_status ro_debug_read(ro_ctx* c, uint32_t what, void* host, uint64_t bytes) {
     default: return set_err(c, RO_ERR_INVALID_ARG, "ro_debug_read: unknown array");
   }
   if (bytes != size) return set_err(c, RO_ERR_INVALID_ARG, "ro_debug_read: size mismatch");
+  RO_TRY(wait_stream(c, "ro_debug_read"));
   RO_TRY(cuda_check(c, cudaMemcpyAsync(host, src, size, cudaMemcpyDeviceToHost, c->stream), "ro_debug_read"));
   return wait_stream(c, "ro_debug_read");
 }
