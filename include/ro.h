@@ -190,7 +190,8 @@ typedef struct {
 /* Per-frame rendering parameters.
  *  dt          lattice spacing along the ray, physical units, > 0
  *  lod_t       desired-level thresholds: lod(t) = #{l in 1..k-1 : t >= lod_t[l]}
- *              (t = physical distance from the ray origin); index 0 unused
+ *              (t = physical distance from the ray origin); index 0 unused;
+ *              lod_t[1..k-1] must be non-decreasing (+inf allowed)
  *  lmin, lmax  per-channel level range, 0 <= lmin <= lmax < k (Sec. 6.2)
  *  start_depth octree depth at which traversal starts (Sec. 7), <= depth
  *  skip        1 = empty-space skipping on

@@ -83,6 +83,7 @@ ro_status make_geometry(const ro_desc* d, Geometry* g, std::string* why) {
       int v = g->dims0[a];
       for (int q = 0; q < l; ++q) v = (v + 1) / 2;
       g->ldims[l][a] = v;
+      g->ldimf[l][a] = (float)(v - 1);
       g->nb[l][a] = (v + g->B - 1) / g->B;
       if (g->nb[l][a] > 256) return fail("more than 256 bricks per axis (8-bit brick offsets)");
     }
@@ -615,6 +616,8 @@ ro_status ro_render(ro_ctx* c, const ro_camera* cam, const ro_tf* tfs, const ro_
   const Geometry& g = c->g;
   if (!(p->dt > 0.0f) || !std::isfinite(p->dt)) return set_err(c, RO_ERR_INVALID_ARG, "ro_render: dt must be positive");
   if (p->start_depth > (uint32_t)g.D) return set_err(c, RO_ERR_INVALID_ARG, "ro_render: start_depth beyond the octree depth");
+  for (int l = 2; l < g.k; ++l)
+    if (!(p->lod_t[l] >= p->lod_t[l - 1])) return set_err(c, RO_ERR_INVALID_ARG, "ro_render: lod_t must be non-decreasing");
   for (int ch = 0; ch < g.m; ++ch) {
     if (p->lmin[ch] > p->lmax[ch] || p->lmax[ch] >= (uint32_t)g.k)
       return set_err(c, RO_ERR_INVALID_ARG, "ro_render: need lmin <= lmax < levels");

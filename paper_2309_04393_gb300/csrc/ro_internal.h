@@ -23,6 +23,7 @@ struct Geometry {
   int leaf_log2[3];
   int D;                      // octree depth (leaves at depth D)
   int ldims[kMaxL][3];        // level dims
+  float ldimf[kMaxL][3];      // level dims - 1, as floats (trilinear clamp bound)
   int nb[kMaxL][3];           // bricks per axis per level
   uint32_t pt_off[kMaxC * kMaxL + 1];  // page-table offset of table c*k + l; [m*k] = n_bricks
   uint64_t node_off[kMaxDepth + 2];    // first node of each depth; [D+1] = n_nodes

@@ -40,6 +40,20 @@ __device__ __forceinline__ int classify(uint32_t w, const uint16_t* pre, int ld,
 
 __device__ __forceinline__ bool terminal(int s) { return s == kEmpty || s == kHomog || s == kUnmapped; }
 
+// CPL consecutive node words (one vector load; CPL = 4, 2 or 1).
+template <int CPL>
+__device__ __forceinline__ void load_cpl(const uint32_t* p, uint32_t (&w)[CPL]) {
+  if constexpr (CPL == 4) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+  } else if constexpr (CPL == 2) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+    w[0] = v.x; w[1] = v.y;
+  } else {
+    w[0] = __ldg(p);
+  }
+}
+
 struct Ray {
   float o[3], d[3];
   float t0, t1;
@@ -107,17 +121,17 @@ __device__ __forceinline__ void node_coords(const Geometry& g, int d, const floa
 
 // Trilinear sample of a level-l apron slot (R15): corners are read from the
 // owner's slot, lerps along x, then y, then z.
-template <int BPV>
+template <int BPV, int EC>
 __device__ __forceinline__ float trilinear(const RenderArgs& a, uint32_t slot, int l, const float (&x)[3]) {
   const Geometry& g = a.g;
-  const int E = (int)g.edge;
+  const int E = EC ? EC : (int)g.edge;  // apron-slot edge, a compile-time constant for 32^3 bricks
   int li[3];
   float f[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const float xl = x[k] * pow2f(-l);
     float u = xl - 0.5f;
-    u = fminf(fmaxf(u, 0.0f), (float)(g.ldims[l][k] - 1));
+    u = fminf(fmaxf(u, 0.0f), g.ldimf[l][k]);
     const int i0 = (int)u;
     f[k] = u - (float)i0;
     const int b = (int)(x[k] * pow2f(-(g.blog2 + l)));
@@ -225,7 +239,7 @@ __device__ __forceinline__ void write_pixel(const RenderArgs& a, int px, int py,
 // warp walks the octree cooperatively, one lane per channel, 32 / MP rays at
 // a time, and writes each ray's states and brick selections; (3) per lane,
 // the skip or the evaluated sample.
-template <int MP, int BPV, bool DBG>
+template <int MP, int BPV, int EC, bool DBG>
 __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_constant__ RenderArgs a) {
   extern __shared__ float4 smem[];
   float4* s_lut = smem;
@@ -248,7 +262,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
 
   Counters cnt = {0, 0, 0, 0, 0, 0};
   Ray r;
-  int px = 0, py = 0, i = 0;
+  int px = 0, py = 0, i = 0, lod = 0;
   float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
   uint32_t h = 0, n_eval = 0, n_bs = 0;
   NodeCache nc;
@@ -272,6 +286,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
         if (px < a.W && py < a.H) {
           r = make_ray(a, px, py);
           i = 0;
+          lod = 0;
           C0 = C1 = C2 = 0.0f;
           T = 1.0f;
           h = 2166136261u;
@@ -301,8 +316,9 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
         active = false;
       } else {
         position(a, r, t, x);
-        int lod = 0;
-        for (int l = 1; l < k; ++l) lod += (t >= a.lod_t[l]);
+        // lod = #{l in 1..k-1 : t >= lod_t[l]} (R7); t never decreases along
+        // a ray and the thresholds are non-decreasing, so the count only grows
+        while (lod < k - 1 && t >= a.lod_t[lod + 1]) ++lod;
         ldp = a.ldp_tab[lod];
         lminu = a.lminu_tab[lod];
         st = a.sdepth[lminu];
@@ -529,7 +545,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
           h = fnv_word(h, 0xFFu); h = fnv_word(h, 0xFFFFFFFFu);
         }
       } else {
-        val = trilinear<BPV>(a, sel & kSelMask, (int)lb, x);
+        val = trilinear<BPV, EC>(a, sel & kSelMask, (int)lb, x);
         if constexpr (DBG) {
           const int bsh = g.blog2 + (int)lb;
           const uint32_t bx = (uint32_t)(x[0] * pow2f(-bsh)), by = (uint32_t)(x[1] * pow2f(-bsh)),
@@ -611,10 +627,10 @@ __global__ void __launch_bounds__(256) prefix_kernel(const __grid_constant__ Pre
   if (q == 0) a.prefix[c * 257 + 256] = s_scan[256];
 }
 
-template <int MP, int BPV, bool DBG>
+template <int MP, int BPV, int EC, bool DBG>
 cudaError_t launch_one(const RenderArgs& a, cudaStream_t s, int* blocks_out) {
   const size_t smem = render_smem_bytes(MP);
-  auto kern = render_kernel<MP, BPV, DBG>;
+  auto kern = render_kernel<MP, BPV, EC, DBG>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
@@ -630,9 +646,14 @@ cudaError_t launch_one(const RenderArgs& a, cudaStream_t s, int* blocks_out) {
   return cudaGetLastError();
 }
 
+template <int MP, int BPV, int EC>
+cudaError_t launch_ec(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out) {
+  return debug ? launch_one<MP, BPV, EC, true>(a, s, blocks_out) : launch_one<MP, BPV, EC, false>(a, s, blocks_out);
+}
+
 template <int MP, int BPV>
 cudaError_t launch_mp(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out) {
-  return debug ? launch_one<MP, BPV, true>(a, s, blocks_out) : launch_one<MP, BPV, false>(a, s, blocks_out);
+  return a.g.edge == 34 ? launch_ec<MP, BPV, 34>(a, debug, s, blocks_out) : launch_ec<MP, BPV, 0>(a, debug, s, blocks_out);
 }
 
 template <int MP>
