@@ -171,11 +171,10 @@ __device__ __forceinline__ float trilinear(const RenderArgs& a, uint32_t slot, i
 }
 
 // TF lookup (R16) and opacity correction for a step of 2^s (R12): returns
-// the corrected opacity's complement q and the colour.
-__device__ __forceinline__ void shade(const RenderArgs& a, const float4* __restrict__ lut, int c, float val, int s,
-                                      float& q, float& r, float& gg, float& b) {
-  const float t = val - a.tf_lo[c];
-  float xq = t * a.tf_scale[c];
+// the corrected opacity's complement q and the colour.  tf = (lo, scale).
+__device__ __forceinline__ void shade(const float4* __restrict__ lut, float2 tf, float val, int s, float& q, float& r,
+                                      float& gg, float& b) {  const float t = val - tf.x;
+  float xq = t * tf.y;
   xq = fminf(fmaxf(xq, 0.0f), 255.0f);
   int j = (int)xq;
   j = j > 254 ? 254 : j;
@@ -249,6 +248,12 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
   const int m = g.m, k = g.k;
   for (int q = threadIdx.x; q < m * 256; q += blockDim.x) s_lut[q] = a.lut[q];
   for (int q = threadIdx.x; q < m * 257; q += blockDim.x) s_pre[q] = a.prefix[q];
+  // per-channel tables read with a per-lane channel index live in shared
+  // memory (a constant-bank read with divergent indices is replayed per index)
+  __shared__ float2 s_tf[kMaxC];
+  __shared__ uint32_t s_pto[kMaxC * kMaxL + 1];
+  for (int q = threadIdx.x; q < m; q += blockDim.x) s_tf[q] = make_float2(a.tf_lo[q], a.tf_scale[q]);
+  for (int q = threadIdx.x; q <= m * k; q += blockDim.x) s_pto[q] = g.pt_off[q];
   __syncthreads();
 
   const unsigned FULL = 0xFFFFFFFFu;
@@ -409,7 +414,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
         if (sc == kUnmapped || (sc == kInvalid && no_use)) {
           const int bsh = g.blog2 + ld;
           const int bx = (int)(sx0 * pow2f(-bsh)), by = (int)(sx1 * pow2f(-bsh)), bz = (int)(sx2 * pow2f(-bsh));
-          const uint64_t pi = g.pt_off[ch * k + ld] + ((uint64_t)bz * g.nb[ld][1] + by) * g.nb[ld][0] + bx;
+          const uint64_t pi = s_pto[ch * k + ld] + ((uint64_t)bz * g.nb[ld][1] + by) * g.nb[ld][0] + bx;
           if (pi >= g.n_bricks) *a.err = kErrPageIndex;
           else a.req[pi] = 1;
         }
@@ -429,7 +434,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
           for (int l = ld; l < k; ++l) {
             const int bsh = g.blog2 + l;
             const int bx = (int)(sx0 * pow2f(-bsh)), by = (int)(sx1 * pow2f(-bsh)), bz = (int)(sx2 * pow2f(-bsh));
-            const uint64_t pi = g.pt_off[ch * k + l] + ((uint64_t)bz * g.nb[l][1] + by) * g.nb[l][0] + bx;
+            const uint64_t pi = s_pto[ch * k + l] + ((uint64_t)bz * g.nb[l][1] + by) * g.nb[l][0] + bx;
             if (pi >= g.n_bricks) { *a.err = kErrPageIndex; break; }
             uint32_t e = 0;
             if ((w >> l) & 1u) e = __ldg(a.pt + pi);
@@ -554,8 +559,11 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
           h = fnv_word(h, ((uint32_t)(c * k + (int)lb) << 24) | (bz << 16) | (by << 8) | bx);
         }
       }
+      // a value at or below the window start maps to knot 0; with a
+      // transparent knot 0 the channel adds exactly nothing (a' = 0, q = 1)
+      if (!((val - s_tf[c].x) * s_tf[c].y > 0.0f) && s_lut[c * 256].w <= 0.0f) continue;
       float q, cr, cg, cb;
-      shade(a, s_lut + c * 256, c, val, s, q, cr, cg, cb);
+      shade(s_lut + c * 256, s_tf[c], val, s, q, cr, cg, cb);
       const float ap = 1.0f - q;
       col0 = fmaf(ap, cr, col0);
       col1 = fmaf(ap, cg, col1);
