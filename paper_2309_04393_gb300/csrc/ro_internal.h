@@ -11,7 +11,7 @@ constexpr int kMaxC = 16;       // channels per context (RO_MAX_CHANNELS)
 constexpr int kMaxL = 16;       // levels per context (RO_MAX_LEVELS)
 constexpr int kMaxDepth = 24;   // octree depth bound (2^24 leaves per axis)
 constexpr int kMaxSamples = 1 << 24;  // lattice indices stay exact in binary32
-constexpr int kRenderThreads = 768;   // persistent blocks, one per SM; rays are taken in 8 x 4 pixel tiles
+constexpr int kRenderThreads = 640;   // persistent blocks, one per SM; rays are taken in 8 x 4 pixel tiles
 constexpr int kStats = 8;             // per-block counters of the render kernel
 
 // Geometry derived once from the descriptor; copied by value into kernels.

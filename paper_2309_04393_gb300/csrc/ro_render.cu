@@ -119,26 +119,39 @@ __device__ __forceinline__ void node_coords(const Geometry& g, int d, const floa
   for (int k = 0; k < 3; ++k) j[k] = (int)(x[k] * pow2f(-(g.leaf_log2[k] + g.D - d)));
 }
 
-// Trilinear sample of a level-l apron slot (R15): corners are read from the
-// owner's slot, lerps along x, then y, then z.
-template <int BPV, int EC>
-__device__ __forceinline__ float trilinear(const RenderArgs& a, uint32_t slot, int l, const float (&x)[3]) {
-  const Geometry& g = a.g;
+// Trilinear sample of a level-l apron slot (R15), in two parts: the
+// in-slot offset of the lower corner and the lerp weights depend only on the
+// position and the level (every channel's bricks share one grid), so they
+// are computed once per level and sample; the fetch reads one channel's
+// corners from its owner's slot and lerps along x, then y, then z.
+struct TriCoords {
+  int idx;     // element offset of the lower corner inside the apron slot
+  float f[3];  // lerp weights
+};
+
+template <int EC>
+__device__ __forceinline__ void tri_coords(const Geometry& g, int l, const float (&x)[3], TriCoords& tc) {
   const int E = EC ? EC : (int)g.edge;  // apron-slot edge, a compile-time constant for 32^3 bricks
   int li[3];
-  float f[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const float xl = x[k] * pow2f(-l);
     float u = xl - 0.5f;
     u = fminf(fmaxf(u, 0.0f), g.ldimf[l][k]);
     const int i0 = (int)u;
-    f[k] = u - (float)i0;
+    tc.f[k] = u - (float)i0;
     const int b = (int)(x[k] * pow2f(-(g.blog2 + l)));
     li[k] = i0 - (b * g.B - 1);
   }
+  tc.idx = (li[2] * E + li[1]) * E + li[0];
+}
+
+template <int BPV, int EC>
+__device__ __forceinline__ float tri_fetch(const RenderArgs& a, uint32_t slot, const TriCoords& tc) {
+  const Geometry& g = a.g;
+  const int E = EC ? EC : (int)g.edge;
   const uint8_t* base = a.cache + (size_t)slot * g.slot_pitch;
-  const int idx = (li[2] * E + li[1]) * E + li[0];
+  const int idx = tc.idx;
   float v[8];
   if constexpr (BPV == 1) {
     const uint8_t* p = base + idx;
@@ -161,13 +174,13 @@ __device__ __forceinline__ float trilinear(const RenderArgs& a, uint32_t slot, i
     v[6] = (float)__ldg(p + E * E + E);
     v[7] = (float)__ldg(p + E * E + E + 1);
   }
-  const float c00 = fmaf(f[0], v[1] - v[0], v[0]);
-  const float c10 = fmaf(f[0], v[3] - v[2], v[2]);
-  const float c01 = fmaf(f[0], v[5] - v[4], v[4]);
-  const float c11 = fmaf(f[0], v[7] - v[6], v[6]);
-  const float c0 = fmaf(f[1], c10 - c00, c00);
-  const float c1 = fmaf(f[1], c11 - c01, c01);
-  return fmaf(f[2], c1 - c0, c0);
+  const float c00 = fmaf(tc.f[0], v[1] - v[0], v[0]);
+  const float c10 = fmaf(tc.f[0], v[3] - v[2], v[2]);
+  const float c01 = fmaf(tc.f[0], v[5] - v[4], v[4]);
+  const float c11 = fmaf(tc.f[0], v[7] - v[6], v[6]);
+  const float c0 = fmaf(tc.f[1], c10 - c00, c00);
+  const float c1 = fmaf(tc.f[1], c11 - c01, c01);
+  return fmaf(tc.f[2], c1 - c0, c0);
 }
 
 // TF lookup (R16) and opacity correction for a step of 2^s (R12): returns
@@ -212,8 +225,10 @@ constexpr uint32_t kSelNone = 0xFFFFFFFFu;
 constexpr uint32_t kSelHomog = 30u;
 constexpr uint32_t kSelMask = (1u << 27) - 1u;
 
+// Per-thread counters of the current tile (a ray's counts stay below 2^28);
+// at every refill the warp adds them to its own 64-bit row in shared memory.
 struct Counters {
-  unsigned long long hit, eval, bs, homog, skip, skipped;
+  uint32_t hit, eval, bs, homog, skip, skipped;
 };
 
 template <int BPV, bool DBG>
@@ -254,6 +269,8 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
   __shared__ uint32_t s_pto[kMaxC * kMaxL + 1];
   for (int q = threadIdx.x; q < m; q += blockDim.x) s_tf[q] = make_float2(a.tf_lo[q], a.tf_scale[q]);
   for (int q = threadIdx.x; q <= m * k; q += blockDim.x) s_pto[q] = g.pt_off[q];
+  __shared__ unsigned long long s_red[kRenderThreads / 32][kStats];
+  for (int q = threadIdx.x; q < kRenderThreads / 32 * kStats; q += blockDim.x) (&s_red[0][0])[q] = 0;
   __syncthreads();
 
   const unsigned FULL = 0xFFFFFFFFu;
@@ -266,6 +283,17 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
   const unsigned lt_mask = (1u << lane) - 1u;
 
   Counters cnt = {0, 0, 0, 0, 0, 0};
+  auto flush = [&]() {
+    const uint32_t vals[6] = {cnt.hit, cnt.eval, cnt.bs, cnt.homog, cnt.skip, cnt.skipped};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      unsigned long long v = vals[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+      if (lane == 0) s_red[warp][q] += v;
+    }
+    cnt = {0, 0, 0, 0, 0, 0};
+  };
   Ray r;
   int px = 0, py = 0, i = 0, lod = 0;
   float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
@@ -278,6 +306,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
     // ------------------------------------------------------------- refill
     const unsigned busy = __ballot_sync(FULL, active);
     if (!busy && !done) {
+      flush();
       unsigned long long base = 0;
       if (lane == 0) base = atomicAdd(a.work, 32ull);
       base = __shfl_sync(FULL, base, 0);
@@ -527,7 +556,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
         h = fnv_word(h, (uint32_t)j);
       }
       ++cnt.skip;
-      cnt.skipped += (unsigned long long)(j - i);
+      cnt.skipped += (uint32_t)(j - i);
       i = j;
       continue;
     }
@@ -538,6 +567,8 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
     cnt.bs += nc.n_brick;
     cnt.homog += __popc(nc.act) - nc.n_brick;
     n_bs += nc.n_brick;
+    int tl = -1;
+    TriCoords tc;
     for (uint32_t mm = nc.act; mm; mm &= mm - 1u) {
       const int c = __ffs(mm) - 1;
       const uint32_t sel = my_sel[c * stride];
@@ -550,7 +581,11 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
           h = fnv_word(h, 0xFFu); h = fnv_word(h, 0xFFFFFFFFu);
         }
       } else {
-        val = trilinear<BPV, EC>(a, sel & kSelMask, (int)lb, x);
+        if ((int)lb != tl) {  // channels at one level share the corner offset and weights
+          tl = (int)lb;
+          tri_coords<EC>(g, tl, x, tc);
+        }
+        val = tri_fetch<BPV, EC>(a, sel & kSelMask, tc);
         if constexpr (DBG) {
           const int bsh = g.blog2 + (int)lb;
           const uint32_t bx = (uint32_t)(x[0] * pow2f(-bsh)), by = (uint32_t)(x[1] * pow2f(-bsh)),
@@ -585,15 +620,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
   }
 
   // per-block counters, reduced without atomics
-  __shared__ unsigned long long s_red[kRenderThreads / 32][kStats];
-  unsigned long long vals[kStats] = {cnt.hit, cnt.eval, cnt.bs, cnt.homog, cnt.skip, cnt.skipped, 0, 0};
-#pragma unroll
-  for (int q = 0; q < kStats; ++q) {
-    unsigned long long v = vals[q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-    if (lane == 0) s_red[warp][q] = v;
-  }
+  flush();
   __syncthreads();
   if (threadIdx.x < kStats) {
     unsigned long long v = 0;
