@@ -40,6 +40,7 @@ extern "C" {
 
 #define RO_MAX_CHANNELS 16
 #define RO_MAX_LEVELS 16
+#define RO_MAX_VIEWS 256
 #define RO_NONE 0xFFFFFFFFu
 
 typedef enum {
@@ -66,6 +67,8 @@ typedef enum {
  *  max_requests  request-list limit per frame (Sec. 4), >= 1
  *  max_upload    bricks per ro_upload_bricks call, >= 1
  *  max_meta      leaf metadata entries per ro_update_residency_octree chunk
+ *  max_batch_tiles  pixel tiles (32 pixels each) one ro_render_batch call may
+ *                cover, summed over its views; 0 = no batches
  * Bricks per axis at every level must be <= 256 (the 8-bit offsets of the
  * brick ID, Sec. 7). */
 typedef struct {
@@ -80,6 +83,7 @@ typedef struct {
   uint32_t max_requests;
   uint32_t max_upload;
   uint32_t max_meta;
+  uint32_t max_batch_tiles;
 } ro_desc;
 
 /* Byte sizes of the parts of the device arena (all 256-byte aligned inside
@@ -102,6 +106,7 @@ typedef struct {
   uint64_t n_nodes;      /* octree nodes, all depths */
   uint32_t depth;        /* octree depth D (leaves at depth D) */
   uint32_t channel_stride;/* u32 words per node: channels rounded up to a power of two */
+  uint64_t batch;        /* batch view table, tile schedule and tile costs (last in the arena) */
 } ro_buffer_sizes;
 
 typedef struct ro_ctx ro_ctx;
@@ -225,6 +230,56 @@ typedef struct {
  * 1 <= W, H <= 16384.  Enqueued on the stream; returns without waiting. */
 ro_status ro_render(ro_ctx* ctx, const ro_camera* camera, const ro_tf* tfs, const ro_render_params* params,
                     float* image, uint32_t W, uint32_t H);
+
+/* One view of a batch: its camera, parameters (as for ro_render, debug
+ * pointers included) and image (device pointer, W*H RGBA float32). */
+typedef struct {
+  ro_camera camera;
+  ro_render_params params;
+  float* image;
+  uint32_t W, H;
+} ro_view;
+
+/* How a batch's pixels are handed to the warps.
+ *  tile_w  tile width in pixels: 1, 2, 4, 8, 16 or 32; a tile is tile_w x
+ *          (32 / tile_w) pixels and one warp renders it
+ *  order   0: views in order, tiles row by row within a view;
+ *          1: tiles by descending cost recorded when the previous batch with
+ *          the same tiling ran (longest first, which shortens the tail of the
+ *          launch); tiles of equal cost in any order.
+ * The schedule changes the speed only: every schedule renders the same
+ * images, requests and counters. */
+typedef struct {
+  uint32_t tile_w;
+  uint32_t order;
+} ro_schedule;
+
+/* Renders n_views views in one persistent launch (the per-pixel rays of
+ * Sec. 6 are independent, so the views share one pool of warps and one
+ * tail).  Each view is rendered exactly as ro_render would render it, with
+ * the same transfer functions tfs (host array of m); requests, node
+ * requests and usage flags of all views accumulate for ro_read_requests, and
+ * ro_get_stats sums over the views.  The launch sequence (uploads of the view
+ * table and the LUTs, prefix sums, schedule, ray casting) is captured once as
+ * a CUDA graph per batch layout (view sizes, schedule, debug on/off) and
+ * replayed while the layout stays the same; cameras, parameters, images and
+ * TFs may change between calls.  The host waits (against the deadline) until
+ * the previous batch's uploads have been read before refilling them.
+ *  schedule  NULL = {8, 0}
+ * 1 <= n_views <= RO_MAX_VIEWS; the views' tiles (ceil(W / tile_w) *
+ * ceil(H / (32 / tile_w)) each) must not exceed max_batch_tiles in total
+ * (RO_ERR_CAPACITY).  Enqueued on the stream; returns without waiting. */
+ro_status ro_render_batch(ro_ctx* ctx, uint32_t n_views, const ro_view* views, const ro_tf* tfs,
+                          const ro_schedule* schedule);
+
+/* Picks the fastest schedule for this batch: every tile width of 4, 8, 16
+ * and 32 pixels with both orders is rendered (once to warm up and record
+ * costs, then timed twice with CUDA events; the faster run counts).  best
+ * receives the winner and best_ms its time (may be NULL).  The renders are
+ * real renders of the batch: they set its requests and usage flags.  Waits
+ * for the stream. */
+ro_status ro_autotune_batch(ro_ctx* ctx, uint32_t n_views, const ro_view* views, const ro_tf* tfs,
+                            ro_schedule* best, float* best_ms);
 
 /* Compacts the flags of the frames rendered since the previous call
  * (Sec. 4: a global request limit keeps the copy small): brick requests as

@@ -32,12 +32,15 @@ int ilog2(uint32_t v) {
   return r;
 }
 
+constexpr int kParts = 12;
+
 struct Layout {
-  uint64_t off[11];
+  uint64_t off[kParts];
   ro_buffer_sizes sz;
   uint64_t req_pad, node_req_pad, used_pad;
   uint64_t sc_counts, sc_totals, sc_items, sc_meta, sc_ins_index, sc_ins_slot, sc_ev_index, sc_stats, sc_err, sc_work;
   uint64_t fr_lut, fr_prefix, li_req, li_node;
+  uint64_t ba_views, ba_tf, ba_order, ba_cost;   // batch region: view table, TF ranges, schedule, tile costs
   uint32_t max_tiles;
 };
 
@@ -160,10 +163,15 @@ void make_layout(const ro_desc* d, const Geometry& g, Layout* L) {
   L->sc_err = o; o = align_up(o + 64, kAlign);
   L->sc_work = o; o = align_up(o + 64, kAlign);
   s.scratch = o;
-  const uint64_t parts[11] = {s.cache, s.page_table, s.octree, s.req_flags, s.node_req_flags, s.used_flags,
-                              s.last_used, s.staging, s.frame, s.lists, s.scratch};
+  L->ba_views = 0;
+  L->ba_tf = (uint64_t)ro::kMaxViews * sizeof(ro::ViewArgs);
+  L->ba_order = align_up(L->ba_tf + (uint64_t)ro::kMaxC * 8, kAlign);
+  L->ba_cost = align_up(L->ba_order + (uint64_t)d->max_batch_tiles * 4, kAlign);
+  s.batch = d->max_batch_tiles ? align_up(L->ba_cost + (uint64_t)d->max_batch_tiles * 4, kAlign) : 0;
+  const uint64_t parts[kParts] = {s.cache, s.page_table, s.octree, s.req_flags, s.node_req_flags, s.used_flags,
+                                  s.last_used, s.staging, s.frame, s.lists, s.scratch, s.batch};
   uint64_t tot = 0;
-  for (int i = 0; i < 11; ++i) {
+  for (int i = 0; i < kParts; ++i) {
     L->off[i] = tot;
     tot = align_up(tot + parts[i], kAlign);
   }
@@ -188,6 +196,18 @@ struct ro_ctx {
   std::vector<uint32_t> free_slots;      // descending, pop_back gives the lowest
   std::vector<uint32_t> pending;         // page-table indices changed since the last update
   std::vector<float4> host_lut;
+  // batches: device view table / TF ranges / schedule / tile costs in the
+  // arena; pinned upload area [views | TF ranges | LUTs]; the captured graph
+  ro::ViewArgs* b_views = nullptr;
+  float2* b_tf = nullptr;
+  uint32_t *b_order = nullptr, *b_cost = nullptr;
+  uint8_t* b_pinned = nullptr;
+  cudaEvent_t b_uploaded = nullptr;   // recorded by the graph once its uploads are done
+  cudaStream_t b_capture = nullptr;   // private stream the graph is captured on
+  cudaGraph_t b_graph = nullptr;
+  cudaGraphExec_t b_exec = nullptr;
+  std::vector<uint32_t> b_key;        // layout the graph was captured for
+  uint32_t b_blocks = 0;
   uint32_t frame = 0;
   uint32_t timeout_ms = 30000;
   uint32_t last_blocks = 0;
@@ -335,6 +355,13 @@ ro_status ro_create(const ro_desc* desc, void* arena_device, uint64_t arena_byte
   c->node_out = reinterpret_cast<uint32_t*>(c->arena + o[9] + c->L.li_node);
   c->scratch = c->arena + o[10];
   c->err = reinterpret_cast<uint32_t*>(c->scratch + c->L.sc_err);
+  if (desc->max_batch_tiles) {
+    uint8_t* b = c->arena + o[11];
+    c->b_views = reinterpret_cast<ro::ViewArgs*>(b + c->L.ba_views);
+    c->b_tf = reinterpret_cast<float2*>(b + c->L.ba_tf);
+    c->b_order = reinterpret_cast<uint32_t*>(b + c->L.ba_order);
+    c->b_cost = reinterpret_cast<uint32_t*>(b + c->L.ba_cost);
+  }
   c->slot_of_brick.assign(c->g.n_bricks, RO_NONE);
   c->brick_of_slot.assign(desc->cache_slots, RO_NONE);
   c->free_slots.resize(desc->cache_slots);
@@ -355,6 +382,7 @@ ro_status ro_create(const ro_desc* desc, void* arena_device, uint64_t arena_byte
   if (e == cudaSuccess) e = cudaMemsetAsync(c->used, 0, z.used_flags, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->last_used, 0, z.last_used, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->scratch, 0, z.scratch, st);
+  if (e == cudaSuccess && z.batch) e = cudaMemsetAsync(c->arena + o[11], 0, z.batch, st);
   if (e != cudaSuccess) {
     g_create_error = std::string("initialisation: ") + cudaGetErrorString(e);
     cudaEventDestroy(c->ev);
@@ -370,6 +398,11 @@ ro_status ro_destroy(ro_ctx* c) {
   ro_status s = RO_OK;
   if (c->latched == RO_OK) s = wait_stream(c, "ro_destroy");
   if (c->ev) cudaEventDestroy(c->ev);
+  if (c->b_exec) cudaGraphExecDestroy(c->b_exec);
+  if (c->b_graph) cudaGraphDestroy(c->b_graph);
+  if (c->b_uploaded) cudaEventDestroy(c->b_uploaded);
+  if (c->b_capture) cudaStreamDestroy(c->b_capture);
+  if (c->b_pinned) cudaFreeHost(c->b_pinned);
   delete c;
   return s == RO_ERR_INTERNAL ? RO_OK : s;
 }
@@ -605,46 +638,61 @@ ro_status ro_update_residency_octree(ro_ctx* c, uint32_t n_meta, const ro_leaf_m
   return RO_OK;
 }
 
-ro_status ro_render(ro_ctx* c, const ro_camera* cam, const ro_tf* tfs, const ro_render_params* p, float* image,
-                    uint32_t W, uint32_t H) {
-  if (!c) return RO_ERR_INVALID_ARG;
-  if (c->latched != RO_OK) return c->latched;
-  if (!cam || !tfs || !p || !image) return set_err(c, RO_ERR_INVALID_ARG, "ro_render: null pointer");
-  if (W < 1 || H < 1 || W > 16384 || H > 16384) return set_err(c, RO_ERR_INVALID_ARG, "ro_render: W and H must be in [1, 16384]");
-  const uint64_t blocks = (uint64_t)((W + 15) / 16) * ((H + 15) / 16);
-  if (blocks > kMaxStatBlocks) return set_err(c, RO_ERR_CAPACITY, "ro_render: image larger than 65536 blocks of 16x16");
+namespace {
+
+// Checks of one view's parameters shared by ro_render and ro_render_batch.
+ro_status check_view(ro_ctx* c, const ro_camera* cam, const ro_render_params* p, const float* image, uint32_t W,
+                     uint32_t H, const char* where) {
+  const std::string w(where);
+  if (!cam || !p || !image) return set_err(c, RO_ERR_INVALID_ARG, w + ": null pointer");
+  if (W < 1 || H < 1 || W > 16384 || H > 16384) return set_err(c, RO_ERR_INVALID_ARG, w + ": W and H must be in [1, 16384]");
   const Geometry& g = c->g;
-  if (!(p->dt > 0.0f) || !std::isfinite(p->dt)) return set_err(c, RO_ERR_INVALID_ARG, "ro_render: dt must be positive");
-  if (p->start_depth > (uint32_t)g.D) return set_err(c, RO_ERR_INVALID_ARG, "ro_render: start_depth beyond the octree depth");
+  if (!(p->dt > 0.0f) || !std::isfinite(p->dt)) return set_err(c, RO_ERR_INVALID_ARG, w + ": dt must be positive");
+  if (p->start_depth > (uint32_t)g.D) return set_err(c, RO_ERR_INVALID_ARG, w + ": start_depth beyond the octree depth");
   for (int l = 2; l < g.k; ++l)
-    if (!(p->lod_t[l] >= p->lod_t[l - 1])) return set_err(c, RO_ERR_INVALID_ARG, "ro_render: lod_t must be non-decreasing");
-  for (int ch = 0; ch < g.m; ++ch) {
+    if (!(p->lod_t[l] >= p->lod_t[l - 1])) return set_err(c, RO_ERR_INVALID_ARG, w + ": lod_t must be non-decreasing");
+  for (int ch = 0; ch < g.m; ++ch)
     if (p->lmin[ch] > p->lmax[ch] || p->lmax[ch] >= (uint32_t)g.k)
-      return set_err(c, RO_ERR_INVALID_ARG, "ro_render: need lmin <= lmax < levels");
-    if (!tfs[ch].lut) return set_err(c, RO_ERR_INVALID_ARG, "ro_render: null LUT");
-  }
-  ro::RenderArgs a{};
-  a.g = g;
+      return set_err(c, RO_ERR_INVALID_ARG, w + ": need lmin <= lmax < levels");
+  return RO_OK;
+}
+
+ro_status check_tfs(ro_ctx* c, const ro_tf* tfs, const char* where) {
+  if (!tfs) return set_err(c, RO_ERR_INVALID_ARG, std::string(where) + ": null pointer");
+  for (int ch = 0; ch < c->g.m; ++ch)
+    if (!tfs[ch].lut) return set_err(c, RO_ERR_INVALID_ARG, std::string(where) + ": null LUT");
+  return RO_OK;
+}
+
+bool has_debug(const ro_render_params* p) {
+  return p->debug_hash || p->debug_n_eval || p->debug_i_end || p->debug_n_bs;
+}
+
+// The per-view part of a launch: camera, per-level tables (R7, R8) and
+// outputs.  Tiles are 2^twl x 2^(5 - twl) pixels.
+void fill_view(const ro_ctx* c, const ro_camera* cam, const ro_render_params* p, float* image, uint32_t W, uint32_t H,
+               int twl, uint32_t tile_base, ro::ViewArgs* v) {
+  const Geometry& g = c->g;
+  std::memset(v, 0, sizeof(*v));
   for (int q = 0; q < 3; ++q) {
-    a.eye[q] = cam->eye[q];
-    a.fwd[q] = cam->forward[q];
-    a.right[q] = cam->right[q];
-    a.up[q] = cam->up[q];
+    v->eye[q] = cam->eye[q];
+    v->fwd[q] = cam->forward[q];
+    v->right[q] = cam->right[q];
+    v->up[q] = cam->up[q];
   }
-  a.persp = cam->perspective ? 1 : 0;
-  a.tan_x = cam->tan_x;
-  a.tan_y = cam->tan_y;
-  a.pixel = cam->pixel;
-  a.W = (int)W;
-  a.H = (int)H;
-  a.dt = p->dt;
-  for (int l = 0; l < ro::kMaxL; ++l) a.lod_t[l] = p->lod_t[l];
-  for (int ch = 0; ch < ro::kMaxC; ++ch) {
-    a.lmin[ch] = ch < g.m ? (int)p->lmin[ch] : 0;
-    a.lmax[ch] = ch < g.m ? (int)p->lmax[ch] : 0;
-    a.tf_lo[ch] = ch < g.m ? tfs[ch].lo : 0.0f;
-    a.tf_scale[ch] = ch < g.m ? tfs[ch].scale : 0.0f;
-  }
+  v->persp = cam->perspective ? 1 : 0;
+  v->tan_x = cam->tan_x;
+  v->tan_y = cam->tan_y;
+  v->pixel = cam->pixel;
+  v->W = (int)W;
+  v->H = (int)H;
+  v->dt = p->dt;
+  v->ert = p->ert;
+  v->start_depth = (int)p->start_depth;
+  v->skip = p->skip ? 1 : 0;
+  v->tiles_x = (W + (1u << twl) - 1) >> twl;
+  v->tile_base = tile_base;
+  for (int l = 0; l < ro::kMaxL; ++l) v->lod_t[l] = p->lod_t[l];
   // traversal depth per level (R8): deepest depth whose nodes are at least
   // one step long along every axis, physically
   for (int l = 0; l < ro::kMaxL; ++l) {
@@ -655,7 +703,7 @@ ro_status ro_render(ro_ctx* c, const ro_camera* cam, const ro_tf* tfs, const ro_
       for (int q = 0; q < 3; ++q) mn = std::min(mn, std::ldexp(1.0, g.leaf_log2[q] + g.D - d) * (double)g.spacing[q]);
       if (mn >= step) best = d;
     }
-    a.sdepth[l] = best;
+    v->sdepth[l] = best;
   }
   // desired levels of every channel for each value of lod (R7): the clamp
   // of lod to the channel's [lmin, lmax]
@@ -668,30 +716,66 @@ ro_status ro_render(ro_ctx* c, const ro_camera* cam, const ro_tf* tfs, const ro_
       ldp |= (uint64_t)l << (4 * ch);
       lminu = l < lminu ? l : lminu;
     }
-    a.ldp_tab[lod] = ldp;
-    a.lminu_tab[lod] = lminu;
+    v->ldp_tab[lod] = ldp;
+    v->lminu_tab[lod] = lminu;
   }
-  a.start_depth = (int)p->start_depth;
-  a.skip = p->skip ? 1 : 0;
-  a.ert = p->ert;
-  a.cache = c->cache;
-  a.pt = c->pt;
-  a.octree = c->octree;
-  a.req = c->req;
-  a.node_req = c->node_req;
-  a.used = c->used;
-  a.lut = c->lut;
-  a.prefix = c->prefix;
-  a.image = reinterpret_cast<float4*>(image);
-  a.dbg_hash = p->debug_hash;
-  a.dbg_n_eval = p->debug_n_eval;
-  a.dbg_i_end = p->debug_i_end;
-  a.dbg_n_bs = p->debug_n_bs;
-  a.block_stats = reinterpret_cast<unsigned long long*>(c->scratch + c->L.sc_stats);
-  a.err = c->err;
-  a.work = reinterpret_cast<unsigned long long*>(c->scratch + c->L.sc_work);
-  a.tiles_x = (W + 7) / 8;
-  a.n_rays = (uint64_t)a.tiles_x * ((H + 3) / 4) * 32;
+  v->image = reinterpret_cast<float4*>(image);
+  v->dbg_hash = p->debug_hash;
+  v->dbg_n_eval = p->debug_n_eval;
+  v->dbg_i_end = p->debug_i_end;
+  v->dbg_n_bs = p->debug_n_bs;
+}
+
+// The context-wide part of a launch.
+void fill_common(ro_ctx* c, const ro_tf* tfs, ro::RenderArgs* a) {
+  const Geometry& g = c->g;
+  a->g = g;
+  for (int ch = 0; ch < ro::kMaxC; ++ch) {
+    a->tf_lo[ch] = ch < g.m ? tfs[ch].lo : 0.0f;
+    a->tf_scale[ch] = ch < g.m ? tfs[ch].scale : 0.0f;
+  }
+  a->cache = c->cache;
+  a->pt = c->pt;
+  a->octree = c->octree;
+  a->req = c->req;
+  a->node_req = c->node_req;
+  a->used = c->used;
+  a->lut = c->lut;
+  a->prefix = c->prefix;
+  a->block_stats = reinterpret_cast<unsigned long long*>(c->scratch + c->L.sc_stats);
+  a->err = c->err;
+  a->work = reinterpret_cast<unsigned long long*>(c->scratch + c->L.sc_work);
+}
+
+// Waits for an event against the context's deadline.
+ro_status wait_event(ro_ctx* c, cudaEvent_t ev, const char* where) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return RO_OK;
+    if (e != cudaErrorNotReady) return cuda_check(c, e, where);
+    const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+    if (ms > (long long)c->timeout_ms) return set_err(c, RO_ERR_TIMEOUT, std::string(where) + ": stream wait timed out");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+}  // namespace
+
+ro_status ro_render(ro_ctx* c, const ro_camera* cam, const ro_tf* tfs, const ro_render_params* p, float* image,
+                    uint32_t W, uint32_t H) {
+  if (!c) return RO_ERR_INVALID_ARG;
+  if (c->latched != RO_OK) return c->latched;
+  RO_TRY(check_view(c, cam, p, image, W, H, "ro_render"));
+  RO_TRY(check_tfs(c, tfs, "ro_render"));
+  const uint64_t blocks = (uint64_t)((W + 15) / 16) * ((H + 15) / 16);
+  if (blocks > kMaxStatBlocks) return set_err(c, RO_ERR_CAPACITY, "ro_render: image larger than 65536 blocks of 16x16");
+  const Geometry& g = c->g;
+  ro::RenderArgs a{};
+  fill_common(c, tfs, &a);
+  fill_view(c, cam, p, image, W, H, 3, 0, &a.v);
+  a.tile_wlog2 = 3;
+  a.n_rays = (uint64_t)a.v.tiles_x * ((H + 3) / 4) * 32;
   for (int ch = 0; ch < g.m; ++ch)
     std::memcpy(&c->host_lut[(size_t)ch * 256], tfs[ch].lut, 256 * sizeof(float4));
   cudaStream_t st = c->stream;
@@ -707,12 +791,155 @@ ro_status ro_render(ro_ctx* c, const ro_camera* cam, const ro_tf* tfs, const ro_
   pa.lut = c->lut;
   pa.prefix = c->prefix;
   RO_TRY(cuda_check(c, ro::launch_prefix(pa, st), "ro_render: prefix"));
-  const bool debug = p->debug_hash || p->debug_n_eval || p->debug_i_end || p->debug_n_bs;
   RO_TRY(cuda_check(c, cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), st), "ro_render: work counter"));
   int launched = 0;
-  RO_TRY(cuda_check(c, ro::launch_render(a, debug, st, &launched), "ro_render: render"));
+  RO_TRY(cuda_check(c, ro::launch_render(a, has_debug(p), st, &launched), "ro_render: render"));
   c->last_blocks = (uint32_t)launched;
   ++c->frame;
+  return RO_OK;
+}
+
+ro_status ro_render_batch(ro_ctx* c, uint32_t n_views, const ro_view* views, const ro_tf* tfs,
+                          const ro_schedule* schedule) {
+  if (!c) return RO_ERR_INVALID_ARG;
+  if (c->latched != RO_OK) return c->latched;
+  const char* where = "ro_render_batch";
+  if (!views || n_views < 1 || n_views > (uint32_t)ro::kMaxViews)
+    return set_err(c, RO_ERR_INVALID_ARG, "ro_render_batch: need 1 <= n_views <= RO_MAX_VIEWS and a view array");
+  RO_TRY(check_tfs(c, tfs, where));
+  const ro_schedule sched = schedule ? *schedule : ro_schedule{8, 0};
+  if (!is_pow2(sched.tile_w) || sched.tile_w > 32 || sched.order > 1)
+    return set_err(c, RO_ERR_INVALID_ARG, "ro_render_batch: tile_w must be 1, 2, 4, 8, 16 or 32 and order 0 or 1");
+  if (!c->desc.max_batch_tiles) return set_err(c, RO_ERR_CAPACITY, "ro_render_batch: context created with max_batch_tiles = 0");
+  const int twl = ilog2(sched.tile_w), thl = 5 - twl;
+  bool debug = false;
+  uint64_t tiles = 0;
+  std::vector<uint32_t> key = {n_views, (uint32_t)twl, sched.order};
+  for (uint32_t v = 0; v < n_views; ++v) {
+    const ro_view& w = views[v];
+    RO_TRY(check_view(c, &w.camera, &w.params, w.image, w.W, w.H, where));
+    debug = debug || has_debug(&w.params);
+    tiles += (uint64_t)((w.W + (1u << twl) - 1) >> twl) * ((w.H + (1u << thl) - 1) >> thl);
+    key.push_back(w.W);
+    key.push_back(w.H);
+  }
+  key.push_back(debug ? 1u : 0u);
+  if (tiles > c->desc.max_batch_tiles) return set_err(c, RO_ERR_CAPACITY, "ro_render_batch: more tiles than max_batch_tiles");
+  const Geometry& g = c->g;
+  const size_t views_bytes = (size_t)ro::kMaxViews * sizeof(ro::ViewArgs);
+  const size_t up_bytes = (size_t)c->L.ba_tf + (size_t)ro::kMaxC * 8;  // view table and TF ranges, one copy
+  const size_t lut_bytes = (size_t)ro::kMaxC * 256 * sizeof(float4);
+  if (!c->b_pinned) {
+    RO_TRY(cuda_check(c, cudaMallocHost(reinterpret_cast<void**>(&c->b_pinned), up_bytes + lut_bytes), "ro_render_batch: pinned upload area"));
+    std::memset(c->b_pinned, 0, up_bytes + lut_bytes);
+    RO_TRY(cuda_check(c, cudaEventCreateWithFlags(&c->b_uploaded, cudaEventDisableTiming), "ro_render_batch: event"));
+    RO_TRY(cuda_check(c, cudaStreamCreateWithFlags(&c->b_capture, cudaStreamNonBlocking), "ro_render_batch: capture stream"));
+  }
+  // the previous batch must have read the upload area before it is refilled
+  RO_TRY(wait_event(c, c->b_uploaded, "ro_render_batch: previous uploads"));
+  ro::ViewArgs* hv = reinterpret_cast<ro::ViewArgs*>(c->b_pinned);
+  uint32_t base = 0;
+  for (uint32_t v = 0; v < n_views; ++v) {
+    const ro_view& w = views[v];
+    fill_view(c, &w.camera, &w.params, w.image, w.W, w.H, twl, base, &hv[v]);
+    base += hv[v].tiles_x * ((w.H + (1u << thl) - 1) >> thl);
+  }
+  float2* htf = reinterpret_cast<float2*>(c->b_pinned + c->L.ba_tf);
+  for (int ch = 0; ch < ro::kMaxC; ++ch)
+    htf[ch] = ch < g.m ? make_float2(tfs[ch].lo, tfs[ch].scale) : make_float2(0.0f, 0.0f);
+  float4* hlut = reinterpret_cast<float4*>(c->b_pinned + up_bytes);
+  for (int ch = 0; ch < g.m; ++ch) std::memcpy(hlut + (size_t)ch * 256, tfs[ch].lut, 256 * sizeof(float4));
+  (void)views_bytes;
+
+  if (!c->b_exec || key != c->b_key) {
+    if (c->b_exec) cudaGraphExecDestroy(c->b_exec);
+    if (c->b_graph) cudaGraphDestroy(c->b_graph);
+    c->b_exec = nullptr;
+    c->b_graph = nullptr;
+    c->b_key.clear();
+    ro::RenderArgs a{};
+    fill_common(c, tfs, &a);
+    a.tile_wlog2 = twl;
+    a.n_rays = tiles * 32;
+    a.views = c->b_views;
+    a.n_views = (int)n_views;
+    a.order = sched.order == 1 ? c->b_order : nullptr;
+    a.tile_cost = c->b_cost;
+    a.tf_dev = c->b_tf;
+    ro::PrefixArgs pa{};
+    pa.m = g.m;
+    pa.bpv = g.bpv;
+    pa.tf_dev = c->b_tf;
+    pa.lut = c->lut;
+    pa.prefix = c->prefix;
+    cudaStream_t cs = c->b_capture;
+    RO_TRY(cuda_check(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed), "ro_render_batch: begin capture"));
+    cudaError_t e = cudaMemcpyAsync(c->b_views, c->b_pinned, up_bytes, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->lut, hlut, (size_t)g.m * 256 * sizeof(float4), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->b_uploaded, cs, cudaEventRecordExternal);  // a node of the graph
+    if (e == cudaSuccess) e = ro::launch_prefix(pa, cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), cs);
+    if (e == cudaSuccess && sched.order == 1) e = ro::launch_cost_order(c->b_cost, (uint32_t)tiles, c->b_order, cs);
+    int launched = 0;
+    if (e == cudaSuccess) e = ro::launch_render_batch(a, debug, cs, &launched);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->b_exec, graph, 0);
+    if (e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      c->b_exec = nullptr;
+      return cuda_check(c, e, "ro_render_batch: capture");
+    }
+    c->b_graph = graph;
+    c->b_key = key;
+    c->b_blocks = (uint32_t)launched;
+  }
+  RO_TRY(cuda_check(c, cudaGraphLaunch(c->b_exec, c->stream), "ro_render_batch: graph launch"));
+  c->last_blocks = c->b_blocks;
+  ++c->frame;
+  return RO_OK;
+}
+
+ro_status ro_autotune_batch(ro_ctx* c, uint32_t n_views, const ro_view* views, const ro_tf* tfs, ro_schedule* best,
+                            float* best_ms) {
+  if (!c) return RO_ERR_INVALID_ARG;
+  if (c->latched != RO_OK) return c->latched;
+  if (!best) return set_err(c, RO_ERR_INVALID_ARG, "ro_autotune_batch: null result");
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  RO_TRY(cuda_check(c, cudaEventCreate(&t0), "ro_autotune_batch: event"));
+  if (cudaEventCreate(&t1) != cudaSuccess) {
+    cudaEventDestroy(t0);
+    return cuda_check(c, cudaErrorMemoryAllocation, "ro_autotune_batch: event");
+  }
+  ro_status s = RO_OK;
+  float best_t = INFINITY;
+  ro_schedule win{8, 0};
+  const uint32_t widths[4] = {8, 4, 16, 32};
+  for (uint32_t wi = 0; wi < 4 && s == RO_OK; ++wi) {
+    for (uint32_t order = 0; order < 2 && s == RO_OK; ++order) {
+      const ro_schedule sc{widths[wi], order};
+      s = ro_render_batch(c, n_views, views, tfs, &sc);  // warm-up; records this tiling's costs
+      for (int rep = 0; rep < 2 && s == RO_OK; ++rep) {
+        s = cuda_check(c, cudaEventRecord(t0, c->stream), "ro_autotune_batch: event");
+        if (s == RO_OK) s = ro_render_batch(c, n_views, views, tfs, &sc);
+        if (s == RO_OK) s = cuda_check(c, cudaEventRecord(t1, c->stream), "ro_autotune_batch: event");
+        if (s == RO_OK) s = wait_event(c, t1, "ro_autotune_batch");
+        float ms = 0.0f;
+        if (s == RO_OK) s = cuda_check(c, cudaEventElapsedTime(&ms, t0, t1), "ro_autotune_batch: timing");
+        if (s == RO_OK && ms < best_t) {
+          best_t = ms;
+          win = sc;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (s != RO_OK) return s;
+  RO_TRY(wait_stream(c, "ro_autotune_batch"));
+  *best = win;
+  if (best_ms) *best_ms = best_t;
   return RO_OK;
 }
 

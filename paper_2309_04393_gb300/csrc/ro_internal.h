@@ -35,19 +35,36 @@ struct Geometry {
   uint32_t edge;              // B + 2 (apron slot edge)
 };
 
-// Everything one render launch needs; passed as a __grid_constant__ parameter.
-struct RenderArgs {
-  Geometry g;
+// One view of a render launch: camera, image and per-view parameters.  A
+// single-view launch carries it in its __grid_constant__ parameter; a batch
+// keeps one per view in device memory and each warp copies the view of its
+// current tile into shared memory.  Size a multiple of 16 bytes.
+struct __align__(16) ViewArgs {
   float eye[3], fwd[3], right[3], up[3];
   int persp;
   float tan_x, tan_y, pixel;
   int W, H;
   float dt;
-  float lod_t[kMaxL];
-  int lmin[kMaxC], lmax[kMaxC];
-  int sdepth[kMaxL];
-  int start_depth, skip;
   float ert;
+  int start_depth, skip;
+  uint32_t tiles_x;                 // tiles per image row
+  uint32_t tile_base;               // first tile of this view in the launch's tile space
+  float lod_t[kMaxL];
+  int sdepth[kMaxL];
+  int lminu_tab[kMaxL];             // finest desired level per lod value
+  uint64_t ldp_tab[kMaxL];          // desired levels of all channels (4 bits each) per lod value
+  float4* image;
+  uint32_t *dbg_hash, *dbg_n_eval, *dbg_i_end, *dbg_n_bs;
+  uint64_t pad;
+};
+static_assert(sizeof(ViewArgs) % 16 == 0, "ViewArgs is copied in 16-byte pieces");
+
+constexpr int kMaxViews = 256;      // views per batch (RO_MAX_VIEWS)
+
+// Everything one render launch needs; passed as a __grid_constant__ parameter.
+struct RenderArgs {
+  Geometry g;
+  ViewArgs v;                       // the view of a single-view launch
   float tf_lo[kMaxC], tf_scale[kMaxC];
   const uint8_t* cache;
   const uint32_t* pt;
@@ -57,20 +74,23 @@ struct RenderArgs {
   uint8_t* used;
   const float4* lut;          // m * 256 knots
   const uint16_t* prefix;     // m * 257 bucket-occupancy prefix sums
-  float4* image;
-  uint32_t *dbg_hash, *dbg_n_eval, *dbg_i_end, *dbg_n_bs;
   unsigned long long* block_stats;  // kStats per block
   uint32_t* err;
   unsigned long long* work;         // ray counter of the persistent launch (zeroed before it)
-  uint32_t tiles_x;                 // 8 x 4 pixel tiles per image row
-  uint64_t n_rays;                  // tiles_x * tiles_y * 32
-  uint64_t ldp_tab[kMaxL];          // desired levels of all channels (4 bits each) per lod value
-  int lminu_tab[kMaxL];             // finest desired level per lod value
+  uint64_t n_rays;                  // tiles * 32
+  int tile_wlog2;                   // tile width log2 (tile = 2^w x 2^(5-w) pixels)
+  // batch launches
+  const ViewArgs* views;            // n_views views, tile_base ascending
+  int n_views;
+  const uint32_t* order;            // schedule position -> tile, or null for the identity
+  uint32_t* tile_cost;              // per tile: loop iterations its warp took (null = not recorded)
+  const float2* tf_dev;             // batch: (lo, scale) per channel in device memory
 };
 
 struct PrefixArgs {
   int m, bpv;
   float tf_lo[kMaxC], tf_scale[kMaxC];
+  const float2* tf_dev;       // if set, (lo, scale) per channel are read from here instead
   const float4* lut;
   uint16_t* prefix;
 };
@@ -144,6 +164,10 @@ enum : uint32_t { kErrNone = 0, kErrNodeIndex = 1, kErrPageIndex = 2, kErrSlot =
 // Launchers (each returns the launch status).
 cudaError_t launch_prefix(const PrefixArgs& a, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out);
+cudaError_t launch_render_batch(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out);
+// Tile order by descending recorded cost (counting sort over log-scale
+// buckets; ties in any order).
+cudaError_t launch_cost_order(const uint32_t* cost, uint32_t n_tiles, uint32_t* order, cudaStream_t s);
 cudaError_t launch_fill_words(uint32_t* words, uint64_t n, uint32_t value, cudaStream_t s);
 cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s);
 cudaError_t launch_write_meta(const UpdateArgs& a, cudaStream_t s);

@@ -1,633 +1,9 @@
-// Mixed-resolution multi-volume ray caster through the residency octree
-// (Sec. 6.1, Algorithm 1 and the multi-channel walk; Sec. 6.2; Sec. 7).
-//
-// One thread per pixel, 16 x 16 pixels per block (8 x 4 per warp).  The
-// channels' transfer-function LUTs and bucket-occupancy prefix sums live in
-// shared memory; node words, page-table entries and brick-cache voxels are
-// read through the read-only path.  Requests and usage are emitted with plain
-// byte stores of 1 (idempotent: no atomics).  Every decision is taken in
-// binary32 with the operation order of the design contract (built with
-// --fmad=false: every fused multiply-add below is an explicit fmaf).
-#include "ro_internal.h"
+// Single-view launches of the ray caster and the bucket-occupancy prefix
+// sums of the transfer functions.
+#include "ro_render_kernel.cuh"
 
 namespace ro {
 namespace {
-
-enum : int { kEmpty = 0, kHomog = 1, kUnmapped = 2, kBrick = 3, kInvalid = 4 };
-
-__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
-
-__device__ __forceinline__ uint32_t fnv_word(uint32_t h, uint32_t w) {
-#pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    h ^= (w >> (8 * b)) & 0xFFu;
-    h *= 16777619u;
-  }
-  return h;
-}
-
-// Per-channel state at one node (Algorithm 1 order: empty, homogeneous,
-// partially mapped at a usable level).
-template <int BPV>
-__device__ __forceinline__ int classify(uint32_t w, const uint16_t* pre, int ld, int k) {
-  const uint32_t mn = (w >> 16) & 0xFFu, mx = w >> 24;
-  if (mn > mx) return kInvalid;
-  if (pre[mx + 1] == pre[mn]) return kEmpty;
-  if (BPV == 1 && mn == mx) return kHomog;
-  const uint32_t usable = (w & 0xFFFFu) & (~0u << ld) & ((1u << k) - 1u);
-  return usable ? kBrick : kUnmapped;
-}
-
-__device__ __forceinline__ bool terminal(int s) { return s == kEmpty || s == kHomog || s == kUnmapped; }
-
-// CPL consecutive node words (one vector load; CPL = 4, 2 or 1).
-template <int CPL>
-__device__ __forceinline__ void load_cpl(const uint32_t* p, uint32_t (&w)[CPL]) {
-  if constexpr (CPL == 4) {
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
-    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
-  } else if constexpr (CPL == 2) {
-    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
-    w[0] = v.x; w[1] = v.y;
-  } else {
-    w[0] = __ldg(p);
-  }
-}
-
-struct Ray {
-  float o[3], d[3];
-  float t0, t1;
-  bool hit;
-};
-
-// Pixel-centre ray, voxel-space origin/direction and slab interval (R17).
-__device__ Ray make_ray(const RenderArgs& a, int px, int py) {
-  Ray r;
-  float o[3], d[3];
-  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
-  if (a.persp) {
-    const float u = __fdiv_rn(fx, (float)a.W), w = __fdiv_rn(fy, (float)a.H);
-    const float sa = (2.0f * u - 1.0f) * a.tan_x;
-    const float sb = (1.0f - 2.0f * w) * a.tan_y;
-    float dd[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) dd[k] = fmaf(sb, a.up[k], fmaf(sa, a.right[k], a.fwd[k]));
-    const float n2 = fmaf(dd[2], dd[2], fmaf(dd[1], dd[1], dd[0] * dd[0]));
-    const float len = __fsqrt_rn(n2);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      o[k] = a.eye[k];
-      d[k] = __fdiv_rn(dd[k], len);
-    }
-  } else {
-    const float sa = (fx - 0.5f * (float)a.W) * a.pixel;
-    const float sb = (0.5f * (float)a.H - fy) * a.pixel;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      o[k] = fmaf(sb, a.up[k], fmaf(sa, a.right[k], a.eye[k]));
-      d[k] = a.fwd[k];
-    }
-  }
-  float tmin = -INFINITY, tmax = INFINITY;
-  r.hit = true;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    r.o[k] = __fdiv_rn(o[k], a.g.spacing[k]);
-    r.d[k] = __fdiv_rn(d[k], a.g.spacing[k]);
-    if (r.d[k] != 0.0f) {
-      const float ta = __fdiv_rn(0.0f - r.o[k], r.d[k]);
-      const float tb = __fdiv_rn((float)a.g.dims0[k] - r.o[k], r.d[k]);
-      tmin = fmaxf(tmin, fminf(ta, tb));
-      tmax = fminf(tmax, fmaxf(ta, tb));
-    } else if (r.o[k] < 0.0f || r.o[k] >= (float)a.g.dims0[k]) {
-      r.hit = false;
-    }
-  }
-  r.t0 = fmaxf(tmin, 0.0f);
-  r.t1 = tmax;
-  if (!(r.t0 < r.t1)) r.hit = false;
-  return r;
-}
-
-__device__ __forceinline__ void position(const RenderArgs& a, const Ray& r, float t, float (&x)[3]) {
-#pragma unroll
-  for (int k = 0; k < 3; ++k) x[k] = fminf(fmaxf(fmaf(t, r.d[k], r.o[k]), 0.0f), a.g.dimm[k]);
-}
-
-__device__ __forceinline__ void node_coords(const Geometry& g, int d, const float (&x)[3], int (&j)[3]) {
-#pragma unroll
-  for (int k = 0; k < 3; ++k) j[k] = (int)(x[k] * pow2f(-(g.leaf_log2[k] + g.D - d)));
-}
-
-// Trilinear sample of a level-l apron slot (R15), in two parts: the
-// in-slot offset of the lower corner and the lerp weights depend only on the
-// position and the level (every channel's bricks share one grid), so they
-// are computed once per level and sample; the fetch reads one channel's
-// corners from its owner's slot and lerps along x, then y, then z.
-struct TriCoords {
-  int idx;     // element offset of the lower corner inside the apron slot
-  float f[3];  // lerp weights
-};
-
-template <int EC>
-__device__ __forceinline__ void tri_coords(const Geometry& g, int l, const float (&x)[3], TriCoords& tc) {
-  const int E = EC ? EC : (int)g.edge;  // apron-slot edge, a compile-time constant for 32^3 bricks
-  int li[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const float xl = x[k] * pow2f(-l);
-    float u = xl - 0.5f;
-    u = fminf(fmaxf(u, 0.0f), g.ldimf[l][k]);
-    const int i0 = (int)u;
-    tc.f[k] = u - (float)i0;
-    const int b = (int)(x[k] * pow2f(-(g.blog2 + l)));
-    li[k] = i0 - (b * g.B - 1);
-  }
-  tc.idx = (li[2] * E + li[1]) * E + li[0];
-}
-
-template <int BPV, int EC>
-__device__ __forceinline__ float tri_fetch(const RenderArgs& a, uint32_t slot, const TriCoords& tc) {
-  const Geometry& g = a.g;
-  const int E = EC ? EC : (int)g.edge;
-  const uint8_t* base = a.cache + (size_t)slot * g.slot_pitch;
-  const int idx = tc.idx;
-  float v[8];
-  if constexpr (BPV == 1) {
-    const uint8_t* p = base + idx;
-    v[0] = (float)__ldg(p);
-    v[1] = (float)__ldg(p + 1);
-    v[2] = (float)__ldg(p + E);
-    v[3] = (float)__ldg(p + E + 1);
-    v[4] = (float)__ldg(p + E * E);
-    v[5] = (float)__ldg(p + E * E + 1);
-    v[6] = (float)__ldg(p + E * E + E);
-    v[7] = (float)__ldg(p + E * E + E + 1);
-  } else {
-    const uint16_t* p = reinterpret_cast<const uint16_t*>(base) + idx;
-    v[0] = (float)__ldg(p);
-    v[1] = (float)__ldg(p + 1);
-    v[2] = (float)__ldg(p + E);
-    v[3] = (float)__ldg(p + E + 1);
-    v[4] = (float)__ldg(p + E * E);
-    v[5] = (float)__ldg(p + E * E + 1);
-    v[6] = (float)__ldg(p + E * E + E);
-    v[7] = (float)__ldg(p + E * E + E + 1);
-  }
-  const float c00 = fmaf(tc.f[0], v[1] - v[0], v[0]);
-  const float c10 = fmaf(tc.f[0], v[3] - v[2], v[2]);
-  const float c01 = fmaf(tc.f[0], v[5] - v[4], v[4]);
-  const float c11 = fmaf(tc.f[0], v[7] - v[6], v[6]);
-  const float c0 = fmaf(tc.f[1], c10 - c00, c00);
-  const float c1 = fmaf(tc.f[1], c11 - c01, c01);
-  return fmaf(tc.f[2], c1 - c0, c0);
-}
-
-// TF lookup (R16) and opacity correction for a step of 2^s (R12): returns
-// the corrected opacity's complement q and the colour.  tf = (lo, scale).
-__device__ __forceinline__ void shade(const float4* __restrict__ lut, float2 tf, float val, int s, float& q, float& r,
-                                      float& gg, float& b) {  const float t = val - tf.x;
-  float xq = t * tf.y;
-  xq = fminf(fmaxf(xq, 0.0f), 255.0f);
-  int j = (int)xq;
-  j = j > 254 ? 254 : j;
-  const float fr = xq - (float)j;
-  const float4 L0 = lut[j], L1 = lut[j + 1];
-  r = fmaf(fr, L1.x - L0.x, L0.x);
-  gg = fmaf(fr, L1.y - L0.y, L0.y);
-  b = fmaf(fr, L1.z - L0.z, L0.z);
-  float al = fmaf(fr, L1.w - L0.w, L0.w);
-  al = fminf(fmaxf(al, 0.0f), 1.0f);
-  q = 1.0f - al;
-  for (int e = 0; e < s; ++e) q = q * q;
-}
-
-// Per-ray cache of the last classification: the final node, the desired
-// levels it was made for and whether every channel may be skipped there.  A
-// sample that lands in the same node with the same desired levels gets the
-// same decisions (the walk, the states, the selected slots and levels),
-// provided the node lies inside one brick of every level a channel may use;
-// requests and usage flags are then already set (the stores are idempotent).
-struct NodeCache {
-  int d;                 // final depth, -1 = empty
-  int jn[3];             // node coordinates at depth d
-  uint64_t ldp;          // desired levels (4 bits per channel)
-  int st;                // traversal depth
-  bool all_skip, one_brick;
-  int s_sel;             // finest level read from a brick, 99 = none
-  uint32_t act;          // channels with a value at this node (brick or node value)
-  uint32_t n_brick;      // how many of them read a brick
-};
-
-// Per-lane selection word (one per channel, in shared memory): bits 31..27
-// the level read (0..15) or kSelHomog, bits 26..0 the slot or the node value.
-constexpr uint32_t kSelNone = 0xFFFFFFFFu;
-constexpr uint32_t kSelHomog = 30u;
-constexpr uint32_t kSelMask = (1u << 27) - 1u;
-
-// Per-thread counters of the current tile (a ray's counts stay below 2^28);
-// at every refill the warp adds them to its own 64-bit row in shared memory.
-struct Counters {
-  uint32_t hit, eval, bs, homog, skip, skipped;
-};
-
-template <int BPV, bool DBG>
-__device__ __forceinline__ void write_pixel(const RenderArgs& a, int px, int py, float C0, float C1, float C2, float T,
-                                            uint32_t h, uint32_t n_eval, int i, uint32_t n_bs) {
-  const size_t p = (size_t)py * a.W + px;
-  a.image[p] = make_float4(fminf(C0, 1.0f), fminf(C1, 1.0f), fminf(C2, 1.0f), 1.0f - T);
-  if constexpr (DBG) {
-    if (a.dbg_hash) a.dbg_hash[p] = h;
-    if (a.dbg_n_eval) a.dbg_n_eval[p] = n_eval;
-    if (a.dbg_i_end) a.dbg_i_end[p] = (uint32_t)i;
-    if (a.dbg_n_bs) a.dbg_n_bs[p] = n_bs;
-  }
-}
-
-// Persistent launch.  Each warp takes the next 8 x 4 pixel tile from a
-// counter once all its lanes are free, so the 32 rays of a warp stay
-// neighbours and their footprints share cache lines.
-// One loop iteration = one lattice step of every active lane, in three
-// phases: (1) per lane, the sample position and desired levels, and whether
-// the cached node still applies; (2) for the lanes that need a new node, the
-// warp walks the octree cooperatively, one lane per channel, 32 / MP rays at
-// a time, and writes each ray's states and brick selections; (3) per lane,
-// the skip or the evaluated sample.
-template <int MP, int BPV, int EC, bool DBG>
-__global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_constant__ RenderArgs a) {
-  extern __shared__ float4 smem[];
-  float4* s_lut = smem;
-  uint16_t* s_pre = reinterpret_cast<uint16_t*>(s_lut + MP * 256);
-  uint32_t* s_sel = reinterpret_cast<uint32_t*>(smem) + MP * 256 * 4 + ((MP * 257 * 2 + 15) & ~15) / 4;
-  const Geometry& g = a.g;
-  const int m = g.m, k = g.k;
-  for (int q = threadIdx.x; q < m * 256; q += blockDim.x) s_lut[q] = a.lut[q];
-  for (int q = threadIdx.x; q < m * 257; q += blockDim.x) s_pre[q] = a.prefix[q];
-  // per-channel tables read with a per-lane channel index live in shared
-  // memory (a constant-bank read with divergent indices is replayed per index)
-  __shared__ float2 s_tf[kMaxC];
-  __shared__ uint32_t s_pto[kMaxC * kMaxL + 1];
-  for (int q = threadIdx.x; q < m; q += blockDim.x) s_tf[q] = make_float2(a.tf_lo[q], a.tf_scale[q]);
-  for (int q = threadIdx.x; q <= m * k; q += blockDim.x) s_pto[q] = g.pt_off[q];
-  __shared__ unsigned long long s_red[kRenderThreads / 32][kStats];
-  for (int q = threadIdx.x; q < kRenderThreads / 32 * kStats; q += blockDim.x) (&s_red[0][0])[q] = 0;
-  __syncthreads();
-
-  const unsigned FULL = 0xFFFFFFFFu;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int stride = blockDim.x;
-  uint32_t* my_sel = s_sel + threadIdx.x;
-  constexpr int G = 32 / MP;                       // rays walked per cooperative pass
-  const int grp = lane / MP, ch = lane % MP;
-  const unsigned gmask = (MP == 32 ? FULL : ((1u << MP) - 1u)) << (grp * MP);
-  const unsigned lt_mask = (1u << lane) - 1u;
-
-  Counters cnt = {0, 0, 0, 0, 0, 0};
-  auto flush = [&]() {
-    const uint32_t vals[6] = {cnt.hit, cnt.eval, cnt.bs, cnt.homog, cnt.skip, cnt.skipped};
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      unsigned long long v = vals[q];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-      if (lane == 0) s_red[warp][q] += v;
-    }
-    cnt = {0, 0, 0, 0, 0, 0};
-  };
-  Ray r;
-  int px = 0, py = 0, i = 0, lod = 0;
-  float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
-  uint32_t h = 0, n_eval = 0, n_bs = 0;
-  NodeCache nc;
-  nc.d = -1;
-  bool active = false, done = false;
-
-  for (;;) {
-    // ------------------------------------------------------------- refill
-    const unsigned busy = __ballot_sync(FULL, active);
-    if (!busy && !done) {
-      flush();
-      unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(a.work, 32ull);
-      base = __shfl_sync(FULL, base, 0);
-      const unsigned long long ray = base + lane;
-      if (base >= a.n_rays) {
-        done = true;
-      } else {
-        const uint32_t tile = (uint32_t)(ray >> 5), w = (uint32_t)(ray & 31);
-        px = (int)((tile % a.tiles_x) * 8 + (w & 7));
-        py = (int)((tile / a.tiles_x) * 4 + (w >> 3));
-        if (px < a.W && py < a.H) {
-          r = make_ray(a, px, py);
-          i = 0;
-          lod = 0;
-          C0 = C1 = C2 = 0.0f;
-          T = 1.0f;
-          h = 2166136261u;
-          n_eval = n_bs = 0;
-          nc.d = -1;
-          if (r.hit) {
-            active = true;
-            ++cnt.hit;
-          } else {
-            write_pixel<BPV, DBG>(a, px, py, C0, C1, C2, T, h, n_eval, i, n_bs);
-          }
-        }
-      }
-    }
-    if (__all_sync(FULL, done)) break;
-
-    // ------------------------------------- phase 1: sample, levels, node?
-    float x[3] = {0.0f, 0.0f, 0.0f};
-    int L[3] = {0, 0, 0};
-    uint64_t ldp = 0;
-    int lminu = 15, st = 0, dstart = 0;
-    bool need = false, same_node = false;
-    if (active) {
-      const float t = fmaf((float)i, a.dt, r.t0);
-      if (i >= kMaxSamples || !(t < r.t1)) {
-        write_pixel<BPV, DBG>(a, px, py, C0, C1, C2, T, h, n_eval, i, n_bs);
-        active = false;
-      } else {
-        position(a, r, t, x);
-        // lod = #{l in 1..k-1 : t >= lod_t[l]} (R7); t never decreases along
-        // a ray and the thresholds are non-decreasing, so the count only grows
-        while (lod < k - 1 && t >= a.lod_t[lod + 1]) ++lod;
-        ldp = a.ldp_tab[lod];
-        lminu = a.lminu_tab[lod];
-        st = a.sdepth[lminu];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) L[q] = (int)(x[q] * pow2f(-g.leaf_log2[q]));
-        const bool same_levels = nc.d >= 0 && ldp == nc.ldp && st == nc.st;
-        if (same_levels) {
-          const int sh = g.D - nc.d;
-          same_node = (L[0] >> sh) == nc.jn[0] && (L[1] >> sh) == nc.jn[1] && (L[2] >> sh) == nc.jn[2];
-        }
-        need = !(same_node && nc.one_brick);
-        // the walk (R9) resumes below the deepest ancestor shared with the
-        // previous sample: those depths were found not all terminal
-        const int d0 = a.start_depth < st ? a.start_depth : st;
-        dstart = d0;
-        if (same_node) {
-          dstart = nc.d;
-        } else if (same_levels) {
-          int dca = 0;
-          for (int q = nc.d; q >= 0; --q) {
-            const int sh = g.D - q, up = nc.d - q;
-            if ((L[0] >> sh) == (nc.jn[0] >> up) && (L[1] >> sh) == (nc.jn[1] >> up) &&
-                (L[2] >> sh) == (nc.jn[2] >> up)) {
-              dca = q;
-              break;
-            }
-          }
-          dstart = dca + 1 > d0 ? dca + 1 : d0;
-        }
-      }
-    }
-
-    // ------------------------------ phase 2: cooperative walk + selection
-    unsigned pending = __ballot_sync(FULL, need);
-    while (pending) {
-      // the q-th lane of `pending` (in lane order) is walked by group q
-      unsigned rest = pending;
-#pragma unroll
-      for (int q = 0; q < G; ++q) rest &= rest - 1u;
-      const unsigned taken = pending & ~rest;
-      pending = rest;
-      unsigned pm = taken;
-      for (int q = 0; q < grp && pm; ++q) pm &= pm - 1u;
-      const int src = pm ? __ffs(pm) - 1 : lane;
-      const bool gact = pm != 0;
-      const float sx0 = __shfl_sync(FULL, x[0], src), sx1 = __shfl_sync(FULL, x[1], src),
-                  sx2 = __shfl_sync(FULL, x[2], src);
-      const int sL0 = __shfl_sync(FULL, L[0], src), sL1 = __shfl_sync(FULL, L[1], src),
-                sL2 = __shfl_sync(FULL, L[2], src);
-      const uint32_t ldp_lo = __shfl_sync(FULL, (uint32_t)ldp, src),
-                     ldp_hi = __shfl_sync(FULL, (uint32_t)(ldp >> 32), src);
-      const uint64_t sldp = ((uint64_t)ldp_hi << 32) | ldp_lo;
-      const int sst = __shfl_sync(FULL, st, src), sds = __shfl_sync(FULL, dstart, src),
-                slm = __shfl_sync(FULL, lminu, src);
-      const bool ssame = __shfl_sync(FULL, (int)same_node, src) != 0;
-      const bool cact = gact && ch < m;
-      const int ld = cact ? (int)((sldp >> (4 * ch)) & 15) : 0;
-
-      int d = sds;
-      bool gdone = !gact, bad = false;
-      int jn0 = 0, jn1 = 0, jn2 = 0;
-      uint64_t node = 0;
-      uint32_t w = 0;
-      int sc = kEmpty;
-      for (;;) {
-        if (!gdone) {
-          const int sh = g.D - d;
-          jn0 = sL0 >> sh; jn1 = sL1 >> sh; jn2 = sL2 >> sh;
-          node = g.node_off[d] + ((uint64_t)jn2 * g.nn[d][1] + jn1) * g.nn[d][0] + jn0;
-          if (node >= g.node_off[d + 1]) {
-            bad = true;
-          } else if (cact) {
-            w = __ldg(a.octree + node * MP + ch);
-            sc = classify<BPV>(w, s_pre + ch * 257, ld, k);
-          }
-        }
-        const unsigned term = __ballot_sync(FULL, gdone || !cact || bad || terminal(sc));
-        if (!gdone && ((term & gmask) == gmask || d == sst || ssame || bad)) gdone = true;
-        if (__all_sync(FULL, gdone)) break;
-        if (!gdone) ++d;
-      }
-      const bool gbad = (__ballot_sync(FULL, bad) & gmask) != 0;
-
-      // requests of channels with nothing usable here, node requests of
-      // INVALID channels
-      if (cact && !gbad) {
-        const bool no_use = ((w & 0xFFFFu) & (~0u << ld) & ((1u << k) - 1u)) == 0;
-        if (sc == kUnmapped || (sc == kInvalid && no_use)) {
-          const int bsh = g.blog2 + ld;
-          const int bx = (int)(sx0 * pow2f(-bsh)), by = (int)(sx1 * pow2f(-bsh)), bz = (int)(sx2 * pow2f(-bsh));
-          const uint64_t pi = s_pto[ch * k + ld] + ((uint64_t)bz * g.nb[ld][1] + by) * g.nb[ld][0] + bx;
-          if (pi >= g.n_bricks) *a.err = kErrPageIndex;
-          else a.req[pi] = 1;
-        }
-        if (sc == kInvalid) a.node_req[node * m + ch] = 1;
-      }
-      const unsigned nonskip = __ballot_sync(FULL, cact && sc != kEmpty && sc != kUnmapped);
-      const bool all_skip = (nonskip & gmask) == 0;
-
-      // brick selection (R11): desired level, else request it and take the
-      // next coarser resident level
-      uint32_t sel = kSelNone;
-      int found = 99;
-      if (cact && !gbad && !all_skip && sc != kEmpty && sc != kUnmapped) {
-        if (sc == kHomog) {
-          sel = (kSelHomog << 27) | ((w >> 16) & 0xFFu);
-        } else if (((w & 0xFFFFu) & (~0u << ld) & ((1u << k) - 1u)) != 0) {
-          for (int l = ld; l < k; ++l) {
-            const int bsh = g.blog2 + l;
-            const int bx = (int)(sx0 * pow2f(-bsh)), by = (int)(sx1 * pow2f(-bsh)), bz = (int)(sx2 * pow2f(-bsh));
-            const uint64_t pi = s_pto[ch * k + l] + ((uint64_t)bz * g.nb[l][1] + by) * g.nb[l][0] + bx;
-            if (pi >= g.n_bricks) { *a.err = kErrPageIndex; break; }
-            uint32_t e = 0;
-            if ((w >> l) & 1u) e = __ldg(a.pt + pi);
-            if (e != 0) {
-              if (e - 1 >= g.cache_slots) { *a.err = kErrSlot; break; }
-              sel = ((uint32_t)l << 27) | (e - 1);
-              a.used[e - 1] = 1;
-              found = l;
-              break;
-            }
-            if (l == ld) a.req[pi] = 1;
-          }
-        }
-      }
-      if (cact) s_sel[ch * stride + warp * 32 + src] = sel;
-      const unsigned chmask = MP == 32 ? FULL : ((1u << MP) - 1u);
-      const uint32_t act = (__ballot_sync(FULL, sel != kSelNone) >> (grp * MP)) & chmask;
-      const uint32_t nbrk = __popc((__ballot_sync(FULL, sel != kSelNone && (sel >> 27) != kSelHomog) >> (grp * MP)) & chmask);
-#pragma unroll
-      for (int o = 1; o < MP; o <<= 1) {
-        const int other = __shfl_xor_sync(FULL, found, o);
-        found = other < found ? other : found;
-      }
-      // hand the walk's result to the lanes it was for
-      const bool mine = (taken >> lane) & 1u;
-      const int from = mine ? __popc(taken & lt_mask) * MP : lane;
-      const int od = __shfl_sync(FULL, d, from);
-      const int oj0 = __shfl_sync(FULL, jn0, from), oj1 = __shfl_sync(FULL, jn1, from),
-                oj2 = __shfl_sync(FULL, jn2, from);
-      const bool oskip = __shfl_sync(FULL, (int)all_skip, from) != 0;
-      const int osel = __shfl_sync(FULL, found, from);
-      const bool obad = __shfl_sync(FULL, (int)gbad, from) != 0;
-      const uint32_t oact = __shfl_sync(FULL, act, from), onb = __shfl_sync(FULL, nbrk, from);
-      (void)slm;
-      if (mine) {
-        if (obad) {
-          *a.err = kErrNodeIndex;
-          write_pixel<BPV, DBG>(a, px, py, C0, C1, C2, T, h, n_eval, i, n_bs);
-          active = false;
-        } else {
-          nc.d = od;
-          nc.jn[0] = oj0; nc.jn[1] = oj1; nc.jn[2] = oj2;
-          nc.ldp = ldp;
-          nc.st = st;
-          nc.all_skip = oskip;
-          nc.s_sel = osel;
-          nc.act = oact;
-          nc.n_brick = onb;
-          const int esh = g.D - od;
-          nc.one_brick = g.leaf_log2[0] + esh <= g.blog2 + lminu && g.leaf_log2[1] + esh <= g.blog2 + lminu &&
-                         g.leaf_log2[2] + esh <= g.blog2 + lminu;
-        }
-      }
-    }
-    __syncwarp();
-
-    // ----------------------------------------- phase 3: skip or evaluate
-    if (!active) continue;
-    if (nc.all_skip && a.skip) {
-      // first lattice index whose sample lies outside the node (R10):
-      // estimate from the node box's exit distance, then correct with the
-      // same position arithmetic
-      const int d = nc.d;
-      float tb = r.t1;
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int sh = g.leaf_log2[q] + g.D - d;
-        const float lo = (float)(nc.jn[q] << sh), hi = (float)((nc.jn[q] + 1) << sh);
-        if (r.d[q] > 0.0f) tb = fminf(tb, __fdiv_rn(hi - r.o[q], r.d[q]));
-        else if (r.d[q] < 0.0f) tb = fminf(tb, __fdiv_rn(lo - r.o[q], r.d[q]));
-      }
-      float fj = ceilf(__fdiv_rn(tb - r.t0, a.dt));
-      fj = fminf(fmaxf(fj, (float)(i + 1)), (float)kMaxSamples);
-      int j = (int)fj;
-      auto inside = [&](int jj) -> bool {
-        const float tj = fmaf((float)jj, a.dt, r.t0);
-        if (!(tj < r.t1)) return false;
-        float xj[3];
-        int jc[3];
-        position(a, r, tj, xj);
-        node_coords(g, d, xj, jc);
-        return jc[0] == nc.jn[0] && jc[1] == nc.jn[1] && jc[2] == nc.jn[2];
-      };
-      while (j < kMaxSamples && inside(j)) ++j;
-      while (j > i + 1 && !inside(j - 1)) --j;
-      if constexpr (DBG) {
-        h = fnv_word(h, (uint32_t)i);
-        h = fnv_word(h, 0xFFFFFFFFu);
-        h = fnv_word(h, (uint32_t)d);
-        h = fnv_word(h, (uint32_t)j);
-      }
-      ++cnt.skip;
-      cnt.skipped += (uint32_t)(j - i);
-      i = j;
-      continue;
-    }
-
-    // shade and composite (R12-R14)
-    const int s = nc.s_sel == 99 ? lminu : nc.s_sel;
-    float col0 = 0.0f, col1 = 0.0f, col2 = 0.0f, trans = 1.0f;
-    cnt.bs += nc.n_brick;
-    cnt.homog += __popc(nc.act) - nc.n_brick;
-    n_bs += nc.n_brick;
-    int tl = -1;
-    TriCoords tc;
-    for (uint32_t mm = nc.act; mm; mm &= mm - 1u) {
-      const int c = __ffs(mm) - 1;
-      const uint32_t sel = my_sel[c * stride];
-      const uint32_t lb = sel >> 27;
-      float val;
-      if (lb == kSelHomog) {
-        val = (float)(sel & kSelMask);
-        if constexpr (DBG) {
-          h = fnv_word(h, (uint32_t)i); h = fnv_word(h, (uint32_t)c);
-          h = fnv_word(h, 0xFFu); h = fnv_word(h, 0xFFFFFFFFu);
-        }
-      } else {
-        if ((int)lb != tl) {  // channels at one level share the corner offset and weights
-          tl = (int)lb;
-          tri_coords<EC>(g, tl, x, tc);
-        }
-        val = tri_fetch<BPV, EC>(a, sel & kSelMask, tc);
-        if constexpr (DBG) {
-          const int bsh = g.blog2 + (int)lb;
-          const uint32_t bx = (uint32_t)(x[0] * pow2f(-bsh)), by = (uint32_t)(x[1] * pow2f(-bsh)),
-                         bz = (uint32_t)(x[2] * pow2f(-bsh));
-          h = fnv_word(h, (uint32_t)i); h = fnv_word(h, (uint32_t)c); h = fnv_word(h, lb);
-          h = fnv_word(h, ((uint32_t)(c * k + (int)lb) << 24) | (bz << 16) | (by << 8) | bx);
-        }
-      }
-      // a value at or below the window start maps to knot 0; with a
-      // transparent knot 0 the channel adds exactly nothing (a' = 0, q = 1)
-      if (!((val - s_tf[c].x) * s_tf[c].y > 0.0f) && s_lut[c * 256].w <= 0.0f) continue;
-      float q, cr, cg, cb;
-      shade(s_lut + c * 256, s_tf[c], val, s, q, cr, cg, cb);
-      const float ap = 1.0f - q;
-      col0 = fmaf(ap, cr, col0);
-      col1 = fmaf(ap, cg, col1);
-      col2 = fmaf(ap, cb, col2);
-      trans = trans * q;
-    }
-    C0 = fmaf(T, col0, C0);
-    C1 = fmaf(T, col1, C1);
-    C2 = fmaf(T, col2, C2);
-    T = T * trans;
-    ++n_eval;
-    ++cnt.eval;
-    if (T < a.ert) {
-      write_pixel<BPV, DBG>(a, px, py, C0, C1, C2, T, h, n_eval, i, n_bs);
-      active = false;
-      continue;
-    }
-    i += 1 << s;
-  }
-
-  // per-block counters, reduced without atomics
-  flush();
-  __syncthreads();
-  if (threadIdx.x < kStats) {
-    unsigned long long v = 0;
-    for (int q = 0; q < kRenderThreads / 32; ++q) v += s_red[q][threadIdx.x];
-    a.block_stats[(size_t)blockIdx.x * kStats + threadIdx.x] = v;
-  }
-}
 
 // Bucket-occupancy prefix sums per channel (R5): one block per channel.
 __global__ void __launch_bounds__(256) prefix_kernel(const __grid_constant__ PrefixArgs a) {
@@ -638,9 +14,10 @@ __global__ void __launch_bounds__(256) prefix_kernel(const __grid_constant__ Pre
   float vlo, vhi;
   if (a.bpv == 1) { vlo = (float)q; vhi = (float)q; }
   else { vlo = (float)(q * 256); vhi = (float)(q * 256 + 255); }
+  const float lo = a.tf_dev ? a.tf_dev[c].x : a.tf_lo[c], scale = a.tf_dev ? a.tf_dev[c].y : a.tf_scale[c];
   auto coord = [&](float v) {
-    const float t = v - a.tf_lo[c];
-    const float xq = t * a.tf_scale[c];
+    const float t = v - lo;
+    const float xq = t * scale;
     return fminf(fmaxf(xq, 0.0f), 255.0f);
   };
   const float xa = coord(vlo), xb = coord(vhi);
@@ -662,40 +39,6 @@ __global__ void __launch_bounds__(256) prefix_kernel(const __grid_constant__ Pre
   if (q == 0) a.prefix[c * 257 + 256] = s_scan[256];
 }
 
-template <int MP, int BPV, int EC, bool DBG>
-cudaError_t launch_one(const RenderArgs& a, cudaStream_t s, int* blocks_out) {
-  const size_t smem = render_smem_bytes(MP);
-  auto kern = render_kernel<MP, BPV, EC, DBG>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, per_sm = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRenderThreads, smem)) != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const uint64_t need = (a.n_rays + kRenderThreads - 1) / kRenderThreads;
-  int blocks = sms * per_sm;
-  if ((uint64_t)blocks > need) blocks = (int)need;
-  kern<<<blocks, kRenderThreads, smem, s>>>(a);
-  *blocks_out = blocks;
-  return cudaGetLastError();
-}
-
-template <int MP, int BPV, int EC>
-cudaError_t launch_ec(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out) {
-  return debug ? launch_one<MP, BPV, EC, true>(a, s, blocks_out) : launch_one<MP, BPV, EC, false>(a, s, blocks_out);
-}
-
-template <int MP, int BPV>
-cudaError_t launch_mp(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out) {
-  return a.g.edge == 34 ? launch_ec<MP, BPV, 34>(a, debug, s, blocks_out) : launch_ec<MP, BPV, 0>(a, debug, s, blocks_out);
-}
-
-template <int MP>
-cudaError_t launch_bpv(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out) {
-  return a.g.bpv == 1 ? launch_mp<MP, 1>(a, debug, s, blocks_out) : launch_mp<MP, 2>(a, debug, s, blocks_out);
-}
-
 }  // namespace
 
 size_t render_smem_bytes(int mp) {
@@ -704,14 +47,7 @@ size_t render_smem_bytes(int mp) {
 }
 
 cudaError_t launch_render(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out) {
-  switch (a.g.mp) {
-    case 1: return launch_bpv<1>(a, debug, s, blocks_out);
-    case 2: return launch_bpv<2>(a, debug, s, blocks_out);
-    case 4: return launch_bpv<4>(a, debug, s, blocks_out);
-    case 8: return launch_bpv<8>(a, debug, s, blocks_out);
-    case 16: return launch_bpv<16>(a, debug, s, blocks_out);
-    default: return cudaErrorInvalidValue;
-  }
+  return launch_any<false>(a, debug, s, blocks_out);
 }
 
 cudaError_t launch_prefix(const PrefixArgs& a, cudaStream_t s) {

@@ -17,12 +17,13 @@ from . import build as _build
 
 RO_MAX_CHANNELS = 16
 RO_MAX_LEVELS = 16
+RO_MAX_VIEWS = 256
 RO_NONE = 0xFFFFFFFF
 STATUS = {0: "RO_OK", 1: "RO_ERR_INVALID_ARG", 2: "RO_ERR_CUDA", 3: "RO_ERR_CAPACITY", 4: "RO_ERR_TIMEOUT",
           5: "RO_ERR_INTERNAL"}
 EXPORTS = ["ro_query_sizes", "ro_create", "ro_destroy", "ro_upload_bricks", "ro_update_residency_octree", "ro_render",
            "ro_read_requests", "ro_get_stats", "ro_debug_read", "ro_brick_index", "ro_set_timeout", "ro_last_error",
-           "ro_compact_flags_noalloc"]
+           "ro_compact_flags_noalloc", "ro_render_batch", "ro_autotune_batch"]
 
 
 class RoError(RuntimeError):
@@ -35,14 +36,15 @@ class Desc(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_uint32 * 3), ("spacing", ctypes.c_float * 3), ("channels", ctypes.c_uint32),
                 ("value_bits", ctypes.c_uint32), ("brick", ctypes.c_uint32), ("levels", ctypes.c_uint32),
                 ("leaf_extent", ctypes.c_uint32 * 3), ("cache_slots", ctypes.c_uint32),
-                ("max_requests", ctypes.c_uint32), ("max_upload", ctypes.c_uint32), ("max_meta", ctypes.c_uint32)]
+                ("max_requests", ctypes.c_uint32), ("max_upload", ctypes.c_uint32), ("max_meta", ctypes.c_uint32),
+                ("max_batch_tiles", ctypes.c_uint32)]
 
 
 class Sizes(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("cache", "page_table", "octree", "req_flags", "node_req_flags",
                                                 "used_flags", "last_used", "staging", "frame", "lists", "scratch",
                                                 "total", "slot_pitch", "n_bricks", "n_nodes")] + \
-               [("depth", ctypes.c_uint32), ("channel_stride", ctypes.c_uint32)]
+               [("depth", ctypes.c_uint32), ("channel_stride", ctypes.c_uint32), ("batch", ctypes.c_uint64)]
 
 
 class Camera(ctypes.Structure):
@@ -61,6 +63,15 @@ class RenderParams(ctypes.Structure):
                 ("start_depth", ctypes.c_uint32), ("skip", ctypes.c_uint32), ("ert", ctypes.c_float),
                 ("debug_hash", ctypes.c_void_p), ("debug_n_eval", ctypes.c_void_p),
                 ("debug_i_end", ctypes.c_void_p), ("debug_n_bs", ctypes.c_void_p)]
+
+
+class View(ctypes.Structure):
+    _fields_ = [("camera", Camera), ("params", RenderParams), ("image", ctypes.c_void_p), ("W", ctypes.c_uint32),
+                ("H", ctypes.c_uint32)]
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_uint32), ("order", ctypes.c_uint32)]
 
 
 class LeafMeta(ctypes.Structure):
@@ -101,6 +112,8 @@ def load(build_if_missing: bool = True):
     L.ro_last_error.restype = ctypes.c_char_p
     L.ro_last_error.argtypes = [vp]
     L.ro_compact_flags_noalloc.argtypes = [vp, u64, vp, u32, vp, vp]
+    L.ro_render_batch.argtypes = [vp, u32, vp, vp, ctypes.POINTER(Schedule)]
+    L.ro_autotune_batch.argtypes = [vp, u32, vp, vp, ctypes.POINTER(Schedule), ctypes.POINTER(ctypes.c_float)]
     for f in EXPORTS:
         getattr(L, f).restype = getattr(L, f).restype if f in ("ro_brick_index", "ro_last_error") else ctypes.c_int
     _lib = L
@@ -108,7 +121,7 @@ def load(build_if_missing: bool = True):
 
 
 def make_desc(dims, spacing, channels, value_bits, brick, levels, leaf_extent, cache_slots, max_requests=65536,
-              max_upload=1024, max_meta=65536) -> Desc:
+              max_upload=1024, max_meta=65536, max_batch_tiles=0) -> Desc:
     d = Desc()
     d.dims[:] = [int(v) for v in dims]
     d.spacing[:] = [float(v) for v in spacing]
@@ -116,6 +129,7 @@ def make_desc(dims, spacing, channels, value_bits, brick, levels, leaf_extent, c
     d.leaf_extent[:] = [int(v) for v in leaf_extent]
     d.cache_slots, d.max_requests, d.max_upload, d.max_meta = int(cache_slots), int(max_requests), int(max_upload), \
         int(max_meta)
+    d.max_batch_tiles = int(max_batch_tiles)
     return d
 
 
@@ -207,6 +221,33 @@ class Context:
         self._check(self.L.ro_render(self.h, ctypes.byref(camera), arr, ctypes.byref(params),
                                      ctypes.c_void_p(image.data_ptr()), int(W), int(H)))
 
+    def _tf_array(self, tfs):
+        luts = [np.ascontiguousarray(np.asarray(t[2], np.float32).reshape(256, 4)) for t in tfs]
+        arr = (TF * len(tfs))()
+        for i, (lo, sc, _) in enumerate(tfs):
+            arr[i].lo, arr[i].scale, arr[i].lut = float(lo), float(sc), luts[i].ctypes.data
+        return arr, luts
+
+    def render_batch(self, views, tfs, tile_w=8, order=0):
+        """views: list of (Camera, RenderParams, image cuda tensor, W, H); tfs as for render."""
+        arr, luts = self._tf_array(tfs)
+        vs = (View * len(views))()
+        for i, (cam, par, img, W, H) in enumerate(views):
+            assert img.is_cuda and img.dtype == self.torch.float32 and img.numel() >= W * H * 4
+            vs[i].camera, vs[i].params, vs[i].image, vs[i].W, vs[i].H = cam, par, img.data_ptr(), int(W), int(H)
+        sched = Schedule(int(tile_w), int(order))
+        self._check(self.L.ro_render_batch(self.h, len(views), vs, arr, ctypes.byref(sched)))
+
+    def autotune_batch(self, views, tfs):
+        """Returns ((tile_w, order), ms) of the fastest schedule for this batch."""
+        arr, luts = self._tf_array(tfs)
+        vs = (View * len(views))()
+        for i, (cam, par, img, W, H) in enumerate(views):
+            vs[i].camera, vs[i].params, vs[i].image, vs[i].W, vs[i].H = cam, par, img.data_ptr(), int(W), int(H)
+        best, ms = Schedule(), ctypes.c_float()
+        self._check(self.L.ro_autotune_batch(self.h, len(views), vs, arr, ctypes.byref(best), ctypes.byref(ms)))
+        return (int(best.tile_w), int(best.order)), float(ms.value)
+
     def read_requests(self, cap=None, node_cap=None):
         cap = int(self.desc.max_requests if cap is None else cap)
         node_cap = int(self.desc.max_requests if node_cap is None else node_cap)
@@ -276,6 +317,25 @@ def params_struct(frame, debug=None) -> RenderParams:
     if debug is not None:
         p.debug_hash, p.debug_n_eval, p.debug_i_end, p.debug_n_bs = [int(t.data_ptr()) for t in debug]
     return p
+
+
+def render_batch(ctx: Context, frames, images=None, tile_w=8, order=0, debug=False):
+    """Render several synth.Frame-like views (same TFs: those of frames[0])
+    in one batch launch.  Returns the list of (H, W, 4) images and, with
+    debug=True, the per-view debug tensors."""
+    torch = ctx.torch
+    if images is None:
+        images = [torch.empty((int(f.H), int(f.W), 4), dtype=torch.float32, device=ctx.device) for f in frames]
+    dbgs = []
+    views = []
+    for f, img in zip(frames, images):
+        dbg = None
+        if debug:
+            dbg = [torch.zeros((int(f.H), int(f.W)), dtype=torch.int32, device=ctx.device) for _ in range(4)]
+        dbgs.append(dbg)
+        views.append((camera_struct(f.camera), params_struct(f, dbg), img, int(f.W), int(f.H)))
+    ctx.render_batch(views, [(t.lo, t.scale, t.lut) for t in frames[0].tfs], tile_w=tile_w, order=order)
+    return images, dbgs
 
 
 def render_frame(ctx: Context, frame, image=None, debug=False):
