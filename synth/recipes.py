@@ -153,3 +153,34 @@ def cells_large(seed=3, m=16, dims=(4096, 4096, 96), ncells=480000, k=7, W=1920,
         cam = orbit(center, r, elevation, arc_deg * v / n_views + 7.0, W, H, fovy)
         s.frames.append(Frame(W, H, cam, tfs, 0.5 * min(spacing), lod, [0] * m, [k - 1] * m))
     return s
+
+
+VIEW_SIZES = ((256, 256), (512, 512), (1024, 768), (1920, 1080))
+
+
+def cells_views(seed=5, m=16, dims=(1024, 1024, 64), ncells=20000, k=5, n_views=64, sizes=VIEW_SIZES, fovy=40.0,
+                elevation=(25.0, 60.0), distance=(0.6, 1.2)) -> Scene:
+    """m-channel u16 slab (spacing 1:1:4) of the cell model, bricks generated
+    on request; n_views seeded perspective cameras around the slab, each with
+    an image size drawn uniformly from `sizes`, a seeded azimuth, elevation and
+    distance (a multiple of the distance that frames the whole slab)."""
+    spacing = (1.0, 1.0, 4.0)
+    cells = Cells(seed, ncells, m, dims, spacing)
+    leaf = (16, 16, 4)
+    mins, maxs = zip(*[cells.leaf_bounds(c, leaf) for c in range(m)])
+    s = Scene("cells_views", tuple(dims), spacing, m, k, 32, leaf, 16, cells=cells,
+              leaf_min=np.stack(mins).astype(np.int64), leaf_max=np.stack(maxs).astype(np.int64))
+    center = tuple(d * sp / 2.0 for d, sp in zip(dims, spacing))
+    ext = math.hypot(dims[0] * spacing[0], dims[1] * spacing[1])
+    r0 = 0.55 * ext / math.tan(math.radians(fovy) / 2.0)
+    rng = np.random.default_rng(seed)
+    tfs = _cell_tfs(m)
+    for v in range(n_views):
+        W, H = sizes[int(rng.integers(len(sizes)))]
+        az = float(rng.uniform(0.0, 360.0))
+        el = float(rng.uniform(*elevation))
+        r = r0 * float(rng.uniform(*distance))
+        cam = orbit(center, r, el, az, W, H, fovy)
+        lod = lod_thresholds(min(spacing), H, fovy, k)
+        s.frames.append(Frame(W, H, cam, tfs, 0.5 * min(spacing), lod, [0] * m, [k - 1] * m))
+    return s
