@@ -38,7 +38,7 @@ class _Volume(ctypes.Structure):
                 ("m", ctypes.c_int32), ("k", ctypes.c_int32), ("B", ctypes.c_int32), ("bpv", ctypes.c_int32),
                 ("leaf", ctypes.c_int32 * 3), ("levels", ctypes.POINTER(ctypes.c_void_p)),
                 ("resident", ctypes.c_void_p), ("leaf_min", ctypes.c_void_p), ("leaf_max", ctypes.c_void_p),
-                ("voxel_fn", ctypes.c_void_p), ("voxel_ctx", ctypes.c_void_p)]
+                ("voxel_fn", ctypes.c_void_p), ("voxel_ctx", ctypes.c_void_p), ("sample_format", ctypes.c_int32)]
 
 
 class _Params(ctypes.Structure):
@@ -82,6 +82,10 @@ def lib():
         L.or_brick_id.argtypes = [V] + [ctypes.c_int] * 5
         L.or_set_threads.argtypes = [ctypes.c_int]
         L.or_threads_used.restype = ctypes.c_int
+        L.or_round_fmt.restype = ctypes.c_double
+        L.or_round_fmt.argtypes = [ctypes.c_double, ctypes.c_int]
+        L.or_lerp_fmt.restype = ctypes.c_double
+        L.or_lerp_fmt.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int]
         _lib = L
     return _lib
 
@@ -89,6 +93,16 @@ def lib():
 def _p(a: np.ndarray):
     assert a.flags["C_CONTIGUOUS"]
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def round_fmt(x: float, fmt: int) -> float:
+    """Round-to-nearest-even of x to binary16 (fmt 1) or bfloat16 (fmt 2)."""
+    return float(lib().or_round_fmt(float(x), int(fmt)))
+
+
+def lerp_fmt(f: float, a: float, b: float, fmt: int) -> float:
+    """One low-precision lerp: q(f * q(b - a) + a), each q a single rounding."""
+    return float(lib().or_lerp_fmt(float(f), float(a), float(b), int(fmt)))
 
 
 def set_threads(n: int) -> None:
@@ -106,14 +120,18 @@ class Volume:
     levels[c][l]: numpy array [z][y][x] (uint8 or uint16) of level l.
     resident: iterable of (c, l, bx, by, bz) bricks resident in the cache.
     leaf_min / leaf_max: arrays (m, lz, ly, lx) int64, -1 = no metadata.
+    sample_format: 0 = raw values with binary32 lerps, 1 = binary16,
+    2 = bfloat16 samples (the brick cache's format).
     provider: instead of levels, (m, k, dims_xyz, bytes_per_voxel, fn, ctx)
     where fn is a C function pointer uint32_t(void*, int c, int l, int64 x,
     int64 y, int64 z) and ctx its first argument (a voxel source for
     volumes too large to hold densely).
     """
 
-    def __init__(self, levels, spacing, B, leaf_extent, resident=(), leaf_min=None, leaf_max=None, provider=None):
+    def __init__(self, levels, spacing, B, leaf_extent, resident=(), leaf_min=None, leaf_max=None, provider=None,
+                 sample_format=0):
         self.s = _Volume()
+        self.s.sample_format = int(sample_format)
         if provider is None:
             self.m = len(levels)
             self.k = len(levels[0])

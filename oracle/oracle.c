@@ -64,6 +64,9 @@ typedef struct {
    * already clamped to the level */
   uint32_t (*voxel_fn)(void *ctx, int c, int l, int64_t x, int64_t y, int64_t z);
   void *voxel_ctx;
+  /* sample format of the brick cache: 0 = raw values, binary32 lerps;
+   * 1 = binary16, 2 = bfloat16 (see trilinear_lp) */
+  int32_t sample_format;
 } or_volume;
 
 typedef struct {
@@ -314,7 +317,9 @@ static void *oa_worker(void *arg) {
 /* Residency and culling word of every node and channel: words[node*m + c] =
  * mask[15:0] | min8[23:16] | max8[31:24] (Sec. 7), INVALID = min8 > max8. */
 OR_EXPORT int or_node_words(const or_volume *v, uint32_t *words) {
-  if (v->m < 1 || v->m > OR_MAXC || v->k < 1 || v->k > OR_MAXL || (v->bpv != 1 && v->bpv != 2)) return -1;
+  if (v->m < 1 || v->m > OR_MAXC || v->k < 1 || v->k > OR_MAXL || (v->bpv != 1 && v->bpv != 2) ||
+      v->sample_format < 0 || v->sample_format > 2)
+    return -1;
   oa_ctx x;
   x.v = v;
   x.D = or_depth(v);
@@ -529,6 +534,92 @@ static float trilinear32(const or_volume *v, int c, int l, const float x[3]) {
   return fmaf(fr[2], c1 - c0, c0);
 }
 
+/* Round-to-nearest-even of x to a binary format with p significant bits
+ * whose smallest normal exponent is emin (gradual underflow below it):
+ * binary16 p = 11, emin = -14; bfloat16 p = 8, emin = -126.  x is finite
+ * and within the format's range here (values and weights lie in [-1, 1]).
+ * The quantum is the unit in the last place of x's binade, so x / quantum
+ * is exact and nearbyint rounds it to an integer, ties to even. */
+static double fmt_quantum(double x, int p, int emin) {
+  int e;
+  frexp(x, &e);             /* |x| in [2^(e-1), 2^e) */
+  int lead = e - 1;
+  if (lead < emin) lead = emin;
+  return ldexp(1.0, lead - (p - 1));
+}
+
+static double round_fmt(double x, int fmt) {
+  const int p = fmt == 1 ? 11 : 8, emin = fmt == 1 ? -14 : -126;
+  if (x == 0.0) return x;
+  const double q = fmt_quantum(x, p, emin);
+  return nearbyint(x / q) * q;
+}
+
+/* The format's rounding of an exact value given as hi + lo, hi = fl(hi + lo)
+ * (an error-free sum).  Only when hi is exactly halfway between two format
+ * values can lo change the result: the exact value then lies off the tie,
+ * on lo's side.  Anywhere else hi and hi + lo round alike. */
+static double round_fmt_pair(double hi, double lo, int fmt) {
+  const int p = fmt == 1 ? 11 : 8, emin = fmt == 1 ? -14 : -126;
+  if (hi == 0.0) return round_fmt(lo, fmt);
+  const double q = fmt_quantum(hi, p, emin);
+  const double r = hi / q, fl = floor(r);
+  if (r - fl == 0.5 && lo != 0.0) return (lo > 0.0 ? fl + 1.0 : fl) * q;
+  return nearbyint(r) * q;
+}
+
+/* a + b as an exact pair (Knuth's two-sum). */
+static void two_sum(double a, double b, double *hi, double *lo) {
+  const double s = a + b, bb = s - a;
+  *hi = s;
+  *lo = (a - (s - bb)) + (b - bb);
+}
+
+/* One lerp step in the format: d = q(b - a), then q(f * d + a) with one
+ * rounding (a fused multiply-add in the format).  f * d is exact in a
+ * double (two format values of at most 11 bits each). */
+static double lerp_fmt(double f, double a, double b, int fmt) {
+  double hi, lo;
+  two_sum(b, -a, &hi, &lo);
+  const double d = round_fmt_pair(hi, lo, fmt);
+  two_sum(f * d, a, &hi, &lo);
+  return round_fmt_pair(hi, lo, fmt);
+}
+
+OR_EXPORT double or_round_fmt(double x, int fmt) { return round_fmt(x, fmt); }
+OR_EXPORT double or_lerp_fmt(double f, double a, double b, int fmt) { return lerp_fmt(f, a, b, fmt); }
+
+/* Trilinear value at level l in a low-precision sample format (design
+ * reading P1: the cache holds q(v * 2^-S) with S = 8 (u8) or 16 (u16),
+ * q = round to the format; the binary32 weights of trilinear32 are rounded
+ * to the format; every lerp is lerp_fmt; the result times 2^S is returned
+ * in binary32).  Order as in trilinear32: x, then y, then z. */
+static float trilinear_lp(const or_volume *v, int c, int l, const float x[3], int fmt) {
+  const int S = v->bpv == 1 ? 8 : 16;
+  double fr[3];
+  int64_t i0[3];
+  for (int a = 0; a < 3; ++a) {
+    float xl = ldexpf(x[a], -l);
+    float w = xl - 0.5f;
+    w = fminf(fmaxf(w, 0.0f), (float)(lvl_dim(v->dims[a], l) - 1));
+    i0[a] = (int64_t)w;
+    fr[a] = round_fmt((double)(w - (float)i0[a]), fmt);
+  }
+  double cv[2][2][2];
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx)
+        cv[dz][dy][dx] = round_fmt(ldexp((double)voxel(v, c, l, i0[0] + dx, i0[1] + dy, i0[2] + dz), -S), fmt);
+  double c00 = lerp_fmt(fr[0], cv[0][0][0], cv[0][0][1], fmt);
+  double c10 = lerp_fmt(fr[0], cv[0][1][0], cv[0][1][1], fmt);
+  double c01 = lerp_fmt(fr[0], cv[1][0][0], cv[1][0][1], fmt);
+  double c11 = lerp_fmt(fr[0], cv[1][1][0], cv[1][1][1], fmt);
+  double c0 = lerp_fmt(fr[1], c00, c10, fmt);
+  double c1 = lerp_fmt(fr[1], c01, c11, fmt);
+  double cc = lerp_fmt(fr[2], c0, c1, fmt);
+  return ldexpf((float)cc, S);
+}
+
 /* Same value in binary64 at a binary64 position. */
 static double trilinear64(const or_volume *v, int c, int l, const double x[3]) {
   double fr[3];
@@ -735,7 +826,7 @@ static void march_pixel(const ob_frame *f, int px, int py, int64_t n_out, const 
         has[c] = 1;
         lused[c] = found;
         if (found < s_used) s_used = found;
-        val[c] = trilinear32(v, c, found, x);
+        val[c] = v->sample_format ? trilinear_lp(v, c, found, x, v->sample_format) : trilinear32(v, c, found, x);
         val64[c] = trilinear64(v, c, found, x64);
         ++n_bs;
         h = fnv_word(h, (uint32_t)i); h = fnv_word(h, (uint32_t)c);
@@ -834,7 +925,9 @@ static void *ob_worker(void *arg) {
  * The flag outputs must be zeroed by the caller; they are OR-ed into. */
 OR_EXPORT int or_render(const or_volume *v, const uint32_t *words, const or_params *p, const int32_t *pixels,
                         int64_t n_pixels, const or_outputs *out) {
-  if (v->m < 1 || v->m > OR_MAXC || v->k < 1 || v->k > OR_MAXL || (v->bpv != 1 && v->bpv != 2)) return -1;
+  if (v->m < 1 || v->m > OR_MAXC || v->k < 1 || v->k > OR_MAXL || (v->bpv != 1 && v->bpv != 2) ||
+      v->sample_format < 0 || v->sample_format > 2)
+    return -1;
   for (int c = 0; c < v->m; ++c)
     if (p->lmin[c] < 0 || p->lmin[c] > p->lmax[c] || p->lmax[c] >= v->k) return -2;
   if (!(p->dt > 0.0f) || p->W < 1 || p->H < 1) return -3;
