@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--cache-gib", type=float, default=8.0)
     ap.add_argument("--image", type=str, default=None, help="override the image size, WxH")
     ap.add_argument("--warm-rounds", type=int, default=12, help="at most this many warm-up rounds over the orbit")
+    ap.add_argument("--precision", choices=["f32", "f16", "bf16"], default="f32",
+                    help="brick sample format: raw values with binary32 lerps, or binary16 / bfloat16 samples")
     return ap.parse_args()
 
 
@@ -206,15 +208,20 @@ def measured_hbm_peak():
 
 # ------------------------------------------------------------ CPU oracle
 
-def oracle_volume_all_resident(scene):
+SAMPLE_FORMAT = {"f32": 0, "f16": 1, "bf16": 2}
+
+
+def oracle_volume_all_resident(scene, sample_format=0):
     import oracle
     if scene.cells is not None:
         src = scene.cells.voxel_source(scene.B, capacity=1 << 21)
         vol = oracle.Volume(None, scene.spacing, scene.B, scene.leaf, (), scene.leaf_min, scene.leaf_max,
-                            provider=(scene.m, scene.k, scene.dims, scene.value_bits // 8, src.fn, src.ctx))
+                            provider=(scene.m, scene.k, scene.dims, scene.value_bits // 8, src.fn, src.ctx),
+                            sample_format=sample_format)
         vol._src = src
     else:
-        vol = oracle.Volume(scene.levels, scene.spacing, scene.B, scene.leaf, (), scene.leaf_min, scene.leaf_max)
+        vol = oracle.Volume(scene.levels, scene.spacing, scene.B, scene.leaf, (), scene.leaf_min, scene.leaf_max,
+                            sample_format=sample_format)
     vol.resident[:] = 1
     return vol
 
@@ -248,7 +255,19 @@ def oracle_rate(scene, frame, seconds, seed=0, words=None, vol=None):
     o = oracle.render(vol, words, frame, px)
     dt = time.perf_counter() - t
     return {"samples": int(o["n_eval"].sum()), "seconds": dt, "pixels": len(px), "side": side,
-            "cores": oracle.threads_used(), "vol": vol, "words": words}
+            "cores": oracle.threads_used(), "vol": vol, "words": words, "out": o, "px": px}
+
+
+def precision_check(r, gpu_image, fmt_name):
+    """The GPU image on the oracle's tile: bit-exact against the oracle's
+    binary32 (or binary16 / bfloat16 mirror) image when every desired brick
+    is resident, and its error against the binary64 image."""
+    px = r["px"]
+    g = gpu_image[px[:, 1], px[:, 0]].astype(np.float32)
+    o = r["out"]
+    return {"sample_format": fmt_name, "tile_pixels": int(len(px)),
+            "max_abs_rgba_vs_f64": float(np.abs(g.astype(np.float64) - o["rgba64"]).max()),
+            "rgba32_equal_to_oracle": bool(np.array_equal(g, o["rgba32"]))}
 
 
 # ------------------------------------------------------------------- arms
@@ -307,8 +326,9 @@ def run_ours(args, rank, world, local_rank):
     scene, label, slots = make_workload(args)
     frames = scene.frames
     W, H = frames[0].W, frames[0].H
+    sf = SAMPLE_FORMAT[args.precision]
     desc = ro.make_desc(scene.dims, scene.spacing, scene.m, scene.value_bits, scene.B, scene.k, scene.leaf, slots,
-                        max_requests=1 << 16, max_upload=2048, max_meta=1 << 20)
+                        max_requests=1 << 16, max_upload=2048, max_meta=1 << 20, sample_format=sf)
     ctx = ro.Context(desc)
     t = time.time()
     if scene.resident:
@@ -390,16 +410,20 @@ def run_ours(args, rank, world, local_rank):
     fp_bytes = 16 if scene.value_bits == 16 else 8
     bytes_per_launch = (chan * fp_bytes + W * H * 16) / len(order)
     achieved = bytes_per_launch / avg_render_s / 1e9
-    cpu = None
+    cpu = precision = None
     if world == 1 and not args.no_cpu_baseline:
-        r = oracle_rate(scene, order[0], args.cpu_seconds)
+        ro.render_frame(ctx, order[0], image)
+        gpu_img = image.cpu().numpy()
+        ctx.read_requests()
+        r = oracle_rate(scene, order[0], args.cpu_seconds, vol=oracle_volume_all_resident(scene, sf))
         cpu = {"value": r["samples"] / r["seconds"], "unit": "samples/s", "cores": r["cores"], "kind": "oracle",
                "sample": f"a seeded {r['side']}x{r['side']} pixel tile of one 1920x1080 orbit frame (every brick resident), "
                          f"{r['samples']} samples in {r['seconds']:.1f} s (second pass timed)"}
+        precision = precision_check(r, gpu_img, args.precision)
     out = {"metric": "ray samples/s", "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / len(order), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded procedural cells; no dataset)",
-           "config": dict(label, l2="inputs larger than L2 (8 GiB brick cache)",
+           "vs_baseline": None, "dtype": args.precision, "data": "synthetic (seeded procedural cells; no dataset)",
+           "config": dict(label, l2="inputs larger than L2 (8 GiB brick cache)", precision=args.precision,
                           parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                           render_ms_avg=round(avg_render_s * 1000, 3),
                           channel_samples_per_step=chan // len(order), samples_per_step=samples // len(order),
@@ -412,7 +436,8 @@ def run_ours(args, rank, world, local_rank):
            "e2e": {"value": samples_all / e2e_s, "unit": "samples/s",
                    "h2d_bytes_per_step": lut_bytes, "d2h_bytes_per_step": W * H * 16 + req_bytes // len(order)},
            "gpu_launches": 9 * len(order),
-           "cpu_baseline": cpu}
+           "cpu_baseline": cpu,
+           "precision": precision}
     print(json.dumps(out), flush=True)
     ctx.close()
     return 0
@@ -438,8 +463,10 @@ def run_views(args, rank, world, local_rank):
     frames = scene.frames
     slots = len(scene.all_bricks())
     max_tiles = max(batch_tiles(frames, w) for w in (1, 2, 4, 8, 16, 32))
+    sf = SAMPLE_FORMAT[args.precision]
     desc = ro.make_desc(scene.dims, scene.spacing, scene.m, scene.value_bits, scene.B, scene.k, scene.leaf, slots,
-                        max_requests=1 << 16, max_upload=2048, max_meta=1 << 20, max_batch_tiles=max_tiles)
+                        max_requests=1 << 16, max_upload=2048, max_meta=1 << 20, max_batch_tiles=max_tiles,
+                        sample_format=sf)
     ctx = ro.Context(desc)
     from paper_2309_04393_gb300 import loader
     ctx.update_residency_octree(loader.meta_rows(scene.leaf_min, scene.leaf_max))
@@ -537,22 +564,28 @@ def run_views(args, rank, world, local_rank):
     peak, peak_kind = measured_hbm_peak()
     avg_render_s = float(np.mean(render_ms)) / 1000.0
     achieved = (chan * 16 + pixels * 16) / avg_render_s / 1e9
-    cpu = None
+    cpu = precision = None
     if world == 1 and not args.no_cpu_baseline:
-        big = next(f for f in frames if f.W == 1920)
-        r = oracle_rate(scene, big, args.cpu_seconds)
+        bi = next(i for i, f in enumerate(frames) if f.W == 1920)
+        big = frames[bi]
+        ctx.render_batch(views, tfs, tile_w=tile_w, order=order)
+        gpu_img = images[bi].cpu().numpy()
+        ctx.read_requests()
+        r = oracle_rate(scene, big, args.cpu_seconds, vol=oracle_volume_all_resident(scene, sf))
+        precision = precision_check(r, gpu_img, args.precision)
         cpu = {"value": r["samples"] / r["seconds"], "unit": "samples/s", "cores": r["cores"], "kind": "oracle",
                "sample": f"a seeded {r['side']}x{r['side']} pixel tile of one 1920x1080 view (every brick resident), "
                          f"{r['samples']} samples in {r['seconds']:.1f} s (second pass timed)"}
     n_steps = args.steps * world
     out = {"metric": "ray samples/s", "value": samples_all / (total_ms / 1000.0), "unit": "samples/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
            "data": "synthetic (seeded procedural cells; no dataset)",
            "config": {"workload": "views64: 64 seeded perspective views, sizes uniform in {256^2, 512^2, 1024x768, "
                                   "1920x1080}, over a 16-channel 1024x1024x64 u16 cell slab (spacing 1:1:4), "
                                   "32^3 bricks, 5 levels, every requested brick resident",
                       "views": len(frames), "pixels_per_step": pixels, "channels": scene.m,
+                      "precision": args.precision,
                       "dims": list(scene.dims), "levels": scene.k,
                       "schedule": {"tile": [tile_w, 32 // tile_w], "order": ["view-major", "longest-first"][order],
                                    "autotune_ms": round(tune_ms, 3)},
@@ -571,7 +604,8 @@ def run_views(args, rank, world, local_rank):
            "e2e": {"value": samples_all / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": pixels * 16 + req_bytes // args.steps},
            "gpu_launches": (9 + order) * args.steps,
-           "cpu_baseline": cpu}
+           "cpu_baseline": cpu,
+           "precision": precision}
     # per batch: the whole view table (256 entries), the TF ranges and the LUTs
     out["e2e"]["h2d_bytes_per_step"] = 256 * 464 + 16 * 8 + scene.m * 256 * 16
     print(json.dumps(out), flush=True)

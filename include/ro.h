@@ -69,6 +69,13 @@ typedef enum {
  *  max_meta      leaf metadata entries per ro_update_residency_octree chunk
  *  max_batch_tiles  pixel tiles (32 pixels each) one ro_render_batch call may
  *                cover, summed over its views; 0 = no batches
+ *  sample_format 0: the cache holds the raw values and trilinear lerps run in
+ *                binary32; 1: binary16, 2: bfloat16 - the cache holds
+ *                round(v * 2^-bits) in the format (2 bytes per voxel, also
+ *                for 8-bit data), the lerps run in the format with one
+ *                rounding per step and the result times 2^bits continues in
+ *                binary32 (TF, opacity correction and compositing stay
+ *                binary32)
  * Bricks per axis at every level must be <= 256 (the 8-bit offsets of the
  * brick ID, Sec. 7). */
 typedef struct {
@@ -84,6 +91,7 @@ typedef struct {
   uint32_t max_upload;
   uint32_t max_meta;
   uint32_t max_batch_tiles;
+  uint32_t sample_format;
 } ro_desc;
 
 /* Byte sizes of the parts of the device arena (all 256-byte aligned inside
@@ -101,7 +109,7 @@ typedef struct {
   uint64_t lists;        /* request / node-request output lists + counts */
   uint64_t scratch;      /* compaction partial counts, update item lists, stats */
   uint64_t total;
-  uint64_t slot_pitch;   /* bytes per cache slot ((B+2)^3 voxels, padded) */
+  uint64_t slot_pitch;   /* bytes per cache slot ((B+2)^3 voxels of 1 or 2 bytes, padded) */
   uint64_t n_bricks;     /* bricks of the virtual hierarchy, all channels and levels */
   uint64_t n_nodes;      /* octree nodes, all depths */
   uint32_t depth;        /* octree depth D (leaves at depth D) */

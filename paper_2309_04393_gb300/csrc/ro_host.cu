@@ -73,6 +73,9 @@ ro_status make_geometry(const ro_desc* d, Geometry* g, std::string* why) {
   g->B = (int)d->brick;
   g->blog2 = ilog2(d->brick);
   g->bpv = d->value_bits / 8;
+  if (d->sample_format > 2) return fail("sample_format must be 0, 1 or 2");
+  g->sf = (int)d->sample_format;
+  g->cbpv = g->sf ? 2 : g->bpv;
   g->edge = d->brick + 2;
   g->cache_slots = d->cache_slots;
   for (int a = 0; a < 3; ++a) {
@@ -120,7 +123,7 @@ ro_status make_geometry(const ro_desc* d, Geometry* g, std::string* why) {
   }
   g->node_off[D + 1] = noff;
   g->n_nodes = noff;
-  const uint64_t slot_bytes = (uint64_t)g->edge * g->edge * g->edge * g->bpv;
+  const uint64_t slot_bytes = (uint64_t)g->edge * g->edge * g->edge * g->cbpv;
   g->slot_pitch = (uint32_t)align_up(slot_bytes, kAlign);
   return RO_OK;
 }
@@ -521,6 +524,9 @@ ro_status ro_upload_bricks(ro_ctx* c, uint32_t n, const uint32_t* ids, const voi
   a.cache_slots = c->desc.cache_slots;
   a.n_bricks = c->g.n_bricks;
   a.err = c->err;
+  a.sf = c->g.sf;
+  a.bpv = c->g.bpv;
+  a.n_el = c->g.edge * c->g.edge * c->g.edge;
   RO_TRY(cuda_check(c, ro::launch_scatter(a, st), "ro_upload_bricks: scatter"));
   // the caller's host buffers may be reused once the copies have landed
   RO_TRY(wait_stream(c, "ro_upload_bricks"));

@@ -20,6 +20,8 @@ struct Geometry {
   float spacing[3];
   float dimm[3];              // largest binary32 value below dims0 (position clamp)
   int m, mp, k, B, blog2, bpv;
+  int sf;                     // sample format: 0 raw / binary32 lerps, 1 binary16, 2 bfloat16
+  int cbpv;                   // bytes per voxel in the cache (2 when sf != 0)
   int leaf_log2[3];
   int D;                      // octree depth (leaves at depth D)
   int ldims[kMaxL][3];        // level dims
@@ -133,6 +135,8 @@ struct ScatterArgs {
   uint32_t cache_slots;
   uint64_t n_bricks;
   uint32_t* err;
+  int sf, bpv;               // sample format; raw bytes per voxel in the staging area
+  uint32_t n_el;             // voxels per brick ((B+2)^3)
 };
 
 struct CompactArgs {
@@ -165,6 +169,9 @@ enum : uint32_t { kErrNone = 0, kErrNodeIndex = 1, kErrPageIndex = 2, kErrSlot =
 cudaError_t launch_prefix(const PrefixArgs& a, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out);
 cudaError_t launch_render_batch(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out);
+// the same launches for the binary16 / bfloat16 sample formats (g.sf != 0)
+cudaError_t launch_render_lp(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out);
+cudaError_t launch_render_batch_lp(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out);
 // Tile order by descending recorded cost (counting sort over log-scale
 // buckets; ties in any order).
 cudaError_t launch_cost_order(const uint32_t* cost, uint32_t n_tiles, uint32_t* order, cudaStream_t s);

@@ -47,7 +47,8 @@ size_t render_smem_bytes(int mp) {
 }
 
 cudaError_t launch_render(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out) {
-  return launch_any<false>(a, debug, s, blocks_out);
+  if (a.g.sf != 0) return launch_render_lp(a, debug, s, blocks_out);
+  return launch_any<false, 0>(a, debug, s, blocks_out);
 }
 
 cudaError_t launch_prefix(const PrefixArgs& a, cudaStream_t s) {

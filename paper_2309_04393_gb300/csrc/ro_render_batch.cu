@@ -46,7 +46,8 @@ __global__ void __launch_bounds__(kOrderThreads) cost_order_kernel(const uint32_
 }  // namespace
 
 cudaError_t launch_render_batch(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out) {
-  return launch_any<true>(a, debug, s, blocks_out);
+  if (a.g.sf != 0) return launch_render_batch_lp(a, debug, s, blocks_out);
+  return launch_any<true, 0>(a, debug, s, blocks_out);
 }
 
 cudaError_t launch_cost_order(const uint32_t* cost, uint32_t n_tiles, uint32_t* order, cudaStream_t s) {

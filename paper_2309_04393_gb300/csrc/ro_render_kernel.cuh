@@ -10,6 +10,9 @@
 // binary32 with the operation order of the design contract (built with
 // --fmad=false: every fused multiply-add below is an explicit fmaf).
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "ro_internal.h"
 
 namespace ro {
@@ -127,11 +130,44 @@ __device__ __forceinline__ void node_coords(const Geometry& g, int d, const floa
 // are computed once per level and sample; the fetch reads one channel's
 // corners from its owner's slot and lerps along x, then y, then z.
 struct TriCoords {
-  int idx;     // element offset of the lower corner inside the apron slot
-  float f[3];  // lerp weights
+  int idx;        // element offset of the lower corner inside the apron slot
+  float f[3];     // lerp weights (binary32)
+  uint32_t h[3];  // the weights in the sample format (reading P1): (f0, f0), (f1, f1), f2
 };
 
-template <int EC>
+// Two 16-bit values packed into one 32-bit register, low half first.
+__device__ __forceinline__ uint32_t pack2(uint32_t lo, uint32_t hi) { return __byte_perm(lo, hi, 0x5410); }
+
+__device__ __forceinline__ __half __low2half_any(__half2 v) { return __low2half(v); }
+__device__ __forceinline__ __half __high2half_any(__half2 v) { return __high2half(v); }
+__device__ __forceinline__ __nv_bfloat16 __low2half_any(__nv_bfloat162 v) { return __low2bfloat16(v); }
+__device__ __forceinline__ __nv_bfloat16 __high2half_any(__nv_bfloat162 v) { return __high2bfloat16(v); }
+
+template <int SF> struct Fmt;
+template <> struct Fmt<1> {
+  using T = __half;
+  using T2 = __half2;
+  static __device__ __forceinline__ uint32_t dup(float f) {
+    const __half2 v = __float2half2_rn(f);
+    return *reinterpret_cast<const uint32_t*>(&v);
+  }
+  static __device__ __forceinline__ T2 v2(uint32_t u) { return *reinterpret_cast<const T2*>(&u); }
+  static __device__ __forceinline__ uint32_t u2(T2 h) { return *reinterpret_cast<const uint32_t*>(&h); }
+  static __device__ __forceinline__ float to_float(T h) { return __half2float(h); }
+};
+template <> struct Fmt<2> {
+  using T = __nv_bfloat16;
+  using T2 = __nv_bfloat162;
+  static __device__ __forceinline__ uint32_t dup(float f) {
+    const __nv_bfloat162 v = __float2bfloat162_rn(f);
+    return *reinterpret_cast<const uint32_t*>(&v);
+  }
+  static __device__ __forceinline__ T2 v2(uint32_t u) { return *reinterpret_cast<const T2*>(&u); }
+  static __device__ __forceinline__ uint32_t u2(T2 h) { return *reinterpret_cast<const uint32_t*>(&h); }
+  static __device__ __forceinline__ float to_float(T h) { return __bfloat162float(h); }
+};
+
+template <int EC, int SF>
 __device__ __forceinline__ void tri_coords(const Geometry& g, int l, const float (&x)[3], TriCoords& tc) {
   const int E = EC ? EC : (int)g.edge;  // apron-slot edge, a compile-time constant for 32^3 bricks
   int li[3];
@@ -146,43 +182,71 @@ __device__ __forceinline__ void tri_coords(const Geometry& g, int l, const float
     li[k] = i0 - (b * g.B - 1);
   }
   tc.idx = (li[2] * E + li[1]) * E + li[0];
+  if constexpr (SF != 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) tc.h[k] = Fmt<SF>::dup(tc.f[k]);
+  }
 }
 
-template <int BPV, int EC>
+template <int BPV, int EC, int SF>
 __device__ __forceinline__ float tri_fetch(const RenderArgs& a, uint32_t slot, const TriCoords& tc) {
   const Geometry& g = a.g;
   const int E = EC ? EC : (int)g.edge;
   const uint8_t* base = a.cache + (size_t)slot * g.slot_pitch;
   const int idx = tc.idx;
-  float v[8];
-  if constexpr (BPV == 1) {
-    const uint8_t* p = base + idx;
-    v[0] = (float)__ldg(p);
-    v[1] = (float)__ldg(p + 1);
-    v[2] = (float)__ldg(p + E);
-    v[3] = (float)__ldg(p + E + 1);
-    v[4] = (float)__ldg(p + E * E);
-    v[5] = (float)__ldg(p + E * E + 1);
-    v[6] = (float)__ldg(p + E * E + E);
-    v[7] = (float)__ldg(p + E * E + E + 1);
-  } else {
+  if constexpr (SF != 0) {
+    // the slot holds the format's values; x lerps on the pairs (v0, v2) /
+    // (v1, v3) and (v4, v6) / (v5, v7), the y lerp on (c00, c01) / (c10,
+    // c11), the z lerp alone: each d = b - a, then fma(f, d, a), one
+    // rounding per operation as in the format's arithmetic
+    using F = Fmt<SF>;
     const uint16_t* p = reinterpret_cast<const uint16_t*>(base) + idx;
-    v[0] = (float)__ldg(p);
-    v[1] = (float)__ldg(p + 1);
-    v[2] = (float)__ldg(p + E);
-    v[3] = (float)__ldg(p + E + 1);
-    v[4] = (float)__ldg(p + E * E);
-    v[5] = (float)__ldg(p + E * E + 1);
-    v[6] = (float)__ldg(p + E * E + E);
-    v[7] = (float)__ldg(p + E * E + E + 1);
+    const uint32_t r0 = __ldg(p), r1 = __ldg(p + 1), r2 = __ldg(p + E), r3 = __ldg(p + E + 1);
+    const uint32_t r4 = __ldg(p + E * E), r5 = __ldg(p + E * E + 1), r6 = __ldg(p + E * E + E),
+                   r7 = __ldg(p + E * E + E + 1);
+    const typename F::T2 A = F::v2(pack2(r0, r2)), B = F::v2(pack2(r1, r3));
+    const typename F::T2 A2 = F::v2(pack2(r4, r6)), B2 = F::v2(pack2(r5, r7));
+    const typename F::T2 f0 = F::v2(tc.h[0]), f1 = F::v2(tc.h[1]);
+    const typename F::T2 cx0 = __hfma2(f0, __hsub2(B, A), A);      // (c00, c10)
+    const typename F::T2 cx1 = __hfma2(f0, __hsub2(B2, A2), A2);   // (c01, c11)
+    const uint32_t u0 = F::u2(cx0), u1 = F::u2(cx1);
+    const typename F::T2 lo = F::v2(pack2(u0, u1)), hi = F::v2(pack2(u0 >> 16, u1 >> 16));
+    const typename F::T2 cy = __hfma2(f1, __hsub2(hi, lo), lo);    // (c0, c1)
+    const typename F::T c0 = __low2half_any(cy), c1 = __high2half_any(cy);
+    const typename F::T f2 = __low2half_any(F::v2(tc.h[2]));
+    const typename F::T c = __hfma(f2, __hsub(c1, c0), c0);
+    return F::to_float(c) * (BPV == 1 ? 256.0f : 65536.0f);
+  } else {
+    float v[8];
+    if constexpr (BPV == 1) {
+      const uint8_t* p = base + idx;
+      v[0] = (float)__ldg(p);
+      v[1] = (float)__ldg(p + 1);
+      v[2] = (float)__ldg(p + E);
+      v[3] = (float)__ldg(p + E + 1);
+      v[4] = (float)__ldg(p + E * E);
+      v[5] = (float)__ldg(p + E * E + 1);
+      v[6] = (float)__ldg(p + E * E + E);
+      v[7] = (float)__ldg(p + E * E + E + 1);
+    } else {
+      const uint16_t* p = reinterpret_cast<const uint16_t*>(base) + idx;
+      v[0] = (float)__ldg(p);
+      v[1] = (float)__ldg(p + 1);
+      v[2] = (float)__ldg(p + E);
+      v[3] = (float)__ldg(p + E + 1);
+      v[4] = (float)__ldg(p + E * E);
+      v[5] = (float)__ldg(p + E * E + 1);
+      v[6] = (float)__ldg(p + E * E + E);
+      v[7] = (float)__ldg(p + E * E + E + 1);
+    }
+    const float c00 = fmaf(tc.f[0], v[1] - v[0], v[0]);
+    const float c10 = fmaf(tc.f[0], v[3] - v[2], v[2]);
+    const float c01 = fmaf(tc.f[0], v[5] - v[4], v[4]);
+    const float c11 = fmaf(tc.f[0], v[7] - v[6], v[6]);
+    const float c0 = fmaf(tc.f[1], c10 - c00, c00);
+    const float c1 = fmaf(tc.f[1], c11 - c01, c01);
+    return fmaf(tc.f[2], c1 - c0, c0);
   }
-  const float c00 = fmaf(tc.f[0], v[1] - v[0], v[0]);
-  const float c10 = fmaf(tc.f[0], v[3] - v[2], v[2]);
-  const float c01 = fmaf(tc.f[0], v[5] - v[4], v[4]);
-  const float c11 = fmaf(tc.f[0], v[7] - v[6], v[6]);
-  const float c0 = fmaf(tc.f[1], c10 - c00, c00);
-  const float c1 = fmaf(tc.f[1], c11 - c01, c01);
-  return fmaf(tc.f[2], c1 - c0, c0);
 }
 
 // TF lookup (R16) and opacity correction for a step of 2^s (R12): returns
@@ -264,7 +328,7 @@ __device__ __forceinline__ const ViewArgs& view_of(const RenderArgs& a, const Vi
   else return a.v;
 }
 
-template <int MP, int BPV, int EC, bool DBG, bool BATCH>
+template <int MP, int BPV, int EC, bool DBG, bool BATCH, int SF>
 __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_constant__ RenderArgs a) {
   extern __shared__ float4 smem[];
   float4* s_lut = smem;
@@ -627,9 +691,9 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
       } else {
         if ((int)lb != tl) {  // channels at one level share the corner offset and weights
           tl = (int)lb;
-          tri_coords<EC>(g, tl, x, tc);
+          tri_coords<EC, SF>(g, tl, x, tc);
         }
-        val = tri_fetch<BPV, EC>(a, sel & kSelMask, tc);
+        val = tri_fetch<BPV, EC, SF>(a, sel & kSelMask, tc);
         if constexpr (DBG) {
           const int bsh = g.blog2 + (int)lb;
           const uint32_t bx = (uint32_t)(x[0] * pow2f(-bsh)), by = (uint32_t)(x[1] * pow2f(-bsh)),
@@ -673,10 +737,10 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
   }
 }
 
-template <int MP, int BPV, int EC, bool DBG, bool BATCH>
+template <int MP, int BPV, int EC, bool DBG, bool BATCH, int SF>
 cudaError_t launch_one(const RenderArgs& a, cudaStream_t s, int* blocks_out) {
   const size_t smem = render_smem_bytes(MP);
-  auto kern = render_kernel<MP, BPV, EC, DBG, BATCH>;
+  auto kern = render_kernel<MP, BPV, EC, DBG, BATCH, SF>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
@@ -692,29 +756,29 @@ cudaError_t launch_one(const RenderArgs& a, cudaStream_t s, int* blocks_out) {
   return cudaGetLastError();
 }
 
-template <int MP, int BPV, int EC, bool BATCH>
+template <int MP, int BPV, int EC, bool BATCH, int SF>
 cudaError_t launch_ec(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out) {
-  return debug ? launch_one<MP, BPV, EC, true, BATCH>(a, s, blocks_out) : launch_one<MP, BPV, EC, false, BATCH>(a, s, blocks_out);
+  return debug ? launch_one<MP, BPV, EC, true, BATCH, SF>(a, s, blocks_out) : launch_one<MP, BPV, EC, false, BATCH, SF>(a, s, blocks_out);
 }
 
-template <int MP, int BPV, bool BATCH>
+template <int MP, int BPV, bool BATCH, int SF>
 cudaError_t launch_mp(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out) {
-  return a.g.edge == 34 ? launch_ec<MP, BPV, 34, BATCH>(a, debug, s, blocks_out) : launch_ec<MP, BPV, 0, BATCH>(a, debug, s, blocks_out);
+  return a.g.edge == 34 ? launch_ec<MP, BPV, 34, BATCH, SF>(a, debug, s, blocks_out) : launch_ec<MP, BPV, 0, BATCH, SF>(a, debug, s, blocks_out);
 }
 
-template <int MP, bool BATCH>
+template <int MP, bool BATCH, int SF>
 cudaError_t launch_bpv(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out) {
-  return a.g.bpv == 1 ? launch_mp<MP, 1, BATCH>(a, debug, s, blocks_out) : launch_mp<MP, 2, BATCH>(a, debug, s, blocks_out);
+  return a.g.bpv == 1 ? launch_mp<MP, 1, BATCH, SF>(a, debug, s, blocks_out) : launch_mp<MP, 2, BATCH, SF>(a, debug, s, blocks_out);
 }
 
-template <bool BATCH>
+template <bool BATCH, int SF>
 cudaError_t launch_any(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out) {
   switch (a.g.mp) {
-    case 1: return launch_bpv<1, BATCH>(a, debug, s, blocks_out);
-    case 2: return launch_bpv<2, BATCH>(a, debug, s, blocks_out);
-    case 4: return launch_bpv<4, BATCH>(a, debug, s, blocks_out);
-    case 8: return launch_bpv<8, BATCH>(a, debug, s, blocks_out);
-    case 16: return launch_bpv<16, BATCH>(a, debug, s, blocks_out);
+    case 1: return launch_bpv<1, BATCH, SF>(a, debug, s, blocks_out);
+    case 2: return launch_bpv<2, BATCH, SF>(a, debug, s, blocks_out);
+    case 4: return launch_bpv<4, BATCH, SF>(a, debug, s, blocks_out);
+    case 8: return launch_bpv<8, BATCH, SF>(a, debug, s, blocks_out);
+    case 16: return launch_bpv<16, BATCH, SF>(a, debug, s, blocks_out);
     default: return cudaErrorInvalidValue;
   }
 }

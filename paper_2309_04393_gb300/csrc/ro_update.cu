@@ -8,6 +8,9 @@
 // (INVALID if any child is), depth by depth from the leaves up.  Every write
 // recomputes a word from the final page table / children, so concurrent
 // writers of the same word store the same value: no atomics are needed.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "ro_internal.h"
 
 namespace ro {
@@ -21,14 +24,53 @@ __global__ void fill_words_kernel(uint32_t* __restrict__ w, uint64_t n, uint32_t
 // Copy each staged brick into its slot (16-byte vectors; slot_pitch is a
 // multiple of 256) and write the page-table entries of inserted (slot + 1)
 // and evicted (0) bricks.
+// A raw value in the cache's sample format (reading P1): round(v * 2^-S) to
+// binary16 (sf 1) or bfloat16 (sf 2), S = 8 or 16 bits, nearest even; the
+// scaling by a power of two is exact in binary32.
+__device__ __forceinline__ uint16_t to_format(uint32_t v, int sf, int bpv) {
+  const float x = (float)v * (bpv == 1 ? 0.00390625f : 1.52587890625e-05f);
+  if (sf == 1) return __half_as_ushort(__float2half_rn(x));
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
 __global__ void __launch_bounds__(256) scatter_kernel(const __grid_constant__ ScatterArgs a) {
   const uint32_t b = blockIdx.x;
   if (b < a.n_ins) {
     const uint32_t slot = a.ins_slot[b];
     if (slot >= a.cache_slots) { if (threadIdx.x == 0) *a.err = kErrSlot; return; }
-    const uint4* src = reinterpret_cast<const uint4*>(a.staging + (size_t)b * a.slot_pitch);
-    uint4* dst = reinterpret_cast<uint4*>(a.cache + (size_t)slot * a.slot_pitch);
-    for (uint32_t i = threadIdx.x; i < a.slot_pitch / 16; i += blockDim.x) dst[i] = src[i];
+    const uint8_t* srow = a.staging + (size_t)b * a.slot_pitch;
+    uint8_t* drow = a.cache + (size_t)slot * a.slot_pitch;
+    if (a.sf == 0) {
+      const uint4* src = reinterpret_cast<const uint4*>(srow);
+      uint4* dst = reinterpret_cast<uint4*>(drow);
+      for (uint32_t i = threadIdx.x; i < a.slot_pitch / 16; i += blockDim.x) dst[i] = src[i];
+    } else {
+      // eight voxels per step: raw u16 (16 bytes) or u8 (8 bytes) in, 16 bytes out
+      uint16_t* dst = reinterpret_cast<uint16_t*>(drow);
+      const uint32_t n8 = a.n_el / 8;
+      for (uint32_t i = threadIdx.x; i < n8; i += blockDim.x) {
+        uint32_t v[8];
+        if (a.bpv == 2) {
+          const uint4 r = reinterpret_cast<const uint4*>(srow)[i];
+          const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) { v[2 * q] = w[q] & 0xFFFFu; v[2 * q + 1] = w[q] >> 16; }
+        } else {
+          const uint2 r = reinterpret_cast<const uint2*>(srow)[i];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) { v[q] = (r.x >> (8 * q)) & 0xFFu; v[4 + q] = (r.y >> (8 * q)) & 0xFFu; }
+        }
+        uint32_t o[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          o[q] = (uint32_t)to_format(v[2 * q], a.sf, a.bpv) | ((uint32_t)to_format(v[2 * q + 1], a.sf, a.bpv) << 16);
+        reinterpret_cast<uint4*>(dst)[i] = make_uint4(o[0], o[1], o[2], o[3]);
+      }
+      for (uint32_t i = n8 * 8 + threadIdx.x; i < a.n_el; i += blockDim.x) {
+        const uint32_t v = a.bpv == 2 ? reinterpret_cast<const uint16_t*>(srow)[i] : srow[i];
+        dst[i] = to_format(v, a.sf, a.bpv);
+      }
+    }
     if (threadIdx.x == 0) {
       const uint32_t pi = a.ins_index[b];
       if (pi >= a.n_bricks) *a.err = kErrPageIndex;

@@ -37,7 +37,7 @@ class Desc(ctypes.Structure):
                 ("value_bits", ctypes.c_uint32), ("brick", ctypes.c_uint32), ("levels", ctypes.c_uint32),
                 ("leaf_extent", ctypes.c_uint32 * 3), ("cache_slots", ctypes.c_uint32),
                 ("max_requests", ctypes.c_uint32), ("max_upload", ctypes.c_uint32), ("max_meta", ctypes.c_uint32),
-                ("max_batch_tiles", ctypes.c_uint32)]
+                ("max_batch_tiles", ctypes.c_uint32), ("sample_format", ctypes.c_uint32)]
 
 
 class Sizes(ctypes.Structure):
@@ -121,7 +121,8 @@ def load(build_if_missing: bool = True):
 
 
 def make_desc(dims, spacing, channels, value_bits, brick, levels, leaf_extent, cache_slots, max_requests=65536,
-              max_upload=1024, max_meta=65536, max_batch_tiles=0) -> Desc:
+              max_upload=1024, max_meta=65536, max_batch_tiles=0, sample_format=0) -> Desc:
+    """sample_format: 0 raw values with binary32 lerps, 1 binary16, 2 bfloat16."""
     d = Desc()
     d.dims[:] = [int(v) for v in dims]
     d.spacing[:] = [float(v) for v in spacing]
@@ -130,6 +131,7 @@ def make_desc(dims, spacing, channels, value_bits, brick, levels, leaf_extent, c
     d.cache_slots, d.max_requests, d.max_upload, d.max_meta = int(cache_slots), int(max_requests), int(max_upload), \
         int(max_meta)
     d.max_batch_tiles = int(max_batch_tiles)
+    d.sample_format = int(sample_format)
     return d
 
 
