@@ -190,7 +190,7 @@ def recorded_traffic(args):
             with open(os.path.join(ROOT, f), "rb") as fh:
                 h.update(fh.read())
         default = (args.workload == "cells16" and args.image is None and args.cache_gib == 8.0 and args.arc == 30.0
-                   and args.lod_bias is None and args.radius is None)
+                   and args.lod_bias is None and args.radius is None and args.precision == "f32")
         if h.hexdigest() == rec["source_sha256"] and default:
             return int(rec["dram_read_bytes_per_launch"]) + int(rec["dram_write_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
