@@ -1,0 +1,73 @@
+"""Pins of the compensator oracle: the upsample reproduces linear fields
+exactly (trilinear interpolation is exact on them) and constants; the
+convolution of an identity or a one-tap shift kernel is the input itself or
+the shifted input with zero fill; the hand-written gradients match finite
+differences of the loss; bfloat16 rounding at exact ties goes to even."""
+import numpy as np
+import pytest
+
+from oracle import compensator as mc
+
+
+@pytest.mark.parametrize("octant", [(0, 0, 0), (1, 0, 1), (1, 1, 1)])
+def test_upsample_reproduces_linear_fields(octant):
+    z, y, x = np.meshgrid(np.arange(34), np.arange(34), np.arange(34), indexing="ij")
+    a, bx, by, bz = 1000.0, 3.0, -2.0, 5.0
+    slot = a + bx * (x - 1) + by * (y - 1) + bz * (z - 1)          # level-1 voxel u = slot index - 1
+    up = mc.upsample(slot, octant)
+    X = np.arange(34) - 1 + 32 * np.array(octant)[:, None]          # per axis (x, y, z)
+    u = (X + 0.5) / 2 - 0.5
+    want = a + bx * u[0][None, None, :] + by * u[1][None, :, None] + bz * u[2][:, None, None]
+    assert np.allclose(up, want, rtol=0, atol=1e-9)
+    assert np.allclose(mc.upsample(np.full((34, 34, 34), 77.0), octant), 77.0, atol=0)
+
+
+def test_conv_identity_and_shift_kernels():
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(5, 6, 7, 3))
+    W = np.zeros((27, 3, 3))
+    W[13] = np.eye(3)                                               # centre tap
+    b = np.array([0.5, -1.0, 2.0])
+    assert np.allclose(mc.conv3(x, W, b), x + b, atol=1e-12)
+    W = np.zeros((27, 3, 3))
+    W[(2 * 3 + 1) * 3 + 1] = np.eye(3)                              # tap dz = +1: out[z] = x[z + 1]
+    out = mc.conv3(x, W, np.zeros(3))
+    assert np.allclose(out[:-1], x[1:], atol=1e-12) and np.all(out[-1] == 0)
+
+
+def test_gradients_match_finite_differences():
+    rng = np.random.default_rng(2)
+    params = [(W * 30.0, rng.normal(0, 0.05, b.shape)) for W, b in mc.init_params(3)]
+    x0 = rng.uniform(0.0, 1.0, (4, 5, 4))
+    target = x0 + rng.normal(0.0, 0.1, x0.shape)
+    loss, grads = mc.loss_and_grads(params, x0, target)
+    h = 1e-6
+    for li in range(4):
+        W, b = params[li]
+        for _ in range(6):
+            t, ci, co = rng.integers(27), rng.integers(W.shape[1]), rng.integers(W.shape[2])
+            for s in (+1, -1):
+                Wp = W.copy()
+                Wp[t, ci, co] += s * h
+                p2 = list(params)
+                p2[li] = (Wp, b)
+                if s > 0:
+                    lp = mc.loss_and_grads(p2, x0, target)[0]
+                else:
+                    lm = mc.loss_and_grads(p2, x0, target)[0]
+            num = (lp - lm) / (2 * h)
+            assert abs(num - grads[li][0][t, ci, co]) <= 1e-6 + 1e-4 * abs(num)
+        co = rng.integers(b.shape[0])
+        bp, bm = b.copy(), b.copy()
+        bp[co] += h
+        bm[co] -= h
+        p2, p3 = list(params), list(params)
+        p2[li], p3[li] = (W, bp), (W, bm)
+        num = (mc.loss_and_grads(p2, x0, target)[0] - mc.loss_and_grads(p3, x0, target)[0]) / (2 * h)
+        assert abs(num - grads[li][1][co]) <= 1e-6 + 1e-4 * abs(num)
+
+
+def test_bf16_ties_to_even():
+    assert mc.bf16(1.0 + 2.0 ** -8) == 1.0                         # halfway, to even
+    assert mc.bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6          # halfway, to even (up)
+    assert mc.bf16(1.0 + 2.0 ** -8 + 2.0 ** -20) == 1.0 + 2.0 ** -7  # above halfway
