@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 SO = os.path.join(OUT_DIR, "libro.so")
 SOURCES = ["ro_host.cu", "ro_render.cu", "ro_render_lp.cu", "ro_render_batch.cu", "ro_render_batch_lp.cu", "ro_update.cu",
-           "ro_compact.cu", "ro_noalloc.cu"]
+           "ro_compact.cu", "ro_noalloc.cu", "ro_mc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-prec-div=true", "-prec-sqrt=true", "-ftz=false",
          "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

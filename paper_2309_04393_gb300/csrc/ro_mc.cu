@@ -1,0 +1,473 @@
+// Learned miss compensator (include/ro_mc.h): upsample of a level-1 apron
+// slot to the level-0 apron grid, a residual 3D CNN (four 3x3x3 'same'
+// convolutions, 1 -> 32 -> 32 -> 32 -> 1), its gradients and Adam.
+//
+// Activations are channels-last binary32 grids of 34^3 voxels.  The weights
+// take part as bfloat16 values (the parameters are rounded once per update
+// into an effective binary32 copy); every sum is binary32.  A convolution
+// block computes an 8 x 8 x 4 voxel tile for all output channels from a
+// shared-memory copy of the input tile with its one-voxel halo (zero outside
+// the grid) and of the layer's weights; the input-gradient pass is the same
+// kernel on the spatially flipped, channel-transposed weights.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ro_mc.h"
+
+namespace {
+
+constexpr int EG = RO_MC_EDGE;        // grid edge
+constexpr int NV = RO_MC_VOXELS;      // voxels per grid
+constexpr int HID = 32;               // hidden channels
+constexpr int TX = 8, TY = 8, TZ = 4; // output tile of one block
+constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
+constexpr int kConvThreads = TX * TY * TZ;
+constexpr int kTilesX = (EG + TX - 1) / TX, kTilesY = (EG + TY - 1) / TY, kTilesZ = (EG + TZ - 1) / TZ;
+
+// layer shapes and offsets of W and b in the parameter vector
+constexpr int kCin[4] = {1, HID, HID, HID};
+constexpr int kCout[4] = {HID, HID, HID, 1};
+constexpr int kWOff[4] = {0, 896, 28576, 56256};        // W of layer i
+constexpr int kBOff[4] = {864, 28544, 56224, 57120};    // b of layer i (after W)
+static_assert(kBOff[3] + 1 == RO_MC_PARAMS, "parameter layout");
+
+// channel stride of a shared-memory tile: padded so that neighbouring
+// voxels of one channel fall in different banks
+__host__ __device__ constexpr int pad_stride(int c) { return c > 1 ? c + 1 : 1; }
+
+enum : int { kEpiNone = 0, kEpiRelu = 1, kEpiResidual = 2, kEpiMask = 3 };
+
+// ------------------------------------------------------------- upsample
+// Level-0 voxel X (relative to the child's apron origin) sits at level-1
+// coordinate u = (X - 1 + 32 o + 0.5) / 2 - 0.5 relative to the parent's
+// first interior voxel; slot index = floor(u) + 1; weights 0.25 / 0.75.
+__global__ void upsample_kernel(const uint16_t* __restrict__ slots, const uint32_t* __restrict__ octants,
+                                float* __restrict__ x0) {
+  const int n = blockIdx.x;
+  const uint16_t* s = slots + (size_t)n * NV;
+  const uint32_t o = octants[n];
+  const int oc[3] = {(int)(o & 1u), (int)((o >> 1) & 1u), (int)((o >> 2) & 1u)};
+  for (int v = threadIdx.x; v < NV; v += blockDim.x) {
+    const int X[3] = {v % EG, (v / EG) % EG, v / (EG * EG)};
+    int i0[3];
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int q = X[a] - 1 + 32 * oc[a];            // level-0 voxel relative to the parent's x2 origin
+      // u = (q + 0.5) / 2 - 0.5 = q / 2 - 0.25: even q -> (q/2 - 1) + 0.75, odd q -> (q - 1)/2 + 0.25
+      const int fl = (q >= 0 ? q : q - 1) / 2;        // floor(q / 2)
+      if (q & 1) { i0[a] = fl; f[a] = 0.25f; }
+      else { i0[a] = fl - 1; f[a] = 0.75f; }
+    }
+    float acc = 0.0f;
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+          const float w = (dz ? f[2] : 1.0f - f[2]) * (dy ? f[1] : 1.0f - f[1]) * (dx ? f[0] : 1.0f - f[0]);
+          const int idx = ((i0[2] + 1 + dz) * EG + (i0[1] + 1 + dy)) * EG + (i0[0] + 1 + dx);
+          acc = fmaf(w, (float)s[idx], acc);
+        }
+    x0[(size_t)n * NV + v] = acc * 1.52587890625e-05f;  // 2^-16
+  }
+}
+
+// ---------------------------------------------------------- convolution
+// out[v][co] = epi(sum_tap sum_ci in[v + off(tap)][ci] * w[tap][ci][co] + b[co])
+// aux: the residual x0 (kEpiResidual, COUT = 1) or the activation whose
+// positive entries pass the gradient (kEpiMask).
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(kConvThreads) conv_kernel(const float* __restrict__ in, const float* __restrict__ w,
+                                                           const float* __restrict__ bias, float* __restrict__ out,
+                                                           const float* __restrict__ aux) {
+  extern __shared__ float sm[];
+  constexpr int SC = pad_stride(CIN);
+  float* s_in = sm;                              // HZ * HY * HX * SC
+  float* s_w = sm + HZ * HY * HX * SC;           // 27 * CIN * COUT
+  const int tile = blockIdx.x, n = blockIdx.y;
+  const int x0t = (tile % kTilesX) * TX, y0t = ((tile / kTilesX) % kTilesY) * TY, z0t = (tile / (kTilesX * kTilesY)) * TZ;
+  const float* src = in + (size_t)n * NV * CIN;
+  for (int q = threadIdx.x; q < HZ * HY * HX * CIN; q += blockDim.x) {
+    const int c = q % CIN, p = q / CIN;
+    const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
+    const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
+    float val = 0.0f;
+    if (gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
+      val = src[((size_t)(gz * EG + gy) * EG + gx) * CIN + c];
+    s_in[p * SC + c] = val;
+  }
+  for (int q = threadIdx.x; q < 27 * CIN * COUT; q += blockDim.x) s_w[q] = w[q];
+  __syncthreads();
+  const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+  const int gx = x0t + tx, gy = y0t + ty, gz = z0t + tz;
+  float acc[COUT];
+#pragma unroll
+  for (int co = 0; co < COUT; ++co) acc[co] = 0.0f;
+  for (int t = 0; t < 27; ++t) {
+    const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+    const float* a = s_in + (((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * SC;
+    const float* wt = s_w + t * CIN * COUT;
+#pragma unroll 4
+    for (int ci = 0; ci < CIN; ++ci) {
+      const float xv = a[ci];
+      const float* wr = wt + ci * COUT;
+#pragma unroll
+      for (int co = 0; co < COUT; ++co) acc[co] = fmaf(xv, wr[co], acc[co]);
+    }
+  }
+  if (gx >= EG || gy >= EG || gz >= EG) return;
+  const size_t v = (size_t)n * NV + (size_t)(gz * EG + gy) * EG + gx;
+#pragma unroll
+  for (int co = 0; co < COUT; ++co) {
+    float r = acc[co];
+    if constexpr (EPI == kEpiRelu) r = fmaxf(r + bias[co], 0.0f);
+    else if constexpr (EPI == kEpiNone) r = r + bias[co];
+    else if constexpr (EPI == kEpiResidual) r = r + bias[co] + aux[v];
+    else r = aux[v * COUT + co] > 0.0f ? r : 0.0f;
+    out[v * COUT + co] = r;
+  }
+}
+
+template <int CIN, int COUT>
+constexpr size_t conv_smem() {
+  return (size_t)(HZ * HY * HX * pad_stride(CIN) + 27 * CIN * COUT) * sizeof(float);
+}
+
+// ------------------------------------------------------ weight gradients
+// dW[tap][ci][co] += sum_v in[v + off(tap)][ci] * g[v][co] and db[co] +=
+// sum_v g[v][co] over one tile position of every grid; each block owns one
+// tile position and adds its sums once (atomically) at the end.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kConvThreads) wgrad_kernel(const float* __restrict__ in, const float* __restrict__ g,
+                                                            int n_grids, float* __restrict__ dW,
+                                                            float* __restrict__ db) {
+  extern __shared__ float sm[];
+  constexpr int SC = pad_stride(CIN);
+  constexpr int NP = 27 * CIN;                            // (tap, ci) pairs
+  constexpr int PPT = (NP + kConvThreads - 1) / kConvThreads;
+  float* s_in = sm;                                       // HZ * HY * HX * SC
+  float* s_g = sm + HZ * HY * HX * SC;                    // TZ * TY * TX * COUT
+  const int tile = blockIdx.x;
+  const int x0t = (tile % kTilesX) * TX, y0t = ((tile / kTilesX) % kTilesY) * TY, z0t = (tile / (kTilesX * kTilesY)) * TZ;
+  float acc[PPT][COUT];
+#pragma unroll
+  for (int j = 0; j < PPT; ++j)
+#pragma unroll
+    for (int co = 0; co < COUT; ++co) acc[j][co] = 0.0f;
+  float bacc = 0.0f;
+  for (int n = 0; n < n_grids; ++n) {
+    const float* src = in + (size_t)n * NV * CIN;
+    const float* gs = g + (size_t)n * NV * COUT;
+    __syncthreads();
+    for (int q = threadIdx.x; q < HZ * HY * HX * CIN; q += blockDim.x) {
+      const int c = q % CIN, p = q / CIN;
+      const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
+      const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
+      float val = 0.0f;
+      if (gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
+        val = src[((size_t)(gz * EG + gy) * EG + gx) * CIN + c];
+      s_in[p * SC + c] = val;
+    }
+    for (int q = threadIdx.x; q < TZ * TY * TX * COUT; q += blockDim.x) {
+      const int c = q % COUT, p = q / COUT;
+      const int tx = p % TX, ty = (p / TX) % TY, tz = p / (TX * TY);
+      const int gx = x0t + tx, gy = y0t + ty, gz = z0t + tz;
+      float val = 0.0f;                                   // voxels outside the grid add nothing
+      if (gx < EG && gy < EG && gz < EG) val = gs[((size_t)(gz * EG + gy) * EG + gx) * COUT + c];
+      s_g[q] = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      const int pr = threadIdx.x + j * kConvThreads;
+      if (pr >= NP) break;
+      const int t = pr / CIN, ci = pr % CIN;
+      const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+      for (int p = 0; p < TZ * TY * TX; ++p) {
+        const int tx = p % TX, ty = (p / TX) % TY, tz = p / (TX * TY);
+        const float xv = s_in[(((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * SC + ci];
+        const float* gr = s_g + p * COUT;
+#pragma unroll
+        for (int co = 0; co < COUT; ++co) acc[j][co] = fmaf(xv, gr[co], acc[j][co]);
+      }
+    }
+    if (threadIdx.x < COUT)
+      for (int p = 0; p < TZ * TY * TX; ++p) bacc += s_g[p * COUT + threadIdx.x];
+  }
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    const int pr = threadIdx.x + j * kConvThreads;
+    if (pr >= NP) break;
+#pragma unroll
+    for (int co = 0; co < COUT; ++co) atomicAdd(&dW[pr * COUT + co], acc[j][co]);
+  }
+  if (threadIdx.x < COUT) atomicAdd(&db[threadIdx.x], bacc);
+}
+
+template <int CIN, int COUT>
+constexpr size_t wgrad_smem() {
+  return (size_t)(HZ * HY * HX * pad_stride(CIN) + TZ * TY * TX * COUT) * sizeof(float);
+}
+
+// ----------------------------------------------------------------- loss
+// g[v] = 2 (y[v] - t[v]) / N over the N voxels of all grids; loss += sum of
+// squares / N (block partial sums added once per block).
+__global__ void loss_kernel(const float* __restrict__ y, const float* __restrict__ t, size_t n, float inv_n,
+                            float* __restrict__ g, float* __restrict__ loss) {
+  __shared__ float s_part[32];
+  float part = 0.0f;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float d = y[i] - t[i];
+    g[i] = 2.0f * d * inv_n;
+    part = fmaf(d, d, part);
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0 && loss) {
+    float s = 0.0f;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += s_part[q];
+    atomicAdd(loss, s * inv_n);
+  }
+}
+
+// ------------------------------------------------------------ parameters
+// The effective weights: each W rounded to bfloat16 (nearest even), biases
+// as they are; and for layers 1..3 the input-gradient weights
+// wt[26 - tap][co][ci] = W[tap][ci][co].
+__global__ void refresh_kernel(const float* __restrict__ P, float* __restrict__ Pq, float* __restrict__ Wt1,
+                               float* __restrict__ Wt2, float* __restrict__ Wt3) {
+  const int woff[4] = {kWOff[0], kWOff[1], kWOff[2], kWOff[3]}, boff[4] = {kBOff[0], kBOff[1], kBOff[2], kBOff[3]};
+  const int cin[4] = {kCin[0], kCin[1], kCin[2], kCin[3]}, cout[4] = {kCout[0], kCout[1], kCout[2], kCout[3]};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < RO_MC_PARAMS; i += gridDim.x * blockDim.x) {
+    int layer = 3;
+    while (layer > 0 && i < woff[layer]) --layer;
+    const bool is_w = i < boff[layer];
+    const float q = is_w ? __bfloat162float(__float2bfloat16_rn(P[i])) : P[i];
+    Pq[i] = q;
+    if (is_w && layer > 0) {
+      const int ci_n = cin[layer], co_n = cout[layer];
+      const int r = i - woff[layer];
+      const int t = r / (ci_n * co_n), ci = (r / co_n) % ci_n, co = r % co_n;
+      float* wt = layer == 1 ? Wt1 : (layer == 2 ? Wt2 : Wt3);
+      wt[((26 - t) * co_n + co) * ci_n + ci] = q;
+    }
+  }
+}
+
+// Adam on the binary32 parameters (bias corrections folded into lr_t and
+// eps_t by the host).
+__global__ void adam_kernel(float* __restrict__ P, float* __restrict__ M, float* __restrict__ V,
+                            const float* __restrict__ G, float lr_t, float eps_t) {
+  const float b1 = 0.9f, b2 = 0.999f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < RO_MC_PARAMS; i += gridDim.x * blockDim.x) {
+    const float g = G[i];
+    const float m = fmaf(b1, M[i], (1.0f - b1) * g);
+    const float v = fmaf(b2, V[i], (1.0f - b2) * g * g);
+    M[i] = m;
+    V[i] = v;
+    P[i] -= lr_t * m / (sqrtf(v) + eps_t);
+  }
+}
+
+}  // namespace
+
+// ================================================================ host side
+
+struct ro_mc {
+  ro_mc_desc desc;
+  cudaStream_t stream = nullptr;
+  float *P, *Pq, *M, *V, *G;          // parameters, effective copy, Adam moments, gradients
+  float *Wt1, *Wt2, *Wt3;             // input-gradient weights of layers 1..3
+  float *a1, *a2, *a3;                // hidden activations (after ReLU), n * NV * 32
+  float *ga, *gb;                     // hidden gradients, n * NV * 32
+  float *g4, *y;                      // output gradient and output, n * NV
+  float* loss;                        // scratch loss when the caller passes none
+  uint32_t step = 0;
+};
+
+namespace {
+
+constexpr uint64_t kMcAlign = 256;
+uint64_t mc_align(uint64_t v) { return (v + kMcAlign - 1) / kMcAlign * kMcAlign; }
+
+struct McLayout {
+  uint64_t P, Pq, M, V, G, Wt1, Wt2, Wt3, a1, a2, a3, ga, gb, g4, y, loss, total;
+};
+
+McLayout mc_layout(uint32_t nb) {
+  McLayout L{};
+  uint64_t o = 0;
+  auto take = [&](uint64_t bytes) { const uint64_t at = o; o = mc_align(o + bytes); return at; };
+  const uint64_t pb = (uint64_t)RO_MC_PARAMS * 4, hid = (uint64_t)nb * NV * HID * 4, one = (uint64_t)nb * NV * 4;
+  L.P = take(pb); L.Pq = take(pb); L.M = take(pb); L.V = take(pb); L.G = take(pb);
+  L.Wt1 = take(27ull * HID * HID * 4); L.Wt2 = take(27ull * HID * HID * 4); L.Wt3 = take(27ull * HID * 4);
+  L.a1 = take(hid); L.a2 = take(hid); L.a3 = take(hid); L.ga = take(hid); L.gb = take(hid);
+  L.g4 = take(one); L.y = take(one); L.loss = take(4);
+  L.total = o;
+  return L;
+}
+
+bool mc_ok(cudaError_t e) { return e == cudaSuccess; }
+
+template <int CIN, int COUT, int EPI>
+cudaError_t conv(const float* in, const float* w, const float* b, float* out, const float* aux, uint32_t n,
+                 cudaStream_t s) {
+  auto k = conv_kernel<CIN, COUT, EPI>;
+  constexpr size_t sm = conv_smem<CIN, COUT>();
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(kTilesX * kTilesY * kTilesZ, n), kConvThreads, sm, s>>>(in, w, b, out, aux);
+  return cudaGetLastError();
+}
+
+template <int CIN, int COUT>
+cudaError_t wgrad(const float* in, const float* g, uint32_t n, float* dW, float* db, cudaStream_t s) {
+  auto k = wgrad_kernel<CIN, COUT>;
+  constexpr size_t sm = wgrad_smem<CIN, COUT>();
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k<<<kTilesX * kTilesY * kTilesZ, kConvThreads, sm, s>>>(in, g, (int)n, dW, db);
+  return cudaGetLastError();
+}
+
+ro_status mc_err(cudaError_t e) { return e == cudaSuccess ? RO_OK : RO_ERR_CUDA; }
+
+// y = x0 + f(x0); keeps the hidden activations for a backward pass
+cudaError_t mc_forward(ro_mc* m, uint32_t n, const float* x0, float* y) {
+  cudaStream_t s = m->stream;
+  const float* Pq = m->Pq;
+  cudaError_t e = conv<1, HID, kEpiRelu>(x0, Pq + kWOff[0], Pq + kBOff[0], m->a1, nullptr, n, s);
+  if (e == cudaSuccess) e = conv<HID, HID, kEpiRelu>(m->a1, Pq + kWOff[1], Pq + kBOff[1], m->a2, nullptr, n, s);
+  if (e == cudaSuccess) e = conv<HID, HID, kEpiRelu>(m->a2, Pq + kWOff[2], Pq + kBOff[2], m->a3, nullptr, n, s);
+  if (e == cudaSuccess) e = conv<HID, 1, kEpiResidual>(m->a3, Pq + kWOff[3], Pq + kBOff[3], y, x0, n, s);
+  return e;
+}
+
+// loss and gradients into G (zeroed first)
+cudaError_t mc_backward(ro_mc* m, uint32_t n, const float* x0, const float* target, float* G, float* loss) {
+  cudaStream_t s = m->stream;
+  cudaError_t e = mc_forward(m, n, x0, m->y);
+  if (e == cudaSuccess) e = cudaMemsetAsync(G, 0, (size_t)RO_MC_PARAMS * 4, s);
+  if (e == cudaSuccess && loss) e = cudaMemsetAsync(loss, 0, 4, s);
+  const size_t nv = (size_t)n * NV;
+  if (e == cudaSuccess) {
+    loss_kernel<<<152 * 4, 256, 0, s>>>(m->y, target, nv, 1.0f / (float)nv, m->g4, loss);
+    e = cudaGetLastError();
+  }
+  const float* zero_bias = nullptr;
+  // layer 4 (32 -> 1)
+  if (e == cudaSuccess) e = wgrad<HID, 1>(m->a3, m->g4, n, G + kWOff[3], G + kBOff[3], s);
+  if (e == cudaSuccess) e = conv<1, HID, kEpiMask>(m->g4, m->Wt3, zero_bias, m->ga, m->a3, n, s);
+  // layer 3 (32 -> 32)
+  if (e == cudaSuccess) e = wgrad<HID, HID>(m->a2, m->ga, n, G + kWOff[2], G + kBOff[2], s);
+  if (e == cudaSuccess) e = conv<HID, HID, kEpiMask>(m->ga, m->Wt2, zero_bias, m->gb, m->a2, n, s);
+  // layer 2 (32 -> 32)
+  if (e == cudaSuccess) e = wgrad<HID, HID>(m->a1, m->gb, n, G + kWOff[1], G + kBOff[1], s);
+  if (e == cudaSuccess) e = conv<HID, HID, kEpiMask>(m->gb, m->Wt1, zero_bias, m->ga, m->a1, n, s);
+  // layer 1 (1 -> 32)
+  if (e == cudaSuccess) e = wgrad<1, HID>(x0, m->ga, n, G + kWOff[0], G + kBOff[0], s);
+  return e;
+}
+
+cudaError_t mc_refresh(ro_mc* m) {
+  refresh_kernel<<<64, 256, 0, m->stream>>>(m->P, m->Pq, m->Wt1, m->Wt2, m->Wt3);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+ro_status ro_mc_query_bytes(const ro_mc_desc* d, uint64_t* bytes) {
+  if (!d || !bytes || d->max_batch < 1) return RO_ERR_INVALID_ARG;
+  *bytes = mc_layout(d->max_batch).total;
+  return RO_OK;
+}
+
+ro_status ro_mc_create(const ro_mc_desc* d, void* arena, uint64_t arena_bytes, void* stream, ro_mc** out) {
+  if (!out) return RO_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!d || d->max_batch < 1 || !arena || reinterpret_cast<uintptr_t>(arena) % kMcAlign) return RO_ERR_INVALID_ARG;
+  const McLayout L = mc_layout(d->max_batch);
+  if (arena_bytes < L.total) return RO_ERR_CAPACITY;
+  ro_mc* m = new (std::nothrow) ro_mc();
+  if (!m) return RO_ERR_CAPACITY;
+  m->desc = *d;
+  m->stream = static_cast<cudaStream_t>(stream);
+  uint8_t* b = static_cast<uint8_t*>(arena);
+  auto f = [&](uint64_t off) { return reinterpret_cast<float*>(b + off); };
+  m->P = f(L.P); m->Pq = f(L.Pq); m->M = f(L.M); m->V = f(L.V); m->G = f(L.G);
+  m->Wt1 = f(L.Wt1); m->Wt2 = f(L.Wt2); m->Wt3 = f(L.Wt3);
+  m->a1 = f(L.a1); m->a2 = f(L.a2); m->a3 = f(L.a3); m->ga = f(L.ga); m->gb = f(L.gb);
+  m->g4 = f(L.g4); m->y = f(L.y); m->loss = f(L.loss);
+  cudaError_t e = cudaMemsetAsync(arena, 0, L.Wt1, m->stream);   // parameters, copies, moments, gradients
+  if (e == cudaSuccess) e = mc_refresh(m);
+  if (e != cudaSuccess) {
+    delete m;
+    return RO_ERR_CUDA;
+  }
+  *out = m;
+  return RO_OK;
+}
+
+ro_status ro_mc_destroy(ro_mc* m) {
+  if (!m) return RO_ERR_INVALID_ARG;
+  const cudaError_t e = cudaStreamSynchronize(m->stream);
+  delete m;
+  return mc_err(e);
+}
+
+ro_status ro_mc_set_params(ro_mc* m, const float* host) {
+  if (!m || !host) return RO_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpyAsync(m->P, host, (size_t)RO_MC_PARAMS * 4, cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->M, 0, (size_t)RO_MC_PARAMS * 4, m->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->V, 0, (size_t)RO_MC_PARAMS * 4, m->stream);
+  if (e == cudaSuccess) e = mc_refresh(m);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);   // the host buffer may be reused at once
+  m->step = 0;
+  return mc_err(e);
+}
+
+ro_status ro_mc_get_params(ro_mc* m, float* host) {
+  if (!m || !host) return RO_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpyAsync(host, m->P, (size_t)RO_MC_PARAMS * 4, cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  return mc_err(e);
+}
+
+ro_status ro_mc_upsample(ro_mc* m, uint32_t n, const uint16_t* slots, const uint32_t* octants, float* x0) {
+  if (!m || !slots || !octants || !x0 || n < 1 || n > m->desc.max_batch) return RO_ERR_INVALID_ARG;
+  upsample_kernel<<<n, 256, 0, m->stream>>>(slots, octants, x0);
+  return mc_err(cudaGetLastError());
+}
+
+ro_status ro_mc_forward(ro_mc* m, uint32_t n, const float* x0, float* y) {
+  if (!m || !x0 || !y || n < 1 || n > m->desc.max_batch) return RO_ERR_INVALID_ARG;
+  return mc_err(mc_forward(m, n, x0, y));
+}
+
+ro_status ro_mc_gradients(ro_mc* m, uint32_t n, const float* x0, const float* target, float* grads, float* loss) {
+  if (!m || !x0 || !target || !grads || n < 1 || n > m->desc.max_batch) return RO_ERR_INVALID_ARG;
+  return mc_err(mc_backward(m, n, x0, target, grads, loss));
+}
+
+ro_status ro_mc_train_step(ro_mc* m, uint32_t n, const float* x0, const float* target, float lr, float* loss) {
+  if (!m || !x0 || !target || n < 1 || n > m->desc.max_batch || !(lr > 0.0f)) return RO_ERR_INVALID_ARG;
+  cudaError_t e = mc_backward(m, n, x0, target, m->G, loss);
+  ++m->step;
+  // Adam bias corrections: lr_t = lr * sqrt(1 - b2^t) / (1 - b1^t), eps scaled alike
+  const double c1 = 1.0 - std::pow(0.9, (double)m->step), c2 = 1.0 - std::pow(0.999, (double)m->step);
+  const float lr_t = (float)(lr * std::sqrt(c2) / c1), eps_t = (float)(1e-8 * std::sqrt(c2));
+  if (e == cudaSuccess) {
+    adam_kernel<<<64, 256, 0, m->stream>>>(m->P, m->M, m->V, m->G, lr_t, eps_t);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = mc_refresh(m);
+  return mc_err(e);
+}
