@@ -310,7 +310,8 @@ ro_status ro_get_stats(ro_ctx* ctx, uint64_t out[8]);
 /* Copies one internal array to the host (waits for the stream):
  * what = 0 octree words (n_nodes * channel_stride u32), 1 page table
  * (n_bricks u32), 2 last_used (cache_slots u32), 3 request flags (n_bricks
- * bytes), 4 used flags (cache_slots bytes).  bytes must equal the array's
+ * bytes), 4 used flags (cache_slots bytes), 5 the brick cache
+ * (cache_slots * slot_pitch bytes).  bytes must equal the array's
  * size. */
 ro_status ro_debug_read(ro_ctx* ctx, uint32_t what, void* host, uint64_t bytes);
 

@@ -78,6 +78,21 @@ ro_status ro_mc_gradients(ro_mc* mc, uint32_t n, const float* x0, const float* t
  * gradients of n grids; loss as above (device, may be NULL). */
 ro_status ro_mc_train_step(ro_mc* mc, uint32_t n, const float* x0, const float* target, float lr, float* loss);
 
+/* Makes n missing level-0 bricks resident with predicted data (the
+ * substitution of Sec. 6.1 refined by the compensator): for each ID the
+ * level-1 parent must be resident; its cache slot is upsampled to the
+ * child's apron grid, the network's output y is converted to raw values
+ * (round(y * 65536), clamped to [0, 65535]) and placed like ro_upload_bricks
+ * places a brick (free slot, else least recently used; a parent of this call
+ * is never evicted).  The renderer then samples the predicted brick and no
+ * longer requests it; ro_upload_bricks of the same ID later replaces the
+ * prediction with the real data.  Needs 32^3 u16 bricks, sample_format 0 and
+ * at least 2 levels; n <= max_upload, n <= cache_slots and n <= the
+ * compensator's max_batch (RO_ERR_CAPACITY).  IDs must be level 0, not
+ * resident, without duplicates (RO_ERR_INVALID_ARG).  out_slots (host, may
+ * be NULL) receives the slots.  Waits for the stream. */
+ro_status ro_compensate_bricks(ro_ctx* ctx, ro_mc* mc, uint32_t n, const uint32_t* level0_ids, uint32_t* out_slots);
+
 #ifdef __cplusplus
 }
 #endif

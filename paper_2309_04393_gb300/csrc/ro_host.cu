@@ -12,6 +12,7 @@
 
 #include "ro.h"
 #include "ro_internal.h"
+#include "ro_mc.h"
 
 using ro::Geometry;
 
@@ -425,26 +426,30 @@ uint32_t ro_brick_index(const ro_ctx* c, uint32_t id) {
   return decode_id(c, id, &ch, &l, &pi) ? pi : RO_NONE;
 }
 
-ro_status ro_upload_bricks(ro_ctx* c, uint32_t n, const uint32_t* ids, const void* voxels, uint32_t* out_slots,
-                           uint32_t* out_evicted) {
-  if (!c) return RO_ERR_INVALID_ARG;
-  if (c->latched != RO_OK) return c->latched;
-  if (n == 0) return RO_OK;
-  if (!ids || !voxels) return set_err(c, RO_ERR_INVALID_ARG, "ro_upload_bricks: null pointer");
-  if (n > c->desc.max_upload || n > c->desc.cache_slots)
-    return set_err(c, RO_ERR_CAPACITY, "ro_upload_bricks: n exceeds max_upload or cache_slots");
-  std::vector<uint32_t> pis(n);
+extern "C++" {
+namespace {
+
+// Validation of brick IDs shared by the two ways of making bricks resident.
+ro_status check_ids(ro_ctx* c, uint32_t n, const uint32_t* ids, std::vector<uint32_t>& pis, const char* where) {
+  pis.resize(n);
   for (uint32_t i = 0; i < n; ++i) {
     int ch, l;
     if (!decode_id(c, ids[i], &ch, &l, &pis[i]))
-      return set_err(c, RO_ERR_INVALID_ARG, "ro_upload_bricks: brick id outside the hierarchy");
+      return set_err(c, RO_ERR_INVALID_ARG, std::string(where) + ": brick id outside the hierarchy");
   }
-  {
-    std::vector<uint32_t> s(pis);
-    std::sort(s.begin(), s.end());
-    if (std::adjacent_find(s.begin(), s.end()) != s.end())
-      return set_err(c, RO_ERR_INVALID_ARG, "ro_upload_bricks: duplicate brick id");
-  }
+  std::vector<uint32_t> s(pis);
+  std::sort(s.begin(), s.end());
+  if (std::adjacent_find(s.begin(), s.end()) != s.end())
+    return set_err(c, RO_ERR_INVALID_ARG, std::string(where) + ": duplicate brick id");
+  return RO_OK;
+}
+
+// Slot choice (keep resident bricks' slots, then free slots, then LRU),
+// then `fill` enqueues the n bricks' voxels into the staging rows and the
+// scatter kernel writes slots and page-table entries.
+template <class Fill>
+ro_status place_bricks(ro_ctx* c, uint32_t n, const std::vector<uint32_t>& pis, Fill fill, uint32_t* out_slots,
+                       uint32_t* out_evicted, const std::vector<uint32_t>* keep_slots = nullptr) {
   // slot choice: keep resident bricks' slots, then free slots, then LRU
   std::vector<uint32_t> slots(n, RO_NONE), evicted(n, RO_NONE);
   std::vector<uint8_t> taken;  // slots assigned in this call
@@ -463,6 +468,8 @@ ro_status ro_upload_bricks(ro_ctx* c, uint32_t n, const uint32_t* ids, const voi
     std::vector<uint8_t> keep(c->desc.cache_slots, 0);
     for (uint32_t i = 0; i < n; ++i)
       if (slots[i] != RO_NONE) keep[slots[i]] = 1;
+    if (keep_slots)
+      for (uint32_t sl : *keep_slots) keep[sl] = 1;
     std::vector<uint32_t> cand;
     cand.reserve(c->desc.cache_slots);
     for (uint32_t sl = 0; sl < c->desc.cache_slots; ++sl)
@@ -499,10 +506,8 @@ ro_status ro_upload_bricks(ro_ctx* c, uint32_t n, const uint32_t* ids, const voi
     c->slot_of_brick[pis[i]] = sl;
     c->pending.push_back(pis[i]);
   }
-  const uint64_t bytes = (uint64_t)c->g.edge * c->g.edge * c->g.edge * c->g.bpv;
   cudaStream_t st = c->stream;
-  RO_TRY(cuda_check(c, cudaMemcpy2DAsync(c->staging, c->g.slot_pitch, voxels, bytes, bytes, n, cudaMemcpyHostToDevice, st),
-                    "ro_upload_bricks: voxels"));
+  RO_TRY(fill(st));
   uint32_t* d_ins_index = reinterpret_cast<uint32_t*>(c->scratch + c->L.sc_ins_index);
   uint32_t* d_ins_slot = reinterpret_cast<uint32_t*>(c->scratch + c->L.sc_ins_slot);
   uint32_t* d_ev_index = reinterpret_cast<uint32_t*>(c->scratch + c->L.sc_ev_index);
@@ -533,6 +538,66 @@ ro_status ro_upload_bricks(ro_ctx* c, uint32_t n, const uint32_t* ids, const voi
   if (out_slots) std::memcpy(out_slots, slots.data(), 4ull * n);
   if (out_evicted) std::memcpy(out_evicted, evicted.data(), 4ull * n);
   return RO_OK;
+}
+
+}  // namespace
+}  // extern "C++"
+
+ro_status ro_upload_bricks(ro_ctx* c, uint32_t n, const uint32_t* ids, const void* voxels, uint32_t* out_slots,
+                           uint32_t* out_evicted) {
+  if (!c) return RO_ERR_INVALID_ARG;
+  if (c->latched != RO_OK) return c->latched;
+  if (n == 0) return RO_OK;
+  if (!ids || !voxels) return set_err(c, RO_ERR_INVALID_ARG, "ro_upload_bricks: null pointer");
+  if (n > c->desc.max_upload || n > c->desc.cache_slots)
+    return set_err(c, RO_ERR_CAPACITY, "ro_upload_bricks: n exceeds max_upload or cache_slots");
+  std::vector<uint32_t> pis;
+  RO_TRY(check_ids(c, n, ids, pis, "ro_upload_bricks"));
+  auto fill = [&](cudaStream_t st) {
+    const uint64_t bytes = (uint64_t)c->g.edge * c->g.edge * c->g.edge * c->g.bpv;
+    return cuda_check(c, cudaMemcpy2DAsync(c->staging, c->g.slot_pitch, voxels, bytes, bytes, n, cudaMemcpyHostToDevice, st),
+                      "ro_upload_bricks: voxels");
+  };
+  return place_bricks(c, n, pis, fill, out_slots, out_evicted);
+}
+
+ro_status ro_compensate_bricks(ro_ctx* c, ro_mc* mc, uint32_t n, const uint32_t* ids, uint32_t* out_slots) {
+  if (!c) return RO_ERR_INVALID_ARG;
+  if (c->latched != RO_OK) return c->latched;
+  if (n == 0) return RO_OK;
+  const char* where = "ro_compensate_bricks";
+  if (!mc || !ids) return set_err(c, RO_ERR_INVALID_ARG, "ro_compensate_bricks: null pointer");
+  if (c->g.edge != RO_MC_EDGE || c->g.bpv != 2 || c->g.sf != 0 || c->g.k < 2)
+    return set_err(c, RO_ERR_INVALID_ARG, "ro_compensate_bricks: needs 32^3 u16 bricks, raw samples, >= 2 levels");
+  if (n > c->desc.max_upload || n > c->desc.cache_slots || n > ro::mc_max_batch(mc))
+    return set_err(c, RO_ERR_CAPACITY, "ro_compensate_bricks: n exceeds max_upload, cache_slots or the batch");
+  std::vector<uint32_t> pis;
+  RO_TRY(check_ids(c, n, ids, pis, where));
+  std::vector<uint32_t> parent_slot(n), octant(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    int ch, l;
+    uint32_t b[3];
+    index_to_brick(c->g, pis[i], &ch, &l, b);
+    if (l != 0) return set_err(c, RO_ERR_INVALID_ARG, "ro_compensate_bricks: not a level-0 brick");
+    if (c->slot_of_brick[pis[i]] != RO_NONE) return set_err(c, RO_ERR_INVALID_ARG, "ro_compensate_bricks: brick resident");
+    const uint32_t pid = ((uint32_t)(ch * c->g.k + 1) << 24) | ((b[2] >> 1) << 16) | ((b[1] >> 1) << 8) | (b[0] >> 1);
+    int pc, pl;
+    uint32_t ppi;
+    if (!decode_id(c, pid, &pc, &pl, &ppi) || c->slot_of_brick[ppi] == RO_NONE)
+      return set_err(c, RO_ERR_INVALID_ARG, "ro_compensate_bricks: level-1 parent not resident");
+    parent_slot[i] = c->slot_of_brick[ppi];
+    octant[i] = (b[0] & 1u) | ((b[1] & 1u) << 1) | ((b[2] & 1u) << 2);
+  }
+  // parents' slots and octants in the update-item scratch (free during uploads)
+  uint32_t* d_parent = reinterpret_cast<uint32_t*>(c->scratch + c->L.sc_items);
+  uint32_t* d_oct = d_parent + n;
+  auto fill = [&](cudaStream_t st) {
+    RO_TRY(cuda_check(c, cudaMemcpyAsync(d_parent, parent_slot.data(), 4ull * n, cudaMemcpyHostToDevice, st), where));
+    RO_TRY(cuda_check(c, cudaMemcpyAsync(d_oct, octant.data(), 4ull * n, cudaMemcpyHostToDevice, st), where));
+    return cuda_check(c, ro::mc_synthesize(mc, n, c->cache, c->g.slot_pitch, d_parent, d_oct, c->staging, c->g.slot_pitch, st),
+                      "ro_compensate_bricks: network");
+  };
+  return place_bricks(c, n, pis, fill, out_slots, nullptr, &parent_slot);  // parents are read, never evicted
 }
 
 ro_status ro_update_residency_octree(ro_ctx* c, uint32_t n_meta, const ro_leaf_meta* meta) {
@@ -1024,6 +1089,7 @@ ro_status ro_debug_read(ro_ctx* c, uint32_t what, void* host, uint64_t bytes) {
     case 2: src = c->last_used; size = 4ull * c->desc.cache_slots; break;
     case 3: src = c->req; size = c->g.n_bricks; break;
     case 4: src = c->used; size = c->desc.cache_slots; break;
+    case 5: src = c->cache; size = (uint64_t)c->desc.cache_slots * c->g.slot_pitch; break;
     default: return set_err(c, RO_ERR_INVALID_ARG, "ro_debug_read: unknown array");
   }
   if (bytes != size) return set_err(c, RO_ERR_INVALID_ARG, "ro_debug_read: size mismatch");

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct ro_mc;
+
 namespace ro {
 
 constexpr int kMaxC = 16;       // channels per context (RO_MAX_CHANNELS)
@@ -184,5 +186,12 @@ cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
 cudaError_t launch_usage(const UsageArgs& a, cudaStream_t s);
 
 size_t render_smem_bytes(int mp);
+
+// Compensator entry points used by ro_compensate_bricks: the batch limit,
+// and the synthesis of n level-0 apron slots (u16 raw values at out_pitch)
+// from the level-1 parents' cache slots and the children's octants.
+uint32_t mc_max_batch(const ::ro_mc* mc);
+cudaError_t mc_synthesize(::ro_mc* mc, uint32_t n, const uint8_t* cache, uint32_t pitch, const uint32_t* parent_slots,
+                          const uint32_t* octants, uint8_t* out, uint32_t out_pitch, cudaStream_t s);
 
 }  // namespace ro

@@ -17,6 +17,7 @@
 #include <string>
 #include <vector>
 
+#include "ro_internal.h"
 #include "ro_mc.h"
 
 namespace {
@@ -46,10 +47,10 @@ enum : int { kEpiNone = 0, kEpiRelu = 1, kEpiResidual = 2, kEpiMask = 3 };
 // Level-0 voxel X (relative to the child's apron origin) sits at level-1
 // coordinate u = (X - 1 + 32 o + 0.5) / 2 - 0.5 relative to the parent's
 // first interior voxel; slot index = floor(u) + 1; weights 0.25 / 0.75.
-__global__ void upsample_kernel(const uint16_t* __restrict__ slots, const uint32_t* __restrict__ octants,
-                                float* __restrict__ x0) {
+__global__ void upsample_kernel(const uint8_t* __restrict__ base, size_t pitch, const uint32_t* __restrict__ slot_of,
+                                const uint32_t* __restrict__ octants, float* __restrict__ x0) {
   const int n = blockIdx.x;
-  const uint16_t* s = slots + (size_t)n * NV;
+  const uint16_t* s = reinterpret_cast<const uint16_t*>(base + (slot_of ? (size_t)slot_of[n] : (size_t)n) * pitch);
   const uint32_t o = octants[n];
   const int oc[3] = {(int)(o & 1u), (int)((o >> 1) & 1u), (int)((o >> 2) & 1u)};
   for (int v = threadIdx.x; v < NV; v += blockDim.x) {
@@ -76,6 +77,16 @@ __global__ void upsample_kernel(const uint16_t* __restrict__ slots, const uint32
           acc = fmaf(w, (float)s[idx], acc);
         }
     x0[(size_t)n * NV + v] = acc * 1.52587890625e-05f;  // 2^-16
+  }
+}
+
+// y (scaled) -> raw u16 values, nearest, clamped to [0, 65535], at out_pitch
+__global__ void to_raw_kernel(const float* __restrict__ y, uint8_t* __restrict__ out, size_t out_pitch) {
+  const int n = blockIdx.x;
+  uint16_t* o = reinterpret_cast<uint16_t*>(out + (size_t)n * out_pitch);
+  for (int v = threadIdx.x; v < NV; v += blockDim.x) {
+    const float r = rintf(y[(size_t)n * NV + v] * 65536.0f);
+    o[v] = (uint16_t)fminf(fmaxf(r, 0.0f), 65535.0f);
   }
 }
 
@@ -443,7 +454,8 @@ ro_status ro_mc_get_params(ro_mc* m, float* host) {
 
 ro_status ro_mc_upsample(ro_mc* m, uint32_t n, const uint16_t* slots, const uint32_t* octants, float* x0) {
   if (!m || !slots || !octants || !x0 || n < 1 || n > m->desc.max_batch) return RO_ERR_INVALID_ARG;
-  upsample_kernel<<<n, 256, 0, m->stream>>>(slots, octants, x0);
+  upsample_kernel<<<n, 256, 0, m->stream>>>(reinterpret_cast<const uint8_t*>(slots), (size_t)NV * 2, nullptr, octants,
+                                             x0);
   return mc_err(cudaGetLastError());
 }
 
@@ -471,3 +483,27 @@ ro_status ro_mc_train_step(ro_mc* m, uint32_t n, const float* x0, const float* t
   if (e == cudaSuccess) e = mc_refresh(m);
   return mc_err(e);
 }
+
+namespace ro {
+
+uint32_t mc_max_batch(const ::ro_mc* m) { return m ? m->desc.max_batch : 0; }
+
+// x0 goes to the compensator's output-gradient buffer (unused outside
+// training), y to its output buffer; the work runs on the caller's stream.
+cudaError_t mc_synthesize(::ro_mc* m, uint32_t n, const uint8_t* cache, uint32_t pitch, const uint32_t* parent_slots,
+                          const uint32_t* octants, uint8_t* out, uint32_t out_pitch, cudaStream_t s) {
+  if (!m || n < 1 || n > m->desc.max_batch) return cudaErrorInvalidValue;
+  cudaStream_t keep = m->stream;
+  m->stream = s;
+  upsample_kernel<<<n, 256, 0, s>>>(cache, pitch, parent_slots, octants, m->g4);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = mc_forward(m, n, m->g4, m->y);
+  if (e == cudaSuccess) {
+    to_raw_kernel<<<n, 256, 0, s>>>(m->y, out, out_pitch);
+    e = cudaGetLastError();
+  }
+  m->stream = keep;
+  return e;
+}
+
+}  // namespace ro

@@ -35,8 +35,9 @@ def _lib():
         L.ro_mc_forward.argtypes = [vp, u32, vp, vp]
         L.ro_mc_gradients.argtypes = [vp, u32, vp, vp, vp, vp]
         L.ro_mc_train_step.argtypes = [vp, u32, vp, vp, ctypes.c_float, vp]
+        L.ro_compensate_bricks.argtypes = [vp, vp, u32, vp, vp]
         for f in ("ro_mc_query_bytes", "ro_mc_create", "ro_mc_destroy", "ro_mc_set_params", "ro_mc_get_params",
-                  "ro_mc_upsample", "ro_mc_forward", "ro_mc_gradients", "ro_mc_train_step"):
+                  "ro_mc_upsample", "ro_mc_forward", "ro_mc_gradients", "ro_mc_train_step", "ro_compensate_bricks"):
             getattr(L, f).restype = ctypes.c_int
         L._mc_typed = True
     return L
@@ -132,3 +133,13 @@ class Compensator:
         ptr = ctypes.c_void_p(loss.data_ptr()) if loss is not None else None
         self._check(self.L.ro_mc_train_step(self.h, x0.shape[0], ctypes.c_void_p(x0.data_ptr()),
                                             ctypes.c_void_p(target.data_ptr()), ctypes.c_float(lr), ptr))
+
+
+def compensate_bricks(ctx, comp: Compensator, ids) -> np.ndarray:
+    """ro_compensate_bricks: predicted level-0 bricks for the given IDs
+    (their level-1 parents resident); returns the slots."""
+    ids = np.ascontiguousarray(np.asarray(ids, np.uint32))
+    slots = np.zeros(max(1, ids.size), np.uint32)
+    ctx._check(_lib().ro_compensate_bricks(ctx.h, comp.h, ids.size, ids.ctypes.data_as(ctypes.c_void_p),
+                                           slots.ctypes.data_as(ctypes.c_void_p)))
+    return slots[:ids.size]

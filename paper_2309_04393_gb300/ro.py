@@ -269,7 +269,8 @@ class Context:
         s = self.sizes
         shape = {0: (int(s.n_nodes) * int(s.channel_stride), np.uint32), 1: (int(s.n_bricks), np.uint32),
                  2: (int(self.desc.cache_slots), np.uint32), 3: (int(s.n_bricks), np.uint8),
-                 4: (int(self.desc.cache_slots), np.uint8)}[what]
+                 4: (int(self.desc.cache_slots), np.uint8),
+                 5: (int(self.desc.cache_slots) * int(s.slot_pitch), np.uint8)}[what]
         out = np.zeros(shape[0], shape[1])
         self._check(self.L.ro_debug_read(self.h, int(what), _ptr(out), out.nbytes))
         return out

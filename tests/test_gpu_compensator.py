@@ -83,3 +83,41 @@ def test_training_lowers_the_loss(mc):
             first = float(loss.item())
     last = float(loss.item())
     assert last < 0.5 * first
+
+
+def test_compensate_bricks_writes_the_predictions_into_the_cache(mc):
+    import torch
+    from paper_2309_04393_gb300 import loader, ro
+    from synth import recipes
+    mcmod, m = mc
+    m.set_params(omc.init_params(7))
+    scene = recipes.cells_slab(m=2, dims=(128, 128, 64), ncells=300, k=3, W=64, H=64, n_views=1, resident_l0=0.5)
+    d = ro.make_desc(scene.dims, scene.spacing, scene.m, scene.value_bits, scene.B, scene.k, scene.leaf,
+                     len(scene.all_bricks()), max_upload=64)
+    ctx = ro.Context(d)
+    loader.load_scene(ctx, scene)
+    res = set(scene.resident)
+    missing = [b for b in scene.all_bricks(levels=[0]) if b not in res][:4]
+    assert len(missing) == 4
+    ids = [ro.brick_id(c, 0, bx, by, bz, scene.k) for (c, l, bx, by, bz) in missing]
+    slots = mcmod.compensate_bricks(ctx, m, ids)
+    pt = ctx.debug_read(1)
+    for i, s in zip(ids, slots):
+        assert pt[ctx.brick_index(i)] == s + 1
+    cache = ctx.debug_read(5).reshape(int(d.cache_slots), -1)
+    # expected: the network on the parents' upsampled slots, to raw values
+    parents = np.stack([scene.bricks(np.array([[c, 1, bx // 2, by // 2, bz // 2]], np.int32))[0]
+                        for (c, l, bx, by, bz) in missing])
+    octs = np.array([(bx & 1) | ((by & 1) << 1) | ((bz & 1) << 2) for (c, l, bx, by, bz) in missing], np.int32)
+    x0 = m.upsample(torch.from_numpy(parents.view(np.int16)).cuda(), torch.from_numpy(octs).cuda())
+    y = m.forward(x0).cpu().numpy()
+    want = np.clip(np.rint(y * 65536.0), 0, 65535).astype(np.uint16)
+    for k, s in enumerate(slots):
+        got = cache[s, :34 ** 3 * 2].view(np.uint16).reshape(34, 34, 34)
+        assert np.array_equal(got, want[k])
+    with pytest.raises(ro.RoError):                              # already resident now
+        mcmod.compensate_bricks(ctx, m, ids[:1])
+    with pytest.raises(ro.RoError):                              # a level-1 id
+        mcmod.compensate_bricks(ctx, m, [ro.brick_id(0, 1, 0, 0, 0, scene.k)])
+    img, _ = ro.render_frame(ctx, scene.frames[0])               # the context still renders
+    assert float(img[..., 3].max()) > 0
