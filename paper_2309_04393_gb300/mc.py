@@ -60,6 +60,18 @@ def unflatten(v: np.ndarray):
     return out
 
 
+def init_params(seed: int = 0) -> np.ndarray:
+    """Seeded He-normal weights (the last layer 100x smaller, so the network
+    starts near y = x0) and zero biases, as the RO_MC_PARAMS vector."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for i, (ci, co) in enumerate(LAYERS):
+        std = np.sqrt(2.0 / (27 * ci)) * (0.01 if i == len(LAYERS) - 1 else 1.0)
+        parts.append(rng.normal(0.0, std, 27 * ci * co))
+        parts.append(np.zeros(co))
+    return np.concatenate(parts).astype(np.float32)
+
+
 class Compensator:
     def __init__(self, max_batch: int, stream=None, device=None):
         import torch
