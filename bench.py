@@ -623,10 +623,10 @@ def psnr(a, b):
 
 
 def run_compensator(args, rank, world, local_rank):
-    """Config 4: the learned miss compensator.  Training pairs (level-1
-    parent slot, level-0 brick) come from other seeds of config 2's cell
-    model; the evaluated volume (seed 2) is held out.  Then config 2's views
-    with 50 % of the level-0 bricks missing are rendered with plain coarser
+    """The learned miss compensator.  Training pairs (level-1 parent slot,
+    level-0 brick) come from other seeds of the 4-channel 1024x1024x64 cell
+    model; the evaluated volume (seed 2) is held out.  Then that volume's
+    views with 50 % of the level-0 bricks missing are rendered with plain coarser
     substitution, with the requested level-0 bricks predicted by the
     compensator, and with every brick resident (the reference)."""
     import torch
@@ -713,7 +713,7 @@ def run_compensator(args, rank, world, local_rank):
     out = {"metric": "PSNR dB vs full residency (compensated)", "value": p_comp, "unit": "dB", "n_gpus": 1,
            "steps": steps, "warmup": 0, "higher_is_better": True, "vs_baseline": None, "dtype": "f32 (bf16 weights)",
            "data": "synthetic (seeded procedural cells; no dataset)",
-           "config": {"workload": "compensator: config 2's 4-channel 1024x1024x64 u16 cell slab, 50 % of level-0 "
+           "config": {"workload": "compensator: 4-channel 1024x1024x64 u16 cell slab (seed 2), 50 % of level-0 "
                                   "bricks missing, 4 perspective 1024^2 views at level 0; network 1-32-32-32-1 "
                                   "3x3x3 convolutions trained on pairs from 8 other seeds of the cell model",
                       "pairs": steps * batch, "batch": batch, "missing_bricks_predicted": len(missing)},

@@ -15,6 +15,9 @@ network   y = x0 + f(x0): f is four 3x3x3 convolutions with zero padding
           the first three.  Weight layout W[tap, ci, co], tap = (dz * 3 +
           dy) * 3 + dx; activations channels-last [z, y, x, c].
 loss      mean squared error against the true level-0 apron slot (scaled).
+reading P2  the GPU runs the two 32 -> 32 layers on the tensor cores with
+          bfloat16 inputs (binary32 sums); forward(..., bf16_inputs=(1, 2))
+          mirrors that rounding of the layer inputs.
 
 Parity unpinned where the GPU's binary32 accumulation order differs: the
 GPU kernels are compared within a tolerance derived from that order.
@@ -91,22 +94,26 @@ def init_params(seed: int = 0):
     return params
 
 
-def forward(params, x0: np.ndarray):
-    """x0 [Z, Y, X] (scaled) -> (y [Z, Y, X], saved activations)."""
+def forward(params, x0: np.ndarray, bf16_inputs=()):
+    """x0 [Z, Y, X] (scaled) -> (y [Z, Y, X], the input of every layer).
+    bf16_inputs: layers whose input enters rounded to bfloat16 (reading P2:
+    the tensor-core layers)."""
     a = x0[..., None]
-    acts = [a]
+    acts = []
     for i, (W, b) in enumerate(params):
+        if i in bf16_inputs:
+            a = bf16(a)
+        acts.append(a)
         a = conv3(a, W, b)
         if i < len(params) - 1:
             a = np.maximum(a, 0.0)
-        acts.append(a)
     return x0 + a[..., 0], acts
 
 
-def loss_and_grads(params, x0: np.ndarray, target: np.ndarray):
+def loss_and_grads(params, x0: np.ndarray, target: np.ndarray, bf16_inputs=()):
     """Mean squared error of forward(x0) against target and its gradients
     with respect to every weight and bias."""
-    y, acts = forward(params, x0)
+    y, acts = forward(params, x0, bf16_inputs)
     n = y.size
     d = y - target
     loss = float((d * d).sum() / n)

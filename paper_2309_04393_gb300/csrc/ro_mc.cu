@@ -4,7 +4,9 @@
 //
 // Activations are channels-last binary32 grids of 34^3 voxels.  The weights
 // take part as bfloat16 values (the parameters are rounded once per update
-// into an effective binary32 copy); every sum is binary32.  A convolution
+// into an effective binary32 copy); every sum is binary32.  The two 32 -> 32
+// layers (forward and input gradient) run on the tensor cores with their
+// inputs rounded to bfloat16; the rest on the binary32 cores.  A convolution
 // block computes an 8 x 8 x 4 voxel tile for all output channels from a
 // shared-memory copy of the input tile with its one-voxel halo (zero outside
 // the grid) and of the layer's weights; the input-gradient pass is the same
@@ -151,6 +153,132 @@ constexpr size_t conv_smem() {
   return (size_t)(HZ * HY * HX * pad_stride(CIN) + 27 * CIN * COUT) * sizeof(float);
 }
 
+// ------------------------------------------- tensor-core 32 -> 32 layers
+// The same convolution as conv_kernel<32, 32, EPI> as an implicit GEMM on
+// the tensor cores: M = the block's 256 output voxels, N = 32 output
+// channels, K = 27 taps x 32 input channels, mma.sync m16n8k16 with bfloat16
+// operands and binary32 accumulators.  The input tile enters shared memory
+// rounded to bfloat16 (reading P2), one 80-byte row per voxel (32 channels
+// + padding, so the eight rows of an ldmatrix fall in different banks); the
+// weights come as bfloat16 rows [tap][co][ci] (wb).  Warp w owns voxels
+// 32w .. 32w + 31 of the tile (two m16 tiles) and all four n8 tiles.
+constexpr int kRowB = 80;                                  // bytes per shared row (32 bf16 + 8 pad)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kConvThreads) conv_mma_kernel(const float* __restrict__ in,
+                                                               const __nv_bfloat16* __restrict__ wb,
+                                                               const float* __restrict__ bias, float* __restrict__ out,
+                                                               const float* __restrict__ aux) {
+  extern __shared__ __align__(16) uint8_t smb[];
+  uint8_t* s_a = smb;                                       // HZ * HY * HX rows
+  uint8_t* s_b = smb + HZ * HY * HX * kRowB;                // 27 * 32 rows
+  const int tile = blockIdx.x, n = blockIdx.y;
+  const int x0t = (tile % kTilesX) * TX, y0t = ((tile / kTilesX) % kTilesY) * TY, z0t = (tile / (kTilesX * kTilesY)) * TZ;
+  const float* src = in + (size_t)n * NV * HID;
+  // input tile with halo, bfloat16, channel pairs
+  for (int q = threadIdx.x; q < HZ * HY * HX * (HID / 2); q += blockDim.x) {
+    const int c2 = q % (HID / 2), p = q / (HID / 2);
+    const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
+    const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
+    float2 v = make_float2(0.0f, 0.0f);
+    if (gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
+      v = *reinterpret_cast<const float2*>(src + ((size_t)(gz * EG + gy) * EG + gx) * HID + 2 * c2);
+    *reinterpret_cast<__nv_bfloat162*>(s_a + p * kRowB + 4 * c2) = __floats2bfloat162_rn(v.x, v.y);
+  }
+  // weights: 27 * 32 rows of 64 bytes
+  for (int q = threadIdx.x; q < 27 * HID * 4; q += blockDim.x) {
+    const int row = q / 4, part = q % 4;
+    *reinterpret_cast<uint4*>(s_b + row * kRowB + 16 * part) = reinterpret_cast<const uint4*>(wb)[q];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t4 = lane & 3;
+  // this lane's ldmatrix row for A: matrix i = lane / 8 -> row r + 8 (i & 1), k offset 8 (i >> 1)
+  const int mi = lane >> 3, mr = lane & 7;
+  int arow_pos[2];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    const int p = 32 * warp + 16 * mt + mr + 8 * (mi & 1);
+    const int x = p % TX, y = (p / TX) % TY, z = p / (TX * TY);
+    arow_pos[mt] = (z * HY + y) * HX + x;
+  }
+  const int a_koff = 16 * (mi >> 1);                        // bytes
+  // B: matrices 0, 1 = n-tile j (k lo, k hi), 2, 3 = n-tile j + 1
+  const int b_row = 8 * (mi >> 1) + mr, b_koff = 16 * (mi & 1);
+  float acc[2][4][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.0f;
+  const uint32_t a_base = smem_u32(s_a), b_base = smem_u32(s_b);
+  for (int t = 0; t < 27; ++t) {
+    const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+    const int toff = (dz * HY + dy) * HX + dx;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      uint32_t a[2][4], b[4][2];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+        ldsm_x4(a_base + (arow_pos[mt] + toff) * kRowB + 32 * kk + a_koff, a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+#pragma unroll
+      for (int nj = 0; nj < 2; ++nj)
+        ldsm_x4(b_base + (t * HID + 16 * nj + b_row) * kRowB + 32 * kk + b_koff, b[2 * nj][0], b[2 * nj][1],
+                b[2 * nj + 1][0], b[2 * nj + 1][1]);
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+          mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b[nt][0], b[nt][1]);
+    }
+  }
+  // epilogue: rows g and g + 8 of each m tile, channel pairs 2 t4 of each n tile
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int p = 32 * warp + 16 * mt + g + 8 * h;
+      const int gx = x0t + p % TX, gy = y0t + (p / TX) % TY, gz = z0t + p / (TX * TY);
+      if (gx >= EG || gy >= EG || gz >= EG) continue;
+      const size_t v = (size_t)n * NV + (size_t)(gz * EG + gy) * EG + gx;
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int co = 8 * nt + 2 * t4;
+        float r0 = acc[mt][nt][2 * h], r1 = acc[mt][nt][2 * h + 1];
+        if constexpr (EPI == kEpiRelu) {
+          r0 = fmaxf(r0 + bias[co], 0.0f);
+          r1 = fmaxf(r1 + bias[co + 1], 0.0f);
+        } else {
+          r0 = aux[v * HID + co] > 0.0f ? r0 : 0.0f;
+          r1 = aux[v * HID + co + 1] > 0.0f ? r1 : 0.0f;
+        }
+        *reinterpret_cast<float2*>(out + v * HID + co) = make_float2(r0, r1);
+      }
+    }
+}
+
+constexpr size_t conv_mma_smem() { return (size_t)(HZ * HY * HX + 27 * HID) * kRowB; }
+
 // ------------------------------------------------------ weight gradients
 // dW[tap][ci][co] += sum_v in[v + off(tap)][ci] * g[v][co] and db[co] +=
 // sum_v g[v][co] over one tile position of every grid; each block owns one
@@ -253,8 +381,12 @@ __global__ void loss_kernel(const float* __restrict__ y, const float* __restrict
 // The effective weights: each W rounded to bfloat16 (nearest even), biases
 // as they are; and for layers 1..3 the input-gradient weights
 // wt[26 - tap][co][ci] = W[tap][ci][co].
+// For the tensor-core layers 1 and 2 also bfloat16 rows: forward
+// wf[tap][co][ci] and input gradient wd[26 - tap][ci][co] (= W[tap][ci][co]).
 __global__ void refresh_kernel(const float* __restrict__ P, float* __restrict__ Pq, float* __restrict__ Wt1,
-                               float* __restrict__ Wt2, float* __restrict__ Wt3) {
+                               float* __restrict__ Wt2, float* __restrict__ Wt3, __nv_bfloat16* __restrict__ wf1,
+                               __nv_bfloat16* __restrict__ wf2, __nv_bfloat16* __restrict__ wd1,
+                               __nv_bfloat16* __restrict__ wd2) {
   const int woff[4] = {kWOff[0], kWOff[1], kWOff[2], kWOff[3]}, boff[4] = {kBOff[0], kBOff[1], kBOff[2], kBOff[3]};
   const int cin[4] = {kCin[0], kCin[1], kCin[2], kCin[3]}, cout[4] = {kCout[0], kCout[1], kCout[2], kCout[3]};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < RO_MC_PARAMS; i += gridDim.x * blockDim.x) {
@@ -269,6 +401,11 @@ __global__ void refresh_kernel(const float* __restrict__ P, float* __restrict__ 
       const int t = r / (ci_n * co_n), ci = (r / co_n) % ci_n, co = r % co_n;
       float* wt = layer == 1 ? Wt1 : (layer == 2 ? Wt2 : Wt3);
       wt[((26 - t) * co_n + co) * ci_n + ci] = q;
+      if (layer <= 2) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(q);
+        (layer == 1 ? wf1 : wf2)[(t * co_n + co) * ci_n + ci] = h;
+        (layer == 1 ? wd1 : wd2)[((26 - t) * ci_n + ci) * co_n + co] = h;
+      }
     }
   }
 }
@@ -297,6 +434,7 @@ struct ro_mc {
   cudaStream_t stream = nullptr;
   float *P, *Pq, *M, *V, *G;          // parameters, effective copy, Adam moments, gradients
   float *Wt1, *Wt2, *Wt3;             // input-gradient weights of layers 1..3
+  __nv_bfloat16 *wf1, *wf2, *wd1, *wd2;  // tensor-core rows of layers 1 and 2 (forward, input gradient)
   float *a1, *a2, *a3;                // hidden activations (after ReLU), n * NV * 32
   float *ga, *gb;                     // hidden gradients, n * NV * 32
   float *g4, *y;                      // output gradient and output, n * NV
@@ -310,7 +448,7 @@ constexpr uint64_t kMcAlign = 256;
 uint64_t mc_align(uint64_t v) { return (v + kMcAlign - 1) / kMcAlign * kMcAlign; }
 
 struct McLayout {
-  uint64_t P, Pq, M, V, G, Wt1, Wt2, Wt3, a1, a2, a3, ga, gb, g4, y, loss, total;
+  uint64_t P, Pq, M, V, G, Wt1, Wt2, Wt3, wf1, wf2, wd1, wd2, a1, a2, a3, ga, gb, g4, y, loss, total;
 };
 
 McLayout mc_layout(uint32_t nb) {
@@ -320,6 +458,8 @@ McLayout mc_layout(uint32_t nb) {
   const uint64_t pb = (uint64_t)RO_MC_PARAMS * 4, hid = (uint64_t)nb * NV * HID * 4, one = (uint64_t)nb * NV * 4;
   L.P = take(pb); L.Pq = take(pb); L.M = take(pb); L.V = take(pb); L.G = take(pb);
   L.Wt1 = take(27ull * HID * HID * 4); L.Wt2 = take(27ull * HID * HID * 4); L.Wt3 = take(27ull * HID * 4);
+  L.wf1 = take(27ull * HID * HID * 2); L.wf2 = take(27ull * HID * HID * 2);
+  L.wd1 = take(27ull * HID * HID * 2); L.wd2 = take(27ull * HID * HID * 2);
   L.a1 = take(hid); L.a2 = take(hid); L.a3 = take(hid); L.ga = take(hid); L.gb = take(hid);
   L.g4 = take(one); L.y = take(one); L.loss = take(4);
   L.total = o;
@@ -336,6 +476,17 @@ cudaError_t conv(const float* in, const float* w, const float* b, float* out, co
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k<<<dim3(kTilesX * kTilesY * kTilesZ, n), kConvThreads, sm, s>>>(in, w, b, out, aux);
+  return cudaGetLastError();
+}
+
+template <int EPI>
+cudaError_t conv_tc(const float* in, const __nv_bfloat16* wb, const float* b, float* out, const float* aux, uint32_t n,
+                    cudaStream_t s) {
+  auto k = conv_mma_kernel<EPI>;
+  constexpr size_t sm = conv_mma_smem();
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(kTilesX * kTilesY * kTilesZ, n), kConvThreads, sm, s>>>(in, wb, b, out, aux);
   return cudaGetLastError();
 }
 
@@ -356,8 +507,8 @@ cudaError_t mc_forward(ro_mc* m, uint32_t n, const float* x0, float* y) {
   cudaStream_t s = m->stream;
   const float* Pq = m->Pq;
   cudaError_t e = conv<1, HID, kEpiRelu>(x0, Pq + kWOff[0], Pq + kBOff[0], m->a1, nullptr, n, s);
-  if (e == cudaSuccess) e = conv<HID, HID, kEpiRelu>(m->a1, Pq + kWOff[1], Pq + kBOff[1], m->a2, nullptr, n, s);
-  if (e == cudaSuccess) e = conv<HID, HID, kEpiRelu>(m->a2, Pq + kWOff[2], Pq + kBOff[2], m->a3, nullptr, n, s);
+  if (e == cudaSuccess) e = conv_tc<kEpiRelu>(m->a1, m->wf1, Pq + kBOff[1], m->a2, nullptr, n, s);
+  if (e == cudaSuccess) e = conv_tc<kEpiRelu>(m->a2, m->wf2, Pq + kBOff[2], m->a3, nullptr, n, s);
   if (e == cudaSuccess) e = conv<HID, 1, kEpiResidual>(m->a3, Pq + kWOff[3], Pq + kBOff[3], y, x0, n, s);
   return e;
 }
@@ -379,17 +530,17 @@ cudaError_t mc_backward(ro_mc* m, uint32_t n, const float* x0, const float* targ
   if (e == cudaSuccess) e = conv<1, HID, kEpiMask>(m->g4, m->Wt3, zero_bias, m->ga, m->a3, n, s);
   // layer 3 (32 -> 32)
   if (e == cudaSuccess) e = wgrad<HID, HID>(m->a2, m->ga, n, G + kWOff[2], G + kBOff[2], s);
-  if (e == cudaSuccess) e = conv<HID, HID, kEpiMask>(m->ga, m->Wt2, zero_bias, m->gb, m->a2, n, s);
+  if (e == cudaSuccess) e = conv_tc<kEpiMask>(m->ga, m->wd2, zero_bias, m->gb, m->a2, n, s);
   // layer 2 (32 -> 32)
   if (e == cudaSuccess) e = wgrad<HID, HID>(m->a1, m->gb, n, G + kWOff[1], G + kBOff[1], s);
-  if (e == cudaSuccess) e = conv<HID, HID, kEpiMask>(m->gb, m->Wt1, zero_bias, m->ga, m->a1, n, s);
+  if (e == cudaSuccess) e = conv_tc<kEpiMask>(m->gb, m->wd1, zero_bias, m->ga, m->a1, n, s);
   // layer 1 (1 -> 32)
   if (e == cudaSuccess) e = wgrad<1, HID>(x0, m->ga, n, G + kWOff[0], G + kBOff[0], s);
   return e;
 }
 
 cudaError_t mc_refresh(ro_mc* m) {
-  refresh_kernel<<<64, 256, 0, m->stream>>>(m->P, m->Pq, m->Wt1, m->Wt2, m->Wt3);
+  refresh_kernel<<<64, 256, 0, m->stream>>>(m->P, m->Pq, m->Wt1, m->Wt2, m->Wt3, m->wf1, m->wf2, m->wd1, m->wd2);
   return cudaGetLastError();
 }
 
@@ -415,6 +566,8 @@ ro_status ro_mc_create(const ro_mc_desc* d, void* arena, uint64_t arena_bytes, v
   auto f = [&](uint64_t off) { return reinterpret_cast<float*>(b + off); };
   m->P = f(L.P); m->Pq = f(L.Pq); m->M = f(L.M); m->V = f(L.V); m->G = f(L.G);
   m->Wt1 = f(L.Wt1); m->Wt2 = f(L.Wt2); m->Wt3 = f(L.Wt3);
+  auto h = [&](uint64_t off) { return reinterpret_cast<__nv_bfloat16*>(b + off); };
+  m->wf1 = h(L.wf1); m->wf2 = h(L.wf2); m->wd1 = h(L.wd1); m->wd2 = h(L.wd2);
   m->a1 = f(L.a1); m->a2 = f(L.a2); m->a3 = f(L.a3); m->ga = f(L.ga); m->gb = f(L.gb);
   m->g4 = f(L.g4); m->y = f(L.y); m->loss = f(L.loss);
   cudaError_t e = cudaMemsetAsync(arena, 0, L.Wt1, m->stream);   // parameters, copies, moments, gradients

@@ -50,19 +50,31 @@ def test_forward_and_gradients_match_oracle(mc):
                  for W, b in params])
     x0f = x0.astype(np.float32).astype(np.float64)
     for k in range(2):
-        want, _ = omc.forward(q, x0f[k])
-        assert np.abs(y[k] - want).max() <= 2e-4 * max(1.0, np.abs(want).max())
+        want, _ = omc.forward(q, x0f[k], bf16_inputs=(1, 2))
+        err = np.abs(y[k] - want)
+        # binary32 sums agree to ~1e-7; where an activation lies within a
+        # binary32 step of a bfloat16 rounding boundary the two sides round
+        # it one bfloat16 step apart, which moves the 27 neighbours of the
+        # next layer by about |w| * |a| * 2^-8 and spreads from there.  The
+        # oracle with binary32-sized noise (2^-23) on the layer inputs gives
+        # median 0, 99 % 2.3e-4, 99.9 % 4.8e-4, max 9.2e-4 on these inputs:
+        # the bounds below sit about 2x above that
+        assert np.median(err) <= 1e-6
+        assert np.quantile(err, 0.99) <= 5e-4
+        assert err.max() <= 3e-3 * max(1.0, np.abs(want).max())
     g, loss = m.gradients(tx, tt)
     g = g.cpu().numpy()
     tf = target.astype(np.float32).astype(np.float64)
     # the oracle's loss over both grids: the mean of the per-grid means
-    losses, grads = zip(*[omc.loss_and_grads(q, x0f[k], tf[k]) for k in range(2)])
+    losses, grads = zip(*[omc.loss_and_grads(q, x0f[k], tf[k], bf16_inputs=(1, 2)) for k in range(2)])
     want_loss = sum(losses) / 2
     assert abs(float(loss.item()) - want_loss) <= 1e-4 * want_loss
     want_g = mcmod.flatten([(sum(gr[i][0] for gr in grads) / 2, sum(gr[i][1] for gr in grads) / 2)
                             for i in range(4)]).astype(np.float64)
+    # the GPU also rounds the gradients entering the two tensor-core input-
+    # gradient passes to bfloat16 (relative error 2^-9 per term)
     scale = np.abs(want_g).max()
-    assert np.abs(g - want_g).max() <= 1e-3 * scale
+    assert np.abs(g - want_g).max() <= 2e-2 * scale
 
 
 def test_training_lowers_the_loss(mc):
