@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--cache-gib", type=float, default=8.0)
     ap.add_argument("--image", type=str, default=None, help="override the image size, WxH")
     ap.add_argument("--warm-rounds", type=int, default=12, help="at most this many warm-up rounds over the orbit")
+    ap.add_argument("--order", type=int, choices=[0, 1], default=0,
+                    help="tile order of ro_render: 0 rows, 1 longest first by the previous frame's costs")
     ap.add_argument("--precision", choices=["f32", "f16", "bf16"], default="f32",
                     help="brick sample format: raw values with binary32 lerps, or binary16 / bfloat16 samples")
     return ap.parse_args()
@@ -191,7 +193,8 @@ def recorded_traffic(args):
             with open(os.path.join(ROOT, f), "rb") as fh:
                 h.update(fh.read())
         default = (args.workload == "cells16" and args.image is None and args.cache_gib == 8.0 and args.arc == 30.0
-                   and args.lod_bias is None and args.radius is None and args.precision == "f32")
+                   and args.lod_bias is None and args.radius is None and args.precision == "f32"
+                   and args.order == rec.get("order", 0))
         if h.hexdigest() == rec["source_sha256"] and default:
             return int(rec["dram_read_bytes_per_launch"]) + int(rec["dram_write_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -329,7 +332,8 @@ def run_ours(args, rank, world, local_rank):
     W, H = frames[0].W, frames[0].H
     sf = SAMPLE_FORMAT[args.precision]
     desc = ro.make_desc(scene.dims, scene.spacing, scene.m, scene.value_bits, scene.B, scene.k, scene.leaf, slots,
-                        max_requests=1 << 16, max_upload=2048, max_meta=1 << 20, sample_format=sf)
+                        max_requests=1 << 16, max_upload=2048, max_meta=1 << 20, sample_format=sf,
+                        max_batch_tiles=((W + 7) // 8) * ((H + 3) // 4))
     ctx = ro.Context(desc)
     t = time.time()
     if scene.resident:
@@ -342,7 +346,7 @@ def run_ours(args, rank, world, local_rank):
     warm = warm_cache(ctx, scene, image, args.warm_seconds, args.warm_rounds)
 
     def step(f):
-        ro.render_frame(ctx, f, image)
+        ro.render_frame(ctx, f, image, order=args.order)
         ctx.read_requests()
         ctx.update_residency_octree()
 
@@ -359,7 +363,7 @@ def run_ours(args, rank, world, local_rank):
     ev0.record()
     for f, (a, b) in zip(order, er):
         a.record()
-        ro.render_frame(ctx, f, image)
+        ro.render_frame(ctx, f, image, order=args.order)
         b.record()
         ctx.read_requests()
         ctx.update_residency_octree()
@@ -376,7 +380,7 @@ def run_ours(args, rank, world, local_rank):
     samples = chan = hit = 0
     for f in order:
         torch.cuda.nvtx.range_push("stats_render")
-        ro.render_frame(ctx, f, image)
+        ro.render_frame(ctx, f, image, order=args.order)
         torch.cuda.nvtx.range_pop()
         st = ctx.stats()
         hit += int(st[0])
@@ -394,7 +398,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for f in order:
-        ro.render_frame(ctx, f, image)
+        ro.render_frame(ctx, f, image, order=args.order)
         host_img.copy_(image, non_blocking=True)
         ids, ov, nodes = ctx.read_requests()
         req_bytes += 4 * (ids.size + nodes.size) + 12
@@ -425,6 +429,7 @@ def run_ours(args, rank, world, local_rank):
            "warmup": args.warmup, "ms_per_step": total_ms / len(order), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": args.precision, "data": "synthetic (seeded procedural cells; no dataset)",
            "config": dict(label, l2="inputs larger than L2 (8 GiB brick cache)", precision=args.precision,
+                          tile_order=["rows", "longest first (previous frame's costs)"][args.order],
                           parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                           render_ms_avg=round(avg_render_s * 1000, 3),
                           channel_samples_per_step=chan // len(order), samples_per_step=samples // len(order),
@@ -436,7 +441,7 @@ def run_ours(args, rank, world, local_rank):
            "clocks": clk,
            "e2e": {"value": samples_all / e2e_s, "unit": "samples/s",
                    "h2d_bytes_per_step": lut_bytes, "d2h_bytes_per_step": W * H * 16 + req_bytes // len(order)},
-           "gpu_launches": 9 * len(order),
+           "gpu_launches": (9 + args.order) * len(order),
            "cpu_baseline": cpu,
            "precision": precision}
     print(json.dumps(out), flush=True)

@@ -211,7 +211,12 @@ typedef struct {
  *  ert         early ray termination once transmittance < ert; 0 = off
  *  debug_*     optional device pointers (W*H u32 each) for the per-pixel
  *              selection hash, evaluated samples, final lattice index and
- *              brick samples; NULL to skip. */
+ *              brick samples; NULL to skip.
+ *  order       ro_render only: 0 = pixel tiles row by row; 1 = longest tiles
+ *              first, by the per-tile costs the previous frame of the same
+ *              size recorded (the frame then runs as a one-view batch, see
+ *              ro_render_batch; needs max_batch_tiles >= its tiles, else
+ *              rows are used).  Changes the speed only. */
 typedef struct {
   float dt;
   float lod_t[RO_MAX_LEVELS];
@@ -224,6 +229,7 @@ typedef struct {
   uint32_t* debug_n_eval;
   uint32_t* debug_i_end;
   uint32_t* debug_n_bs;
+  uint32_t order;
 } ro_render_params;
 
 /* Renders one frame (Sec. 6): one thread per pixel marches its ray through

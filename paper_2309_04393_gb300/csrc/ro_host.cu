@@ -839,6 +839,17 @@ ro_status ro_render(ro_ctx* c, const ro_camera* cam, const ro_tf* tfs, const ro_
   if (c->latched != RO_OK) return c->latched;
   RO_TRY(check_view(c, cam, p, image, W, H, "ro_render"));
   RO_TRY(check_tfs(c, tfs, "ro_render"));
+  if (p->order == 1 && c->desc.max_batch_tiles >= (uint64_t)((W + 7) / 8) * ((H + 3) / 4)) {
+    // longest tiles first: the one-view batch path records and uses per-tile costs
+    ro_view v{};
+    v.camera = *cam;
+    v.params = *p;
+    v.image = image;
+    v.W = W;
+    v.H = H;
+    const ro_schedule sc{8, 1};
+    return ro_render_batch(c, 1, &v, tfs, &sc);
+  }
   const uint64_t blocks = (uint64_t)((W + 15) / 16) * ((H + 15) / 16);
   if (blocks > kMaxStatBlocks) return set_err(c, RO_ERR_CAPACITY, "ro_render: image larger than 65536 blocks of 16x16");
   const Geometry& g = c->g;

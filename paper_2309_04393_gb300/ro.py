@@ -62,7 +62,7 @@ class RenderParams(ctypes.Structure):
                 ("lmin", ctypes.c_uint32 * RO_MAX_CHANNELS), ("lmax", ctypes.c_uint32 * RO_MAX_CHANNELS),
                 ("start_depth", ctypes.c_uint32), ("skip", ctypes.c_uint32), ("ert", ctypes.c_float),
                 ("debug_hash", ctypes.c_void_p), ("debug_n_eval", ctypes.c_void_p),
-                ("debug_i_end", ctypes.c_void_p), ("debug_n_bs", ctypes.c_void_p)]
+                ("debug_i_end", ctypes.c_void_p), ("debug_n_bs", ctypes.c_void_p), ("order", ctypes.c_uint32)]
 
 
 class View(ctypes.Structure):
@@ -310,13 +310,14 @@ def camera_struct(cam) -> Camera:
     return c
 
 
-def params_struct(frame, debug=None) -> RenderParams:
+def params_struct(frame, debug=None, order=0) -> RenderParams:
     p = RenderParams()
     p.dt = frame.dt
     p.lod_t[:] = list(frame.lod_t) + [float("inf")] * (RO_MAX_LEVELS - len(frame.lod_t))
     p.lmin[:] = list(frame.lmin) + [0] * (RO_MAX_CHANNELS - len(frame.lmin))
     p.lmax[:] = list(frame.lmax) + [0] * (RO_MAX_CHANNELS - len(frame.lmax))
     p.start_depth, p.skip, p.ert = int(frame.start_depth), int(frame.skip), float(frame.ert)
+    p.order = int(order)
     if debug is not None:
         p.debug_hash, p.debug_n_eval, p.debug_i_end, p.debug_n_bs = [int(t.data_ptr()) for t in debug]
     return p
@@ -341,7 +342,7 @@ def render_batch(ctx: Context, frames, images=None, tile_w=8, order=0, debug=Fal
     return images, dbgs
 
 
-def render_frame(ctx: Context, frame, image=None, debug=False):
+def render_frame(ctx: Context, frame, image=None, debug=False, order=0):
     """Render one frame described by a synth.Frame-like object (W, H, camera,
     tfs, dt, lod_t, lmin, lmax, start_depth, skip, ert).  Returns the (H, W, 4)
     float32 cuda image and, with debug=True, per-pixel (hash, n_eval, i_end,
@@ -353,6 +354,6 @@ def render_frame(ctx: Context, frame, image=None, debug=False):
     dbg = None
     if debug:
         dbg = [torch.zeros((H, W), dtype=torch.int32, device=ctx.device) for _ in range(4)]
-    ctx.render(camera_struct(frame.camera), [(t.lo, t.scale, t.lut) for t in frame.tfs], params_struct(frame, dbg),
-               image, W, H)
+    ctx.render(camera_struct(frame.camera), [(t.lo, t.scale, t.lut) for t in frame.tfs],
+               params_struct(frame, dbg, order), image, W, H)
     return image, dbg

@@ -157,3 +157,24 @@ def test_batch_errors(scene_ctx):
     assert e.value.status == 3                                   # no batch region
     got, *_ = batch(ctx, frames, 8, 0)                            # still usable
     assert len(got) == len(frames)
+
+
+def test_render_longest_first_order_changes_nothing(scene_ctx):
+    """ro_render with order 1 (a one-view batch ordered by the previous
+    frame's tile costs) renders what order 0 renders."""
+    from paper_2309_04393_gb300 import ro
+    scene, ctx, frames, _ = scene_ctx
+
+    def one(f, order):
+        img, dbg = ro.render_frame(ctx, f, debug=True, order=order)
+        stats = ctx.stats()
+        r, ov, nd = ctx.read_requests()
+        return (img.cpu().numpy(), [_np(t) for t in dbg]), set(r.tolist()), set(nd.tolist()), stats
+
+    for f in frames:
+        ref = one(f, 0)
+        for rep in range(2):                    # the second call orders by the first one's costs
+            got = one(f, 1)
+            assert_same([ref[0]], [got[0]])
+            assert got[1] == ref[1] and got[2] == ref[2]
+            assert np.array_equal(got[3][:6], ref[3][:6])
