@@ -295,6 +295,18 @@ ro_status ro_render_batch(ro_ctx* ctx, uint32_t n_views, const ro_view* views, c
 ro_status ro_autotune_batch(ro_ctx* ctx, uint32_t n_views, const ro_view* views, const ro_tf* tfs,
                             ro_schedule* best, float* best_ms);
 
+/* Frees channel slot ch for another data-set channel (Sec. 5.1: the mapping
+ * of data-set channels to the m channels of the structure changes at run
+ * time; Sec. 5.2: the nodes' information for the new channel is INVALID
+ * until it arrives).  The slot's bricks leave the cache (their slots become
+ * free, their page-table entries 0), every octree node's word for ch becomes
+ * INVALID with an empty mask, and the slot's pending brick requests are
+ * dropped.  The caller keeps the mapping: from now on IDs and node requests
+ * of ch refer to the new data-set channel, whose leaf metadata and bricks
+ * arrive through ro_update_residency_octree and ro_upload_bricks as the
+ * renderer requests them.  Enqueued on the stream. */
+ro_status ro_replace_channel(ro_ctx* ctx, uint32_t ch);
+
 /* Compacts the flags of the frames rendered since the previous call
  * (Sec. 4: a global request limit keeps the copy small): brick requests as
  * sorted IDs, node requests as node*m + channel, usage as

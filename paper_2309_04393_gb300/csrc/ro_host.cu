@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <thread>
 #include <vector>
@@ -1022,6 +1023,32 @@ ro_status ro_autotune_batch(ro_ctx* c, uint32_t n_views, const ro_view* views, c
   RO_TRY(wait_stream(c, "ro_autotune_batch"));
   *best = win;
   if (best_ms) *best_ms = best_t;
+  return RO_OK;
+}
+
+ro_status ro_replace_channel(ro_ctx* c, uint32_t ch) {
+  if (!c) return RO_ERR_INVALID_ARG;
+  if (c->latched != RO_OK) return c->latched;
+  const Geometry& g = c->g;
+  if (ch >= (uint32_t)g.m) return set_err(c, RO_ERR_INVALID_ARG, "ro_replace_channel: channel out of range");
+  const uint64_t first = g.pt_off[ch * g.k], last = g.pt_off[(ch + 1) * g.k];
+  // the channel's resident bricks give their slots back
+  for (uint64_t pi = first; pi < last; ++pi) {
+    const uint32_t sl = c->slot_of_brick[pi];
+    if (sl == RO_NONE) continue;
+    c->slot_of_brick[pi] = RO_NONE;
+    c->brick_of_slot[sl] = RO_NONE;
+    c->free_slots.push_back(sl);
+  }
+  std::sort(c->free_slots.begin(), c->free_slots.end(), std::greater<uint32_t>());
+  c->pending.erase(std::remove_if(c->pending.begin(), c->pending.end(),
+                                  [&](uint32_t pi) { return pi >= first && pi < last; }),
+                   c->pending.end());
+  cudaStream_t st = c->stream;
+  RO_TRY(cuda_check(c, cudaMemsetAsync(c->pt + first, 0, (last - first) * 4, st), "ro_replace_channel: page tables"));
+  RO_TRY(cuda_check(c, cudaMemsetAsync(c->req + first, 0, last - first, st), "ro_replace_channel: requests"));
+  RO_TRY(cuda_check(c, ro::launch_fill_strided(c->octree + ch, g.n_nodes, (uint32_t)g.mp, 0x00FF0000u, st),
+                    "ro_replace_channel: octree"));
   return RO_OK;
 }
 

@@ -178,6 +178,7 @@ cudaError_t launch_render_batch_lp(const RenderArgs& a, bool debug, cudaStream_t
 // buckets; ties in any order).
 cudaError_t launch_cost_order(const uint32_t* cost, uint32_t n_tiles, uint32_t* order, cudaStream_t s);
 cudaError_t launch_fill_words(uint32_t* words, uint64_t n, uint32_t value, cudaStream_t s);
+cudaError_t launch_fill_strided(uint32_t* first, uint64_t count, uint32_t stride, uint32_t value, cudaStream_t s);
 cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s);
 cudaError_t launch_write_meta(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_leaf_masks(const UpdateArgs& a, cudaStream_t s);

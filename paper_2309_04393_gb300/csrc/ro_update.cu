@@ -21,6 +21,12 @@ __global__ void fill_words_kernel(uint32_t* __restrict__ w, uint64_t n, uint32_t
     w[i] = value;
 }
 
+// Every n-th word starting at `first` (one channel's column of the octree).
+__global__ void fill_strided_kernel(uint32_t* __restrict__ w, uint64_t count, uint32_t stride, uint32_t value) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x)
+    w[i * stride] = value;
+}
+
 // Copy each staged brick into its slot (16-byte vectors; slot_pitch is a
 // multiple of 256) and write the page-table entries of inserted (slot + 1)
 // and evicted (0) bricks.
@@ -174,6 +180,14 @@ cudaError_t launch_fill_words(uint32_t* words, uint64_t n, uint32_t value, cudaS
   uint64_t blocks = (n + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   fill_words_kernel<<<(unsigned)blocks, 256, 0, s>>>(words, n, value);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_strided(uint32_t* first, uint64_t count, uint32_t stride, uint32_t value, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  uint64_t blocks = (count + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  fill_strided_kernel<<<(unsigned)blocks, 256, 0, s>>>(first, count, stride, value);
   return cudaGetLastError();
 }
 

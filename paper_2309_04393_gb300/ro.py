@@ -23,7 +23,7 @@ STATUS = {0: "RO_OK", 1: "RO_ERR_INVALID_ARG", 2: "RO_ERR_CUDA", 3: "RO_ERR_CAPA
           5: "RO_ERR_INTERNAL"}
 EXPORTS = ["ro_query_sizes", "ro_create", "ro_destroy", "ro_upload_bricks", "ro_update_residency_octree", "ro_render",
            "ro_read_requests", "ro_get_stats", "ro_debug_read", "ro_brick_index", "ro_set_timeout", "ro_last_error",
-           "ro_compact_flags_noalloc", "ro_render_batch", "ro_autotune_batch"]
+           "ro_compact_flags_noalloc", "ro_render_batch", "ro_autotune_batch", "ro_replace_channel"]
 
 
 class RoError(RuntimeError):
@@ -113,6 +113,7 @@ def load(build_if_missing: bool = True):
     L.ro_last_error.argtypes = [vp]
     L.ro_compact_flags_noalloc.argtypes = [vp, u64, vp, u32, vp, vp]
     L.ro_render_batch.argtypes = [vp, u32, vp, vp, ctypes.POINTER(Schedule)]
+    L.ro_replace_channel.argtypes = [vp, u32]
     L.ro_autotune_batch.argtypes = [vp, u32, vp, vp, ctypes.POINTER(Schedule), ctypes.POINTER(ctypes.c_float)]
     for f in EXPORTS:
         getattr(L, f).restype = getattr(L, f).restype if f in ("ro_brick_index", "ro_last_error") else ctypes.c_int
@@ -249,6 +250,10 @@ class Context:
         best, ms = Schedule(), ctypes.c_float()
         self._check(self.L.ro_autotune_batch(self.h, len(views), vs, arr, ctypes.byref(best), ctypes.byref(ms)))
         return (int(best.tile_w), int(best.order)), float(ms.value)
+
+    def replace_channel(self, ch: int):
+        """Free channel slot ch for another data-set channel (ro_replace_channel)."""
+        self._check(self.L.ro_replace_channel(self.h, int(ch)))
 
     def read_requests(self, cap=None, node_cap=None):
         cap = int(self.desc.max_requests if cap is None else cap)
