@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=16)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["cells16", "cells4", "blobs", "views64", "compensator"], default="cells16")
+    ap.add_argument("--workload", choices=["cells16", "cells4", "blobs", "views64", "compensator", "leafsweep"],
+                    default="cells16")
     ap.add_argument("--pairs", type=int, default=200000, help="compensator: coarse/fine training pairs")
     ap.add_argument("--warm-seconds", type=float, default=150.0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
@@ -736,6 +737,55 @@ def run_compensator(args, rank, world, local_rank):
     return 0
 
 
+def run_leafsweep(args, rank, world, local_rank):
+    """Render time against the octree's leaf extent and the number of
+    channels (the analogue of the paper's subdivision study): the cell slab
+    of 1024x1024x64 u16 voxels (spacing 1:1:4) with 1, 4 or 16 channels and
+    leaves of 8x8x2 .. 32x32x8 voxels, one 1920x1080 view, every requested
+    brick resident after a ray-guided warm-up; 5 timed renders each."""
+    import torch
+    from paper_2309_04393_gb300 import loader, ro
+    from synth import recipes
+    torch.cuda.set_device(local_rank)
+    if rank != 0:
+        return 0
+    rows = []
+    for m in (1, 4, 16):
+        for leaf in ((8, 8, 2), (16, 16, 4), (32, 32, 8)):
+            scene = recipes.cells_views(m=m, n_views=1, sizes=((1920, 1080),), leaf=leaf)
+            f = scene.frames[0]
+            desc = ro.make_desc(scene.dims, scene.spacing, scene.m, scene.value_bits, scene.B, scene.k, scene.leaf,
+                                len(scene.all_bricks()), max_requests=1 << 16, max_upload=2048, max_meta=1 << 21)
+            ctx = ro.Context(desc)
+            ctx.update_residency_octree(loader.meta_rows(scene.leaf_min, scene.leaf_max))
+            img = torch.empty((f.H, f.W, 4), dtype=torch.float32, device="cuda")
+            warm = warm_cache(ctx, scene, img, 120, 8)
+            ts = []
+            for _ in range(6):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ro.render_frame(ctx, f, img)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+                st = ctx.stats()
+                ctx.read_requests()
+            rows.append({"channels": m, "leaf": list(leaf), "depth": int(ctx.sizes.depth),
+                         "nodes": int(ctx.sizes.n_nodes), "render_ms": round(float(np.median(ts[1:])), 3),
+                         "samples": int(st[1]), "channel_samples": int(st[2]), "skips": int(st[4]),
+                         "warm_rounds": warm["rounds"]})
+            log(f"  m {m} leaf {leaf}: {rows[-1]['render_ms']} ms, depth {rows[-1]['depth']}")
+            ctx.close()
+    best = min(rows, key=lambda r: r["render_ms"] / max(1, r["channels"]))
+    out = {"metric": "render ms (1920x1080) by leaf extent and channels", "value": best["render_ms"], "unit": "ms",
+           "n_gpus": 1, "higher_is_better": False, "dtype": "f32", "data": "synthetic (seeded procedural cells)",
+           "config": {"workload": "leafsweep: 1024x1024x64 u16 cell slab (spacing 1:1:4), 32^3 bricks, 5 levels, "
+                                  "1, 4, 16 channels x leaves 8x8x2, 16x16x4, 32x32x8, one 1920x1080 view"},
+           "rows": rows}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -748,7 +798,8 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    run = {"views64": run_views, "compensator": run_compensator}.get(args.workload, run_ours)
+    run = {"views64": run_views, "compensator": run_compensator, "leafsweep": run_leafsweep}.get(args.workload,
+                                                                                                run_ours)
     rc = run(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist

@@ -159,14 +159,15 @@ VIEW_SIZES = ((256, 256), (512, 512), (1024, 768), (1920, 1080))
 
 
 def cells_views(seed=5, m=16, dims=(1024, 1024, 64), ncells=20000, k=5, n_views=64, sizes=VIEW_SIZES, fovy=40.0,
-                elevation=(25.0, 60.0), distance=(0.6, 1.2)) -> Scene:
+                elevation=(25.0, 60.0), distance=(0.6, 1.2), leaf=(16, 16, 4)) -> Scene:
     """m-channel u16 slab (spacing 1:1:4) of the cell model, bricks generated
     on request; n_views seeded perspective cameras around the slab, each with
     an image size drawn uniformly from `sizes`, a seeded azimuth, elevation and
-    distance (a multiple of the distance that frames the whole slab)."""
+    distance (a multiple of the distance that frames the whole slab); leaf:
+    the octree's leaf extent in level-0 voxels."""
     spacing = (1.0, 1.0, 4.0)
     cells = Cells(seed, ncells, m, dims, spacing)
-    leaf = (16, 16, 4)
+    leaf = tuple(int(v) for v in leaf)
     mins, maxs = zip(*[cells.leaf_bounds(c, leaf) for c in range(m)])
     s = Scene("cells_views", tuple(dims), spacing, m, k, 32, leaf, 16, cells=cells,
               leaf_min=np.stack(mins).astype(np.int64), leaf_max=np.stack(maxs).astype(np.int64))
