@@ -570,7 +570,8 @@ ro_status ro_compensate_bricks(ro_ctx* c, ro_mc* mc, uint32_t n, const uint32_t*
   if (!mc || !ids) return set_err(c, RO_ERR_INVALID_ARG, "ro_compensate_bricks: null pointer");
   if (c->g.edge != RO_MC_EDGE || c->g.bpv != 2 || c->g.sf != 0 || c->g.k < 2)
     return set_err(c, RO_ERR_INVALID_ARG, "ro_compensate_bricks: needs 32^3 u16 bricks, raw samples, >= 2 levels");
-  if (n > c->desc.max_upload || n > c->desc.cache_slots || n > ro::mc_max_batch(mc))
+  if (n > c->desc.max_upload || n > c->desc.cache_slots || n > ro::mc_max_batch(mc) ||
+      2ull * n * sizeof(uint32_t) > (uint64_t)kMaxItems * sizeof(ro::UpdateItem))
     return set_err(c, RO_ERR_CAPACITY, "ro_compensate_bricks: n exceeds max_upload, cache_slots or the batch");
   std::vector<uint32_t> pis;
   RO_TRY(check_ids(c, n, ids, pis, where));
