@@ -279,6 +279,130 @@ __global__ void __launch_bounds__(kConvThreads) conv_mma_kernel(const float* __r
 
 constexpr size_t conv_mma_smem() { return (size_t)(HZ * HY * HX + 27 * HID) * kRowB; }
 
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+// Weight gradients of a 32 -> 32 layer on the tensor cores: for every tap
+// dW[t] (32 x 32) = sum over voxels of in[v + off(t)]^T g[v], i.e. a GEMM
+// with M = input channels, N = output channels, K = voxels.  One block per
+// tile position loops over the batch; the input tile (halo) and the
+// gradient tile enter shared memory as bfloat16 rows, and ldmatrix.trans
+// turns the voxel rows into the K dimension of both operands.  Warp w
+// accumulates taps w, w + 8, w + 16, w + 24 over every grid and adds its
+// sums once (atomically) at the end.
+__global__ void __launch_bounds__(kConvThreads) wgrad_mma_kernel(const float* __restrict__ in,
+                                                                const float* __restrict__ g, int n_grids,
+                                                                float* __restrict__ dW) {
+  extern __shared__ __align__(16) uint8_t smb[];
+  uint8_t* s_x = smb;                                       // HZ * HY * HX rows (input, halo)
+  uint8_t* s_g = smb + HZ * HY * HX * kRowB;                // TZ * TY * TX rows (gradient)
+  const int tile = blockIdx.x;
+  const int x0t = (tile % kTilesX) * TX, y0t = ((tile / kTilesX) % kTilesY) * TY, z0t = (tile / (kTilesX * kTilesY)) * TZ;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g4 = lane >> 2, t4 = lane & 3;
+  const int mi = lane >> 3, mr = lane & 7;
+  constexpr int kTapsPerWarp = 4;
+  float acc[kTapsPerWarp][2][4][4];
+#pragma unroll
+  for (int j = 0; j < kTapsPerWarp; ++j)
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[j][mt][nt][q] = 0.0f;
+  const uint32_t x_base = smem_u32(s_x), g_base = smem_u32(s_g);
+  for (int n = 0; n < n_grids; ++n) {
+    const float* src = in + (size_t)n * NV * HID;
+    const float* gs = g + (size_t)n * NV * HID;
+    __syncthreads();
+    for (int q = threadIdx.x; q < HZ * HY * HX * (HID / 2); q += blockDim.x) {
+      const int c2 = q % (HID / 2), p = q / (HID / 2);
+      const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
+      const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
+      float2 v = make_float2(0.0f, 0.0f);
+      if (gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
+        v = *reinterpret_cast<const float2*>(src + ((size_t)(gz * EG + gy) * EG + gx) * HID + 2 * c2);
+      *reinterpret_cast<__nv_bfloat162*>(s_x + p * kRowB + 4 * c2) = __floats2bfloat162_rn(v.x, v.y);
+    }
+    for (int q = threadIdx.x; q < TZ * TY * TX * (HID / 2); q += blockDim.x) {
+      const int c2 = q % (HID / 2), p = q / (HID / 2);
+      const int gx = x0t + p % TX, gy = y0t + (p / TX) % TY, gz = z0t + p / (TX * TY);
+      float2 v = make_float2(0.0f, 0.0f);                   // voxels outside the grid add nothing
+      if (gx < EG && gy < EG && gz < EG)
+        v = *reinterpret_cast<const float2*>(gs + ((size_t)(gz * EG + gy) * EG + gx) * HID + 2 * c2);
+      *reinterpret_cast<__nv_bfloat162*>(s_g + p * kRowB + 4 * c2) = __floats2bfloat162_rn(v.x, v.y);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kTapsPerWarp; ++j) {
+      const int t = warp + 8 * j;
+      if (t >= 27) break;
+      const int toff = ((t / 9) * HY + (t / 3) % 3) * HX + t % 3;
+      for (int kc = 0; kc < (TZ * TY * TX) / 16; ++kc) {
+        // A (input channels x voxels): voxel row r + 8 (i >> 1), channels 8 (i & 1) (+16 per m tile)
+        const int pa = 16 * kc + mr + 8 * (mi >> 1);
+        const int pos = ((pa / (TX * TY)) * HY + (pa / TX) % TY) * HX + pa % TX + toff;
+        uint32_t a[2][4], b[4][2];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+          ldsm_x4_t(x_base + pos * kRowB + 16 * (mi & 1) + 32 * mt, a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+        // B (voxels x output channels): voxel row r + 8 (i & 1), channels 8 (i >> 1) + 16 nj
+        const int pb = 16 * kc + mr + 8 * (mi & 1);
+#pragma unroll
+        for (int nj = 0; nj < 2; ++nj)
+          ldsm_x4_t(g_base + pb * kRowB + 16 * (mi >> 1) + 32 * nj, b[2 * nj][0], b[2 * nj][1], b[2 * nj + 1][0],
+                    b[2 * nj + 1][1]);
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt)
+            mma_bf16(acc[j][mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b[nt][0], b[nt][1]);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kTapsPerWarp; ++j) {
+    const int t = warp + 8 * j;
+    if (t >= 27) break;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int ci = 16 * mt + g4 + 8 * h;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          const int co = 8 * nt + 2 * t4;
+          atomicAdd(&dW[(t * HID + ci) * HID + co], acc[j][mt][nt][2 * h]);
+          atomicAdd(&dW[(t * HID + ci) * HID + co + 1], acc[j][mt][nt][2 * h + 1]);
+        }
+      }
+  }
+}
+
+constexpr size_t wgrad_mma_smem() { return (size_t)(HZ * HY * HX + TZ * TY * TX) * kRowB; }
+
+// Bias gradients db[c] += sum over voxels of g[v][c] (block partial sums).
+template <int C>
+__global__ void bias_grad_kernel(const float* __restrict__ g, size_t n_vox, float* __restrict__ db) {
+  float part = 0.0f;
+  const int c = threadIdx.x % C;
+  for (size_t v = (size_t)blockIdx.x * (blockDim.x / C) + threadIdx.x / C; v < n_vox;
+       v += (size_t)gridDim.x * (blockDim.x / C))
+    part += g[v * C + c];
+  __shared__ float s_p[256];
+  s_p[threadIdx.x] = part;
+  __syncthreads();
+  if (threadIdx.x < C) {
+    float s = 0.0f;
+    for (int q = threadIdx.x; q < (int)blockDim.x; q += C) s += s_p[q];
+    atomicAdd(&db[threadIdx.x], s);
+  }
+}
+
 // ------------------------------------------------------ weight gradients
 // dW[tap][ci][co] += sum_v in[v + off(tap)][ci] * g[v][co] and db[co] +=
 // sum_v g[v][co] over one tile position of every grid; each block owns one
@@ -490,6 +614,16 @@ cudaError_t conv_tc(const float* in, const __nv_bfloat16* wb, const float* b, fl
   return cudaGetLastError();
 }
 
+cudaError_t wgrad_tc(const float* in, const float* g, uint32_t n, float* dW, float* db, cudaStream_t s) {
+  constexpr size_t sm = wgrad_mma_smem();
+  cudaError_t e = cudaFuncSetAttribute(wgrad_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  wgrad_mma_kernel<<<kTilesX * kTilesY * kTilesZ, kConvThreads, sm, s>>>(in, g, (int)n, dW);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  bias_grad_kernel<HID><<<152 * 2, 256, 0, s>>>(g, (size_t)n * NV, db);
+  return cudaGetLastError();
+}
+
 template <int CIN, int COUT>
 cudaError_t wgrad(const float* in, const float* g, uint32_t n, float* dW, float* db, cudaStream_t s) {
   auto k = wgrad_kernel<CIN, COUT>;
@@ -529,10 +663,10 @@ cudaError_t mc_backward(ro_mc* m, uint32_t n, const float* x0, const float* targ
   if (e == cudaSuccess) e = wgrad<HID, 1>(m->a3, m->g4, n, G + kWOff[3], G + kBOff[3], s);
   if (e == cudaSuccess) e = conv<1, HID, kEpiMask>(m->g4, m->Wt3, zero_bias, m->ga, m->a3, n, s);
   // layer 3 (32 -> 32)
-  if (e == cudaSuccess) e = wgrad<HID, HID>(m->a2, m->ga, n, G + kWOff[2], G + kBOff[2], s);
+  if (e == cudaSuccess) e = wgrad_tc(m->a2, m->ga, n, G + kWOff[2], G + kBOff[2], s);
   if (e == cudaSuccess) e = conv_tc<kEpiMask>(m->ga, m->wd2, zero_bias, m->gb, m->a2, n, s);
   // layer 2 (32 -> 32)
-  if (e == cudaSuccess) e = wgrad<HID, HID>(m->a1, m->gb, n, G + kWOff[1], G + kBOff[1], s);
+  if (e == cudaSuccess) e = wgrad_tc(m->a1, m->gb, n, G + kWOff[1], G + kBOff[1], s);
   if (e == cudaSuccess) e = conv_tc<kEpiMask>(m->gb, m->wd1, zero_bias, m->ga, m->a1, n, s);
   // layer 1 (1 -> 32)
   if (e == cudaSuccess) e = wgrad<1, HID>(x0, m->ga, n, G + kWOff[0], G + kBOff[0], s);
