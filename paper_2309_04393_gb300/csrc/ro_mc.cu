@@ -503,14 +503,13 @@ __global__ void loss_kernel(const float* __restrict__ y, const float* __restrict
 
 // ------------------------------------------------------------ parameters
 // The effective weights: each W rounded to bfloat16 (nearest even), biases
-// as they are; and for layers 1..3 the input-gradient weights
-// wt[26 - tap][co][ci] = W[tap][ci][co].
-// For the tensor-core layers 1 and 2 also bfloat16 rows: forward
-// wf[tap][co][ci] and input gradient wd[26 - tap][ci][co] (= W[tap][ci][co]).
-__global__ void refresh_kernel(const float* __restrict__ P, float* __restrict__ Pq, float* __restrict__ Wt1,
-                               float* __restrict__ Wt2, float* __restrict__ Wt3, __nv_bfloat16* __restrict__ wf1,
-                               __nv_bfloat16* __restrict__ wf2, __nv_bfloat16* __restrict__ wd1,
-                               __nv_bfloat16* __restrict__ wd2) {
+// as they are.  Layer 3 (32 -> 1) also gets its binary32 input-gradient
+// weights wt3[26 - tap][co][ci] = W[tap][ci][co]; the tensor-core layers 1
+// and 2 get bfloat16 rows: forward wf[tap][co][ci] and input gradient
+// wd[26 - tap][ci][co] (= W[tap][ci][co]).
+__global__ void refresh_kernel(const float* __restrict__ P, float* __restrict__ Pq, float* __restrict__ Wt3,
+                               __nv_bfloat16* __restrict__ wf1, __nv_bfloat16* __restrict__ wf2,
+                               __nv_bfloat16* __restrict__ wd1, __nv_bfloat16* __restrict__ wd2) {
   const int woff[4] = {kWOff[0], kWOff[1], kWOff[2], kWOff[3]}, boff[4] = {kBOff[0], kBOff[1], kBOff[2], kBOff[3]};
   const int cin[4] = {kCin[0], kCin[1], kCin[2], kCin[3]}, cout[4] = {kCout[0], kCout[1], kCout[2], kCout[3]};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < RO_MC_PARAMS; i += gridDim.x * blockDim.x) {
@@ -523,9 +522,9 @@ __global__ void refresh_kernel(const float* __restrict__ P, float* __restrict__ 
       const int ci_n = cin[layer], co_n = cout[layer];
       const int r = i - woff[layer];
       const int t = r / (ci_n * co_n), ci = (r / co_n) % ci_n, co = r % co_n;
-      float* wt = layer == 1 ? Wt1 : (layer == 2 ? Wt2 : Wt3);
-      wt[((26 - t) * co_n + co) * ci_n + ci] = q;
-      if (layer <= 2) {
+      if (layer == 3) {
+        Wt3[((26 - t) * co_n + co) * ci_n + ci] = q;
+      } else {
         const __nv_bfloat16 h = __float2bfloat16_rn(q);
         (layer == 1 ? wf1 : wf2)[(t * co_n + co) * ci_n + ci] = h;
         (layer == 1 ? wd1 : wd2)[((26 - t) * ci_n + ci) * co_n + co] = h;
@@ -557,7 +556,7 @@ struct ro_mc {
   ro_mc_desc desc;
   cudaStream_t stream = nullptr;
   float *P, *Pq, *M, *V, *G;          // parameters, effective copy, Adam moments, gradients
-  float *Wt1, *Wt2, *Wt3;             // input-gradient weights of layers 1..3
+  float* Wt3;                         // binary32 input-gradient weights of layer 3
   __nv_bfloat16 *wf1, *wf2, *wd1, *wd2;  // tensor-core rows of layers 1 and 2 (forward, input gradient)
   float *a1, *a2, *a3;                // hidden activations (after ReLU), n * NV * 32
   float *ga, *gb;                     // hidden gradients, n * NV * 32
@@ -572,7 +571,7 @@ constexpr uint64_t kMcAlign = 256;
 uint64_t mc_align(uint64_t v) { return (v + kMcAlign - 1) / kMcAlign * kMcAlign; }
 
 struct McLayout {
-  uint64_t P, Pq, M, V, G, Wt1, Wt2, Wt3, wf1, wf2, wd1, wd2, a1, a2, a3, ga, gb, g4, y, loss, total;
+  uint64_t P, Pq, M, V, G, Wt3, wf1, wf2, wd1, wd2, a1, a2, a3, ga, gb, g4, y, loss, total;
 };
 
 McLayout mc_layout(uint32_t nb) {
@@ -581,7 +580,7 @@ McLayout mc_layout(uint32_t nb) {
   auto take = [&](uint64_t bytes) { const uint64_t at = o; o = mc_align(o + bytes); return at; };
   const uint64_t pb = (uint64_t)RO_MC_PARAMS * 4, hid = (uint64_t)nb * NV * HID * 4, one = (uint64_t)nb * NV * 4;
   L.P = take(pb); L.Pq = take(pb); L.M = take(pb); L.V = take(pb); L.G = take(pb);
-  L.Wt1 = take(27ull * HID * HID * 4); L.Wt2 = take(27ull * HID * HID * 4); L.Wt3 = take(27ull * HID * 4);
+  L.Wt3 = take(27ull * HID * 4);
   L.wf1 = take(27ull * HID * HID * 2); L.wf2 = take(27ull * HID * HID * 2);
   L.wd1 = take(27ull * HID * HID * 2); L.wd2 = take(27ull * HID * HID * 2);
   L.a1 = take(hid); L.a2 = take(hid); L.a3 = take(hid); L.ga = take(hid); L.gb = take(hid);
@@ -589,8 +588,6 @@ McLayout mc_layout(uint32_t nb) {
   L.total = o;
   return L;
 }
-
-bool mc_ok(cudaError_t e) { return e == cudaSuccess; }
 
 template <int CIN, int COUT, int EPI>
 cudaError_t conv(const float* in, const float* w, const float* b, float* out, const float* aux, uint32_t n,
@@ -674,7 +671,7 @@ cudaError_t mc_backward(ro_mc* m, uint32_t n, const float* x0, const float* targ
 }
 
 cudaError_t mc_refresh(ro_mc* m) {
-  refresh_kernel<<<64, 256, 0, m->stream>>>(m->P, m->Pq, m->Wt1, m->Wt2, m->Wt3, m->wf1, m->wf2, m->wd1, m->wd2);
+  refresh_kernel<<<64, 256, 0, m->stream>>>(m->P, m->Pq, m->Wt3, m->wf1, m->wf2, m->wd1, m->wd2);
   return cudaGetLastError();
 }
 
@@ -699,12 +696,12 @@ ro_status ro_mc_create(const ro_mc_desc* d, void* arena, uint64_t arena_bytes, v
   uint8_t* b = static_cast<uint8_t*>(arena);
   auto f = [&](uint64_t off) { return reinterpret_cast<float*>(b + off); };
   m->P = f(L.P); m->Pq = f(L.Pq); m->M = f(L.M); m->V = f(L.V); m->G = f(L.G);
-  m->Wt1 = f(L.Wt1); m->Wt2 = f(L.Wt2); m->Wt3 = f(L.Wt3);
+  m->Wt3 = f(L.Wt3);
   auto h = [&](uint64_t off) { return reinterpret_cast<__nv_bfloat16*>(b + off); };
   m->wf1 = h(L.wf1); m->wf2 = h(L.wf2); m->wd1 = h(L.wd1); m->wd2 = h(L.wd2);
   m->a1 = f(L.a1); m->a2 = f(L.a2); m->a3 = f(L.a3); m->ga = f(L.ga); m->gb = f(L.gb);
   m->g4 = f(L.g4); m->y = f(L.y); m->loss = f(L.loss);
-  cudaError_t e = cudaMemsetAsync(arena, 0, L.Wt1, m->stream);   // parameters, copies, moments, gradients
+  cudaError_t e = cudaMemsetAsync(arena, 0, L.Wt3, m->stream);   // parameters, copies, moments, gradients
   if (e == cudaSuccess) e = mc_refresh(m);
   if (e != cudaSuccess) {
     delete m;
