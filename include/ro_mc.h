@@ -59,7 +59,11 @@ ro_status ro_mc_destroy(ro_mc* mc);
  * and zeroes the Adam moments and step count. */
 ro_status ro_mc_set_params(ro_mc* mc, const float* host_params);
 
-/* Copies the RO_MC_PARAMS binary32 parameters to the host (waits). */
+/* Copies the RO_MC_PARAMS binary32 parameters to the host (waits).
+ * Returns RO_ERR_INTERNAL, with the parameters copied, once a tensor-core
+ * convolution of this context gave up waiting for its matrix instructions
+ * (half a second; its output grid is then incomplete).  The flag is latched
+ * for the life of the context. */
 ro_status ro_mc_get_params(ro_mc* mc, float* host_params);
 
 /* n <= max_batch level-1 apron slots (device, n * RO_MC_VOXELS u16 raw

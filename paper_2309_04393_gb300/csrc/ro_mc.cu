@@ -5,12 +5,14 @@
 // Activations are channels-last binary32 grids of 34^3 voxels.  The weights
 // take part as bfloat16 values (the parameters are rounded once per update
 // into an effective binary32 copy); every sum is binary32.  The two 32 -> 32
-// layers (forward and input gradient) run on the tensor cores with their
-// inputs rounded to bfloat16; the rest on the binary32 cores.  A convolution
-// block computes an 8 x 8 x 4 voxel tile for all output channels from a
-// shared-memory copy of the input tile with its one-voxel halo (zero outside
-// the grid) and of the layer's weights; the input-gradient pass is the same
-// kernel on the spatially flipped, channel-transposed weights.
+// layers (forward, input gradient and weight gradient) run on the tensor
+// cores with their inputs rounded to bfloat16; the rest on the binary32
+// cores.  A binary32 convolution block computes an 8 x 8 x 4 voxel tile for
+// all output channels from a shared-memory copy of the input tile with its
+// one-voxel halo (zero outside the grid) and of the layer's weights; the
+// tcgen05 convolution marches an 8 x 16 column along z.  An input-gradient
+// pass is the forward kernel on the spatially flipped, channel-transposed
+// weights.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -153,25 +155,15 @@ constexpr size_t conv_smem() {
   return (size_t)(HZ * HY * HX * pad_stride(CIN) + 27 * CIN * COUT) * sizeof(float);
 }
 
-// ------------------------------------------- tensor-core 32 -> 32 layers
-// The same convolution as conv_kernel<32, 32, EPI> as an implicit GEMM on
-// the tensor cores: M = the block's 256 output voxels, N = 32 output
-// channels, K = 27 taps x 32 input channels, mma.sync m16n8k16 with bfloat16
-// operands and binary32 accumulators.  The input tile enters shared memory
-// rounded to bfloat16 (reading P2), one 80-byte row per voxel (32 channels
-// + padding, so the eight rows of an ldmatrix fall in different banks); the
-// weights come as bfloat16 rows [tap][co][ci] (wb).  Warp w owns voxels
-// 32w .. 32w + 31 of the tile (two m16 tiles) and all four n8 tiles.
+// ----------------------------------------- warp-level tensor-core helpers
+// Shared-memory rows of 32 bfloat16 channels padded to 80 bytes (the eight
+// rows of an ldmatrix fall in different banks), ldmatrix and the mma.sync
+// m16n8k16 bfloat16 product with binary32 accumulators, used by the
+// weight-gradient kernel.
 constexpr int kRowB = 80;                                  // bytes per shared row (32 bf16 + 8 pad)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(addr));
 }
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
@@ -183,101 +175,216 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-template <int EPI>
-__global__ void __launch_bounds__(kConvThreads) conv_mma_kernel(const float* __restrict__ in,
-                                                               const __nv_bfloat16* __restrict__ wb,
-                                                               const float* __restrict__ bias, float* __restrict__ out,
-                                                               const float* __restrict__ aux) {
-  extern __shared__ __align__(16) uint8_t smb[];
-  uint8_t* s_a = smb;                                       // HZ * HY * HX rows
-  uint8_t* s_b = smb + HZ * HY * HX * kRowB;                // 27 * 32 rows
-  const int tile = blockIdx.x, n = blockIdx.y;
-  const int x0t = (tile % kTilesX) * TX, y0t = ((tile / kTilesX) % kTilesY) * TY, z0t = (tile / (kTilesX * kTilesY)) * TZ;
-  const float* src = in + (size_t)n * NV * HID;
-  // input tile with halo, bfloat16, channel pairs
-  for (int q = threadIdx.x; q < HZ * HY * HX * (HID / 2); q += blockDim.x) {
-    const int c2 = q % (HID / 2), p = q / (HID / 2);
-    const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
-    const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
-    float2 v = make_float2(0.0f, 0.0f);
-    if (gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
-      v = *reinterpret_cast<const float2*>(src + ((size_t)(gz * EG + gy) * EG + gx) * HID + 2 * c2);
-    *reinterpret_cast<__nv_bfloat162*>(s_a + p * kRowB + 4 * c2) = __floats2bfloat162_rn(v.x, v.y);
-  }
-  // weights: 27 * 32 rows of 64 bytes
-  for (int q = threadIdx.x; q < 27 * HID * 4; q += blockDim.x) {
-    const int row = q / 4, part = q % 4;
-    *reinterpret_cast<uint4*>(s_b + row * kRowB + 16 * part) = reinterpret_cast<const uint4*>(wb)[q];
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t4 = lane & 3;
-  // this lane's ldmatrix row for A: matrix i = lane / 8 -> row r + 8 (i & 1), k offset 8 (i >> 1)
-  const int mi = lane >> 3, mr = lane & 7;
-  int arow_pos[2];
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt) {
-    const int p = 32 * warp + 16 * mt + mr + 8 * (mi & 1);
-    const int x = p % TX, y = (p / TX) % TY, z = p / (TX * TY);
-    arow_pos[mt] = (z * HY + y) * HX + x;
-  }
-  const int a_koff = 16 * (mi >> 1);                        // bytes
-  // B: matrices 0, 1 = n-tile j (k lo, k hi), 2, 3 = n-tile j + 1
-  const int b_row = 8 * (mi >> 1) + mr, b_koff = 16 * (mi & 1);
-  float acc[2][4][4];
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.0f;
-  const uint32_t a_base = smem_u32(s_a), b_base = smem_u32(s_b);
-  for (int t = 0; t < 27; ++t) {
-    const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-    const int toff = (dz * HY + dy) * HX + dx;
-#pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-      uint32_t a[2][4], b[4][2];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
-        ldsm_x4(a_base + (arow_pos[mt] + toff) * kRowB + 32 * kk + a_koff, a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
-#pragma unroll
-      for (int nj = 0; nj < 2; ++nj)
-        ldsm_x4(b_base + (t * HID + 16 * nj + b_row) * kRowB + 32 * kk + b_koff, b[2 * nj][0], b[2 * nj][1],
-                b[2 * nj + 1][0], b[2 * nj + 1][1]);
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-          mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b[nt][0], b[nt][1]);
-    }
-  }
-  // epilogue: rows g and g + 8 of each m tile, channel pairs 2 t4 of each n tile
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int p = 32 * warp + 16 * mt + g + 8 * h;
-      const int gx = x0t + p % TX, gy = y0t + (p / TX) % TY, gz = z0t + p / (TX * TY);
-      if (gx >= EG || gy >= EG || gz >= EG) continue;
-      const size_t v = (size_t)n * NV + (size_t)(gz * EG + gy) * EG + gx;
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int co = 8 * nt + 2 * t4;
-        float r0 = acc[mt][nt][2 * h], r1 = acc[mt][nt][2 * h + 1];
-        if constexpr (EPI == kEpiRelu) {
-          r0 = fmaxf(r0 + bias[co], 0.0f);
-          r1 = fmaxf(r1 + bias[co + 1], 0.0f);
-        } else {
-          r0 = aux[v * HID + co] > 0.0f ? r0 : 0.0f;
-          r1 = aux[v * HID + co + 1] > 0.0f ? r1 : 0.0f;
-        }
-        *reinterpret_cast<float2*>(out + v * HID + co) = make_float2(r0, r1);
-      }
-    }
+// ------------------------------------ fifth-generation tensor cores (tcgen05)
+// The 32 -> 32 convolution with tcgen05.mma.  A block owns an 8 (x) by 16 (y)
+// column of output voxels over kZChunk consecutive z slices and marches along
+// z: the weights stay in shared memory for the whole column, the input sits
+// in a ring of four z slices (bfloat16, reading P2), and while the matrix
+// instructions of slice z run, the block stores slice z - 1 and loads slice
+// z + 2 of the halo.  Per slice the 128 x 32 binary32 accumulator D (two of
+// them in tensor memory, used in turn) receives, for each of the 27 taps,
+// A_t (128 voxels x 32 input channels) times the tap's weights as two K = 16
+// steps: 54 instructions from one thread, one commit.  Operands use the
+// canonical K-major layout without swizzle: core matrices of 8 rows x 16
+// bytes, 128 bytes apart along K and 256 bytes from one 8-row group to the
+// next.  D's row groups are the 16 y rows of the column (8 voxels along x
+// each), so a tap's y offset moves the operand's start by whole groups and
+// its z offset picks the ring slot; the x offset needs its own copy of each
+// slice, written once for dx = 0, 1, 2.  Waits are bounded: on a timeout
+// the block records an error, stops, waits (bounded) for its instructions
+// in flight and still frees tensor memory.
+constexpr int T5X = 8, T5Y = 16, kZChunk = 17;
+constexpr int H5X = T5X + 2, H5Y = T5Y + 2;
+constexpr int kT5Threads = 256;
+constexpr int kT5TilesX = (EG + T5X - 1) / T5X, kT5TilesY = (EG + T5Y - 1) / T5Y, kT5Chunks = (EG + kZChunk - 1) / kZChunk;
+constexpr int kT5Units = kT5TilesX * kT5TilesY * kT5Chunks;  // columns per grid
+constexpr int kDxBytes = 2 * H5Y * 256;                      // one x-shifted copy: [ks][hy][chunk][row][16 B]
+constexpr int kSlotBytes = 3 * kDxBytes;                     // one z slice: three copies
+constexpr int kRing = 4;
+constexpr int kBBytesTap = 2 * 4 * 256;                      // one tap's B: [ks][co group][chunk][row][16 B]
+constexpr int kT5BBytes = 27 * kBBytesTap;
+constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint64_t kWaitNs = 500000000ull;           // half a second
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+  // start >> 4; leading byte offset 128 (next K chunk); stride byte offset
+  // 256 (next 8-row group); descriptor version 1; no swizzle
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+         ((uint64_t)1 << 46);
 }
 
-constexpr size_t conv_mma_smem() { return (size_t)(HZ * HY * HX + 27 * HID) * kRowB; }
+// gives up after kWaitLimit polls or kWaitNs nanoseconds, whichever comes first
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+    if (ok) return true;
+    if ((it & 1023u) == 1023u) {
+      uint64_t t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > kWaitNs) break;
+    }
+  }
+  return false;
+}
+
+// slice gz of grid src (zeros outside the grid) into ring slot `slot`
+__device__ __forceinline__ void t5_load_slice(const float* __restrict__ src, uint8_t* slot, int x0t, int y0t, int gz,
+                                              int tid) {
+  for (int w = tid; w < H5Y * H5X * 4; w += kT5Threads) {
+    const int q = w % 4, hx = (w / 4) % H5X, hy = w / (4 * H5X);
+    const int gx = x0t + hx - 1, gy = y0t + hy - 1;
+    float4 lo = make_float4(0.0f, 0.0f, 0.0f, 0.0f), hi = lo;
+    if (gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG) {
+      const float4* p4 = reinterpret_cast<const float4*>(src + ((size_t)(gz * EG + gy) * EG + gx) * HID + 8 * q);
+      lo = __ldg(p4);
+      hi = __ldg(p4 + 1);
+    }
+    __nv_bfloat162 h[4] = {__floats2bfloat162_rn(lo.x, lo.y), __floats2bfloat162_rn(lo.z, lo.w),
+                           __floats2bfloat162_rn(hi.x, hi.y), __floats2bfloat162_rn(hi.z, hi.w)};
+    const uint4 val = *reinterpret_cast<const uint4*>(h);
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) {
+      const int r = hx - dx;                                 // row of the copy that holds this voxel
+      if (r < 0 || r >= T5X) continue;
+      *reinterpret_cast<uint4*>(slot + dx * kDxBytes + ((q >> 1) * H5Y + hy) * 256 + (q & 1) * 128 + r * 16) = val;
+    }
+  }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kT5Threads, 1) conv_tc05_kernel(const float* __restrict__ in,
+                                                                 const __nv_bfloat16* __restrict__ wb,
+                                                                 const float* __restrict__ bias, float* __restrict__ out,
+                                                                 const float* __restrict__ aux, uint32_t* __restrict__ err) {
+  extern __shared__ __align__(128) uint8_t sm5[];
+  uint8_t* s_b = sm5;                                        // 27 taps x kBBytesTap
+  uint8_t* s_a = sm5 + kT5BBytes;                            // kRing slices x kSlotBytes
+  __shared__ __align__(8) uint64_t s_mbar[2];
+  __shared__ uint32_t s_tmem, s_fail;
+  __shared__ float s_bias[HID];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int unit = blockIdx.x, n = blockIdx.y;
+  const int x0t = (unit % kT5TilesX) * T5X, y0t = ((unit / kT5TilesX) % kT5TilesY) * T5Y;
+  const int z0 = (unit / (kT5TilesX * kT5TilesY)) * kZChunk;
+  const int nz = min(kZChunk, EG - z0);                      // output slices of this column
+  const float* src = in + (size_t)n * NV * HID;
+  // weights wb[tap][co][ci] (64-byte rows) into the canonical layout
+  for (int q = tid; q < 27 * HID * 4; q += kT5Threads) {
+    const int t = q / (HID * 4), co = (q / 4) % HID, ch = q % 4;
+    *reinterpret_cast<uint4*>(s_b + t * kBBytesTap + (ch >> 1) * 1024 + (co >> 3) * 256 + (ch & 1) * 128 +
+                              (co & 7) * 16) = __ldg(reinterpret_cast<const uint4*>(wb) + q);
+  }
+  if (tid < HID) s_bias[tid] = EPI == kEpiRelu ? bias[tid] : 0.0f;
+  // input slices z0 - 1, z0, z0 + 1 (ring slots 0, 1, 2)
+  for (int li = 0; li < 3; ++li) t5_load_slice(src, s_a + li * kSlotBytes, x0t, y0t, z0 - 1 + li, tid);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&s_mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&s_mbar[1])));
+    s_fail = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" :: "r"(smem_u32(&s_tmem)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  const uint32_t a0 = smem_u32(s_a), b0 = smem_u32(s_b);
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(HID >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  int issued = 0;                                            // slices whose instructions were issued
+  for (int zl = 0; zl <= nz; ++zl) {
+    if (zl < nz && tid == 128) {                             // one thread of the loader warps issues slice zl
+      const uint32_t d_tmem = tmem + (uint32_t)(32 * (zl & 1));
+      for (int t = 0; t < 27; ++t) {
+        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+        const uint32_t a_t = a0 + ((zl + dz) % kRing) * kSlotBytes + dx * kDxBytes + dy * 256;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          const uint64_t da = umma_desc(a_t + ks * (H5Y * 256));
+          const uint64_t db = umma_desc(b0 + t * kBBytesTap + ks * 1024);
+          const uint32_t acc = (t > 0 || ks > 0) ? 1u : 0u;
+          asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                       :: "r"(d_tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(smem_u32(&s_mbar[zl & 1])) : "memory");
+    }
+    if (zl < nz) issued = zl + 1;
+    if (zl >= 1) {
+      // slice zl - 1 done: store it (warps 0-3: one accumulator row each)
+      const int zp = zl - 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&s_mbar[zp & 1]), (uint32_t)((zp >> 1) & 1)));
+      if (!ok) {
+        atomicExch(err, 1u);
+        s_fail = 1;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (ok && warp < 4) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * (zp & 1));
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                     "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                       "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                       "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                       "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                       "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                     : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // accumulator row tid: y row tid / 8 of the column, x tid % 8
+        const int gx = x0t + tid % T5X, gy = y0t + tid / T5X, gz = z0 + zp;
+        if (gx < EG && gy < EG) {
+          const size_t v = (size_t)n * NV + (size_t)(gz * EG + gy) * EG + gx;
+          float4* o4 = reinterpret_cast<float4*>(out + v * HID);
+#pragma unroll
+          for (int c4 = 0; c4 < HID / 4; ++c4) {
+            float o[4];
+            float4 m4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if constexpr (EPI != kEpiRelu) m4 = __ldg(reinterpret_cast<const float4*>(aux + v * HID) + c4);
+            const float mk[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float val = __uint_as_float(r[4 * c4 + e]);
+              if constexpr (EPI == kEpiRelu) o[e] = fmaxf(val + s_bias[4 * c4 + e], 0.0f);
+              else o[e] = mk[e] > 0.0f ? val : 0.0f;
+            }
+            o4[c4] = make_float4(o[0], o[1], o[2], o[3]);
+          }
+        }
+      }
+    }
+    // slice zl + 2 of the column (input slice li = zl + 3) into the slot
+    // that slice zl - 2 left; every instruction that read it has completed
+    if (zl + 3 <= nz + 1) t5_load_slice(src, s_a + ((zl + 3) % kRing) * kSlotBytes, x0t, y0t, z0 + zl + 2, tid);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (s_fail) break;
+  }
+  if (s_fail && issued > 0) {
+    // a wait gave up: a last bounded wait for the newest commit before freeing
+    const int zp = issued - 1;
+    mbar_wait(smem_u32(&s_mbar[zp & 1]), (uint32_t)((zp >> 1) & 1));
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" :: "r"(tmem));
+  }
+}
+
+constexpr size_t conv_tc05_smem() { return (size_t)kT5BBytes + (size_t)kRing * kSlotBytes; }
+static_assert(conv_tc05_smem() <= 227 * 1024, "shared memory of the tcgen05 convolution");
 
 __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
@@ -562,6 +669,7 @@ struct ro_mc {
   float *ga, *gb;                     // hidden gradients, n * NV * 32
   float *g4, *y;                      // output gradient and output, n * NV
   float* loss;                        // scratch loss when the caller passes none
+  uint32_t* flag;                     // set by a tensor-core wait that gave up (latched)
   uint32_t step = 0;
 };
 
@@ -571,7 +679,7 @@ constexpr uint64_t kMcAlign = 256;
 uint64_t mc_align(uint64_t v) { return (v + kMcAlign - 1) / kMcAlign * kMcAlign; }
 
 struct McLayout {
-  uint64_t P, Pq, M, V, G, Wt3, wf1, wf2, wd1, wd2, a1, a2, a3, ga, gb, g4, y, loss, total;
+  uint64_t P, Pq, M, V, G, flag, Wt3, wf1, wf2, wd1, wd2, a1, a2, a3, ga, gb, g4, y, loss, total;
 };
 
 McLayout mc_layout(uint32_t nb) {
@@ -579,7 +687,7 @@ McLayout mc_layout(uint32_t nb) {
   uint64_t o = 0;
   auto take = [&](uint64_t bytes) { const uint64_t at = o; o = mc_align(o + bytes); return at; };
   const uint64_t pb = (uint64_t)RO_MC_PARAMS * 4, hid = (uint64_t)nb * NV * HID * 4, one = (uint64_t)nb * NV * 4;
-  L.P = take(pb); L.Pq = take(pb); L.M = take(pb); L.V = take(pb); L.G = take(pb);
+  L.P = take(pb); L.Pq = take(pb); L.M = take(pb); L.V = take(pb); L.G = take(pb); L.flag = take(4);
   L.Wt3 = take(27ull * HID * 4);
   L.wf1 = take(27ull * HID * HID * 2); L.wf2 = take(27ull * HID * HID * 2);
   L.wd1 = take(27ull * HID * HID * 2); L.wd2 = take(27ull * HID * HID * 2);
@@ -602,12 +710,12 @@ cudaError_t conv(const float* in, const float* w, const float* b, float* out, co
 
 template <int EPI>
 cudaError_t conv_tc(const float* in, const __nv_bfloat16* wb, const float* b, float* out, const float* aux, uint32_t n,
-                    cudaStream_t s) {
-  auto k = conv_mma_kernel<EPI>;
-  constexpr size_t sm = conv_mma_smem();
+                    uint32_t* flag, cudaStream_t s) {
+  auto k = conv_tc05_kernel<EPI>;
+  constexpr size_t sm = conv_tc05_smem();
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k<<<dim3(kTilesX * kTilesY * kTilesZ, n), kConvThreads, sm, s>>>(in, wb, b, out, aux);
+  k<<<dim3(kT5Units, n), kT5Threads, sm, s>>>(in, wb, b, out, aux, flag);
   return cudaGetLastError();
 }
 
@@ -638,8 +746,8 @@ cudaError_t mc_forward(ro_mc* m, uint32_t n, const float* x0, float* y) {
   cudaStream_t s = m->stream;
   const float* Pq = m->Pq;
   cudaError_t e = conv<1, HID, kEpiRelu>(x0, Pq + kWOff[0], Pq + kBOff[0], m->a1, nullptr, n, s);
-  if (e == cudaSuccess) e = conv_tc<kEpiRelu>(m->a1, m->wf1, Pq + kBOff[1], m->a2, nullptr, n, s);
-  if (e == cudaSuccess) e = conv_tc<kEpiRelu>(m->a2, m->wf2, Pq + kBOff[2], m->a3, nullptr, n, s);
+  if (e == cudaSuccess) e = conv_tc<kEpiRelu>(m->a1, m->wf1, Pq + kBOff[1], m->a2, nullptr, n, m->flag, s);
+  if (e == cudaSuccess) e = conv_tc<kEpiRelu>(m->a2, m->wf2, Pq + kBOff[2], m->a3, nullptr, n, m->flag, s);
   if (e == cudaSuccess) e = conv<HID, 1, kEpiResidual>(m->a3, Pq + kWOff[3], Pq + kBOff[3], y, x0, n, s);
   return e;
 }
@@ -661,10 +769,10 @@ cudaError_t mc_backward(ro_mc* m, uint32_t n, const float* x0, const float* targ
   if (e == cudaSuccess) e = conv<1, HID, kEpiMask>(m->g4, m->Wt3, zero_bias, m->ga, m->a3, n, s);
   // layer 3 (32 -> 32)
   if (e == cudaSuccess) e = wgrad_tc(m->a2, m->ga, n, G + kWOff[2], G + kBOff[2], s);
-  if (e == cudaSuccess) e = conv_tc<kEpiMask>(m->ga, m->wd2, zero_bias, m->gb, m->a2, n, s);
+  if (e == cudaSuccess) e = conv_tc<kEpiMask>(m->ga, m->wd2, zero_bias, m->gb, m->a2, n, m->flag, s);
   // layer 2 (32 -> 32)
   if (e == cudaSuccess) e = wgrad_tc(m->a1, m->gb, n, G + kWOff[1], G + kBOff[1], s);
-  if (e == cudaSuccess) e = conv_tc<kEpiMask>(m->gb, m->wd1, zero_bias, m->ga, m->a1, n, s);
+  if (e == cudaSuccess) e = conv_tc<kEpiMask>(m->gb, m->wd1, zero_bias, m->ga, m->a1, n, m->flag, s);
   // layer 1 (1 -> 32)
   if (e == cudaSuccess) e = wgrad<1, HID>(x0, m->ga, n, G + kWOff[0], G + kBOff[0], s);
   return e;
@@ -701,7 +809,8 @@ ro_status ro_mc_create(const ro_mc_desc* d, void* arena, uint64_t arena_bytes, v
   m->wf1 = h(L.wf1); m->wf2 = h(L.wf2); m->wd1 = h(L.wd1); m->wd2 = h(L.wd2);
   m->a1 = f(L.a1); m->a2 = f(L.a2); m->a3 = f(L.a3); m->ga = f(L.ga); m->gb = f(L.gb);
   m->g4 = f(L.g4); m->y = f(L.y); m->loss = f(L.loss);
-  cudaError_t e = cudaMemsetAsync(arena, 0, L.Wt3, m->stream);   // parameters, copies, moments, gradients
+  m->flag = reinterpret_cast<uint32_t*>(b + L.flag);
+  cudaError_t e = cudaMemsetAsync(arena, 0, L.Wt3, m->stream);   // parameters, copies, moments, gradients, flag
   if (e == cudaSuccess) e = mc_refresh(m);
   if (e != cudaSuccess) {
     delete m;
@@ -731,8 +840,11 @@ ro_status ro_mc_set_params(ro_mc* m, const float* host) {
 
 ro_status ro_mc_get_params(ro_mc* m, float* host) {
   if (!m || !host) return RO_ERR_INVALID_ARG;
+  uint32_t flag = 0;
   cudaError_t e = cudaMemcpyAsync(host, m->P, (size_t)RO_MC_PARAMS * 4, cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, m->flag, 4, cudaMemcpyDeviceToHost, m->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e == cudaSuccess && flag) return RO_ERR_INTERNAL;
   return mc_err(e);
 }
 
