@@ -231,20 +231,39 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
-// slice gz of grid src (zeros outside the grid) into ring slot `slot`
-__device__ __forceinline__ void t5_load_slice(const float* __restrict__ src, uint8_t* slot, int x0t, int y0t, int gz,
-                                              int tid) {
-  for (int w = tid; w < H5Y * H5X * 4; w += kT5Threads) {
+// A z slice of the halo column is kSliceItems 8-channel pieces (32 bytes of
+// binary32 input each), at most kItemsT5 per thread.  t5_fetch reads this
+// thread's pieces of slice gz into registers (zeros outside the grid);
+// t5_store rounds them to bfloat16 and writes them into every x-shifted copy
+// of ring slot `slot` whose 8-voxel rows hold them.  Fetching one step
+// ahead keeps the loads in flight while the matrix instructions run.
+constexpr int kSliceItems = H5Y * H5X * 4;
+constexpr int kItemsT5 = (kSliceItems + kT5Threads - 1) / kT5Threads;
+
+__device__ __forceinline__ void t5_fetch(const float* __restrict__ src, int x0t, int y0t, int gz, int tid,
+                                         float4 (&v)[kItemsT5][2]) {
+#pragma unroll
+  for (int j = 0; j < kItemsT5; ++j) {
+    const int w = tid + j * kT5Threads;
+    v[j][0] = v[j][1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     const int q = w % 4, hx = (w / 4) % H5X, hy = w / (4 * H5X);
     const int gx = x0t + hx - 1, gy = y0t + hy - 1;
-    float4 lo = make_float4(0.0f, 0.0f, 0.0f, 0.0f), hi = lo;
-    if (gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG) {
+    if (w < kSliceItems && gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG) {
       const float4* p4 = reinterpret_cast<const float4*>(src + ((size_t)(gz * EG + gy) * EG + gx) * HID + 8 * q);
-      lo = __ldg(p4);
-      hi = __ldg(p4 + 1);
+      v[j][0] = __ldg(p4);
+      v[j][1] = __ldg(p4 + 1);
     }
-    __nv_bfloat162 h[4] = {__floats2bfloat162_rn(lo.x, lo.y), __floats2bfloat162_rn(lo.z, lo.w),
-                           __floats2bfloat162_rn(hi.x, hi.y), __floats2bfloat162_rn(hi.z, hi.w)};
+  }
+}
+
+__device__ __forceinline__ void t5_store(uint8_t* slot, int tid, const float4 (&v)[kItemsT5][2]) {
+#pragma unroll
+  for (int j = 0; j < kItemsT5; ++j) {
+    const int w = tid + j * kT5Threads;
+    if (w >= kSliceItems) continue;
+    const int q = w % 4, hx = (w / 4) % H5X, hy = w / (4 * H5X);
+    __nv_bfloat162 h[4] = {__floats2bfloat162_rn(v[j][0].x, v[j][0].y), __floats2bfloat162_rn(v[j][0].z, v[j][0].w),
+                           __floats2bfloat162_rn(v[j][1].x, v[j][1].y), __floats2bfloat162_rn(v[j][1].z, v[j][1].w)};
     const uint4 val = *reinterpret_cast<const uint4*>(h);
 #pragma unroll
     for (int dx = 0; dx < 3; ++dx) {
@@ -280,7 +299,19 @@ __global__ void __launch_bounds__(kT5Threads, 1) conv_tc05_kernel(const float* _
   }
   if (tid < HID) s_bias[tid] = EPI == kEpiRelu ? bias[tid] : 0.0f;
   // input slices z0 - 1, z0, z0 + 1 (ring slots 0, 1, 2)
-  for (int li = 0; li < 3; ++li) t5_load_slice(src, s_a + li * kSlotBytes, x0t, y0t, z0 - 1 + li, tid);
+  float4 pre[kItemsT5][2];
+  for (int li = 0; li < 3; ++li) {
+    t5_fetch(src, x0t, y0t, z0 - 1 + li, tid, pre);
+    t5_store(s_a + li * kSlotBytes, tid, pre);
+  }
+  t5_fetch(src, x0t, y0t, z0 + 2, tid, pre);                 // input slice 3, stored in the first step
+  // this thread's accumulator row (warps 0-3): voxel (ex, ey) of each slice;
+  // am holds its mask row (input-gradient pass), fetched a step ahead
+  const int ex = x0t + tid % T5X, ey = y0t + tid / T5X;
+  const bool erow = warp < 4 && ex < EG && ey < EG;
+  float4 am[HID / 4];
+#pragma unroll
+  for (int c4 = 0; c4 < HID / 4; ++c4) am[c4] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&s_mbar[0])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&s_mbar[1])));
@@ -340,16 +371,13 @@ __global__ void __launch_bounds__(kT5Threads, 1) conv_tc05_kernel(const float* _
                      : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         // accumulator row tid: y row tid / 8 of the column, x tid % 8
-        const int gx = x0t + tid % T5X, gy = y0t + tid / T5X, gz = z0 + zp;
-        if (gx < EG && gy < EG) {
-          const size_t v = (size_t)n * NV + (size_t)(gz * EG + gy) * EG + gx;
+        if (erow) {
+          const size_t v = (size_t)n * NV + (size_t)((z0 + zp) * EG + ey) * EG + ex;
           float4* o4 = reinterpret_cast<float4*>(out + v * HID);
 #pragma unroll
           for (int c4 = 0; c4 < HID / 4; ++c4) {
             float o[4];
-            float4 m4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if constexpr (EPI != kEpiRelu) m4 = __ldg(reinterpret_cast<const float4*>(aux + v * HID) + c4);
-            const float mk[4] = {m4.x, m4.y, m4.z, m4.w};
+            const float mk[4] = {am[c4].x, am[c4].y, am[c4].z, am[c4].w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const float val = __uint_as_float(r[4 * c4 + e]);
@@ -363,7 +391,16 @@ __global__ void __launch_bounds__(kT5Threads, 1) conv_tc05_kernel(const float* _
     }
     // slice zl + 2 of the column (input slice li = zl + 3) into the slot
     // that slice zl - 2 left; every instruction that read it has completed
-    if (zl + 3 <= nz + 1) t5_load_slice(src, s_a + ((zl + 3) % kRing) * kSlotBytes, x0t, y0t, z0 + zl + 2, tid);
+    if (zl + 3 <= nz + 1) t5_store(s_a + ((zl + 3) % kRing) * kSlotBytes, tid, pre);
+    if (zl + 4 <= nz + 1) t5_fetch(src, x0t, y0t, z0 + zl + 3, tid, pre);
+    if constexpr (EPI != kEpiRelu) {                         // mask rows of output slice zl, stored next step
+      if (erow && zl < nz) {
+        const float4* a4 =
+            reinterpret_cast<const float4*>(aux + ((size_t)n * NV + (size_t)((z0 + zl) * EG + ey) * EG + ex) * HID);
+#pragma unroll
+        for (int c4 = 0; c4 < HID / 4; ++c4) am[c4] = __ldg(a4 + c4);
+      }
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
