@@ -95,6 +95,36 @@ __global__ void to_raw_kernel(const float* __restrict__ y, uint8_t* __restrict__
 }
 
 // ---------------------------------------------------------- convolution
+// The HZ x HY x HX input tile with its one-voxel halo (zeros outside the
+// grid) into shared memory at channel stride pad_stride(CIN); 16-byte loads
+// when the channels allow.
+template <int CIN>
+__device__ __forceinline__ void load_halo(const float* __restrict__ src, float* s_in, int x0t, int y0t, int z0t) {
+  constexpr int SC = pad_stride(CIN);
+  if constexpr (CIN % 4 == 0) {
+    for (int q = threadIdx.x; q < HZ * HY * HX * (CIN / 4); q += blockDim.x) {
+      const int c4 = q % (CIN / 4), p = q / (CIN / 4);
+      const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
+      const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
+      float4 val = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
+        val = __ldg(reinterpret_cast<const float4*>(src + ((size_t)(gz * EG + gy) * EG + gx) * CIN) + c4);
+      float* d = s_in + p * SC + 4 * c4;
+      d[0] = val.x; d[1] = val.y; d[2] = val.z; d[3] = val.w;
+    }
+  } else {
+    for (int q = threadIdx.x; q < HZ * HY * HX * CIN; q += blockDim.x) {
+      const int c = q % CIN, p = q / CIN;
+      const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
+      const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
+      float val = 0.0f;
+      if (gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
+        val = src[((size_t)(gz * EG + gy) * EG + gx) * CIN + c];
+      s_in[p * SC + c] = val;
+    }
+  }
+}
+
 // out[v][co] = epi(sum_tap sum_ci in[v + off(tap)][ci] * w[tap][ci][co] + b[co])
 // aux: the residual x0 (kEpiResidual, COUT = 1) or the activation whose
 // positive entries pass the gradient (kEpiMask).
@@ -108,16 +138,7 @@ __global__ void __launch_bounds__(kConvThreads) conv_kernel(const float* __restr
   float* s_w = sm + HZ * HY * HX * SC;           // 27 * CIN * COUT
   const int tile = blockIdx.x, n = blockIdx.y;
   const int x0t = (tile % kTilesX) * TX, y0t = ((tile / kTilesX) % kTilesY) * TY, z0t = (tile / (kTilesX * kTilesY)) * TZ;
-  const float* src = in + (size_t)n * NV * CIN;
-  for (int q = threadIdx.x; q < HZ * HY * HX * CIN; q += blockDim.x) {
-    const int c = q % CIN, p = q / CIN;
-    const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
-    const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
-    float val = 0.0f;
-    if (gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
-      val = src[((size_t)(gz * EG + gy) * EG + gx) * CIN + c];
-    s_in[p * SC + c] = val;
-  }
+  load_halo<CIN>(in + (size_t)n * NV * CIN, s_in, x0t, y0t, z0t);
   for (int q = threadIdx.x; q < 27 * CIN * COUT; q += blockDim.x) s_w[q] = w[q];
   __syncthreads();
   const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
@@ -431,15 +452,17 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t&
 
 // Weight gradients of a 32 -> 32 layer on the tensor cores: for every tap
 // dW[t] (32 x 32) = sum over voxels of in[v + off(t)]^T g[v], i.e. a GEMM
-// with M = input channels, N = output channels, K = voxels.  One block per
-// tile position loops over the batch; the input tile (halo) and the
-// gradient tile enter shared memory as bfloat16 rows, and ldmatrix.trans
-// turns the voxel rows into the K dimension of both operands.  Warp w
-// accumulates taps w, w + 8, w + 16, w + 24 over every grid and adds its
-// sums once (atomically) at the end.
+// with M = input channels, N = output channels, K = voxels.  Block
+// (tile position, s) loops over grids s, s + kWgradSplitTc, ...; the input
+// tile (halo) and the gradient tile enter shared memory as bfloat16 rows,
+// and ldmatrix.trans turns the voxel rows into the K dimension of both
+// operands.  Warp w accumulates taps w, w + 8, w + 16, w + 24 and adds its
+// sums once (atomically) at the end.  The bias gradient db[co] = sum over
+// voxels of g[v][co] is summed in binary32 from the same loads.
+constexpr int kWgradSplitTc = 2;
 __global__ void __launch_bounds__(kConvThreads) wgrad_mma_kernel(const float* __restrict__ in,
                                                                 const float* __restrict__ g, int n_grids,
-                                                                float* __restrict__ dW) {
+                                                                float* __restrict__ dW, float* __restrict__ db) {
   extern __shared__ __align__(16) uint8_t smb[];
   uint8_t* s_x = smb;                                       // HZ * HY * HX rows (input, halo)
   uint8_t* s_g = smb + HZ * HY * HX * kRowB;                // TZ * TY * TX rows (gradient)
@@ -459,7 +482,10 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_mma_kernel(const float* __
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[j][mt][nt][q] = 0.0f;
   const uint32_t x_base = smem_u32(s_x), g_base = smem_u32(s_g);
-  for (int n = 0; n < n_grids; ++n) {
+  // kConvThreads is a multiple of HID / 2: a thread's channel pair is fixed
+  static_assert(kConvThreads % (HID / 2) == 0, "channel pair per thread");
+  float2 bsum = make_float2(0.0f, 0.0f);
+  for (int n = blockIdx.y; n < n_grids; n += kWgradSplitTc) {
     const float* src = in + (size_t)n * NV * HID;
     const float* gs = g + (size_t)n * NV * HID;
     __syncthreads();
@@ -478,6 +504,8 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_mma_kernel(const float* __
       float2 v = make_float2(0.0f, 0.0f);                   // voxels outside the grid add nothing
       if (gx < EG && gy < EG && gz < EG)
         v = *reinterpret_cast<const float2*>(gs + ((size_t)(gz * EG + gy) * EG + gx) * HID + 2 * c2);
+      bsum.x += v.x;
+      bsum.y += v.y;
       *reinterpret_cast<__nv_bfloat162*>(s_g + p * kRowB + 4 * c2) = __floats2bfloat162_rn(v.x, v.y);
     }
     __syncthreads();
@@ -525,32 +553,30 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_mma_kernel(const float* __
         }
       }
   }
+  // bias gradient: the threads of one channel pair, then one add per channel
+  __syncthreads();
+  float2* s_red = reinterpret_cast<float2*>(smb);
+  s_red[threadIdx.x] = bsum;
+  __syncthreads();
+  if (threadIdx.x < HID / 2) {
+    float2 t = make_float2(0.0f, 0.0f);
+    for (int q = threadIdx.x; q < kConvThreads; q += HID / 2) {
+      t.x += s_red[q].x;
+      t.y += s_red[q].y;
+    }
+    atomicAdd(&db[2 * threadIdx.x], t.x);
+    atomicAdd(&db[2 * threadIdx.x + 1], t.y);
+  }
 }
 
 constexpr size_t wgrad_mma_smem() { return (size_t)(HZ * HY * HX + TZ * TY * TX) * kRowB; }
 
-// Bias gradients db[c] += sum over voxels of g[v][c] (block partial sums).
-template <int C>
-__global__ void bias_grad_kernel(const float* __restrict__ g, size_t n_vox, float* __restrict__ db) {
-  float part = 0.0f;
-  const int c = threadIdx.x % C;
-  for (size_t v = (size_t)blockIdx.x * (blockDim.x / C) + threadIdx.x / C; v < n_vox;
-       v += (size_t)gridDim.x * (blockDim.x / C))
-    part += g[v * C + c];
-  __shared__ float s_p[256];
-  s_p[threadIdx.x] = part;
-  __syncthreads();
-  if (threadIdx.x < C) {
-    float s = 0.0f;
-    for (int q = threadIdx.x; q < (int)blockDim.x; q += C) s += s_p[q];
-    atomicAdd(&db[threadIdx.x], s);
-  }
-}
-
 // ------------------------------------------------------ weight gradients
 // dW[tap][ci][co] += sum_v in[v + off(tap)][ci] * g[v][co] and db[co] +=
-// sum_v g[v][co] over one tile position of every grid; each block owns one
-// tile position and adds its sums once (atomically) at the end.
+// sum_v g[v][co] over one tile position of the grids blockIdx.y,
+// blockIdx.y + kWgradSplit, ...; each block owns one tile position and one
+// share of the grids and adds its sums once (atomically) at the end.
+constexpr int kWgradSplit = 4;
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(kConvThreads) wgrad_kernel(const float* __restrict__ in, const float* __restrict__ g,
                                                             int n_grids, float* __restrict__ dW,
@@ -569,26 +595,30 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_kernel(const float* __rest
 #pragma unroll
     for (int co = 0; co < COUT; ++co) acc[j][co] = 0.0f;
   float bacc = 0.0f;
-  for (int n = 0; n < n_grids; ++n) {
+  for (int n = blockIdx.y; n < n_grids; n += kWgradSplit) {
     const float* src = in + (size_t)n * NV * CIN;
     const float* gs = g + (size_t)n * NV * COUT;
     __syncthreads();
-    for (int q = threadIdx.x; q < HZ * HY * HX * CIN; q += blockDim.x) {
-      const int c = q % CIN, p = q / CIN;
-      const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
-      const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
-      float val = 0.0f;
-      if (gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
-        val = src[((size_t)(gz * EG + gy) * EG + gx) * CIN + c];
-      s_in[p * SC + c] = val;
-    }
-    for (int q = threadIdx.x; q < TZ * TY * TX * COUT; q += blockDim.x) {
-      const int c = q % COUT, p = q / COUT;
-      const int tx = p % TX, ty = (p / TX) % TY, tz = p / (TX * TY);
-      const int gx = x0t + tx, gy = y0t + ty, gz = z0t + tz;
-      float val = 0.0f;                                   // voxels outside the grid add nothing
-      if (gx < EG && gy < EG && gz < EG) val = gs[((size_t)(gz * EG + gy) * EG + gx) * COUT + c];
-      s_g[q] = val;
+    load_halo<CIN>(src, s_in, x0t, y0t, z0t);
+    if constexpr (COUT % 4 == 0) {
+      for (int q = threadIdx.x; q < TZ * TY * TX * (COUT / 4); q += blockDim.x) {
+        const int c4 = q % (COUT / 4), p = q / (COUT / 4);
+        const int tx = p % TX, ty = (p / TX) % TY, tz = p / (TX * TY);
+        const int gx = x0t + tx, gy = y0t + ty, gz = z0t + tz;
+        float4 val = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // voxels outside the grid add nothing
+        if (gx < EG && gy < EG && gz < EG)
+          val = __ldg(reinterpret_cast<const float4*>(gs + ((size_t)(gz * EG + gy) * EG + gx) * COUT) + c4);
+        reinterpret_cast<float4*>(s_g)[q] = val;
+      }
+    } else {
+      for (int q = threadIdx.x; q < TZ * TY * TX * COUT; q += blockDim.x) {
+        const int c = q % COUT, p = q / COUT;
+        const int tx = p % TX, ty = (p / TX) % TY, tz = p / (TX * TY);
+        const int gx = x0t + tx, gy = y0t + ty, gz = z0t + tz;
+        float val = 0.0f;                                 // voxels outside the grid add nothing
+        if (gx < EG && gy < EG && gz < EG) val = gs[((size_t)(gz * EG + gy) * EG + gx) * COUT + c];
+        s_g[q] = val;
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -760,9 +790,7 @@ cudaError_t wgrad_tc(const float* in, const float* g, uint32_t n, float* dW, flo
   constexpr size_t sm = wgrad_mma_smem();
   cudaError_t e = cudaFuncSetAttribute(wgrad_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  wgrad_mma_kernel<<<kTilesX * kTilesY * kTilesZ, kConvThreads, sm, s>>>(in, g, (int)n, dW);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  bias_grad_kernel<HID><<<152 * 2, 256, 0, s>>>(g, (size_t)n * NV, db);
+  wgrad_mma_kernel<<<dim3(kTilesX * kTilesY * kTilesZ, kWgradSplitTc), kConvThreads, sm, s>>>(in, g, (int)n, dW, db);
   return cudaGetLastError();
 }
 
@@ -772,7 +800,7 @@ cudaError_t wgrad(const float* in, const float* g, uint32_t n, float* dW, float*
   constexpr size_t sm = wgrad_smem<CIN, COUT>();
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k<<<kTilesX * kTilesY * kTilesZ, kConvThreads, sm, s>>>(in, g, (int)n, dW, db);
+  k<<<dim3(kTilesX * kTilesY * kTilesZ, kWgradSplit), kConvThreads, sm, s>>>(in, g, (int)n, dW, db);
   return cudaGetLastError();
 }
 
