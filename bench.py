@@ -211,6 +211,15 @@ def measured_hbm_peak():
         return 6800.0, "fallback"
 
 
+def measured_bf16_sustained_peak():
+    """Dense bf16 tensor throughput (TFLOP/s) of a seconds-long cuBLAS loop."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops_sustained"]), "measured"
+    except Exception:
+        return 1700.0, "fallback"
+
+
 # ------------------------------------------------------------ CPU oracle
 
 SAMPLE_FORMAT = {"f32": 0, "f16": 1, "bf16": 2}
@@ -677,6 +686,8 @@ def run_compensator(args, rank, world, local_rank):
             log(f"  step {step}/{steps}: loss {losses[-1][1]:.3e}")
     flops_per_grid = 3 * 2 * 34 ** 3 * 27 * (1 * 32 + 32 * 32 + 32 * 32 + 32 * 1)   # forward + two backward GEMMs
     train_tflops = steps * batch * flops_per_grid / train_s / 1e12
+    tensor_share = (32 * 32 + 32 * 32) / (1 * 32 + 32 * 32 + 32 * 32 + 32 * 1)     # flops of the 32 -> 32 layers
+    bf16_peak, bf16_kind = measured_bf16_sustained_peak()
     # -------------------------------------------------------- evaluation
     scene = recipes.cells_slab(m=m_ch, dense=False, resident_l0=0.5, n_views=4)
     slots = len(scene.all_bricks())
@@ -726,9 +737,11 @@ def run_compensator(args, rank, world, local_rank):
            "plain_substitution_psnr_db": p_plain,
            "train": {"pairs": steps * batch, "seconds_gpu": round(train_s, 2), "seconds_data": round(gen_s, 2),
                      "loss_curve": losses,
-                     "roofline": {"bound": "alu", "achieved": train_tflops, "peak": FP32_PEAK_TFLOPS,
-                                  "unit": "TFLOP/s", "frac": train_tflops / FP32_PEAK_TFLOPS,
-                                  "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}},
+                     "roofline": {"bound": "tensor", "achieved": train_tflops, "peak": bf16_peak,
+                                  "unit": "TFLOP/s", "frac": train_tflops / bf16_peak,
+                                  "peak_source": f"{bf16_kind} dense bf16, sustained",
+                                  "tensor_core_flop_share": tensor_share,
+                                  "binary32_peak_derived": FP32_PEAK_TFLOPS}},
            "inference": {"bricks": len(missing), "seconds": round(comp_s, 3),
                          "bricks_per_s": len(missing) / comp_s if comp_s > 0 else None}}
     print(json.dumps(out), flush=True)
