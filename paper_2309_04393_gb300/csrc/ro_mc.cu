@@ -42,8 +42,9 @@ constexpr int kBOff[4] = {864, 28544, 56224, 57120};    // b of layer i (after W
 static_assert(kBOff[3] + 1 == RO_MC_PARAMS, "parameter layout");
 
 // channel stride of a shared-memory tile: padded so that neighbouring
-// voxels of one channel fall in different banks
-__host__ __device__ constexpr int pad_stride(int c) { return c > 1 ? c + 1 : 1; }
+// voxels fall in different banks; a multiple of 4 for 16-byte accesses
+// (36 floats: eight 16-byte reads of neighbouring voxels cover all banks)
+__host__ __device__ constexpr int pad_stride(int c) { return c > 1 ? (c % 4 == 0 ? c + 4 : c + 1) : 1; }
 
 enum : int { kEpiNone = 0, kEpiRelu = 1, kEpiResidual = 2, kEpiMask = 3 };
 
@@ -109,8 +110,7 @@ __device__ __forceinline__ void load_halo(const float* __restrict__ src, float* 
       float4 val = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       if (gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
         val = __ldg(reinterpret_cast<const float4*>(src + ((size_t)(gz * EG + gy) * EG + gx) * CIN) + c4);
-      float* d = s_in + p * SC + 4 * c4;
-      d[0] = val.x; d[1] = val.y; d[2] = val.z; d[3] = val.w;
+      *reinterpret_cast<float4*>(s_in + p * SC + 4 * c4) = val;
     }
   } else {
     for (int q = threadIdx.x; q < HZ * HY * HX * CIN; q += blockDim.x) {
@@ -150,24 +150,57 @@ __global__ void __launch_bounds__(kConvThreads) conv_kernel(const float* __restr
     const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
     const float* a = s_in + (((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * SC;
     const float* wt = s_w + t * CIN * COUT;
-#pragma unroll 4
-    for (int ci = 0; ci < CIN; ++ci) {
-      const float xv = a[ci];
-      const float* wr = wt + ci * COUT;
+    if constexpr (CIN % 4 == 0 && COUT == 1) {
+      // 16-byte reads of four channels and their four weights
 #pragma unroll
-      for (int co = 0; co < COUT; ++co) acc[co] = fmaf(xv, wr[co], acc[co]);
+      for (int c4 = 0; c4 < CIN / 4; ++c4) {
+        const float4 xv = *reinterpret_cast<const float4*>(a + 4 * c4);
+        const float4 wv = *reinterpret_cast<const float4*>(wt + 4 * c4);
+        acc[0] = fmaf(xv.x, wv.x, acc[0]);
+        acc[0] = fmaf(xv.y, wv.y, acc[0]);
+        acc[0] = fmaf(xv.z, wv.z, acc[0]);
+        acc[0] = fmaf(xv.w, wv.w, acc[0]);
+      }
+    } else {
+#pragma unroll 4
+      for (int ci = 0; ci < CIN; ++ci) {
+        const float xv = a[ci];
+        const float* wr = wt + ci * COUT;
+#pragma unroll
+        for (int co = 0; co < COUT; ++co) acc[co] = fmaf(xv, wr[co], acc[co]);
+      }
     }
   }
   if (gx >= EG || gy >= EG || gz >= EG) return;
   const size_t v = (size_t)n * NV + (size_t)(gz * EG + gy) * EG + gx;
+  if constexpr (COUT % 4 == 0) {
+    // 16-byte stores (and mask reads) of four channels
 #pragma unroll
-  for (int co = 0; co < COUT; ++co) {
-    float r = acc[co];
-    if constexpr (EPI == kEpiRelu) r = fmaxf(r + bias[co], 0.0f);
-    else if constexpr (EPI == kEpiNone) r = r + bias[co];
-    else if constexpr (EPI == kEpiResidual) r = r + bias[co] + aux[v];
-    else r = aux[v * COUT + co] > 0.0f ? r : 0.0f;
-    out[v * COUT + co] = r;
+    for (int c4 = 0; c4 < COUT / 4; ++c4) {
+      float r[4] = {acc[4 * c4], acc[4 * c4 + 1], acc[4 * c4 + 2], acc[4 * c4 + 3]};
+      float4 m4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if constexpr (EPI == kEpiMask) m4 = __ldg(reinterpret_cast<const float4*>(aux + v * COUT) + c4);
+      const float mk[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int co = 4 * c4 + e;
+        if constexpr (EPI == kEpiRelu) r[e] = fmaxf(r[e] + bias[co], 0.0f);
+        else if constexpr (EPI == kEpiNone) r[e] = r[e] + bias[co];
+        else if constexpr (EPI == kEpiResidual) r[e] = r[e] + bias[co] + aux[v];
+        else r[e] = mk[e] > 0.0f ? r[e] : 0.0f;
+      }
+      reinterpret_cast<float4*>(out + v * COUT)[c4] = make_float4(r[0], r[1], r[2], r[3]);
+    }
+  } else {
+#pragma unroll
+    for (int co = 0; co < COUT; ++co) {
+      float r = acc[co];
+      if constexpr (EPI == kEpiRelu) r = fmaxf(r + bias[co], 0.0f);
+      else if constexpr (EPI == kEpiNone) r = r + bias[co];
+      else if constexpr (EPI == kEpiResidual) r = r + bias[co] + aux[v];
+      else r = aux[v * COUT + co] > 0.0f ? r : 0.0f;
+      out[v * COUT + co] = r;
+    }
   }
 }
 
