@@ -133,3 +133,48 @@ def test_compensate_bricks_writes_the_predictions_into_the_cache(mc):
         mcmod.compensate_bricks(ctx, m, [ro.brick_id(0, 1, 0, 0, 0, scene.k)])
     img, _ = ro.render_frame(ctx, scene.frames[0])               # the context still renders
     assert float(img[..., 3].max()) > 0
+
+
+def test_full_batch_matches_oracle_samples_and_per_grid_gradients(mc):
+    """The training batch of the bench (32 grids, the launch configuration
+    it times): sampled grids of the forward pass against the oracle, and the
+    batch gradient against the mean of the 32 one-grid gradients (the loss
+    is a mean over the batch, so this holds at any size; it checks how the
+    weight-gradient kernels share a batch between blocks)."""
+    import torch
+    mcmod, _ = mc
+    n = 32
+    big = mcmod.Compensator(n)
+    try:
+        rng = np.random.default_rng(11)
+        params = [(W * 3.0, rng.normal(0, 0.05, b.shape)) for W, b in omc.init_params(6)]
+        big.set_params(params)
+        x0 = rng.uniform(0.0, 1.0, (n, 34, 34, 34))
+        target = np.clip(x0 + rng.normal(0.0, 0.05, x0.shape), 0, 1)
+        tx = torch.from_numpy(x0.astype(np.float32)).cuda()
+        tt = torch.from_numpy(target.astype(np.float32)).cuda()
+        y = big.forward(tx).cpu().numpy()
+        q = rounded([(W.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64))
+                     for W, b in params])
+        x0f = x0.astype(np.float32).astype(np.float64)
+        for k in (0, 17, n - 1):
+            want, _ = omc.forward(q, x0f[k], bf16_inputs=(1, 2))
+            err = np.abs(y[k] - want)
+            # bounds of the two-grid forward test (bfloat16 rounding flips, P2)
+            assert np.median(err) <= 1e-6
+            assert np.quantile(err, 0.99) <= 5e-4
+            assert err.max() <= 3e-3 * max(1.0, np.abs(want).max())
+        g, loss = big.gradients(tx, tt)
+        g = g.cpu().numpy().astype(np.float64)
+        mean_g = np.zeros_like(g)
+        mean_loss = 0.0
+        for k in range(n):
+            gk, lk = big.gradients(tx[k:k + 1], tt[k:k + 1])
+            mean_g += gk.cpu().numpy().astype(np.float64) / n
+            mean_loss += float(lk.item()) / n
+        # the per-grid terms are the same binary32 / bfloat16 values scaled by
+        # 2^-5 (exact); only the order of the binary32 sums differs
+        assert abs(float(loss.item()) - mean_loss) <= 1e-5 * mean_loss
+        assert np.abs(g - mean_g).max() <= 1e-4 * np.abs(mean_g).max()
+    finally:
+        big.close()
