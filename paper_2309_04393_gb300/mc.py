@@ -18,6 +18,11 @@ PARAMS = 57121
 LAYERS = ((1, 32), (32, 32), (32, 32), (32, 1))
 
 
+# every entry point include/ro_mc.h declares
+EXPORTS = ["ro_mc_query_bytes", "ro_mc_create", "ro_mc_destroy", "ro_mc_set_params", "ro_mc_get_params",
+           "ro_mc_upsample", "ro_mc_forward", "ro_mc_gradients", "ro_mc_train_step", "ro_compensate_bricks"]
+
+
 class McDesc(ctypes.Structure):
     _fields_ = [("max_batch", ctypes.c_uint32)]
 
@@ -36,8 +41,7 @@ def _lib():
         L.ro_mc_gradients.argtypes = [vp, u32, vp, vp, vp, vp]
         L.ro_mc_train_step.argtypes = [vp, u32, vp, vp, ctypes.c_float, vp]
         L.ro_compensate_bricks.argtypes = [vp, vp, u32, vp, vp]
-        for f in ("ro_mc_query_bytes", "ro_mc_create", "ro_mc_destroy", "ro_mc_set_params", "ro_mc_get_params",
-                  "ro_mc_upsample", "ro_mc_forward", "ro_mc_gradients", "ro_mc_train_step", "ro_compensate_bricks"):
+        for f in EXPORTS:
             getattr(L, f).restype = ctypes.c_int
         L._mc_typed = True
     return L
