@@ -94,7 +94,9 @@ ro_status ro_mc_train_step(ro_mc* mc, uint32_t n, const float* x0, const float* 
  * at least 2 levels; n <= max_upload, n <= cache_slots and n <= the
  * compensator's max_batch (RO_ERR_CAPACITY).  IDs must be level 0, not
  * resident, without duplicates (RO_ERR_INVALID_ARG).  out_slots (host, may
- * be NULL) receives the slots.  Waits for the stream. */
+ * be NULL) receives the slots.  Waits for the stream.  Should a tensor-core
+ * wait of the network give up (the latched flag ro_mc_get_params reports),
+ * the predictions placed by that call are incomplete. */
 ro_status ro_compensate_bricks(ro_ctx* ctx, ro_mc* mc, uint32_t n, const uint32_t* level0_ids, uint32_t* out_slots);
 
 #ifdef __cplusplus
