@@ -181,22 +181,50 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def code_digest(paths):
+    """sha256 of C/C++/CUDA sources with comments and white space removed, so
+    that a comment edit does not count as a change of the compiled code."""
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(p, encoding="utf-8") as fh:
+            src = fh.read()
+        out, i, n = [], 0, len(src)
+        while i < n:
+            ch = src[i]
+            if ch in "\"'":                                  # string or character literal, kept whole
+                j = i + 1
+                while j < n and src[j] != ch:
+                    j += 2 if src[j] == "\\" else 1
+                out.append(src[i:j + 1])
+                i = j + 1
+            elif src.startswith("//", i):
+                j = src.find("\n", i)
+                i = n if j < 0 else j
+            elif src.startswith("/*", i):
+                j = src.find("*/", i + 2)
+                i = n if j < 0 else j + 2
+            else:
+                if not ch.isspace():
+                    out.append(ch)
+                i += 1
+        h.update("".join(out).encode("utf-8"))
+        h.update(b"\0")
+    return h.hexdigest()
+
+
 def recorded_traffic(args):
     """DRAM bytes per render launch from the committed ncu record, only while
-    the render kernel's source is the one that record was taken from and the
+    the render kernel's code is the code that record was taken from and the
     workload is the default one; else None."""
-    import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "render_kernel_cells16_traffic.json")) as fh:
             rec = json.load(fh)
-        h = hashlib.sha256()
-        for f in rec["source_files"]:
-            with open(os.path.join(ROOT, f), "rb") as fh:
-                h.update(fh.read())
+        digest = code_digest([os.path.join(ROOT, f) for f in rec["source_files"]])
         default = (args.workload == "cells16" and args.image is None and args.cache_gib == 8.0 and args.arc == 30.0
                    and args.lod_bias is None and args.radius is None and args.precision == "f32"
                    and args.order == rec.get("order", 0))
-        if h.hexdigest() == rec["source_sha256"] and default:
+        if digest == rec["code_sha256"] and default:
             return int(rec["dram_read_bytes_per_launch"]) + int(rec["dram_write_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
         pass
