@@ -15,7 +15,7 @@ network   y = x0 + f(x0): f is four 3x3x3 convolutions with zero padding
           the first three.  Weight layout W[tap, ci, co], tap = (dz * 3 +
           dy) * 3 + dx; activations channels-last [z, y, x, c].
 loss      mean squared error against the true level-0 apron slot (scaled).
-reading P2  the GPU runs the two 32 -> 32 layers on the tensor cores with
+precision the GPU runs the two 32 -> 32 layers on the tensor cores with
           bfloat16 inputs (binary32 sums); forward(..., bf16_inputs=(1, 2))
           mirrors that rounding of the layer inputs.
 
@@ -96,8 +96,8 @@ def init_params(seed: int = 0):
 
 def forward(params, x0: np.ndarray, bf16_inputs=()):
     """x0 [Z, Y, X] (scaled) -> (y [Z, Y, X], the input of every layer).
-    bf16_inputs: layers whose input enters rounded to bfloat16 (reading P2:
-    the tensor-core layers)."""
+    bf16_inputs: layers whose input enters rounded to bfloat16 (the layers
+    the GPU runs on the tensor cores)."""
     a = x0[..., None]
     acts = []
     for i, (W, b) in enumerate(params):

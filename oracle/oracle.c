@@ -589,8 +589,9 @@ static double lerp_fmt(double f, double a, double b, int fmt) {
 OR_EXPORT double or_round_fmt(double x, int fmt) { return round_fmt(x, fmt); }
 OR_EXPORT double or_lerp_fmt(double f, double a, double b, int fmt) { return lerp_fmt(f, a, b, fmt); }
 
-/* Trilinear value at level l in a low-precision sample format (design
- * reading P1: the cache holds q(v * 2^-S) with S = 8 (u8) or 16 (u16),
+/* Trilinear value at level l in a low-precision sample format (the paper
+ * samples 8/16-bit textures and states no arithmetic; this is the reading
+ * both sides implement: the cache holds q(v * 2^-S) with S = 8 (u8) or 16 (u16),
  * q = round to the format; the binary32 weights of trilinear32 are rounded
  * to the format; every lerp is lerp_fmt; the result times 2^S is returned
  * in binary32).  Order as in trilinear32: x, then y, then z. */

@@ -741,8 +741,8 @@ bool has_debug(const ro_render_params* p) {
   return p->debug_hash || p->debug_n_eval || p->debug_i_end || p->debug_n_bs;
 }
 
-// The per-view part of a launch: camera, per-level tables (R7, R8) and
-// outputs.  Tiles are 2^twl x 2^(5 - twl) pixels.
+// The per-view part of a launch: camera, per-level tables (Sec. 6.2,
+// Algorithm 1) and outputs.  Tiles are 2^twl x 2^(5 - twl) pixels.
 void fill_view(const ro_ctx* c, const ro_camera* cam, const ro_render_params* p, float* image, uint32_t W, uint32_t H,
                int twl, uint32_t tile_base, ro::ViewArgs* v) {
   const Geometry& g = c->g;
@@ -766,7 +766,7 @@ void fill_view(const ro_ctx* c, const ro_camera* cam, const ro_render_params* p,
   v->tiles_x = (W + (1u << twl) - 1) >> twl;
   v->tile_base = tile_base;
   for (int l = 0; l < ro::kMaxL; ++l) v->lod_t[l] = p->lod_t[l];
-  // traversal depth per level (R8): deepest depth whose nodes are at least
+  // traversal depth per level (Algorithm 1): deepest depth whose nodes are at least
   // one step long along every axis, physically
   for (int l = 0; l < ro::kMaxL; ++l) {
     const double step = (double)p->dt * std::ldexp(1.0, l);
@@ -778,7 +778,7 @@ void fill_view(const ro_ctx* c, const ro_camera* cam, const ro_render_params* p,
     }
     v->sdepth[l] = best;
   }
-  // desired levels of every channel for each value of lod (R7): the clamp
+  // desired levels of every channel for each value of lod (Sec. 6.2): the clamp
   // of lod to the channel's [lmin, lmax]
   for (int lod = 0; lod < ro::kMaxL; ++lod) {
     uint64_t ldp = 0;

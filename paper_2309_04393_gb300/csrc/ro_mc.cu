@@ -233,7 +233,7 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
 // The 32 -> 32 convolution with tcgen05.mma.  A block owns an 8 (x) by 16 (y)
 // column of output voxels over kZChunk consecutive z slices and marches along
 // z: the weights stay in shared memory for the whole column, the input sits
-// in a ring of four z slices (bfloat16, reading P2), and while the matrix
+// in a ring of four z slices (rounded to bfloat16), and while the matrix
 // instructions of slice z run, the block stores slice z - 1 and loads slice
 // z + 2 of the halo.  Per slice the 128 x 32 binary32 accumulator D (two of
 // them in tensor memory, used in turn) receives, for each of the 27 taps,

@@ -5,7 +5,8 @@
 namespace ro {
 namespace {
 
-// Bucket-occupancy prefix sums per channel (R5): one block per channel.
+// Bucket-occupancy prefix sums per channel (a bucket is occupied when the
+// TF gives some value in it a non-zero opacity): one block per channel.
 __global__ void __launch_bounds__(256) prefix_kernel(const __grid_constant__ PrefixArgs a) {
   __shared__ uint16_t s_occ[256];
   __shared__ uint16_t s_scan[257];

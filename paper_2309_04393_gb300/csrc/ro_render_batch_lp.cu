@@ -1,5 +1,5 @@
 // Batch launches of the ray caster for the binary16 and bfloat16 sample
-// formats (reading P1).
+// formats.
 #include "ro_render_kernel.cuh"
 
 namespace ro {

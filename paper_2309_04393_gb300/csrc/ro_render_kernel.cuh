@@ -65,7 +65,8 @@ struct Ray {
   bool hit;
 };
 
-// Pixel-centre ray, voxel-space origin/direction and slab interval (R17).
+// Pixel-centre ray (pixel i at i + 0.5), voxel-space origin/direction and
+// slab interval.
 __device__ Ray make_ray(const Geometry& g, const ViewArgs& V, int px, int py) {
   Ray r;
   float o[3], d[3];
@@ -124,7 +125,7 @@ __device__ __forceinline__ void node_coords(const Geometry& g, int d, const floa
   for (int k = 0; k < 3; ++k) j[k] = (int)(x[k] * pow2f(-(g.leaf_log2[k] + g.D - d)));
 }
 
-// Trilinear sample of a level-l apron slot (R15), in two parts: the
+// Trilinear sample of a level-l apron slot, in two parts: the
 // in-slot offset of the lower corner and the lerp weights depend only on the
 // position and the level (every channel's bricks share one grid), so they
 // are computed once per level and sample; the fetch reads one channel's
@@ -132,7 +133,7 @@ __device__ __forceinline__ void node_coords(const Geometry& g, int d, const floa
 struct TriCoords {
   int idx;        // element offset of the lower corner inside the apron slot
   float f[3];     // lerp weights (binary32)
-  uint32_t h[3];  // the weights in the sample format (reading P1): (f0, f0), (f1, f1), f2
+  uint32_t h[3];  // the weights in a 16-bit sample format: (f0, f0), (f1, f1), f2
 };
 
 // Two 16-bit values packed into one 32-bit register, low half first.
@@ -249,7 +250,8 @@ __device__ __forceinline__ float tri_fetch(const RenderArgs& a, uint32_t slot, c
   }
 }
 
-// TF lookup (R16) and opacity correction for a step of 2^s (R12): returns
+// TF lookup (linear between the 256 LUT entries) and opacity correction for
+// a step of 2^s (s squarings of 1 - alpha, Sec. 6.1): returns
 // the corrected opacity's complement q and the colour.  tf = (lo, scale).
 __device__ __forceinline__ void shade(const float4* __restrict__ lut, float2 tf, float val, int s, float& q, float& r,
                                       float& gg, float& b) {  const float t = val - tf.x;
@@ -458,7 +460,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
         active = false;
       } else {
         position(g, r, t, x);
-        // lod = #{l in 1..k-1 : t >= lod_t[l]} (R7); t never decreases along
+        // lod = #{l in 1..k-1 : t >= lod_t[l]} (Sec. 6.2); t never decreases along
         // a ray and the thresholds are non-decreasing, so the count only grows
         while (lod < k - 1 && t >= V.lod_t[lod + 1]) ++lod;
         ldp = V.ldp_tab[lod];
@@ -472,7 +474,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
           same_node = (L[0] >> sh) == nc.jn[0] && (L[1] >> sh) == nc.jn[1] && (L[2] >> sh) == nc.jn[2];
         }
         need = !(same_node && nc.one_brick);
-        // the walk (R9) resumes below the deepest ancestor shared with the
+        // the walk (Sec. 6.1) resumes below the deepest ancestor shared with the
         // previous sample: those depths were found not all terminal
         const int d0 = V.start_depth < st ? V.start_depth : st;
         dstart = d0;
@@ -560,7 +562,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
       const unsigned nonskip = __ballot_sync(FULL, cact && sc != kEmpty && sc != kUnmapped);
       const bool all_skip = (nonskip & gmask) == 0;
 
-      // brick selection (R11): desired level, else request it and take the
+      // brick selection (Algorithm 1): desired level, else request it and take the
       // next coarser resident level
       uint32_t sel = kSelNone;
       int found = 99;
@@ -631,7 +633,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
     // ----------------------------------------- phase 3: skip or evaluate
     if (!active) continue;
     if (nc.all_skip && V.skip) {
-      // first lattice index whose sample lies outside the node (R10):
+      // first lattice index whose sample lies outside the node (Algorithm 1):
       // estimate from the node box's exit distance, then correct with the
       // same position arithmetic
       const int d = nc.d;
@@ -669,7 +671,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
       continue;
     }
 
-    // shade and composite (R12-R14)
+    // shade, composite front to back, stop early once transmittance is low
     const int s = nc.s_sel == 99 ? lminu : nc.s_sel;
     float col0 = 0.0f, col1 = 0.0f, col2 = 0.0f, trans = 1.0f;
     cnt.bs += nc.n_brick;

@@ -1,5 +1,5 @@
 // Single-view launches of the ray caster for the binary16 and bfloat16
-// sample formats (reading P1); a translation unit of its own so that the
+// sample formats; a translation unit of its own so that the
 // instantiations compile in parallel with the others.
 #include "ro_render_kernel.cuh"
 

@@ -30,7 +30,7 @@ __global__ void fill_strided_kernel(uint32_t* __restrict__ w, uint64_t count, ui
 // Copy each staged brick into its slot (16-byte vectors; slot_pitch is a
 // multiple of 256) and write the page-table entries of inserted (slot + 1)
 // and evicted (0) bricks.
-// A raw value in the cache's sample format (reading P1): round(v * 2^-S) to
+// A raw value in the cache's sample format: round(v * 2^-S) to
 // binary16 (sf 1) or bfloat16 (sf 2), S = 8 or 16 bits, nearest even; the
 // scaling by a power of two is exact in binary32.
 __device__ __forceinline__ uint16_t to_format(uint32_t v, int sf, int bpv) {

@@ -160,7 +160,7 @@ def test_full_batch_matches_oracle_samples_and_per_grid_gradients(mc):
         for k in (0, 17, n - 1):
             want, _ = omc.forward(q, x0f[k], bf16_inputs=(1, 2))
             err = np.abs(y[k] - want)
-            # bounds of the two-grid forward test (bfloat16 rounding flips, P2)
+            # bounds of the two-grid forward test (bfloat16 rounding flips)
             assert np.median(err) <= 1e-6
             assert np.quantile(err, 0.99) <= 5e-4
             assert err.max() <= 3e-3 * max(1.0, np.abs(want).max())

@@ -1,5 +1,5 @@
 """Low-precision sampling on the GPU (sample_format 1 = binary16, 2 =
-bfloat16; reading P1) against the oracle's mirror of the same arithmetic:
+bfloat16) against the oracle's mirror of the same arithmetic:
 selection hashes, evaluated samples, final lattice indices, brick samples,
 the binary32 image, requests, node requests and used bricks bit-exact.  The
 error of the image against the binary64 oracle is the precision study's
