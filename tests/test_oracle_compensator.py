@@ -2,7 +2,9 @@
 exactly (trilinear interpolation is exact on them) and constants; the
 convolution of an identity or a one-tap shift kernel is the input itself or
 the shifted input with zero fill; the hand-written gradients match finite
-differences of the loss; bfloat16 rounding at exact ties goes to even."""
+differences of the loss; random asymmetric weights match scipy's
+cross-correlation and the input gradient is the convolution's adjoint;
+bfloat16 rounding at exact ties goes to even."""
 import numpy as np
 import pytest
 
@@ -33,6 +35,31 @@ def test_conv_identity_and_shift_kernels():
     W[(2 * 3 + 1) * 3 + 1] = np.eye(3)                              # tap dz = +1: out[z] = x[z + 1]
     out = mc.conv3(x, W, np.zeros(3))
     assert np.allclose(out[:-1], x[1:], atol=1e-12) and np.all(out[-1] == 0)
+
+
+def test_conv_matches_scipy_correlate_for_asymmetric_weights():
+    """Random, non-symmetric weights against scipy's n-d cross-correlation
+    with zero fill: a transposed weight index or a swapped tap axis fails
+    here (the identity and shift kernels above are symmetric in both)."""
+    from scipy import ndimage
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=(5, 6, 7, 2))
+    W = rng.normal(size=(27, 2, 3))
+    b = rng.normal(size=3)
+    out = mc.conv3(x, W, b)
+    for co in range(3):
+        want = np.full(x.shape[:3], b[co])
+        for ci in range(2):
+            # tap (dz * 3 + dy) * 3 + dx reads the input at offset (dz-1, dy-1, dx-1)
+            K = W[:, ci, co].reshape(3, 3, 3)
+            want += ndimage.correlate(x[..., ci], K, mode="constant", cval=0.0)
+        assert np.allclose(out[..., co], want, rtol=0, atol=1e-12)
+    # the input gradient is the adjoint of the convolution: <conv(x), g> = <x, conv^T(g)>
+    g = rng.normal(size=(5, 6, 7, 3))
+    dx, dW, db = mc.conv3_backward(x, W, g)
+    lhs = float(np.sum((mc.conv3(x, W, np.zeros(3))) * g))
+    assert abs(lhs - float(np.sum(x * dx))) <= 1e-9 * max(1.0, abs(lhs))
+    assert np.allclose(db, g.sum(axis=(0, 1, 2)), atol=1e-12)
 
 
 def test_gradients_match_finite_differences():
