@@ -17,7 +17,14 @@ network   y = x0 + f(x0): f is four 3x3x3 convolutions with zero padding
 loss      mean squared error against the true level-0 apron slot (scaled).
 precision the GPU runs the two 32 -> 32 layers on the tensor cores with
           bfloat16 inputs (binary32 sums); forward(..., bf16_inputs=(1, 2))
-          mirrors that rounding of the layer inputs.
+          mirrors that rounding of the layer inputs, and
+          loss_and_grads(..., bf16_grads=(1, 2)) the rounding of the output
+          gradients that enter those layers' weight- and input-gradient
+          products (their bias gradients sum the unrounded values).
+adam      one step of Adam (Kingma and Ba, 2015, Algorithm 1): exponential
+          moving averages of the gradient and its square, both divided by
+          their bias corrections 1 - beta^t, then a step of lr * m_hat /
+          (sqrt(v_hat) + eps).
 
 Parity unpinned where the GPU's binary32 accumulation order differs: the
 GPU kernels are compared within a tolerance derived from that order.
@@ -110,9 +117,11 @@ def forward(params, x0: np.ndarray, bf16_inputs=()):
     return x0 + a[..., 0], acts
 
 
-def loss_and_grads(params, x0: np.ndarray, target: np.ndarray, bf16_inputs=()):
+def loss_and_grads(params, x0: np.ndarray, target: np.ndarray, bf16_inputs=(), bf16_grads=()):
     """Mean squared error of forward(x0) against target and its gradients
-    with respect to every weight and bias."""
+    with respect to every weight and bias.  bf16_grads: layers whose output
+    gradient enters the weight- and input-gradient products rounded to
+    bfloat16 (the bias gradient is summed from the unrounded values)."""
     y, acts = forward(params, x0, bf16_inputs)
     n = y.size
     d = y - target
@@ -121,7 +130,8 @@ def loss_and_grads(params, x0: np.ndarray, target: np.ndarray, bf16_inputs=()):
     grads = [None] * len(params)
     for i in range(len(params) - 1, -1, -1):
         W, _ = params[i]
-        gx, gW, gb = conv3_backward(acts[i], W, g)
+        gx, gW, _ = conv3_backward(acts[i], W, bf16(g) if i in bf16_grads else g)
+        gb = g.sum(axis=(0, 1, 2))
         grads[i] = (gW, gb)
         if i > 0:
             g = gx * (acts[i] > 0.0)
@@ -134,3 +144,15 @@ def bf16(x: np.ndarray) -> np.ndarray:
     u = f.view(np.uint32).astype(np.uint64)
     r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
     return r.view(np.float32).astype(np.float64)
+
+
+def adam_step(p: np.ndarray, g: np.ndarray, m: np.ndarray, v: np.ndarray, t: int, lr: float,
+              beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    """Adam step t >= 1 (Kingma and Ba, 2015, Algorithm 1), binary64, on flat
+    arrays: returns the new parameters and the new first and second moment
+    estimates."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    return p - lr * m_hat / (np.sqrt(v_hat) + eps), m, v

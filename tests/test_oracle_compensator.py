@@ -98,3 +98,86 @@ def test_bf16_ties_to_even():
     assert mc.bf16(1.0 + 2.0 ** -8) == 1.0                         # halfway, to even
     assert mc.bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6          # halfway, to even (up)
     assert mc.bf16(1.0 + 2.0 ** -8 + 2.0 ** -20) == 1.0 + 2.0 ** -7  # above halfway
+
+
+def test_bf16_gradient_rounding_bound():
+    """The bfloat16 rounding of the output gradients of layers 1 and 2 moves
+    each of their weight gradients by at most the unit roundoff 2^-8 times
+    sum(|input| * |gradient|) over the voxels and taps that enter it; the
+    bias gradients and the first and last layers' gradients only change
+    through the rounded gradient that flows further down."""
+    rng = np.random.default_rng(6)
+    params = [(W * 3.0, rng.normal(0, 0.05, b.shape)) for W, b in mc.init_params(5)]
+    params = [(mc.bf16(W), b) for W, b in params]
+    x0 = rng.uniform(0.0, 1.0, (6, 5, 7))
+    target = np.clip(x0 + rng.normal(0.0, 0.05, x0.shape), 0, 1)
+    _, exact = mc.loss_and_grads(params, x0, target, bf16_inputs=(1, 2))
+    _, rounded = mc.loss_and_grads(params, x0, target, bf16_inputs=(1, 2), bf16_grads=(2,))
+    # only layer 2's own products use the rounded gradient: its bias
+    # gradient and layer 3's gradients are unchanged
+    assert np.array_equal(rounded[3][0], exact[3][0]) and np.array_equal(rounded[3][1], exact[3][1])
+    assert np.array_equal(rounded[2][1], exact[2][1])
+    # bound for layer 2's weight gradient from |bf16(g) - g| <= 2^-8 |g|
+    y, acts = mc.forward(params, x0, bf16_inputs=(1, 2))
+    g = (2.0 / y.size) * (y - target)[..., None]
+    for i in (2,):
+        g = mc.conv3_backward(acts[i + 1], params[i + 1][0], g)[0] * (acts[i + 1] > 0.0)
+    _, bound, _ = mc.conv3_backward(np.abs(acts[2]), np.abs(params[2][0]), np.abs(g))
+    diff = np.abs(rounded[2][0] - exact[2][0])
+    assert np.all(diff <= 2.0 ** -8 * bound + 1e-18)
+    assert diff.max() > 0.0
+    _, both = mc.loss_and_grads(params, x0, target, bf16_inputs=(1, 2), bf16_grads=(1, 2))
+    assert not np.array_equal(both[1][0], rounded[1][0]) and np.array_equal(both[2][0], rounded[2][0])
+
+
+@pytest.mark.parametrize("g", [0.3, -2.0e3, 1.0e-9])
+def test_adam_constant_gradient_closed_form(g):
+    """With one constant gradient g the bias-corrected moments are exactly g
+    and g^2 at every step, so every step moves the parameter by
+    -lr * g / (|g| + eps): lr * sign(g) for |g| >> eps, lr / 11 at g = 1e-9
+    (eps = 1e-8 added to the root, not under it)."""
+    lr, eps = 0.01, 1e-8
+    p, m, v = np.array([0.25]), np.zeros(1), np.zeros(1)
+    for t in range(1, 11):
+        p_new, m, v = mc.adam_step(p, np.array([g]), m, v, t, lr)
+        step = lr * g / (abs(g) + eps)
+        assert abs((p - p_new)[0] - step) <= 1e-12 * max(1.0, abs(step))
+        p = p_new
+    if g == 1.0e-9:
+        assert abs(step - lr / 11.0) < 1e-15
+
+
+def test_adam_weighted_average_form():
+    """After t steps the bias-corrected moments are weighted means of the
+    gradients so far, m_hat = sum beta1^(t-i) g_i / sum beta1^(t-i) (and v_hat
+    of g_i^2 with beta2): the parameter trajectory written from that explicit
+    form equals the recursion's."""
+    rng = np.random.default_rng(8)
+    lr, b1, b2, eps = 0.003, 0.9, 0.999, 1e-8
+    G = rng.normal(0.0, 1.0, (7, 5)) * np.array([1e-3, 1.0, 50.0, 1e-6, 3.0])
+    p0 = rng.normal(size=5)
+    p, m, v = p0.copy(), np.zeros(5), np.zeros(5)
+    want = p0.copy()
+    for t in range(1, 8):
+        p, m, v = mc.adam_step(p, G[t - 1], m, v, t, lr)
+        w1 = b1 ** np.arange(t - 1, -1, -1)
+        w2 = b2 ** np.arange(t - 1, -1, -1)
+        m_hat = (w1[:, None] * G[:t]).sum(0) / w1.sum()
+        v_hat = (w2[:, None] * G[:t] ** 2).sum(0) / w2.sum()
+        want = want - lr * m_hat / (np.sqrt(v_hat) + eps)
+        assert np.allclose(p, want, rtol=0, atol=1e-12)
+        # the moments themselves are the unnormalised sums
+        assert np.allclose(m, (1 - b1) * (w1[:, None] * G[:t]).sum(0), rtol=1e-12, atol=0)
+        assert np.allclose(v, (1 - b2) * (w2[:, None] * G[:t] ** 2).sum(0), rtol=1e-12, atol=0)
+
+
+def test_adam_is_invariant_to_gradient_scale():
+    rng = np.random.default_rng(9)
+    G = rng.normal(size=(5, 4))
+    runs = []
+    for scale in (1.0, 1000.0):
+        p, m, v = np.ones(4), np.zeros(4), np.zeros(4)
+        for t in range(1, 6):
+            p, m, v = mc.adam_step(p, scale * G[t - 1], m, v, t, 0.01)
+        runs.append(p)
+    assert np.allclose(runs[0], runs[1], rtol=0, atol=1e-9)
