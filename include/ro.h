@@ -172,9 +172,38 @@ typedef struct {
  * recomputes the partial-residency masks of every leaf that overlaps a brick
  * uploaded or evicted since the previous call, and recomputes every
  * ancestor of a changed leaf as the bitwise OR of its children's masks and
- * the hull of their ranges (INVALID if any child is).  No atomics.
- * meta is a host pointer (NULL if n_meta = 0). */
+ * the hull of their ranges when all children are valid, else the range
+ * given for the node itself (ro_update_node_metadata), else INVALID.  An
+ * INVALID word (Sec. 5.2) keeps its mask and holds min8 = 255 and max8 =
+ * the depth of the node's nearest valid ancestor, or RO_UNKNOWN_DEPTH when
+ * no ancestor is valid; the renderer reads such a word with that
+ * ancestor's range.  No atomics.  meta is a host pointer (NULL if
+ * n_meta = 0). */
 ro_status ro_update_residency_octree(ro_ctx* ctx, uint32_t n_meta, const ro_leaf_meta* meta);
+
+#define RO_UNKNOWN_DEPTH 254u
+
+/* Metadata for a volume region of any size (Sec. 5.3: metadata arriving
+ * for a region, e.g. in answer to a node request): the raw value range of
+ * channel `channel` over node `node`, numbered as node requests number nodes
+ * (depth-major from the root, then z, y, x; leaves last).  For a leaf it is
+ * the leaf range of ro_leaf_meta.  For an inner node it is used while not all
+ * of its children are valid (then their hull is tighter); it must cover
+ * every level-0 voxel whose trilinear support reaches the node.
+ * vmin > vmax withdraws a given range. */
+typedef struct {
+  uint32_t node;
+  uint32_t channel;
+  uint32_t vmin;
+  uint32_t vmax;
+} ro_node_meta;
+
+/* Writes n_meta node ranges, then brings the octree up to date as
+ * ro_update_residency_octree does (pending brick changes included); the
+ * INVALID words below a node that gained a range point to it.  meta is a
+ * host pointer (NULL if n_meta = 0); RO_ERR_INVALID_ARG for a node or
+ * channel out of range. */
+ro_status ro_update_node_metadata(ro_ctx* ctx, uint32_t n_meta, const ro_node_meta* meta);
 
 /* Camera (physical units).  ortho (perspective = 0): pixel (i, j) starts at
  * eye + a*right + b*up, a = (i + 0.5 - W/2)*pixel, b = (H/2 - j - 0.5)*pixel,
@@ -360,6 +389,8 @@ const char* ro_last_error(const ro_ctx* ctx);
  *  total    device pointer to one u32: the number of set flags.
  *  stream   cudaStream_t the work is enqueued on (NULL = legacy default
  *           stream); the call returns without waiting.
+ * flags, ids, total and stream must belong to the calling thread's current
+ * device: the scratch used is that device's copy.
  * Its per-tile counts live in one 256 KiB array in device memory, part of the
  * library itself, which every GPU that loads the library holds until the
  * process exits; it never calls cudaMalloc, cudaFree or any allocating

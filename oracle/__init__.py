@@ -38,7 +38,8 @@ class _Volume(ctypes.Structure):
                 ("m", ctypes.c_int32), ("k", ctypes.c_int32), ("B", ctypes.c_int32), ("bpv", ctypes.c_int32),
                 ("leaf", ctypes.c_int32 * 3), ("levels", ctypes.POINTER(ctypes.c_void_p)),
                 ("resident", ctypes.c_void_p), ("leaf_min", ctypes.c_void_p), ("leaf_max", ctypes.c_void_p),
-                ("voxel_fn", ctypes.c_void_p), ("voxel_ctx", ctypes.c_void_p), ("sample_format", ctypes.c_int32)]
+                ("voxel_fn", ctypes.c_void_p), ("voxel_ctx", ctypes.c_void_p), ("sample_format", ctypes.c_int32),
+                ("node_min", ctypes.c_void_p), ("node_max", ctypes.c_void_p)]
 
 
 class _Params(ctypes.Structure):
@@ -120,6 +121,8 @@ class Volume:
     levels[c][l]: numpy array [z][y][x] (uint8 or uint16) of level l.
     resident: iterable of (c, l, bx, by, bz) bricks resident in the cache.
     leaf_min / leaf_max: arrays (m, lz, ly, lx) int64, -1 = no metadata.
+    node_min / node_max: ranges given for inner nodes, arrays (m, n_nodes)
+    int64 by node index (depth-major), -1 = none (entries of leaves unused).
     sample_format: 0 = raw values with binary32 lerps, 1 = binary16,
     2 = bfloat16 samples (the brick cache's format).
     provider: instead of levels, (m, k, dims_xyz, bytes_per_voxel, fn, ctx)
@@ -129,7 +132,7 @@ class Volume:
     """
 
     def __init__(self, levels, spacing, B, leaf_extent, resident=(), leaf_min=None, leaf_max=None, provider=None,
-                 sample_format=0):
+                 sample_format=0, node_min=None, node_max=None):
         self.s = _Volume()
         self.s.sample_format = int(sample_format)
         if provider is None:
@@ -170,6 +173,20 @@ class Volume:
             self.leaf_max[:] = np.asarray(leaf_max, np.int64).reshape(self.m, n_leaves)
         self.s.leaf_min = self.leaf_min.ctypes.data
         self.s.leaf_max = self.leaf_max.ctypes.data
+        self.set_node_ranges(node_min, node_max)
+
+    def set_node_ranges(self, node_min, node_max):
+        """Ranges the data source gave for inner nodes ((m, n_nodes) int64,
+        -1 = none), or None for none."""
+        if node_min is None:
+            self.node_min = self.node_max = None
+            self.s.node_min = self.s.node_max = None
+            return
+        n = self.n_nodes
+        self.node_min = np.ascontiguousarray(np.asarray(node_min, np.int64).reshape(self.m, n))
+        self.node_max = np.ascontiguousarray(np.asarray(node_max, np.int64).reshape(self.m, n))
+        self.s.node_min = self.node_min.ctypes.data
+        self.s.node_max = self.node_max.ctypes.data
 
     @property
     def depth(self) -> int:

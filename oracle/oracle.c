@@ -9,13 +9,16 @@
  * What it computes, and the passage each part follows:
  *
  *  O-a  Residency and culling words of every octree node (Sec. 3 "Fully vs.
- *       partially mapped", Sec. 5.2 node contents, Sec. 7 node layout):
- *       mask bit l of a node is set iff some resident brick of that level and
- *       channel overlaps the node's box with positive volume; the value range
- *       of a node is the range over all leaves below it; a node whose
- *       channel lacks metadata anywhere below it is INVALID.  Computed for
- *       every node straight from these definitions, by scanning bricks and
- *       leaves (no bottom-up propagation).
+ *       partially mapped", Sec. 5.2 node contents and INVALID / UNKNOWN,
+ *       Sec. 5.3 metadata for a volume region, Sec. 7 node layout): mask bit
+ *       l of a node is set iff some resident brick of that level and channel
+ *       overlaps the node's box with positive volume (by scanning bricks).
+ *       The value range of a node: a leaf's is the range the data source
+ *       gave for it; an inner node's is the hull of its children's when all
+ *       of them are valid, else the range the data source gave for the node
+ *       itself; without either the node is INVALID for the channel, and its
+ *       word names the depth of the nearest ancestor that is valid for the
+ *       channel (or UNKNOWN when none is).
  *
  *  O-b  Per-pixel ray march following Sec. 6.1 (Algorithm 1 and the
  *       multi-channel walk that keeps one channel index and stays in the node
@@ -67,6 +70,11 @@ typedef struct {
   /* sample format of the brick cache: 0 = raw values, binary32 lerps;
    * 1 = binary16, 2 = bfloat16 (see trilinear_lp) */
   int32_t sample_format;
+  /* ranges the data source gave for inner nodes: m * n_nodes raw values by
+   * node index (depth-major), -1 = none; entries of leaves are not read.
+   * NULL: none given. */
+  const int64_t *node_min;
+  const int64_t *node_max;
 } or_volume;
 
 typedef struct {
@@ -252,28 +260,9 @@ static void oa_node(const oa_ctx *x, int d, int64_t jx, int64_t jy, int64_t jz) 
           }
       if (found) mask |= 1u << l;
     }
-    /* value range over every leaf below the node; INVALID if any leaf lacks it */
-    int64_t mn = INT64_MAX, mx = -1;
-    int invalid = 0;
-    for (int64_t z = llo[2]; z < lhi[2] && !invalid; ++z)
-      for (int64_t y = llo[1]; y < lhi[1] && !invalid; ++y)
-        for (int64_t xx = llo[0]; xx < lhi[0]; ++xx) {
-          int64_t li = (z * nl[1] + y) * nl[0] + xx;
-          int64_t a = v->leaf_min[(int64_t)c * nleaves + li], b = v->leaf_max[(int64_t)c * nleaves + li];
-          if (a < 0 || b < 0) { invalid = 1; break; }
-          if (a < mn) mn = a;
-          if (b > mx) mx = b;
-        }
-    uint32_t min8, max8;
-    if (invalid) {
-      min8 = 255; max8 = 0;   /* the INVALID sentinel: min > max */
-    } else if (v->bpv == 1) {
-      min8 = (uint32_t)mn; max8 = (uint32_t)mx;
-    } else {                  /* 16-bit data: 8-bit buckets of 256 raw values */
-      min8 = (uint32_t)(mn >> 8); max8 = (uint32_t)(mx >> 8);
-    }
-    x->words[nidx * v->m + c] = mask | (min8 << 16) | (max8 << 24);
+    x->words[nidx * v->m + c] = mask;   /* the range bits are filled in by or_node_words */
   }
+  (void)nleaves; (void)llo; (void)lhi;
 }
 
 typedef struct { oa_ctx *x; int64_t n; int64_t next; pthread_mutex_t mu; } oa_pool;
@@ -314,8 +303,97 @@ static void *oa_worker(void *arg) {
   return NULL;
 }
 
+/* INVALID words: min8 = 255 and max8 = the depth of the nearest valid
+ * ancestor, or OR_UNKNOWN when no ancestor is valid (both below 255, so
+ * min8 > max8 marks INVALID). */
+#define OR_UNKNOWN 254u
+
+/* Value ranges of every node and channel from the data source's ranges
+ * (leaves, and inner nodes where given), depth by depth from the leaves up:
+ * a node is valid if all its children are (range = their hull) or if it was
+ * given a range; then, from the root down, every INVALID node gets the depth
+ * of its nearest valid ancestor. */
+static int oa_ranges(const or_volume *v, const oa_ctx *x, uint32_t *words) {
+  const int m = v->m, D = x->D;
+  const int64_t n_nodes = x->g.node_off[D + 1];
+  int64_t *mn = (int64_t *)malloc((size_t)n_nodes * m * sizeof(int64_t));
+  int64_t *mx = (int64_t *)malloc((size_t)n_nodes * m * sizeof(int64_t));
+  uint8_t *ptr = (uint8_t *)malloc((size_t)n_nodes * m);
+  if (!mn || !mx || !ptr) { free(mn); free(mx); free(ptr); return -1; }
+  /* leaves: the given ranges (mn = -1: invalid) */
+  for (int c = 0; c < m; ++c)
+    for (int64_t li = 0; li < n_nodes - x->g.node_off[D]; ++li) {
+      int64_t a = v->leaf_min[(int64_t)c * (n_nodes - x->g.node_off[D]) + li];
+      int64_t b = v->leaf_max[(int64_t)c * (n_nodes - x->g.node_off[D]) + li];
+      int64_t n = x->g.node_off[D] + li;
+      mn[n * m + c] = (a < 0 || b < 0) ? -1 : a;
+      mx[n * m + c] = (a < 0 || b < 0) ? -1 : b;
+    }
+  /* inner nodes, deepest first */
+  for (int d = D - 1; d >= 0; --d) {
+    const int64_t *nn = x->g.nn[d], *nc = x->g.nn[d + 1];
+    for (int64_t jz = 0; jz < nn[2]; ++jz)
+      for (int64_t jy = 0; jy < nn[1]; ++jy)
+        for (int64_t jx = 0; jx < nn[0]; ++jx) {
+          int64_t n = x->g.node_off[d] + (jz * nn[1] + jy) * nn[0] + jx;
+          for (int c = 0; c < m; ++c) {
+            int all_valid = 1;
+            int64_t lo = INT64_MAX, hi = -1;
+            for (int cz = 0; cz < 2; ++cz)
+              for (int cy = 0; cy < 2; ++cy)
+                for (int cx = 0; cx < 2; ++cx) {
+                  int64_t kx = 2 * jx + cx, ky = 2 * jy + cy, kz = 2 * jz + cz;
+                  if (kx >= nc[0] || ky >= nc[1] || kz >= nc[2]) continue;
+                  int64_t ch = x->g.node_off[d + 1] + (kz * nc[1] + ky) * nc[0] + kx;
+                  if (mn[ch * m + c] < 0) { all_valid = 0; continue; }
+                  if (mn[ch * m + c] < lo) lo = mn[ch * m + c];
+                  if (mx[ch * m + c] > hi) hi = mx[ch * m + c];
+                }
+            if (!all_valid) {
+              int64_t a = v->node_min ? v->node_min[(int64_t)c * n_nodes + n] : -1;
+              int64_t b = v->node_max ? v->node_max[(int64_t)c * n_nodes + n] : -1;
+              if (a >= 0 && b >= 0) { lo = a; hi = b; }
+              else { lo = -1; hi = -1; }
+            }
+            mn[n * m + c] = lo;
+            mx[n * m + c] = hi;
+          }
+        }
+  }
+  /* pointers of INVALID nodes, from the root down */
+  for (int d = 0; d <= D; ++d) {
+    const int64_t *nn = x->g.nn[d];
+    for (int64_t jz = 0; jz < nn[2]; ++jz)
+      for (int64_t jy = 0; jy < nn[1]; ++jy)
+        for (int64_t jx = 0; jx < nn[0]; ++jx) {
+          int64_t n = x->g.node_off[d] + (jz * nn[1] + jy) * nn[0] + jx;
+          int64_t par = d > 0 ? x->g.node_off[d - 1] + ((jz / 2) * x->g.nn[d - 1][1] + jy / 2) * x->g.nn[d - 1][0] + jx / 2 : -1;
+          for (int c = 0; c < m; ++c) {
+            if (d == 0) ptr[n * m + c] = (uint8_t)OR_UNKNOWN;
+            else ptr[n * m + c] = mn[par * m + c] >= 0 ? (uint8_t)(d - 1) : ptr[par * m + c];
+          }
+        }
+  }
+  for (int64_t n = 0; n < n_nodes; ++n)
+    for (int c = 0; c < m; ++c) {
+      uint32_t min8, max8;
+      int64_t a = mn[n * m + c], b = mx[n * m + c];
+      if (a < 0) {
+        min8 = 255; max8 = ptr[n * m + c];
+      } else if (v->bpv == 1) {
+        min8 = (uint32_t)a; max8 = (uint32_t)b;
+      } else {                  /* 16-bit data: 8-bit buckets of 256 raw values */
+        min8 = (uint32_t)(a >> 8); max8 = (uint32_t)(b >> 8);
+      }
+      words[n * m + c] |= (min8 << 16) | (max8 << 24);
+    }
+  free(mn); free(mx); free(ptr);
+  return 0;
+}
+
 /* Residency and culling word of every node and channel: words[node*m + c] =
- * mask[15:0] | min8[23:16] | max8[31:24] (Sec. 7), INVALID = min8 > max8. */
+ * mask[15:0] | min8[23:16] | max8[31:24] (Sec. 7), INVALID = min8 > max8
+ * (then max8 = depth of the nearest valid ancestor, or OR_UNKNOWN). */
 OR_EXPORT int or_node_words(const or_volume *v, uint32_t *words) {
   if (v->m < 1 || v->m > OR_MAXC || v->k < 1 || v->k > OR_MAXL || (v->bpv != 1 && v->bpv != 2) ||
       v->sample_format < 0 || v->sample_format > 2)
@@ -332,7 +410,7 @@ OR_EXPORT int or_node_words(const or_volume *v, uint32_t *words) {
   for (int i = 0; i < nt; ++i) pthread_create(&th[i], NULL, oa_worker, &p);
   for (int i = 0; i < nt; ++i) pthread_join(th[i], NULL);
   pthread_mutex_destroy(&p.mu);
-  return 0;
+  return oa_ranges(v, &x, words);
 }
 
 /* ----------------------------------------------------- O-b / O-c: march */
@@ -489,6 +567,19 @@ static int classify(const ob_frame *f, int c, uint32_t w, int ld) {
   uint32_t usable = (w & 0xFFFFu) & ~((1u << ld) - 1u) & ((1u << f->v->k) - 1u);
   if (!usable) return ST_UNMAPPED;
   return ST_BRICK;
+}
+
+/* An INVALID word whose channel has a valid ancestor (Sec. 5.2: the pointer
+ * to the node in the next lower subdivision level with valid information)
+ * is read with that ancestor's range and its own residency mask; other
+ * words are returned as they are (UNKNOWN stays INVALID). */
+static uint32_t resolve_word(const ob_frame *f, uint32_t w, const float x[3], int c) {
+  uint32_t min8 = (w >> 16) & 0xFFu, max8 = w >> 24;
+  if (min8 <= max8 || max8 == OR_UNKNOWN) return w;
+  int64_t j[3];
+  node_coords(f, (int)max8, x, j);
+  uint32_t a = f->words[node_index(f, (int)max8, j) * f->v->m + c];
+  return (w & 0xFFFFu) | (a & 0xFFFF0000u);
 }
 
 static inline uint32_t fnv_word(uint32_t h, uint32_t w) {
@@ -734,7 +825,7 @@ static void march_pixel(const ob_frame *f, int px, int py, int64_t n_out, const 
       int64_t jn[3];
       while (ch < m) {
         node_coords(f, d, x, jn);
-        uint32_t w = f->words[node_index(f, d, jn) * m + ch];
+        uint32_t w = resolve_word(f, f->words[node_index(f, d, jn) * m + ch], x, ch);
         int s = classify(f, ch, w, ld[ch]);
         int terminal = (s == ST_EMPTY || s == ST_HOMOG || s == ST_UNMAPPED) || d == st;
         if (terminal) ++ch;
@@ -744,12 +835,17 @@ static void march_pixel(const ob_frame *f, int px, int py, int64_t n_out, const 
       int64_t node = node_index(f, d, jn);
       int state[OR_MAXC];
       int all_skip = 1;
+      uint32_t rw[OR_MAXC];   /* the final node's words, INVALID ones resolved */
       for (int c = 0; c < m; ++c) {
-        state[c] = classify(f, c, f->words[node * m + c], ld[c]);
+        rw[c] = resolve_word(f, f->words[node * m + c], x, c);
+        state[c] = classify(f, c, rw[c], ld[c]);
         if (state[c] != ST_EMPTY && state[c] != ST_UNMAPPED) all_skip = 0;
       }
 
-      /* brick requests for channels with no usable level in this node */
+      /* brick requests for channels with no usable level in this node; node
+       * requests (reportNodeRequest) for channels whose own metadata is
+       * missing here, unless the ancestor's range already shows the node
+       * empty or homogeneous */
       for (int c = 0; c < m; ++c) {
         uint32_t w = f->words[node * m + c];
         int unm = state[c] == ST_UNMAPPED ||
@@ -759,7 +855,8 @@ static void march_pixel(const ob_frame *f, int px, int py, int64_t n_out, const 
           owner_brick(f, ld[c], x, b);
           fl->req[brick_index_g(v, &f->g, c, ld[c], b[0], b[1], b[2])] = 1;
         }
-        if (state[c] == ST_INVALID) fl->node_req[node * m + c] = 1;   /* reportNodeRequest */
+        int missing = ((w >> 16) & 0xFFu) > (w >> 24);
+        if (missing && state[c] != ST_EMPTY && state[c] != ST_HOMOG) fl->node_req[node * m + c] = 1;
       }
 
       if (all_skip && p->skip) {
@@ -801,7 +898,7 @@ static void march_pixel(const ob_frame *f, int px, int py, int64_t n_out, const 
       for (int c = 0; c < m; ++c) {
         has[c] = 0;
         lused[c] = -1;
-        uint32_t w = f->words[node * m + c];
+        uint32_t w = rw[c];
         int s = state[c];
         if (s == ST_EMPTY || s == ST_UNMAPPED) continue;
         if (s == ST_HOMOG) {

@@ -42,6 +42,7 @@ struct Layout {
   uint64_t req_pad, node_req_pad, used_pad;
   uint64_t sc_counts, sc_totals, sc_items, sc_meta, sc_ins_index, sc_ins_slot, sc_ev_index, sc_stats, sc_err, sc_work;
   uint64_t fr_lut, fr_prefix, li_req, li_node;
+  uint64_t oc_given;                             // octree part: ranges given for inner nodes after the words
   uint64_t ba_views, ba_tf, ba_order, ba_cost;   // batch region: view table, TF ranges, schedule, tile costs
   uint32_t max_tiles;
 };
@@ -143,7 +144,8 @@ void make_layout(const ro_desc* d, const Geometry& g, Layout* L) {
   L->used_pad = align_up(d->cache_slots, ro::kCompactTile);
   s.cache = (uint64_t)d->cache_slots * g.slot_pitch;
   s.page_table = align_up(g.n_bricks * 4, kAlign);
-  s.octree = align_up(g.n_nodes * (uint64_t)g.mp * 4, kAlign);
+  L->oc_given = align_up(g.n_nodes * (uint64_t)g.mp * 4, kAlign);
+  s.octree = L->oc_given + align_up(g.node_off[g.D] * (uint64_t)g.mp * 4, kAlign);
   s.req_flags = L->req_pad;
   s.node_req_flags = L->node_req_pad;
   s.used_flags = L->used_pad;
@@ -193,7 +195,7 @@ struct ro_ctx {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
   uint8_t *cache, *req, *node_req, *used, *staging, *scratch;
-  uint32_t *pt, *octree, *last_used, *req_out, *node_out, *err;
+  uint32_t *pt, *octree, *given, *last_used, *req_out, *node_out, *err;
   float4* lut;
   uint16_t* prefix;
   std::vector<uint32_t> slot_of_brick;   // page-table index -> slot or RO_NONE
@@ -349,6 +351,7 @@ ro_status ro_create(const ro_desc* desc, void* arena_device, uint64_t arena_byte
   c->cache = c->arena + o[0];
   c->pt = reinterpret_cast<uint32_t*>(c->arena + o[1]);
   c->octree = reinterpret_cast<uint32_t*>(c->arena + o[2]);
+  c->given = reinterpret_cast<uint32_t*>(c->arena + o[2] + c->L.oc_given);
   c->req = c->arena + o[3];
   c->node_req = c->arena + o[4];
   c->used = c->arena + o[5];
@@ -381,7 +384,9 @@ ro_status ro_create(const ro_desc* desc, void* arena_device, uint64_t arena_byte
   const ro_buffer_sizes& z = c->L.sz;
   cudaStream_t st = c->stream;
   e = cudaMemsetAsync(c->pt, 0, z.page_table, st);
-  if (e == cudaSuccess) e = ro::launch_fill_words(c->octree, z.octree / 4, 0x00FF0000u, st);  // INVALID, empty mask
+  // every node INVALID without a valid ancestor, empty mask; no range given
+  if (e == cudaSuccess) e = ro::launch_fill_words(c->octree, c->g.n_nodes * (uint64_t)c->g.mp, ro::kInvalidUnknown, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->given, 0, z.octree - c->L.oc_given, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->req, 0, z.req_flags, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->node_req, 0, z.node_req_flags, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->used, 0, z.used_flags, st);
@@ -602,36 +607,37 @@ ro_status ro_compensate_bricks(ro_ctx* c, ro_mc* mc, uint32_t n, const uint32_t*
   return place_bricks(c, n, pis, fill, out_slots, nullptr, &parent_slot);  // parents are read, never evicted
 }
 
-ro_status ro_update_residency_octree(ro_ctx* c, uint32_t n_meta, const ro_leaf_meta* meta) {
-  if (!c) return RO_ERR_INVALID_ARG;
-  if (c->latched != RO_OK) return c->latched;
-  if (n_meta && !meta) return set_err(c, RO_ERR_INVALID_ARG, "ro_update_residency_octree: null meta");
+}  // extern "C"
+
+namespace {
+
+// Last entry wins for a repeated (channel, index); input already in strictly
+// increasing (channel, index) order needs no sort.
+std::vector<ro::MetaItem> dedup_meta(const std::vector<ro::MetaItem>& in, uint64_t n_index) {
+  auto key = [&](const ro::MetaItem& m) { return (uint64_t)m.channel * n_index + m.leaf; };
+  bool sorted = true;
+  for (size_t i = 1; i < in.size() && sorted; ++i) sorted = key(in[i - 1]) < key(in[i]);
+  if (sorted) return in;
+  std::vector<uint32_t> order(in.size());
+  for (uint32_t i = 0; i < in.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return key(in[a]) < key(in[b]); });
+  std::vector<ro::MetaItem> out;
+  out.reserve(in.size());
+  for (size_t q = 0; q < order.size(); ++q)
+    if (q + 1 == order.size() || key(in[order[q + 1]]) != key(in[order[q]])) out.push_back(in[order[q]]);
+  return out;
+}
+
+// The update of Sec. 5.3 for leaf ranges `lm` (.leaf = leaf index), ranges
+// given for inner nodes `im` (.leaf = node index) and the bricks changed
+// since the last update: range writes, leaf masks, bottom-up recomputation
+// of the changed boxes' ancestors, then the INVALID pointers from the root
+// down over the same boxes.
+ro_status run_update(ro_ctx* c, const std::vector<ro::MetaItem>& lm_in, const std::vector<ro::MetaItem>& im_in) {
   const Geometry& g = c->g;
   const uint64_t n_leaves = (uint64_t)g.nleaf[0] * g.nleaf[1] * g.nleaf[2];
-  for (uint32_t i = 0; i < n_meta; ++i)
-    if (meta[i].leaf >= n_leaves || meta[i].channel >= (uint32_t)g.m)
-      return set_err(c, RO_ERR_INVALID_ARG, "ro_update_residency_octree: leaf or channel out of range");
-  // last entry wins for a repeated (channel, leaf); input already in strictly
-  // increasing (channel, leaf) order needs no sort
-  std::vector<ro::MetaItem> mi;
-  mi.reserve(n_meta);
-  {
-    auto key = [&](uint32_t i) { return (uint64_t)meta[i].channel * n_leaves + meta[i].leaf; };
-    bool sorted = true;
-    for (uint32_t i = 1; i < n_meta && sorted; ++i) sorted = key(i - 1) < key(i);
-    if (sorted) {
-      for (uint32_t i = 0; i < n_meta; ++i) mi.push_back({meta[i].leaf, meta[i].channel, meta[i].vmin, meta[i].vmax});
-    } else {
-      std::vector<uint32_t> order(n_meta);
-      for (uint32_t i = 0; i < n_meta; ++i) order[i] = i;
-      std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return key(a) < key(b); });
-      for (uint32_t q = 0; q < n_meta; ++q) {
-        const uint32_t i = order[q];
-        if (q + 1 == n_meta || key(order[q + 1]) != key(i))
-          mi.push_back({meta[i].leaf, meta[i].channel, meta[i].vmin, meta[i].vmax});
-      }
-    }
-  }
+  const std::vector<ro::MetaItem> mi = dedup_meta(lm_in, n_leaves);
+  const std::vector<ro::MetaItem> gi = dedup_meta(im_in, g.node_off[g.D]);
   // items: leaf boxes of changed bricks (masks recomputed), then metadata leaves
   std::vector<ro::UpdateItem> brick_items, meta_items;
   std::sort(c->pending.begin(), c->pending.end());
@@ -668,27 +674,48 @@ ro_status ro_update_residency_octree(ro_ctx* c, uint32_t n_meta, const ro_leaf_m
     for (int a = 0; a < 3; ++a) hi[a] = lo[a] + 1;
     push_box(meta_items, m.channel, lo, hi);
   }
+  // an inner node's range: the leaf box of its whole subtree (its ancestors
+  // are recomputed, and its INVALID descendants may now point to it)
+  for (const ro::MetaItem& m : gi) {
+    int d = 0;
+    while (g.node_off[d + 1] <= m.leaf) ++d;
+    const uint64_t j = m.leaf - g.node_off[d];
+    const uint32_t jn[3] = {(uint32_t)(j % g.nn[d][0]), (uint32_t)((j / g.nn[d][0]) % g.nn[d][1]),
+                            (uint32_t)(j / ((uint64_t)g.nn[d][0] * g.nn[d][1]))};
+    uint32_t lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = jn[a] << (g.D - d);
+      hi[a] = std::min<uint32_t>((jn[a] + 1) << (g.D - d), (uint32_t)g.nleaf[a]);
+    }
+    push_box(meta_items, m.channel, lo, hi);
+  }
   cudaStream_t st = c->stream;
   ro::UpdateArgs a{};
   a.g = g;
   a.pt = c->pt;
   a.octree = c->octree;
+  a.given = c->given;
   a.err = c->err;
   ro::UpdateItem* d_items = reinterpret_cast<ro::UpdateItem*>(c->scratch + c->L.sc_items);
   ro::MetaItem* d_meta = reinterpret_cast<ro::MetaItem*>(c->scratch + c->L.sc_meta);
-  // metadata in chunks of max_meta
-  for (size_t q = 0; q < mi.size(); q += c->desc.max_meta) {
-    const uint32_t nm = (uint32_t)std::min<size_t>(c->desc.max_meta, mi.size() - q);
-    RO_TRY(cuda_check(c, cudaMemcpyAsync(d_meta, mi.data() + q, nm * sizeof(ro::MetaItem), cudaMemcpyHostToDevice, st),
-                      "ro_update_residency_octree: meta"));
-    a.meta = d_meta;
-    a.n_meta = nm;
-    RO_TRY(cuda_check(c, ro::launch_write_meta(a, st), "ro_update_residency_octree: write_meta"));
-    // the copy source is pageable host memory: the next chunk may reuse d_meta
-    // only after this launch; stream order guarantees it
+  // range writes in chunks of max_meta: leaves into the node words, inner
+  // nodes into the given ranges
+  for (int kind = 0; kind < 2; ++kind) {
+    const std::vector<ro::MetaItem>& v = kind == 0 ? mi : gi;
+    for (size_t q = 0; q < v.size(); q += c->desc.max_meta) {
+      const uint32_t nm = (uint32_t)std::min<size_t>(c->desc.max_meta, v.size() - q);
+      RO_TRY(cuda_check(c, cudaMemcpyAsync(d_meta, v.data() + q, nm * sizeof(ro::MetaItem), cudaMemcpyHostToDevice, st),
+                        "ro_update_residency_octree: meta"));
+      a.meta = d_meta;
+      a.n_meta = nm;
+      RO_TRY(cuda_check(c, kind == 0 ? ro::launch_write_meta(a, st) : ro::launch_write_given(a, st),
+                        "ro_update_residency_octree: write_meta"));
+      // the copy source is pageable host memory: the next chunk may reuse d_meta
+      // only after this launch; stream order guarantees it
+    }
   }
   a.n_meta = 0;
-  // leaf masks + bottom-up passes, chunk by chunk
+  // leaf masks + bottom-up passes + pointer passes, chunk by chunk
   std::vector<ro::UpdateItem> all(brick_items);
   const size_t n_brick_items = brick_items.size();
   all.insert(all.end(), meta_items.begin(), meta_items.end());
@@ -707,8 +734,57 @@ ro_status ro_update_residency_octree(ro_ctx* c, uint32_t n_meta, const ro_leaf_m
     // d_items is rewritten by the next chunk's copy, which stream order puts
     // after these launches
   }
+  // pointers of INVALID words, after every chunk's ranges are final
+  for (size_t q = 0; q < all.size(); q += kMaxItems) {
+    const uint32_t ni = (uint32_t)std::min<size_t>(kMaxItems, all.size() - q);
+    RO_TRY(cuda_check(c, cudaMemcpyAsync(d_items, all.data() + q, ni * sizeof(ro::UpdateItem), cudaMemcpyHostToDevice, st),
+                      "ro_update_residency_octree: items"));
+    a.items = d_items;
+    a.n_items = ni;
+    for (int d = 1; d <= g.D; ++d) {
+      a.depth = d;
+      RO_TRY(cuda_check(c, ro::launch_pointer_depth(a, st), "ro_update_residency_octree: pointers"));
+    }
+  }
   c->pending.clear();
   return RO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ro_status ro_update_residency_octree(ro_ctx* c, uint32_t n_meta, const ro_leaf_meta* meta) {
+  if (!c) return RO_ERR_INVALID_ARG;
+  if (c->latched != RO_OK) return c->latched;
+  if (n_meta && !meta) return set_err(c, RO_ERR_INVALID_ARG, "ro_update_residency_octree: null meta");
+  const Geometry& g = c->g;
+  const uint64_t n_leaves = (uint64_t)g.nleaf[0] * g.nleaf[1] * g.nleaf[2];
+  std::vector<ro::MetaItem> lm;
+  lm.reserve(n_meta);
+  for (uint32_t i = 0; i < n_meta; ++i) {
+    if (meta[i].leaf >= n_leaves || meta[i].channel >= (uint32_t)g.m)
+      return set_err(c, RO_ERR_INVALID_ARG, "ro_update_residency_octree: leaf or channel out of range");
+    lm.push_back({meta[i].leaf, meta[i].channel, meta[i].vmin, meta[i].vmax});
+  }
+  return run_update(c, lm, {});
+}
+
+ro_status ro_update_node_metadata(ro_ctx* c, uint32_t n_meta, const ro_node_meta* meta) {
+  if (!c) return RO_ERR_INVALID_ARG;
+  if (c->latched != RO_OK) return c->latched;
+  if (n_meta && !meta) return set_err(c, RO_ERR_INVALID_ARG, "ro_update_node_metadata: null meta");
+  const Geometry& g = c->g;
+  std::vector<ro::MetaItem> lm, im;
+  for (uint32_t i = 0; i < n_meta; ++i) {
+    if (meta[i].node >= g.n_nodes || meta[i].channel >= (uint32_t)g.m)
+      return set_err(c, RO_ERR_INVALID_ARG, "ro_update_node_metadata: node or channel out of range");
+    if (meta[i].node >= g.node_off[g.D])
+      lm.push_back({(uint32_t)(meta[i].node - g.node_off[g.D]), meta[i].channel, meta[i].vmin, meta[i].vmax});
+    else
+      im.push_back({meta[i].node, meta[i].channel, meta[i].vmin, meta[i].vmax});
+  }
+  return run_update(c, lm, im);
 }
 
 namespace {
@@ -1048,8 +1124,10 @@ ro_status ro_replace_channel(ro_ctx* c, uint32_t ch) {
   cudaStream_t st = c->stream;
   RO_TRY(cuda_check(c, cudaMemsetAsync(c->pt + first, 0, (last - first) * 4, st), "ro_replace_channel: page tables"));
   RO_TRY(cuda_check(c, cudaMemsetAsync(c->req + first, 0, last - first, st), "ro_replace_channel: requests"));
-  RO_TRY(cuda_check(c, ro::launch_fill_strided(c->octree + ch, g.n_nodes, (uint32_t)g.mp, 0x00FF0000u, st),
+  RO_TRY(cuda_check(c, ro::launch_fill_strided(c->octree + ch, g.n_nodes, (uint32_t)g.mp, ro::kInvalidUnknown, st),
                     "ro_replace_channel: octree"));
+  RO_TRY(cuda_check(c, ro::launch_fill_strided(c->given + ch, g.node_off[g.D], (uint32_t)g.mp, 0u, st),
+                    "ro_replace_channel: given ranges"));
   return RO_OK;
 }
 

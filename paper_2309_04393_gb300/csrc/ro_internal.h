@@ -15,6 +15,8 @@ constexpr int kMaxDepth = 24;   // octree depth bound (2^24 leaves per axis)
 constexpr int kMaxSamples = 1 << 24;  // lattice indices stay exact in binary32
 constexpr int kRenderThreads = 640;   // persistent blocks, one per SM; rays are taken in 8 x 4 pixel tiles
 constexpr int kStats = 8;             // per-block counters of the render kernel
+constexpr int kWalkWin = 4;           // octree depths whose node words the walk loads at once
+constexpr int kTopWords = 10240;      // node words of the octree's top depths kept in shared memory (40 KB)
 
 // Geometry derived once from the descriptor; copied by value into kernels.
 struct Geometry {
@@ -112,10 +114,18 @@ struct MetaItem {
   uint32_t leaf, channel, vmin, vmax;
 };
 
+// INVALID node words: min8 = 255, max8 = the depth of the nearest valid
+// ancestor or kUnknownDepth.  Ranges given for inner nodes are kept apart as
+// kGivenBit | max8 << 8 | min8 (0 = none given).
+constexpr uint32_t kUnknownDepth = 254u;
+constexpr uint32_t kInvalidUnknown = 0xFFu << 16 | kUnknownDepth << 24;
+constexpr uint32_t kGivenBit = 1u << 16;
+
 struct UpdateArgs {
   Geometry g;
   const uint32_t* pt;
   uint32_t* octree;
+  uint32_t* given;           // ranges given for inner nodes, node * mp + channel
   const UpdateItem* items;
   uint32_t n_items;
   const MetaItem* meta;
@@ -183,6 +193,8 @@ cudaError_t launch_scatter(const ScatterArgs& a, cudaStream_t s);
 cudaError_t launch_write_meta(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_leaf_masks(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_reduce_depth(const UpdateArgs& a, cudaStream_t s);
+cudaError_t launch_write_given(const UpdateArgs& a, cudaStream_t s);   // inner-node ranges (meta[].leaf = node)
+cudaError_t launch_pointer_depth(const UpdateArgs& a, cudaStream_t s); // INVALID pointers at a.depth >= 1
 cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
 cudaError_t launch_usage(const UsageArgs& a, cudaStream_t s);
 

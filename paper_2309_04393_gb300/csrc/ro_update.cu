@@ -4,10 +4,12 @@
 // Leaf masks are recomputed from the page table: a leaf (extent a power of
 // two <= B) lies inside exactly one brick of every level, so bit l of a leaf
 // is "the owner brick of level l is resident".  Inner nodes are recomputed as
-// the bitwise OR of their children's masks and the hull of their ranges
-// (INVALID if any child is), depth by depth from the leaves up.  Every write
-// recomputes a word from the final page table / children, so concurrent
-// writers of the same word store the same value: no atomics are needed.
+// the bitwise OR of their children's masks and the hull of their ranges when
+// all children are valid, else the range given for the node, else INVALID,
+// depth by depth from the leaves up; then, from the root down, every INVALID
+// word takes the depth of its nearest valid ancestor (Sec. 5.2).  Every write
+// recomputes a word from the final page table / children / parent, so
+// concurrent writers of the same word store the same value: no atomics.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -103,7 +105,7 @@ __global__ void write_meta_kernel(const __grid_constant__ UpdateArgs a) {
     if (it.leaf >= nl || it.channel >= (uint32_t)g.m) { *a.err = kErrUpdate; continue; }
     uint32_t* p = a.octree + (g.node_off[g.D] + it.leaf) * g.mp + it.channel;
     uint32_t mn8, mx8;
-    if (it.vmin > it.vmax) { mn8 = 255; mx8 = 0; }
+    if (it.vmin > it.vmax) { mn8 = 255; mx8 = kUnknownDepth; }   // the pointer pass fills the depth in
     else { mn8 = quant(it.vmin, g.bpv); mx8 = quant(it.vmax, g.bpv); }
     *p = (*p & 0xFFFFu) | (mn8 << 16) | (mx8 << 24);
   }
@@ -168,8 +170,55 @@ __global__ void __launch_bounds__(256) reduce_depth_kernel(const __grid_constant
           mn = wmn < mn ? wmn : mn;
           mx = wmx > mx ? wmx : mx;
         }
-    if (invalid) { mn = 255; mx = 0; }
-    a.octree[(g.node_off[d] + ((uint64_t)jz * g.nn[d][1] + jy) * g.nn[d][0] + jx) * g.mp + c] = mask | (mn << 16) | (mx << 24);
+    const uint64_t n = g.node_off[d] + ((uint64_t)jz * g.nn[d][1] + jy) * g.nn[d][0] + jx;
+    if (invalid) {
+      const uint32_t gv = a.given[n * g.mp + c];
+      if (gv & kGivenBit) { mn = gv & 0xFFu; mx = (gv >> 8) & 0xFFu; }
+      else { mn = 255; mx = kUnknownDepth; }
+    }
+    a.octree[n * g.mp + c] = mask | (mn << 16) | (mx << 24);
+  }
+}
+
+// Ranges given for inner nodes (meta[].leaf holds the node index).
+__global__ void write_given_kernel(const __grid_constant__ UpdateArgs a) {
+  const Geometry& g = a.g;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_meta; i += gridDim.x * blockDim.x) {
+    const MetaItem it = a.meta[i];
+    if (it.leaf >= g.node_off[g.D] || it.channel >= (uint32_t)g.m) { *a.err = kErrUpdate; continue; }
+    a.given[(uint64_t)it.leaf * g.mp + it.channel] =
+        it.vmin > it.vmax ? 0u : kGivenBit | (quant(it.vmax, g.bpv) << 8) | quant(it.vmin, g.bpv);
+  }
+}
+
+// One block per item: every depth-d node (d >= 1) over the item's leaf box
+// that is INVALID for the item's channel points to its parent if the parent
+// is valid, else to where the parent points.
+__global__ void __launch_bounds__(256) pointer_depth_kernel(const __grid_constant__ UpdateArgs a) {
+  const Geometry& g = a.g;
+  const int d = a.depth;
+  const int sh = g.D - d;
+  const UpdateItem it = a.items[blockIdx.x];
+  uint32_t lo[3], hi[3];
+  for (int q = 0; q < 3; ++q) {
+    lo[q] = it.lo[q] >> sh;
+    hi[q] = ((it.hi[q] - 1) >> sh) + 1;
+    if (hi[q] > (uint32_t)g.nn[d][q]) hi[q] = (uint32_t)g.nn[d][q];
+  }
+  const uint32_t nx = hi[0] - lo[0], ny = hi[1] - lo[1], nz = hi[2] - lo[2];
+  const uint64_t total = (uint64_t)nx * ny * nz;
+  const int c = (int)it.channel;
+  for (uint64_t q = threadIdx.x; q < total; q += blockDim.x) {
+    const uint32_t jx = lo[0] + (uint32_t)(q % nx), jy = lo[1] + (uint32_t)((q / nx) % ny),
+                   jz = lo[2] + (uint32_t)(q / ((uint64_t)nx * ny));
+    uint32_t* p = a.octree + (g.node_off[d] + ((uint64_t)jz * g.nn[d][1] + jy) * g.nn[d][0] + jx) * g.mp + c;
+    const uint32_t w = *p;
+    if (((w >> 16) & 0xFFu) <= (w >> 24)) continue;   // valid
+    const uint32_t pw =
+        a.octree[(g.node_off[d - 1] + ((uint64_t)(jz >> 1) * g.nn[d - 1][1] + (jy >> 1)) * g.nn[d - 1][0] + (jx >> 1)) *
+                     g.mp + c];
+    const uint32_t ptr = ((pw >> 16) & 0xFFu) <= (pw >> 24) ? (uint32_t)(d - 1) : (pw >> 24);
+    *p = (w & 0x00FFFFFFu) | (ptr << 24);
   }
 }
 
@@ -208,6 +257,20 @@ cudaError_t launch_write_meta(const UpdateArgs& a, cudaStream_t s) {
 cudaError_t launch_leaf_masks(const UpdateArgs& a, cudaStream_t s) {
   if (a.n_items == 0) return cudaSuccess;
   leaf_masks_kernel<<<a.n_items, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_write_given(const UpdateArgs& a, cudaStream_t s) {
+  if (a.n_meta == 0) return cudaSuccess;
+  uint32_t blocks = (a.n_meta + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  write_given_kernel<<<blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pointer_depth(const UpdateArgs& a, cudaStream_t s) {
+  if (a.n_items == 0 || a.depth < 1) return cudaSuccess;
+  pointer_depth_kernel<<<a.n_items, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -23,7 +23,9 @@ STATUS = {0: "RO_OK", 1: "RO_ERR_INVALID_ARG", 2: "RO_ERR_CUDA", 3: "RO_ERR_CAPA
           5: "RO_ERR_INTERNAL"}
 EXPORTS = ["ro_query_sizes", "ro_create", "ro_destroy", "ro_upload_bricks", "ro_update_residency_octree", "ro_render",
            "ro_read_requests", "ro_get_stats", "ro_debug_read", "ro_brick_index", "ro_set_timeout", "ro_last_error",
-           "ro_compact_flags_noalloc", "ro_render_batch", "ro_autotune_batch", "ro_replace_channel"]
+           "ro_compact_flags_noalloc", "ro_render_batch", "ro_autotune_batch", "ro_replace_channel",
+           "ro_update_node_metadata"]
+RO_UNKNOWN_DEPTH = 254
 
 
 class RoError(RuntimeError):
@@ -102,6 +104,7 @@ def load(build_if_missing: bool = True):
     L.ro_destroy.argtypes = [vp]
     L.ro_upload_bricks.argtypes = [vp, u32, vp, vp, vp, vp]
     L.ro_update_residency_octree.argtypes = [vp, u32, vp]
+    L.ro_update_node_metadata.argtypes = [vp, u32, vp]
     L.ro_render.argtypes = [vp, ctypes.POINTER(Camera), vp, ctypes.POINTER(RenderParams), vp, u32, u32]
     L.ro_read_requests.argtypes = [vp, vp, u32, vp, vp, vp, u32, vp]
     L.ro_get_stats.argtypes = [vp, vp]
@@ -214,6 +217,12 @@ class Context:
         meta = np.ascontiguousarray(np.asarray(meta, np.uint32).reshape(-1, 4))
         self._check(self.L.ro_update_residency_octree(self.h, meta.shape[0], _ptr(meta)))
 
+    def update_node_metadata(self, meta):
+        """meta: (n, 4) uint32 rows (node, channel, vmin, vmax), nodes numbered
+        as node requests number them (depth-major, leaves last)."""
+        meta = np.ascontiguousarray(np.asarray(meta, np.uint32).reshape(-1, 4))
+        self._check(self.L.ro_update_node_metadata(self.h, meta.shape[0], _ptr(meta) if meta.size else None))
+
     def render(self, camera: Camera, tfs, params: RenderParams, image, W: int, H: int):
         """tfs: list of (lo, scale, lut (256, 4) float32); image: cuda float32 tensor with W*H*4 elements."""
         assert image.is_cuda and image.dtype == self.torch.float32 and image.numel() >= W * H * 4
@@ -291,13 +300,16 @@ class Context:
 
 def compact_flags_noalloc(flags, ids, total, stream=None):
     """ro_compact_flags_noalloc on torch cuda tensors: flags (uint8, length a
-    multiple of 16), ids (int32 capacity), total (int32, one element).  No
-    device memory is allocated by the call."""
+    multiple of 16), ids (int32 capacity), total (int32, one element), all on
+    one device; the call runs with that device current.  No device memory is
+    allocated by the call."""
     import torch
     L = load()
-    st = stream if stream is not None else torch.cuda.current_stream(flags.device)
-    rc = L.ro_compact_flags_noalloc(ctypes.c_void_p(flags.data_ptr()), flags.numel(), ctypes.c_void_p(ids.data_ptr()),
-                                    ids.numel(), ctypes.c_void_p(total.data_ptr()), ctypes.c_void_p(st.cuda_stream))
+    with torch.cuda.device(flags.device):
+        st = stream if stream is not None else torch.cuda.current_stream(flags.device)
+        rc = L.ro_compact_flags_noalloc(ctypes.c_void_p(flags.data_ptr()), flags.numel(),
+                                        ctypes.c_void_p(ids.data_ptr()), ids.numel(),
+                                        ctypes.c_void_p(total.data_ptr()), ctypes.c_void_p(st.cuda_stream))
     if rc != 0:
         raise RoError(rc, "ro_compact_flags_noalloc failed")
 

@@ -44,7 +44,8 @@ def test_replace_channel_then_stream_the_new_one(torch_cuda):
 
     ctx.replace_channel(1)
     words = ctx.octree_words()
-    assert np.all(words[:, 1] == 0x00FF0000) and np.any(words[:, 0] != 0x00FF0000)
+    # the replaced channel: INVALID everywhere with no valid ancestor (UNKNOWN)
+    assert np.all(words[:, 1] == 0xFEFF0000) and np.any(words[:, 0] != 0xFEFF0000)
     pt = ctx.debug_read(1)
     n1 = [ctx.brick_index(ro.brick_id(1, l, x, y, z, 3)) for (c, l, x, y, z) in old.all_bricks() if c == 1]
     assert np.all(pt[n1] == 0)

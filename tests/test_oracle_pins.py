@@ -103,7 +103,7 @@ def brute_words(dims, B, leaf, k, m, resident, lmin, lmax, bpv):
                                 mask |= 1 << l
                         vals = [(lmin[c][lz][ly][lx], lmax[c][lz][ly][lx]) for (lx, ly, lz) in leaves]
                         if any(a < 0 for a, _ in vals):
-                            q0, q1 = 255, 0
+                            q0, q1 = 255, 254      # INVALID, no valid ancestor: UNKNOWN
                         else:
                             a, b = min(v[0] for v in vals), max(v[1] for v in vals)
                             q0, q1 = (a, b) if bpv == 1 else (a >> 8, b >> 8)
