@@ -82,6 +82,18 @@ ro_status ro_mc_gradients(ro_mc* mc, uint32_t n, const float* x0, const float* t
  * gradients of n grids; loss as above (device, may be NULL). */
 ro_status ro_mc_train_step(ro_mc* mc, uint32_t n, const float* x0, const float* target, float lr, float* loss);
 
+/* One Adam step (as ro_mc_train_step) on caller-given gradients (device,
+ * RO_MC_PARAMS floats, the layout of the parameters), e.g. gradients of
+ * several batches or of several data-parallel ranks summed and scaled by
+ * the caller.  Advances the step count that the bias corrections use. */
+ro_status ro_mc_apply_gradients(ro_mc* mc, const float* grads, float lr);
+
+/* Copies the Adam moment estimates (RO_MC_PARAMS floats each: the moving
+ * averages of the gradient and of its square, before bias correction) to
+ * the host and returns the number of Adam steps taken since the last
+ * ro_mc_set_params (step may be NULL).  Waits for the stream. */
+ro_status ro_mc_get_moments(ro_mc* mc, float* host_m, float* host_v, uint32_t* step);
+
 /* Makes n missing level-0 bricks resident with predicted data (the
  * substitution of Sec. 6.1 refined by the compensator): for each ID the
  * level-1 parent must be resident; its cache slot is upsampled to the

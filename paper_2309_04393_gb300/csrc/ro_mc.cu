@@ -744,11 +744,13 @@ __global__ void refresh_kernel(const float* __restrict__ P, float* __restrict__ 
 // eps_t by the host).
 __global__ void adam_kernel(float* __restrict__ P, float* __restrict__ M, float* __restrict__ V,
                             const float* __restrict__ G, float lr_t, float eps_t) {
-  const float b1 = 0.9f, b2 = 0.999f;
+  // each constant the binary32 value nearest to its decimal (1 - 0.999f
+  // would be 1.3e-5 away from 0.001)
+  const float b1 = 0.9f, b2 = 0.999f, c1 = 0.1f, c2 = 0.001f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < RO_MC_PARAMS; i += gridDim.x * blockDim.x) {
     const float g = G[i];
-    const float m = fmaf(b1, M[i], (1.0f - b1) * g);
-    const float v = fmaf(b2, V[i], (1.0f - b2) * g * g);
+    const float m = fmaf(b1, M[i], c1 * g);
+    const float v = fmaf(b2, V[i], c2 * g * g);
     M[i] = m;
     V[i] = v;
     P[i] -= lr_t * m / (sqrtf(v) + eps_t);
@@ -963,18 +965,43 @@ ro_status ro_mc_gradients(ro_mc* m, uint32_t n, const float* x0, const float* ta
   return mc_err(mc_backward(m, n, x0, target, grads, loss));
 }
 
+namespace {
+
+// Adam step m->step + 1 on the gradients G (device), then the refreshed
+// bfloat16 copies.  The bias corrections of Kingma and Ba's Algorithm 1 are
+// folded into the step size and epsilon: lr_t = lr sqrt(1 - b2^t) / (1 -
+// b1^t), eps_t = eps sqrt(1 - b2^t) (their Sec. 2), so that
+// lr_t m / (sqrt(v) + eps_t) = lr m_hat / (sqrt(v_hat) + eps).
+cudaError_t mc_adam(ro_mc* m, const float* G, float lr) {
+  ++m->step;
+  const double c1 = 1.0 - std::pow(0.9, (double)m->step), c2 = 1.0 - std::pow(0.999, (double)m->step);
+  const float lr_t = (float)(lr * std::sqrt(c2) / c1), eps_t = (float)(1e-8 * std::sqrt(c2));
+  adam_kernel<<<64, 256, 0, m->stream>>>(m->P, m->M, m->V, G, lr_t, eps_t);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = mc_refresh(m);
+  return e;
+}
+
+}  // namespace
+
 ro_status ro_mc_train_step(ro_mc* m, uint32_t n, const float* x0, const float* target, float lr, float* loss) {
   if (!m || !x0 || !target || n < 1 || n > m->desc.max_batch || !(lr > 0.0f)) return RO_ERR_INVALID_ARG;
   cudaError_t e = mc_backward(m, n, x0, target, m->G, loss);
-  ++m->step;
-  // Adam bias corrections: lr_t = lr * sqrt(1 - b2^t) / (1 - b1^t), eps scaled alike
-  const double c1 = 1.0 - std::pow(0.9, (double)m->step), c2 = 1.0 - std::pow(0.999, (double)m->step);
-  const float lr_t = (float)(lr * std::sqrt(c2) / c1), eps_t = (float)(1e-8 * std::sqrt(c2));
-  if (e == cudaSuccess) {
-    adam_kernel<<<64, 256, 0, m->stream>>>(m->P, m->M, m->V, m->G, lr_t, eps_t);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = mc_refresh(m);
+  if (e == cudaSuccess) e = mc_adam(m, m->G, lr);
+  return mc_err(e);
+}
+
+ro_status ro_mc_apply_gradients(ro_mc* m, const float* grads, float lr) {
+  if (!m || !grads || !(lr > 0.0f)) return RO_ERR_INVALID_ARG;
+  return mc_err(mc_adam(m, grads, lr));
+}
+
+ro_status ro_mc_get_moments(ro_mc* m, float* host_m, float* host_v, uint32_t* step) {
+  if (!m || !host_m || !host_v) return RO_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpyAsync(host_m, m->M, (size_t)RO_MC_PARAMS * 4, cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_v, m->V, (size_t)RO_MC_PARAMS * 4, cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (step) *step = m->step;
   return mc_err(e);
 }
 

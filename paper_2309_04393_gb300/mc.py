@@ -20,7 +20,8 @@ LAYERS = ((1, 32), (32, 32), (32, 32), (32, 1))
 
 # every entry point include/ro_mc.h declares
 EXPORTS = ["ro_mc_query_bytes", "ro_mc_create", "ro_mc_destroy", "ro_mc_set_params", "ro_mc_get_params",
-           "ro_mc_upsample", "ro_mc_forward", "ro_mc_gradients", "ro_mc_train_step", "ro_compensate_bricks"]
+           "ro_mc_upsample", "ro_mc_forward", "ro_mc_gradients", "ro_mc_train_step", "ro_mc_apply_gradients",
+           "ro_mc_get_moments", "ro_compensate_bricks"]
 
 
 class McDesc(ctypes.Structure):
@@ -40,6 +41,8 @@ def _lib():
         L.ro_mc_forward.argtypes = [vp, u32, vp, vp]
         L.ro_mc_gradients.argtypes = [vp, u32, vp, vp, vp, vp]
         L.ro_mc_train_step.argtypes = [vp, u32, vp, vp, ctypes.c_float, vp]
+        L.ro_mc_apply_gradients.argtypes = [vp, vp, ctypes.c_float]
+        L.ro_mc_get_moments.argtypes = [vp, vp, vp, ctypes.POINTER(u32)]
         L.ro_compensate_bricks.argtypes = [vp, vp, u32, vp, vp]
         for f in EXPORTS:
             getattr(L, f).restype = ctypes.c_int
@@ -149,6 +152,18 @@ class Compensator:
         ptr = ctypes.c_void_p(loss.data_ptr()) if loss is not None else None
         self._check(self.L.ro_mc_train_step(self.h, x0.shape[0], ctypes.c_void_p(x0.data_ptr()),
                                             ctypes.c_void_p(target.data_ptr()), ctypes.c_float(lr), ptr))
+
+    def apply_gradients(self, grads, lr):
+        """One Adam step on given gradients (cuda float32 tensor of PARAMS)."""
+        assert grads.numel() == PARAMS and grads.dtype == self.torch.float32 and grads.is_contiguous()
+        self._check(self.L.ro_mc_apply_gradients(self.h, ctypes.c_void_p(grads.data_ptr()), ctypes.c_float(lr)))
+
+    def get_moments(self):
+        """(m, v, step): the Adam moment estimates and the step count."""
+        m, v, step = np.zeros(PARAMS, np.float32), np.zeros(PARAMS, np.float32), ctypes.c_uint32()
+        self._check(self.L.ro_mc_get_moments(self.h, m.ctypes.data_as(ctypes.c_void_p),
+                                             v.ctypes.data_as(ctypes.c_void_p), ctypes.byref(step)))
+        return m, v, int(step.value)
 
 
 def compensate_bricks(ctx, comp: Compensator, ids) -> np.ndarray:

@@ -87,3 +87,5 @@ def test_compensator_header_exports_and_host_checks_without_gpu():
                           ctypes.byref(h)) == 3                                         # RO_ERR_CAPACITY
     assert h.value is None
     assert L.ro_mc_destroy(None) == 1
+    assert L.ro_mc_apply_gradients(None, ctypes.c_void_p(16), ctypes.c_float(1e-3)) == 1
+    assert L.ro_mc_get_moments(None, ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 1
