@@ -189,24 +189,35 @@ __device__ __forceinline__ void tri_coords(const Geometry& g, int l, const float
   }
 }
 
+// The eight corners of a trilinear footprint as raw integers (u8 / u16
+// values, or the 16-bit patterns of the binary16 / bfloat16 formats), loaded
+// apart from their use so that several channels' corners are in flight at
+// once.  base + idx must address a voxel whose 2x2x2 block lies in its slot.
 template <int BPV, int EC, int SF>
-__device__ __forceinline__ float tri_fetch(const RenderArgs& a, uint32_t slot, const TriCoords& tc) {
-  const Geometry& g = a.g;
+__device__ __forceinline__ void tri_load(const Geometry& g, const uint8_t* base, int idx, uint32_t (&r)[8]) {
   const int E = EC ? EC : (int)g.edge;
-  const uint8_t* base = a.cache + (size_t)slot * g.slot_pitch;
-  const int idx = tc.idx;
+  if constexpr (BPV == 1 && SF == 0) {
+    const uint8_t* p = base + idx;
+    r[0] = __ldg(p); r[1] = __ldg(p + 1); r[2] = __ldg(p + E); r[3] = __ldg(p + E + 1);
+    r[4] = __ldg(p + E * E); r[5] = __ldg(p + E * E + 1); r[6] = __ldg(p + E * E + E); r[7] = __ldg(p + E * E + E + 1);
+  } else {
+    const uint16_t* p = reinterpret_cast<const uint16_t*>(base) + idx;
+    r[0] = __ldg(p); r[1] = __ldg(p + 1); r[2] = __ldg(p + E); r[3] = __ldg(p + E + 1);
+    r[4] = __ldg(p + E * E); r[5] = __ldg(p + E * E + 1); r[6] = __ldg(p + E * E + E); r[7] = __ldg(p + E * E + E + 1);
+  }
+}
+
+// Lerps along x, then y, then z (each fma(f, b - a, a)) of loaded corners.
+template <int BPV, int SF>
+__device__ __forceinline__ float tri_lerp(const uint32_t (&r)[8], const TriCoords& tc) {
   if constexpr (SF != 0) {
     // the slot holds the format's values; x lerps on the pairs (v0, v2) /
     // (v1, v3) and (v4, v6) / (v5, v7), the y lerp on (c00, c01) / (c10,
     // c11), the z lerp alone: each d = b - a, then fma(f, d, a), one
     // rounding per operation as in the format's arithmetic
     using F = Fmt<SF>;
-    const uint16_t* p = reinterpret_cast<const uint16_t*>(base) + idx;
-    const uint32_t r0 = __ldg(p), r1 = __ldg(p + 1), r2 = __ldg(p + E), r3 = __ldg(p + E + 1);
-    const uint32_t r4 = __ldg(p + E * E), r5 = __ldg(p + E * E + 1), r6 = __ldg(p + E * E + E),
-                   r7 = __ldg(p + E * E + E + 1);
-    const typename F::T2 A = F::v2(pack2(r0, r2)), B = F::v2(pack2(r1, r3));
-    const typename F::T2 A2 = F::v2(pack2(r4, r6)), B2 = F::v2(pack2(r5, r7));
+    const typename F::T2 A = F::v2(pack2(r[0], r[2])), B = F::v2(pack2(r[1], r[3]));
+    const typename F::T2 A2 = F::v2(pack2(r[4], r[6])), B2 = F::v2(pack2(r[5], r[7]));
     const typename F::T2 f0 = F::v2(tc.h[0]), f1 = F::v2(tc.h[1]);
     const typename F::T2 cx0 = __hfma2(f0, __hsub2(B, A), A);      // (c00, c10)
     const typename F::T2 cx1 = __hfma2(f0, __hsub2(B2, A2), A2);   // (c01, c11)
@@ -219,27 +230,8 @@ __device__ __forceinline__ float tri_fetch(const RenderArgs& a, uint32_t slot, c
     return F::to_float(c) * (BPV == 1 ? 256.0f : 65536.0f);
   } else {
     float v[8];
-    if constexpr (BPV == 1) {
-      const uint8_t* p = base + idx;
-      v[0] = (float)__ldg(p);
-      v[1] = (float)__ldg(p + 1);
-      v[2] = (float)__ldg(p + E);
-      v[3] = (float)__ldg(p + E + 1);
-      v[4] = (float)__ldg(p + E * E);
-      v[5] = (float)__ldg(p + E * E + 1);
-      v[6] = (float)__ldg(p + E * E + E);
-      v[7] = (float)__ldg(p + E * E + E + 1);
-    } else {
-      const uint16_t* p = reinterpret_cast<const uint16_t*>(base) + idx;
-      v[0] = (float)__ldg(p);
-      v[1] = (float)__ldg(p + 1);
-      v[2] = (float)__ldg(p + E);
-      v[3] = (float)__ldg(p + E + 1);
-      v[4] = (float)__ldg(p + E * E);
-      v[5] = (float)__ldg(p + E * E + 1);
-      v[6] = (float)__ldg(p + E * E + E);
-      v[7] = (float)__ldg(p + E * E + E + 1);
-    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = (float)r[q];
     const float c00 = fmaf(tc.f[0], v[1] - v[0], v[0]);
     const float c10 = fmaf(tc.f[0], v[3] - v[2], v[2]);
     const float c01 = fmaf(tc.f[0], v[5] - v[4], v[4]);
@@ -349,6 +341,19 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
     else s_tf[q] = make_float2(a.tf_lo[q], a.tf_scale[q]);
   }
   for (int q = threadIdx.x; q <= m * k; q += blockDim.x) s_pto[q] = g.pt_off[q];
+  // per-depth node tables and per-level brick counts (indexed per lane)
+  __shared__ unsigned long long s_noff[kMaxDepth + 2];
+  __shared__ int s_nn[kMaxDepth + 1][3];
+  __shared__ int s_nb[kMaxL][3];
+  for (int q = threadIdx.x; q <= g.D + 1; q += blockDim.x) s_noff[q] = g.node_off[q];
+  for (int q = threadIdx.x; q < 3 * (g.D + 1); q += blockDim.x) s_nn[q / 3][q % 3] = g.nn[q / 3][q % 3];
+  for (int q = threadIdx.x; q < 3 * k; q += blockDim.x) s_nb[q / 3][q % 3] = g.nb[q / 3][q % 3];
+  // the octree's top depths (those whose words fit kTopWords) in shared memory
+  uint32_t* s_top = s_sel + MP * kRenderThreads;
+  int top_d = -1;
+  while (top_d < g.D && g.node_off[top_d + 2] * MP <= (uint64_t)kTopWords) ++top_d;
+  const uint32_t n_top = top_d >= 0 ? (uint32_t)(g.node_off[top_d + 1] * MP) : 0u;
+  for (uint32_t q = threadIdx.x; q < n_top; q += blockDim.x) s_top[q] = __ldg(a.octree + q);
   __shared__ unsigned long long s_red[kRenderThreads / 32][kStats];
   for (int q = threadIdx.x; q < kRenderThreads / 32 * kStats; q += blockDim.x) (&s_red[0][0])[q] = 0;
   // batch: first tile of every view (view v owns [s_base[v], s_base[v + 1]))
@@ -520,71 +525,143 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
       const bool ssame = __shfl_sync(FULL, (int)same_node, src) != 0;
       const bool cact = gact && ch < m;
       const int ld = cact ? (int)((sldp >> (4 * ch)) & 15) : 0;
+      const uint16_t* pre = s_pre + ch * 257;
 
-      int d = sds;
-      bool gdone = !gact, bad = false;
-      int jn0 = 0, jn1 = 0, jn2 = 0;
-      uint64_t node = 0;
-      uint32_t w = 0;
+      // the walk (Sec. 6.1), kWalkWin depths at a time: every node word of
+      // the window is loaded before any is classified.  A channel's terminal
+      // states are inherited by the node's children, so the group's final
+      // depth is the first at which all its channels are terminal, or the
+      // traversal depth, or the start depth when the cached node still holds.
+      int dfin = -1;                 // final depth of this lane's group
+      bool bad = false;
+      uint32_t w = 0;                // this lane's channel word at the final depth
+      uint32_t rw = 0;               // the same, an INVALID word read through its pointer
       int sc = kEmpty;
-      for (;;) {
-        if (!gdone) {
-          const int sh = g.D - d;
-          jn0 = sL0 >> sh; jn1 = sL1 >> sh; jn2 = sL2 >> sh;
-          node = g.node_off[d] + ((uint64_t)jn2 * g.nn[d][1] + jn1) * g.nn[d][0] + jn0;
-          if (node >= g.node_off[d + 1]) {
-            bad = true;
-          } else if (cact) {
-            w = __ldg(a.octree + node * MP + ch);
-            sc = classify<BPV>(w, s_pre + ch * 257, ld, k);
+      for (int d0 = sds;; d0 += kWalkWin) {
+        uint32_t wv[kWalkWin];
+        unsigned tm = 0, stop = 0, badm = 0;
+#pragma unroll
+        for (int q = 0; q < kWalkWin; ++q) {
+          const int dd = d0 + q;
+          wv[q] = 0u;
+          if (gact && dfin < 0 && dd <= sst) {
+            const int sh = g.D - dd;
+            const uint64_t node = s_noff[dd] + ((uint64_t)(sL2 >> sh) * s_nn[dd][1] + (sL1 >> sh)) * s_nn[dd][0] + (sL0 >> sh);
+            if (node >= s_noff[dd + 1]) badm |= 1u << q;
+            else if (cact) wv[q] = dd <= top_d ? s_top[node * MP + ch] : __ldg(a.octree + node * MP + ch);
           }
         }
-        const unsigned term = __ballot_sync(FULL, gdone || !cact || bad || terminal(sc));
-        if (!gdone && ((term & gmask) == gmask || d == sst || ssame || bad)) gdone = true;
-        if (__all_sync(FULL, gdone)) break;
-        if (!gdone) ++d;
+        // an INVALID word whose channel has a valid ancestor is read with the
+        // ancestor's range and its own mask (Sec. 5.2: the pointer to the node
+        // of the next lower subdivision level with valid information)
+        uint32_t rv[kWalkWin];
+#pragma unroll
+        for (int q = 0; q < kWalkWin; ++q) {
+          const uint32_t wq = wv[q], pd = wq >> 24;
+          rv[q] = wq;
+          if (cact && ((wq >> 16) & 0xFFu) > pd && (int)pd < d0 + q) {
+            const int sh = g.D - (int)pd;
+            const uint64_t an = s_noff[pd] + ((uint64_t)(sL2 >> sh) * s_nn[pd][1] + (sL1 >> sh)) * s_nn[pd][0] + (sL0 >> sh);
+            const uint32_t aw = (int)pd <= top_d ? s_top[an * MP + ch] : __ldg(a.octree + an * MP + ch);
+            rv[q] = (wq & 0xFFFFu) | (aw & 0xFFFF0000u);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kWalkWin; ++q) {
+          const int dd = d0 + q;
+          if (!cact || terminal(classify<BPV>(rv[q], pre, ld, k))) tm |= 1u << q;
+          if (dd >= sst || dd >= g.D || (ssame && dd == sds)) stop |= 1u << q;
+        }
+        stop |= badm;
+#pragma unroll
+        for (int o = 1; o < MP; o <<= 1) {
+          tm &= __shfl_xor_sync(FULL, tm, o);
+          stop |= __shfl_xor_sync(FULL, stop, o);
+        }
+        const unsigned fin = (tm | stop) & ((1u << kWalkWin) - 1u);
+        if (gact && dfin < 0 && fin) {
+          const int q = __ffs(fin) - 1;
+          dfin = d0 + q;
+          bad = (badm & ((2u << q) - 1u)) != 0;
+#pragma unroll
+          for (int qq = 0; qq < kWalkWin; ++qq)
+            if (qq == q) { w = wv[qq]; rw = rv[qq]; }
+          if (cact) sc = classify<BPV>(rw, pre, ld, k);
+        }
+        if (__all_sync(FULL, !gact || dfin >= 0)) break;
       }
+      const int d = dfin < 0 ? 0 : dfin;
+      const int fsh = g.D - d;
+      const int jn0 = sL0 >> fsh, jn1 = sL1 >> fsh, jn2 = sL2 >> fsh;
+      const uint64_t node = s_noff[d] + ((uint64_t)jn2 * s_nn[d][1] + jn1) * s_nn[d][0] + jn0;
       const bool gbad = (__ballot_sync(FULL, bad) & gmask) != 0;
+      // page-table index of this lane's channel at level l (owner brick of the sample)
+      auto pt_index = [&](int l) -> uint64_t {
+        const int bsh = g.blog2 + l;
+        const int bx = (int)(sx0 * pow2f(-bsh)), by = (int)(sx1 * pow2f(-bsh)), bz = (int)(sx2 * pow2f(-bsh));
+        return s_pto[ch * k + l] + ((uint64_t)bz * s_nb[l][1] + by) * s_nb[l][0] + bx;
+      };
 
-      // requests of channels with nothing usable here, node requests of
-      // INVALID channels
+      // requests of channels with nothing usable here; node requests of
+      // channels whose own metadata is missing here (reportNodeRequest),
+      // unless the ancestor's range shows the node empty or homogeneous
       if (cact && !gbad) {
         const bool no_use = ((w & 0xFFFFu) & (~0u << ld) & ((1u << k) - 1u)) == 0;
         if (sc == kUnmapped || (sc == kInvalid && no_use)) {
-          const int bsh = g.blog2 + ld;
-          const int bx = (int)(sx0 * pow2f(-bsh)), by = (int)(sx1 * pow2f(-bsh)), bz = (int)(sx2 * pow2f(-bsh));
-          const uint64_t pi = s_pto[ch * k + ld] + ((uint64_t)bz * g.nb[ld][1] + by) * g.nb[ld][0] + bx;
+          const uint64_t pi = pt_index(ld);
           if (pi >= g.n_bricks) *a.err = kErrPageIndex;
           else a.req[pi] = 1;
         }
-        if (sc == kInvalid) a.node_req[node * m + ch] = 1;
+        const bool missing = ((w >> 16) & 0xFFu) > (w >> 24);
+        if (missing && sc != kEmpty && sc != kHomog) a.node_req[node * m + ch] = 1;
       }
       const unsigned nonskip = __ballot_sync(FULL, cact && sc != kEmpty && sc != kUnmapped);
       const bool all_skip = (nonskip & gmask) == 0;
 
-      // brick selection (Algorithm 1): desired level, else request it and take the
-      // next coarser resident level
+      // brick selection (Algorithm 1): the desired level, else request it and
+      // take the next coarser resident level.  The page-table entries of the
+      // first two levels the node is partially mapped in are fetched together.
       uint32_t sel = kSelNone;
       int found = 99;
       if (cact && !gbad && !all_skip && sc != kEmpty && sc != kUnmapped) {
         if (sc == kHomog) {
-          sel = (kSelHomog << 27) | ((w >> 16) & 0xFFu);
-        } else if (((w & 0xFFFFu) & (~0u << ld) & ((1u << k) - 1u)) != 0) {
-          for (int l = ld; l < k; ++l) {
-            const int bsh = g.blog2 + l;
-            const int bx = (int)(sx0 * pow2f(-bsh)), by = (int)(sx1 * pow2f(-bsh)), bz = (int)(sx2 * pow2f(-bsh));
-            const uint64_t pi = s_pto[ch * k + l] + ((uint64_t)bz * g.nb[l][1] + by) * g.nb[l][0] + bx;
-            if (pi >= g.n_bricks) { *a.err = kErrPageIndex; break; }
-            uint32_t e = 0;
-            if ((w >> l) & 1u) e = __ldg(a.pt + pi);
-            if (e != 0) {
-              if (e - 1 >= g.cache_slots) { *a.err = kErrSlot; break; }
-              sel = ((uint32_t)l << 27) | (e - 1);
-              a.used[e - 1] = 1;
-              found = l;
-              break;
+          sel = (kSelHomog << 27) | ((rw >> 16) & 0xFFu);
+        } else {
+          uint32_t cand = (w & 0xFFFFu) & (~0u << ld) & ((1u << k) - 1u);
+          if (cand) {
+            const int l1 = __ffs(cand) - 1;
+            cand &= cand - 1u;
+            const int l2 = cand ? __ffs(cand) - 1 : l1;
+            if (cand) cand &= cand - 1u;
+            const uint64_t p1 = pt_index(l1), p2 = pt_index(l2);
+            if (p1 >= g.n_bricks || p2 >= g.n_bricks) {
+              *a.err = kErrPageIndex;
+            } else {
+              const uint32_t e1 = __ldg(a.pt + p1), e2 = l2 != l1 ? __ldg(a.pt + p2) : 0u;
+              if (l1 != ld || e1 == 0) {             // the desired brick is absent
+                const uint64_t pd = l1 == ld ? p1 : pt_index(ld);
+                if (pd >= g.n_bricks) *a.err = kErrPageIndex;
+                else a.req[pd] = 1;
+              }
+              uint32_t e = e1 ? e1 : e2;
+              int lf = e1 ? l1 : l2;
+              while (e == 0 && cand) {               // further coarser levels, one at a time
+                lf = __ffs(cand) - 1;
+                cand &= cand - 1u;
+                const uint64_t pl = pt_index(lf);
+                if (pl >= g.n_bricks) { *a.err = kErrPageIndex; break; }
+                e = __ldg(a.pt + pl);
+              }
+              if (e != 0) {
+                if (e - 1 >= g.cache_slots) {
+                  *a.err = kErrSlot;
+                } else {
+                  sel = ((uint32_t)lf << 27) | (e - 1);
+                  a.used[e - 1] = 1;
+                  found = lf;
+                }
+              }
             }
-            if (l == ld) a.req[pi] = 1;
           }
         }
       }
@@ -677,36 +754,11 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
     cnt.bs += nc.n_brick;
     cnt.homog += __popc(nc.act) - nc.n_brick;
     n_bs += nc.n_brick;
-    int tl = -1;
-    TriCoords tc;
-    for (uint32_t mm = nc.act; mm; mm &= mm - 1u) {
-      const int c = __ffs(mm) - 1;
-      const uint32_t sel = my_sel[c * stride];
-      const uint32_t lb = sel >> 27;
-      float val;
-      if (lb == kSelHomog) {
-        val = (float)(sel & kSelMask);
-        if constexpr (DBG) {
-          h = fnv_word(h, (uint32_t)i); h = fnv_word(h, (uint32_t)c);
-          h = fnv_word(h, 0xFFu); h = fnv_word(h, 0xFFFFFFFFu);
-        }
-      } else {
-        if ((int)lb != tl) {  // channels at one level share the corner offset and weights
-          tl = (int)lb;
-          tri_coords<EC, SF>(g, tl, x, tc);
-        }
-        val = tri_fetch<BPV, EC, SF>(a, sel & kSelMask, tc);
-        if constexpr (DBG) {
-          const int bsh = g.blog2 + (int)lb;
-          const uint32_t bx = (uint32_t)(x[0] * pow2f(-bsh)), by = (uint32_t)(x[1] * pow2f(-bsh)),
-                         bz = (uint32_t)(x[2] * pow2f(-bsh));
-          h = fnv_word(h, (uint32_t)i); h = fnv_word(h, (uint32_t)c); h = fnv_word(h, lb);
-          h = fnv_word(h, ((uint32_t)(c * k + (int)lb) << 24) | (bz << 16) | (by << 8) | bx);
-        }
-      }
+    // per channel: TF, opacity correction, additive colour (channel order)
+    auto add = [&](int c, float val) {
       // a value at or below the window start maps to knot 0; with a
       // transparent knot 0 the channel adds exactly nothing (a' = 0, q = 1)
-      if (!((val - s_tf[c].x) * s_tf[c].y > 0.0f) && s_lut[c * 256].w <= 0.0f) continue;
+      if (!((val - s_tf[c].x) * s_tf[c].y > 0.0f) && s_lut[c * 256].w <= 0.0f) return;
       float q, cr, cg, cb;
       shade(s_lut + c * 256, s_tf[c], val, s, q, cr, cg, cb);
       const float ap = 1.0f - q;
@@ -714,6 +766,56 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
       col1 = fmaf(ap, cg, col1);
       col2 = fmaf(ap, cb, col2);
       trans = trans * q;
+    };
+    auto hash_sel = [&](int c, uint32_t sel) {
+      if constexpr (DBG) {
+        const uint32_t lb = sel >> 27;
+        h = fnv_word(h, (uint32_t)i);
+        h = fnv_word(h, (uint32_t)c);
+        if (lb == kSelHomog) {
+          h = fnv_word(h, 0xFFu);
+          h = fnv_word(h, 0xFFFFFFFFu);
+        } else {
+          const int bsh = g.blog2 + (int)lb;
+          const uint32_t bx = (uint32_t)(x[0] * pow2f(-bsh)), by = (uint32_t)(x[1] * pow2f(-bsh)),
+                         bz = (uint32_t)(x[2] * pow2f(-bsh));
+          h = fnv_word(h, lb);
+          h = fnv_word(h, ((uint32_t)(c * k + (int)lb) << 24) | (bz << 16) | (by << 8) | bx);
+        }
+      }
+    };
+    // two channels per step: both channels' corners are loaded before
+    // either is interpolated (a homogeneous channel loads a dummy footprint
+    // at the start of slot 0 and takes the node's value)
+    int tl = -1;
+    TriCoords tc, tcb;
+    uint32_t mm = nc.act;
+    while (mm) {
+      const int ca = __ffs(mm) - 1;
+      mm &= mm - 1u;
+      const bool two = mm != 0;
+      const int cb = two ? __ffs(mm) - 1 : ca;
+      if (two) mm &= mm - 1u;
+      const uint32_t sa = my_sel[ca * stride], sb = two ? my_sel[cb * stride] : sa;
+      const uint32_t la = sa >> 27, lb = sb >> 27;
+      const bool ha = BPV == 1 && la == kSelHomog, hb = BPV == 1 && lb == kSelHomog;
+      if (!ha && (int)la != tl) {  // channels at one level share the corner offset and weights
+        tl = (int)la;
+        tri_coords<EC, SF>(g, tl, x, tc);
+      }
+      if (!hb && lb != la) tri_coords<EC, SF>(g, (int)lb, x, tcb);
+      else tcb = tc;
+      uint32_t ra[8], rb[8];
+      tri_load<BPV, EC, SF>(g, a.cache + (ha ? 0 : (size_t)(sa & kSelMask) * g.slot_pitch), ha ? 0 : tc.idx, ra);
+      tri_load<BPV, EC, SF>(g, a.cache + (hb ? 0 : (size_t)(sb & kSelMask) * g.slot_pitch), hb ? 0 : tcb.idx, rb);
+      const float va = ha ? (float)(sa & kSelMask) : tri_lerp<BPV, SF>(ra, tc);
+      hash_sel(ca, sa);
+      add(ca, va);
+      if (two) {
+        const float vb = hb ? (float)(sb & kSelMask) : tri_lerp<BPV, SF>(rb, tcb);
+        hash_sel(cb, sb);
+        add(cb, vb);
+      }
     }
     C0 = fmaf(T, col0, C0);
     C1 = fmaf(T, col1, C1);
