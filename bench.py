@@ -282,7 +282,11 @@ def oracle_rate(scene, frame, seconds, seed=0, words=None, vol=None):
     def tile(side):
         side = int(max(8, min(side, frame.W, frame.H)))
         x0 = int(rng.integers(0, frame.W - side + 1))
-        y0 = int(rng.integers(frame.H // 4, max(frame.H // 4 + 1, frame.H - frame.H // 4 - side + 1)))
+        # rows from the middle half of the image where the tile fits there,
+        # else any rows that keep the whole tile inside the image
+        ylo = min(frame.H // 4, frame.H - side)
+        yhi = max(ylo, frame.H - frame.H // 4 - side)
+        y0 = int(rng.integers(ylo, yhi + 1))
         yy, xx = np.meshgrid(np.arange(y0, y0 + side), np.arange(x0, x0 + side), indexing="ij")
         return np.stack([xx.ravel(), yy.ravel()], 1), side
 

@@ -69,3 +69,30 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     rc = L.ro_compact_flags_noalloc(ctypes.c_void_p(flags.data_ptr()), 15, None, 0,
                                     ctypes.c_void_p(total.data_ptr()), stream)
     assert rc == 1  # RO_ERR_INVALID_ARG: not a multiple of 16
+
+
+@pytest.mark.parametrize("n,cap", [(4096 * 3 + 16 * 37, 100), (16 * 5, 3), (4096 * 70 + 48, 0)])
+def test_noalloc_ragged_counts_and_truncation(n, cap):
+    """Flag counts that are not a multiple of the 4096-flag tile, and an
+    output capacity below the number of set flags: the ids are the first
+    `cap` set indices in ascending order, total counts them all, and every
+    flag is cleared; two calls in a row reuse the static scratch."""
+    import torch
+    from paper_2309_04393_gb300 import ro
+    rng = np.random.default_rng(n)
+    for rep in range(2):
+        density = 0.02 * (rep + 1) if n > 1000 else 0.4 + 0.2 * rep
+        host = (rng.random(n) < density).astype(np.uint8) * rng.integers(1, 256, n).astype(np.uint8)
+        flags = torch.from_numpy(host).to("cuda")
+        ids = torch.full((max(cap, 1),), -1, dtype=torch.int32, device="cuda")
+        total = torch.zeros(1, dtype=torch.int32, device="cuda")
+        ro.compact_flags_noalloc(flags, ids[:cap] if cap else ids[:0], total)
+        torch.cuda.synchronize()
+        want = np.nonzero(host)[0]
+        assert want.size > cap
+        assert int(total.item()) == want.size
+        got = ids.cpu().numpy()
+        assert np.array_equal(got[:cap], want[:cap].astype(np.int32))
+        if cap == 0:
+            assert got[0] == -1
+        assert int(flags.sum().item()) == 0
