@@ -76,6 +76,16 @@ typedef enum {
  *                rounding per step and the result times 2^bits continues in
  *                binary32 (TF, opacity correction and compositing stay
  *                binary32)
+ *  keep_axes     downsampling between levels (Sec. 8: anisotropic volumes
+ *                and downsampling ratios, e.g. in two dimensions only): bit a
+ *                of keep_axes[l] set = axis a (x, y, z) keeps its resolution
+ *                from level l to level l + 1; clear = halved (ceil(d / 2)).
+ *                All zero (the default) halves every axis at every level.
+ *                Bits above 2 and entries l >= levels - 1 must be zero.
+ *                The sampling step after a sample read at level l grows by
+ *                2^s, s the largest exponent with 2^s * min(spacing) <= the
+ *                smallest physical extent of a level-l voxel (s = l when
+ *                every axis is halved).
  * Bricks per axis at every level must be <= 256 (the 8-bit offsets of the
  * brick ID, Sec. 7). */
 typedef struct {
@@ -92,6 +102,7 @@ typedef struct {
   uint32_t max_meta;
   uint32_t max_batch_tiles;
   uint32_t sample_format;
+  uint32_t keep_axes[16];
 } ro_desc;
 
 /* Byte sizes of the parts of the device arena (all 256-byte aligned inside

@@ -39,7 +39,8 @@ class _Volume(ctypes.Structure):
                 ("leaf", ctypes.c_int32 * 3), ("levels", ctypes.POINTER(ctypes.c_void_p)),
                 ("resident", ctypes.c_void_p), ("leaf_min", ctypes.c_void_p), ("leaf_max", ctypes.c_void_p),
                 ("voxel_fn", ctypes.c_void_p), ("voxel_ctx", ctypes.c_void_p), ("sample_format", ctypes.c_int32),
-                ("node_min", ctypes.c_void_p), ("node_max", ctypes.c_void_p)]
+                ("node_min", ctypes.c_void_p), ("node_max", ctypes.c_void_p),
+                ("keep_axes", ctypes.c_int32 * MAXL)]
 
 
 class _Params(ctypes.Structure):
@@ -123,6 +124,8 @@ class Volume:
     leaf_min / leaf_max: arrays (m, lz, ly, lx) int64, -1 = no metadata.
     node_min / node_max: ranges given for inner nodes, arrays (m, n_nodes)
     int64 by node index (depth-major), -1 = none (entries of leaves unused).
+    keep_axes: per level l, bit a set = axis a keeps its resolution from
+    level l to level l + 1 (default: every level halves every axis).
     sample_format: 0 = raw values with binary32 lerps, 1 = binary16,
     2 = bfloat16 samples (the brick cache's format).
     provider: instead of levels, (m, k, dims_xyz, bytes_per_voxel, fn, ctx)
@@ -132,9 +135,11 @@ class Volume:
     """
 
     def __init__(self, levels, spacing, B, leaf_extent, resident=(), leaf_min=None, leaf_max=None, provider=None,
-                 sample_format=0, node_min=None, node_max=None):
+                 sample_format=0, node_min=None, node_max=None, keep_axes=None):
         self.s = _Volume()
         self.s.sample_format = int(sample_format)
+        ka = list(keep_axes or []) + [0] * MAXL
+        self.s.keep_axes[:] = [int(v) for v in ka[:MAXL]]
         if provider is None:
             self.m = len(levels)
             self.k = len(levels[0])

@@ -75,6 +75,10 @@ typedef struct {
    * NULL: none given. */
   const int64_t *node_min;
   const int64_t *node_max;
+  /* downsampling between levels (Sec. 8: anisotropic downsampling ratios):
+   * bit a of keep_axes[l] set = axis a keeps its resolution from level l to
+   * level l + 1; clear = halved.  All zero: every level halves every axis. */
+  int32_t keep_axes[OR_MAXL];
 } or_volume;
 
 typedef struct {
@@ -102,14 +106,39 @@ typedef struct {
 
 /* ---------------------------------------------------------------- geometry */
 
-static int lvl_dim(int d0, int l) {
-  int d = d0;
-  for (int i = 0; i < l; ++i) d = (d + 1) / 2;
+/* Level geometry per axis.  lvl_shift: log2 of the level-l voxel extent
+ * along axis a in level-0 voxels (the number of halvings so far); lvl_dim:
+ * voxels along axis a at level l (a halving rounds up: ceil(d / 2)). */
+static int lvl_shift(const or_volume *v, int l, int a) {
+  int s = 0;
+  for (int i = 0; i < l; ++i) s += !((v->keep_axes[i] >> a) & 1);
+  return s;
+}
+
+static int lvl_dim(const or_volume *v, int l, int a) {
+  int d = v->dims[a];
+  for (int i = 0; i < l; ++i)
+    if (!((v->keep_axes[i] >> a) & 1)) d = (d + 1) / 2;
   return d;
 }
 
+/* Step exponent of level l (Sec. 6.1: the sampling distance may grow with
+ * the level a brick comes from): the largest s with 2^s times the smallest
+ * level-0 spacing at most the smallest physical extent of a level-l voxel.
+ * With every axis halved per level this is l. */
+static int lvl_step(const or_volume *v, int l) {
+  double s0 = INFINITY, sl = INFINITY;
+  for (int a = 0; a < 3; ++a) {
+    s0 = fmin(s0, (double)v->spacing[a]);
+    sl = fmin(sl, (double)v->spacing[a] * ldexp(1.0, lvl_shift(v, l, a)));
+  }
+  int s = 0;
+  while (ldexp(s0, s + 1) <= sl) ++s;
+  return s;
+}
+
 static int nbricks(const or_volume *v, int l, int a) {
-  return (lvl_dim(v->dims[a], l) + v->B - 1) / v->B;
+  return (lvl_dim(v, l, a) + v->B - 1) / v->B;
 }
 
 /* Geometry tables computed once per call from the volume description:
@@ -128,7 +157,7 @@ static void make_geom(const or_volume *v, or_geom *g) {
   memset(g, 0, sizeof(*g));
   for (int l = 0; l < v->k; ++l)
     for (int a = 0; a < 3; ++a) {
-      g->ld[l][a] = lvl_dim(v->dims[a], l);
+      g->ld[l][a] = lvl_dim(v, l, a);
       g->nb[l][a] = (g->ld[l][a] + v->B - 1) / v->B;
     }
   int64_t off = 0;
@@ -243,11 +272,13 @@ static void oa_node(const oa_ctx *x, int d, int64_t jx, int64_t jy, int64_t jz) 
   int64_t nleaves = nl[0] * nl[1] * nl[2];
   for (int c = 0; c < v->m; ++c) {
     /* partial mapping, by definition: any resident brick of (c, l) whose box
-     * [b*B*2^l, (b+1)*B*2^l) meets the node box with positive volume */
+     * [b*B*2^s, (b+1)*B*2^s) per axis (s the level's shift along the axis)
+     * meets the node box with positive volume */
     uint32_t mask = 0;
     for (int l = 0; l < v->k; ++l) {
-      int64_t BL = (int64_t)v->B << l, b0[3], b1[3];
+      int64_t b0[3], b1[3];
       for (int a = 0; a < 3; ++a) {
+        int64_t BL = (int64_t)v->B << lvl_shift(v, l, a);
         b0[a] = lo[a] / BL;
         b1[a] = (hi[a] - 1) / BL;
       }
@@ -467,7 +498,7 @@ static void frame_occupancy(ob_frame *f) {
 static void frame_sdepth(ob_frame *f) {
   const or_volume *v = f->v;
   for (int l = 0; l < OR_MAXL; ++l) {
-    double step = (double)f->p->dt * ldexp(1.0, l);
+    double step = (double)f->p->dt * ldexp(1.0, lvl_step(v, l));
     int best = 0;
     for (int d = 0; d <= f->D; ++d) {
       double mn = INFINITY;
@@ -549,9 +580,10 @@ static int64_t node_index(const ob_frame *f, int d, const int64_t j[3]) {
 
 /* owner brick of a position at level l: floor(x / (B 2^l)) per axis */
 static void owner_brick(const ob_frame *f, int l, const float x[3], int b[3]) {
-  int sh = __builtin_ctz((unsigned)f->v->B) + l;
-  float inv = ldexpf(1.0f, -sh);
-  for (int a = 0; a < 3; ++a) b[a] = (int)(x[a] * inv);
+  for (int a = 0; a < 3; ++a) {
+    int sh = __builtin_ctz((unsigned)f->v->B) + lvl_shift(f->v, l, a);
+    b[a] = (int)(x[a] * ldexpf(1.0f, -sh));
+  }
 }
 
 /* Per-channel state at one node (Algorithm 1 order: isEmpty, isHomogeneous,
@@ -588,7 +620,7 @@ static inline uint32_t fnv_word(uint32_t h, uint32_t w) {
 }
 
 static uint32_t voxel(const or_volume *v, int c, int l, int64_t x, int64_t y, int64_t z) {
-  int nx = lvl_dim(v->dims[0], l), ny = lvl_dim(v->dims[1], l), nz = lvl_dim(v->dims[2], l);
+  int nx = lvl_dim(v, l, 0), ny = lvl_dim(v, l, 1), nz = lvl_dim(v, l, 2);
   if (x > nx - 1) x = nx - 1;
   if (y > ny - 1) y = ny - 1;
   if (z > nz - 1) z = nz - 1;
@@ -604,9 +636,9 @@ static float trilinear32(const or_volume *v, int c, int l, const float x[3]) {
   float u[3], fr[3];
   int64_t i0[3];
   for (int a = 0; a < 3; ++a) {
-    float xl = ldexpf(x[a], -l);
+    float xl = ldexpf(x[a], -lvl_shift(v, l, a));
     float w = xl - 0.5f;
-    w = fminf(fmaxf(w, 0.0f), (float)(lvl_dim(v->dims[a], l) - 1));
+    w = fminf(fmaxf(w, 0.0f), (float)(lvl_dim(v, l, a) - 1));
     u[a] = w;
     i0[a] = (int64_t)w;
     fr[a] = w - (float)i0[a];
@@ -691,9 +723,9 @@ static float trilinear_lp(const or_volume *v, int c, int l, const float x[3], in
   double fr[3];
   int64_t i0[3];
   for (int a = 0; a < 3; ++a) {
-    float xl = ldexpf(x[a], -l);
+    float xl = ldexpf(x[a], -lvl_shift(v, l, a));
     float w = xl - 0.5f;
-    w = fminf(fmaxf(w, 0.0f), (float)(lvl_dim(v->dims[a], l) - 1));
+    w = fminf(fmaxf(w, 0.0f), (float)(lvl_dim(v, l, a) - 1));
     i0[a] = (int64_t)w;
     fr[a] = round_fmt((double)(w - (float)i0[a]), fmt);
   }
@@ -717,8 +749,8 @@ static double trilinear64(const or_volume *v, int c, int l, const double x[3]) {
   double fr[3];
   int64_t i0[3];
   for (int a = 0; a < 3; ++a) {
-    double w = ldexp(x[a], -l) - 0.5;
-    double hi = (double)(lvl_dim(v->dims[a], l) - 1);
+    double w = ldexp(x[a], -lvl_shift(v, l, a)) - 0.5;
+    double hi = (double)(lvl_dim(v, l, a) - 1);
     w = w < 0.0 ? 0.0 : (w > hi ? hi : w);
     i0[a] = (int64_t)floor(w);
     fr[a] = w - (double)i0[a];
@@ -930,7 +962,8 @@ static void march_pixel(const ob_frame *f, int px, int py, int64_t n_out, const 
         h = fnv_word(h, (uint32_t)i); h = fnv_word(h, (uint32_t)c);
         h = fnv_word(h, (uint32_t)found); h = fnv_word(h, brick_id(v, c, found, fb[0], fb[1], fb[2]));
       }
-      int s = s_used == 99 ? lmin_used : s_used;   /* adaptive step 2^s */
+      /* adaptive step 2^s: the step exponent of the finest level read */
+      int s = lvl_step(v, s_used == 99 ? lmin_used : s_used);
 
       /* classification + compositing: per-channel TF, opacity corrected for
        * a step of 2^s lattice spacings, additive premultiplied colour,

@@ -87,10 +87,29 @@ ro_status make_geometry(const ro_desc* d, Geometry* g, std::string* why) {
     g->dimm[a] = std::nextafter((float)d->dims[a], 0.0f);
     g->leaf_log2[a] = ilog2(d->leaf_extent[a]);
   }
+  for (int l = 0; l < RO_MAX_LEVELS; ++l)
+    if (d->keep_axes[l] > 7 || (l >= g->k - 1 && d->keep_axes[l] != 0))
+      return fail("keep_axes: three axis bits per level transition, zero beyond the last level");
+  // level geometry per axis: an axis not kept is halved (rounding up)
+  for (int l = 0; l < ro::kMaxL; ++l) {
+    double s0 = INFINITY, sl = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+      int sh = 0;
+      for (int q = 0; q < l; ++q) sh += (d->keep_axes[q] >> a) & 1 ? 0 : 1;
+      g->lsh[l][a] = sh;
+      s0 = std::min(s0, (double)d->spacing[a]);
+      sl = std::min(sl, (double)d->spacing[a] * std::ldexp(1.0, sh));
+    }
+    // step exponent: largest s with 2^s min(spacing) <= the smallest extent of a level-l voxel
+    int s = 0;
+    while (std::ldexp(s0, s + 1) <= sl) ++s;
+    g->lstep[l] = s;
+  }
   for (int l = 0; l < g->k; ++l)
     for (int a = 0; a < 3; ++a) {
       int v = g->dims0[a];
-      for (int q = 0; q < l; ++q) v = (v + 1) / 2;
+      for (int q = 0; q < l; ++q)
+        if (!((d->keep_axes[q] >> a) & 1)) v = (v + 1) / 2;
       g->ldims[l][a] = v;
       g->ldimf[l][a] = (float)(v - 1);
       g->nb[l][a] = (v + g->B - 1) / g->B;
@@ -573,8 +592,9 @@ ro_status ro_compensate_bricks(ro_ctx* c, ro_mc* mc, uint32_t n, const uint32_t*
   if (n == 0) return RO_OK;
   const char* where = "ro_compensate_bricks";
   if (!mc || !ids) return set_err(c, RO_ERR_INVALID_ARG, "ro_compensate_bricks: null pointer");
-  if (c->g.edge != RO_MC_EDGE || c->g.bpv != 2 || c->g.sf != 0 || c->g.k < 2)
-    return set_err(c, RO_ERR_INVALID_ARG, "ro_compensate_bricks: needs 32^3 u16 bricks, raw samples, >= 2 levels");
+  if (c->g.edge != RO_MC_EDGE || c->g.bpv != 2 || c->g.sf != 0 || c->g.k < 2 || c->desc.keep_axes[0] != 0)
+    return set_err(c, RO_ERR_INVALID_ARG,
+                   "ro_compensate_bricks: needs 32^3 u16 bricks, raw samples, >= 2 levels, level 1 halving every axis");
   if (n > c->desc.max_upload || n > c->desc.cache_slots || n > ro::mc_max_batch(mc) ||
       2ull * n * sizeof(uint32_t) > (uint64_t)kMaxItems * sizeof(ro::UpdateItem))
     return set_err(c, RO_ERR_CAPACITY, "ro_compensate_bricks: n exceeds max_upload, cache_slots or the batch");
@@ -647,8 +667,8 @@ ro_status run_update(ro_ctx* c, const std::vector<ro::MetaItem>& lm_in, const st
     uint32_t b[3], lo[3], hi[3];
     index_to_brick(g, pi, &ch, &l, b);
     for (int a = 0; a < 3; ++a) {
-      const uint64_t v0 = (uint64_t)b[a] << (g.blog2 + l);
-      uint64_t v1 = (uint64_t)(b[a] + 1) << (g.blog2 + l);
+      const uint64_t v0 = (uint64_t)b[a] << (g.blog2 + g.lsh[l][a]);
+      uint64_t v1 = (uint64_t)(b[a] + 1) << (g.blog2 + g.lsh[l][a]);
       if (v1 > (uint64_t)g.dims0[a]) v1 = (uint64_t)g.dims0[a];
       lo[a] = (uint32_t)(v0 >> g.leaf_log2[a]);
       hi[a] = (uint32_t)((v1 + (1ull << g.leaf_log2[a]) - 1) >> g.leaf_log2[a]);
@@ -845,7 +865,7 @@ void fill_view(const ro_ctx* c, const ro_camera* cam, const ro_render_params* p,
   // traversal depth per level (Algorithm 1): deepest depth whose nodes are at least
   // one step long along every axis, physically
   for (int l = 0; l < ro::kMaxL; ++l) {
-    const double step = (double)p->dt * std::ldexp(1.0, l);
+    const double step = (double)p->dt * std::ldexp(1.0, g.lstep[l]);
     int best = 0;
     for (int d = 0; d <= g.D; ++d) {
       double mn = INFINITY;

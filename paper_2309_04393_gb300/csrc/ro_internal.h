@@ -17,6 +17,8 @@ constexpr int kRenderThreads = 640;   // persistent blocks, one per SM; rays are
 constexpr int kStats = 8;             // per-block counters of the render kernel
 constexpr int kWalkWin = 4;           // octree depths whose node words the walk loads at once
 constexpr int kTopWords = 10240;      // node words of the octree's top depths kept in shared memory (40 KB)
+constexpr int kWalkCache = 8;         // walk results a warp remembers for its tile
+constexpr int kWalkEntry = 24;        // words per remembered walk (header 5 + 16 selections, padded)
 
 // Geometry derived once from the descriptor; copied by value into kernels.
 struct Geometry {
@@ -30,6 +32,8 @@ struct Geometry {
   int D;                      // octree depth (leaves at depth D)
   int ldims[kMaxL][3];        // level dims
   float ldimf[kMaxL][3];      // level dims - 1, as floats (trilinear clamp bound)
+  int lsh[kMaxL][3];          // log2 of a level-l voxel's extent per axis, in level-0 voxels
+  int lstep[kMaxL];           // step exponent after a sample read at level l
   int nb[kMaxL][3];           // bricks per axis per level
   uint32_t pt_off[kMaxC * kMaxL + 1];  // page-table offset of table c*k + l; [m*k] = n_bricks
   uint64_t node_off[kMaxDepth + 2];    // first node of each depth; [D+1] = n_nodes

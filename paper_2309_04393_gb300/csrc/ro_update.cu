@@ -125,9 +125,9 @@ __global__ void __launch_bounds__(256) leaf_masks_kernel(const __grid_constant__
     uint32_t mask = 0;
     for (int l = 0; l < g.k; ++l) {
       // leaf origin in level-0 voxels, divided by the level-l brick extent
-      const int sh = g.blog2 + l;
-      const uint32_t bx = (lx << g.leaf_log2[0]) >> sh, by = (ly << g.leaf_log2[1]) >> sh,
-                     bz = (lz << g.leaf_log2[2]) >> sh;
+      const uint32_t bx = (lx << g.leaf_log2[0]) >> (g.blog2 + g.lsh[l][0]),
+                     by = (ly << g.leaf_log2[1]) >> (g.blog2 + g.lsh[l][1]),
+                     bz = (lz << g.leaf_log2[2]) >> (g.blog2 + g.lsh[l][2]);
       const uint64_t pi = g.pt_off[c * g.k + l] + ((uint64_t)bz * g.nb[l][1] + by) * g.nb[l][0] + bx;
       if (a.pt[pi] != 0) mask |= 1u << l;
     }

@@ -39,7 +39,8 @@ class Desc(ctypes.Structure):
                 ("value_bits", ctypes.c_uint32), ("brick", ctypes.c_uint32), ("levels", ctypes.c_uint32),
                 ("leaf_extent", ctypes.c_uint32 * 3), ("cache_slots", ctypes.c_uint32),
                 ("max_requests", ctypes.c_uint32), ("max_upload", ctypes.c_uint32), ("max_meta", ctypes.c_uint32),
-                ("max_batch_tiles", ctypes.c_uint32), ("sample_format", ctypes.c_uint32)]
+                ("max_batch_tiles", ctypes.c_uint32), ("sample_format", ctypes.c_uint32),
+                ("keep_axes", ctypes.c_uint32 * RO_MAX_LEVELS)]
 
 
 class Sizes(ctypes.Structure):
@@ -125,8 +126,10 @@ def load(build_if_missing: bool = True):
 
 
 def make_desc(dims, spacing, channels, value_bits, brick, levels, leaf_extent, cache_slots, max_requests=65536,
-              max_upload=1024, max_meta=65536, max_batch_tiles=0, sample_format=0) -> Desc:
-    """sample_format: 0 raw values with binary32 lerps, 1 binary16, 2 bfloat16."""
+              max_upload=1024, max_meta=65536, max_batch_tiles=0, sample_format=0, keep_axes=None) -> Desc:
+    """sample_format: 0 raw values with binary32 lerps, 1 binary16, 2 bfloat16.
+    keep_axes: per level l, bit a set = axis a keeps its resolution from
+    level l to l + 1 (default: every level halves every axis)."""
     d = Desc()
     d.dims[:] = [int(v) for v in dims]
     d.spacing[:] = [float(v) for v in spacing]
@@ -136,6 +139,8 @@ def make_desc(dims, spacing, channels, value_bits, brick, levels, leaf_extent, c
         int(max_meta)
     d.max_batch_tiles = int(max_batch_tiles)
     d.sample_format = int(sample_format)
+    ka = list(keep_axes or []) + [0] * RO_MAX_LEVELS
+    d.keep_axes[:] = [int(v) for v in ka[:RO_MAX_LEVELS]]
     return d
 
 

@@ -49,6 +49,7 @@ def lib():
         L.sy_blobs_u8.argtypes = [c_uint64, c_int, c_int, c_int, c_int, c_double, c_double, c_double, c_double,
                                   c_uint32, c_void_p]
         L.sy_downsample.argtypes = [c_int, c_int, c_int, c_int, c_void_p, c_void_p]
+        L.sy_downsample_axes.argtypes = [c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p]
         L.sy_bricks_from_dense.argtypes = [c_int, c_int, c_int, c_int, c_void_p, c_int, c_int, c_void_p, c_void_p]
         L.sy_leaf_ranges.argtypes = [c_int, c_int, c_int, c_int, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]
         L.sy_cells_create.restype = c_void_p
@@ -95,21 +96,25 @@ def blobs_u8(dims_xyz, seed, n_blobs=40, sigma=(3.0, 10.0), amp=(60.0, 180.0), n
     return out
 
 
-def downsample(vol: np.ndarray) -> np.ndarray:
+def downsample(vol: np.ndarray, keep: int = 0) -> np.ndarray:
+    """Rounded mean over blocks of 2 voxels along each halved axis (bit a of
+    keep set: axis a (x, y, z) keeps its resolution)."""
     nz, ny, nx = vol.shape
     bpv = vol.dtype.itemsize
-    out = np.empty(((nz + 1) // 2, (ny + 1) // 2, (nx + 1) // 2), vol.dtype)
+    f = [1 if (keep >> a) & 1 else 2 for a in range(3)]
+    out = np.empty((-(-nz // f[2]), -(-ny // f[1]), -(-nx // f[0])), vol.dtype)
     vol = np.ascontiguousarray(vol)
-    if lib().sy_downsample(bpv, nx, ny, nz, _ptr(vol), _ptr(out)) != 0:
+    if lib().sy_downsample_axes(bpv, nx, ny, nz, int(keep), _ptr(vol), _ptr(out)) != 0:
         raise ValueError("sy_downsample failed")
     return out
 
 
-def mean_levels(vol0: np.ndarray, k: int) -> list:
-    """Level 0 .. k-1 of the hierarchy, each the rounded mean of the previous."""
+def mean_levels(vol0: np.ndarray, k: int, keep_axes=None) -> list:
+    """Level 0 .. k-1 of the hierarchy, each the rounded mean of the previous;
+    keep_axes[l] (default 0) names the axes level l + 1 keeps unhalved."""
     levels = [np.ascontiguousarray(vol0)]
-    for _ in range(1, k):
-        levels.append(downsample(levels[-1]))
+    for l in range(1, k):
+        levels.append(downsample(levels[-1], 0 if keep_axes is None else keep_axes[l - 1]))
     return levels
 
 

@@ -31,11 +31,13 @@ class Scene:
     leaf_max: np.ndarray = None
     resident: list = field(default_factory=list)  # (c, l, bx, by, bz)
     frames: list = field(default_factory=list)
+    keep_axes: list = None        # per level: bit a set = axis a not halved going to the next level
 
     def level_dims(self, l):
         d = list(self.dims)
-        for _ in range(l):
-            d = [(v + 1) // 2 for v in d]
+        for q in range(l):
+            keep = 0 if self.keep_axes is None else self.keep_axes[q]
+            d = [v if (keep >> a) & 1 else (v + 1) // 2 for a, v in enumerate(d)]
         return tuple(d)
 
     def n_bricks_axis(self, l):

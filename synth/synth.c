@@ -151,7 +151,7 @@ SY_EXPORT int sy_blobs_u8(uint64_t seed, int nx, int ny, int nz, int n_blobs, do
 /* ---------------------------------------------- mean-downsampled level */
 
 typedef struct {
-  int bpv; int nx, ny, nz; int ox, oy, oz; const void *in; void *out;
+  int bpv; int nx, ny, nz; int ox, oy, oz; const void *in; void *out; int fx, fy, fz;
 } sy_down_ctx;
 
 static void sy_down_body(void *vctx, int64_t lo, int64_t hi) {
@@ -160,10 +160,10 @@ static void sy_down_body(void *vctx, int64_t lo, int64_t hi) {
     for (int y = 0; y < c->oy; ++y)
       for (int x = 0; x < c->ox; ++x) {
         uint64_t sum = 0, n = 0;
-        for (int dz = 0; dz < 2; ++dz)
-          for (int dy = 0; dy < 2; ++dy)
-            for (int dx = 0; dx < 2; ++dx) {
-              int64_t ix = 2 * x + dx, iy = 2 * y + dy, iz = 2 * z + dz;
+        for (int dz = 0; dz < c->fz; ++dz)
+          for (int dy = 0; dy < c->fy; ++dy)
+            for (int dx = 0; dx < c->fx; ++dx) {
+              int64_t ix = (int64_t)c->fx * x + dx, iy = (int64_t)c->fy * y + dy, iz = (int64_t)c->fz * z + dz;
               if (ix >= c->nx || iy >= c->ny || iz >= c->nz) continue;
               int64_t idx = (iz * c->ny + iy) * c->nx + ix;
               sum += c->bpv == 1 ? ((const uint8_t *)c->in)[idx] : ((const uint16_t *)c->in)[idx];
@@ -177,12 +177,18 @@ static void sy_down_body(void *vctx, int64_t lo, int64_t hi) {
 }
 
 /* Next coarser level: each output voxel is the mean of the (up to 8) input
- * voxels it covers, rounded half up; output dims are ceil(dims/2). */
-SY_EXPORT int sy_downsample(int bpv, int nx, int ny, int nz, const void *in, void *out) {
+ * voxels it covers, rounded half up.  Bit a of keep set: axis a keeps its
+ * resolution (factor 1), else it is halved (factor 2, output ceil(d/2)). */
+SY_EXPORT int sy_downsample_axes(int bpv, int nx, int ny, int nz, int keep, const void *in, void *out) {
   if ((bpv != 1 && bpv != 2) || nx <= 0 || ny <= 0 || nz <= 0) return -1;
-  sy_down_ctx c = {bpv, nx, ny, nz, (nx + 1) / 2, (ny + 1) / 2, (nz + 1) / 2, in, out};
+  const int fx = (keep & 1) ? 1 : 2, fy = (keep & 2) ? 1 : 2, fz = (keep & 4) ? 1 : 2;
+  sy_down_ctx c = {bpv, nx, ny, nz, (nx + fx - 1) / fx, (ny + fy - 1) / fy, (nz + fz - 1) / fz, in, out, fx, fy, fz};
   sy_parallel(sy_down_body, &c, c.oz, 1);
   return 0;
+}
+
+SY_EXPORT int sy_downsample(int bpv, int nx, int ny, int nz, const void *in, void *out) {
+  return sy_downsample_axes(bpv, nx, ny, nz, 0, in, out);
 }
 
 /* ---------------------------------------------- bricks with a border */

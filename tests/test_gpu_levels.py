@@ -80,3 +80,70 @@ def test_lod_thresholds_on_gpu(gpu, ranges):
         i += 1 << min(levels)
     assert int(g["hash"][0]) == h and int(g["i_end"][0]) == i
     ctx.close()
+
+
+@pytest.mark.parametrize("keep_axes,read", [([4, 0], 1), ([4, 4], 2), ([1, 6], 2)])
+def test_anisotropic_level_value_on_gpu(gpu, keep_axes, read):
+    """Levels that halve only some axes (Sec. 8): bit-exact against the
+    oracle, every octree word included, and the GPU image against the closed
+    form of the per-axis level coordinate."""
+    from test_oracle_levels import closed_value_aniso, level_shifts
+    lv = synth.mean_levels(linear_levels(1)[0], 3, keep_axes)
+    mn, mx = synth.leaf_ranges(lv[0], (16, 16, 16))
+    scene = recipes.Scene("linear_aniso", DIMS, (1.0, 1.0, 1.0), 1, 3, 32, (16, 16, 16), 16, levels=[lv],
+                          leaf_min=mn[None].astype(np.int64), leaf_max=mx[None].astype(np.int64), keep_axes=keep_axes)
+    scene.resident = scene.all_bricks()
+    ctx = gpu.make_ctx(scene)
+    slot_to_id = gpu.load(ctx, scene)
+    vol = gpu.oracle_volume(scene)
+    gpu.check_octree(ctx, vol)
+    W = H = 160
+    cam = oblique_camera(W, H)
+    tf = value_tf()
+    fr = synth.Frame(W, H, cam, [tf], 0.5, [0.0] + [INF] * 15, [read], [read], ert=2.0)
+    o = oracle.render(vol, vol.node_words(), fr)
+    g = gpu.gpu_frame(ctx, fr, slot_to_id)
+    gpu.compare(g, o)
+    x64, inside = first_sample_positions(cam, W, H)
+    sel = np.nonzero(inside)[0]
+    ap = 1.0 - 0.5 ** (2 ** min(level_shifts(keep_axes, read)))
+    got = g["rgba32"][sel, 0].astype(np.float64) * 256.0 / (ap * tf.scale)
+    assert np.abs(got - closed_value_aniso(x64[sel], read, keep_axes)).max() < 0.05
+    ctx.close()
+
+
+@pytest.mark.parametrize("keep_axes,spacing,bias", [([4, 0], (1.0, 1.0, 1.0), 0.8), ([4, 4, 0], (1.0, 1.0, 4.0), 2.0)])
+def test_anisotropic_partial_residency_on_gpu(gpu, keep_axes, spacing, bias):
+    """Two u8 channels over a ragged volume whose first levels halve x and y
+    only, 60 % of level 0 resident (coarser substitution across anisotropic
+    levels), perspective views with distance-dependent levels and two start
+    depths: bit-exact against the oracle."""
+    dims = (100, 90, 70)
+    k = len(keep_axes) + 1
+    vols = [synth.blobs_u8(dims, 61 + c, n_blobs=14) for c in range(2)]
+    levels = [synth.mean_levels(v, k, keep_axes) for v in vols]
+    mn, mx = recipes._exact_meta(levels, (8, 8, 8))
+    scene = recipes.Scene("aniso", dims, spacing, 2, k, 32, (8, 8, 8), 8, levels=levels, leaf_min=mn, leaf_max=mx,
+                          keep_axes=keep_axes)
+    fine = scene.all_bricks(levels=[0])
+    pick = synth.seeded_subset(9, len(fine), int(0.6 * len(fine)))
+    scene.resident = scene.all_bricks(levels=list(range(1, k))) + [fine[i] for i in pick]
+    ctx = gpu.make_ctx(scene)
+    slot_to_id = gpu.load(ctx, scene)
+    vol = gpu.oracle_volume(scene)
+    gpu.check_octree(ctx, vol)
+    words = vol.node_words()
+    sp = np.array(spacing)
+    centre = tuple(np.array(dims) * sp / 2.0)
+    cam = synth.look_at(tuple(np.array(centre) + np.array([-130.0, -100.0, 90.0 * sp[2]])), centre, (0, 0, 1), 90, 70,
+                        fovy_deg=40.0)
+    lod = synth.lod_thresholds(float(sp.min()), 70, 40.0, k, bias=bias)
+    tfs = [synth.tf_ramp(8, 255, rgb=(1, 0.4, 0.1), alpha_max=0.3), synth.tf_ramp(20, 230, rgb=(0.2, 0.6, 1))]
+    for sd in (0, 2):
+        fr = synth.Frame(90, 70, cam, tfs, 0.5 * float(sp.min()), lod, [0, 0], [k - 1, k - 1], start_depth=sd)
+        o = oracle.render(vol, words, fr)
+        g = gpu.gpu_frame(ctx, fr, slot_to_id)
+        gpu.compare(g, o)
+        levels_used = set(((o["used_ids"] >> 24) % k).tolist())
+        assert len(levels_used) >= 2 and o["req_ids"].size > 0
+    ctx.close()

@@ -30,13 +30,14 @@ def make_ctx(scene, cache_slots=None, max_requests=65536, max_upload=512):
     from paper_2309_04393_gb300 import ro
     n_slots = cache_slots if cache_slots is not None else max(1, len(scene.resident))
     d = ro.make_desc(scene.dims, scene.spacing, scene.m, scene.value_bits, scene.B, scene.k, scene.leaf, n_slots,
-                     max_requests=max_requests, max_upload=max_upload)
+                     max_requests=max_requests, max_upload=max_upload, keep_axes=scene.keep_axes)
     return ro.Context(d)
 
 
 def oracle_volume(scene, resident=None):
     return oracle.Volume(scene.levels, scene.spacing, scene.B, scene.leaf,
-                         scene.resident if resident is None else resident, scene.leaf_min, scene.leaf_max)
+                         scene.resident if resident is None else resident, scene.leaf_min, scene.leaf_max,
+                         keep_axes=scene.keep_axes)
 
 
 def gpu_frame(ctx, frame, slot_to_id):

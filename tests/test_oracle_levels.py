@@ -212,3 +212,110 @@ def test_lod_thresholds_exact(ranges):
         assert n == 16 + 8 + 24 and i == 128
     else:
         assert n == 16 + 8 + 48 and i == 128
+
+
+# ------------------------------------------- anisotropic downsampling
+
+def level_shifts(keep_axes, l):
+    """log2 of the level-l voxel extent per axis: halvings so far."""
+    return [sum(0 if (keep_axes[i] >> a) & 1 else 1 for i in range(l)) for a in range(3)]
+
+
+def closed_value_aniso(x64, l, keep_axes):
+    e = level_shifts(keep_axes, l)
+    out = np.full(x64.shape[0], float(A0))
+    for a in range(3):
+        f = float(2 ** e[a])
+        dl = DIMS[a]
+        for i in range(l):
+            if not (keep_axes[i] >> a) & 1:
+                dl = (dl + 1) // 2
+        u = np.clip(x64[:, a] / f - 0.5, 0.0, dl - 1.0)
+        out += SLOPE[a] * (f * u + (f - 1.0) / 2.0)
+    return out
+
+
+@pytest.mark.parametrize("keep_axes", [[4, 0], [4, 4], [1, 6], [3, 0]])
+@pytest.mark.parametrize("read", [1, 2])
+def test_anisotropic_level_value_closed_form(keep_axes, read):
+    """Levels that halve only some axes (Sec. 8: downsampling in two
+    dimensions; Sec. 9: anisotropic subdivision): the 2x2x1 (or 2x1x1) means
+    of a linear field stay linear, the level-l value is the field at the
+    per-axis clamped coordinate x / 2^e_a - 0.5, and the opacity correction
+    uses the level's step exponent, min over axes of e_a at unit spacing."""
+    k = 3
+    lv = synth.mean_levels(linear_levels(1)[0], k, keep_axes)
+    for l in range(k):
+        e = level_shifts(keep_axes, l)
+        z, y, x = np.meshgrid(*[np.arange(n) for n in lv[l].shape], indexing="ij")
+        want = A0 + sum(s * (2.0 ** ea * j + (2.0 ** ea - 1) / 2) for s, j, ea in zip(SLOPE, (x, y, z), e))
+        assert np.array_equal(lv[l].astype(np.float64), want), f"level {l} not linear"
+    mn, mx = synth.leaf_ranges(lv[0], (16, 16, 16))
+    bricks = []
+    for l in range(k):
+        nz, ny, nx = lv[l].shape
+        bricks += [(0, l, x, y, z) for z in range(-(-nz // 32)) for y in range(-(-ny // 32)) for x in range(-(-nx // 32))]
+    vol = oracle.Volume([lv], (1, 1, 1), 32, (16, 16, 16), bricks, mn[None].astype(np.int64), mx[None].astype(np.int64),
+                        keep_axes=keep_axes)
+    W = H = 160
+    cam = oblique_camera(W, H)
+    tf = value_tf()
+    fr = synth.Frame(W, H, cam, [tf], 0.5, [0.0] + [INF] * 15, [read], [read], ert=2.0)
+    o = oracle.render(vol, vol.node_words(), fr)
+    x64, inside = first_sample_positions(cam, W, H)
+    sel = np.nonzero(inside)[0]
+    assert np.all(o["n_eval"][sel] == 1) and np.all(((o["used_ids"] >> 24) & 0xFF) == read)
+    step = min(level_shifts(keep_axes, read))
+    ap = 1.0 - 0.5 ** (2 ** step)
+    got = o["rgba64"][sel, 0] * 256.0 / (ap * tf.scale)
+    assert np.abs(got - closed_value_aniso(x64[sel], read, keep_axes)).max() < 1e-6
+    assert np.allclose(o["rgba64"][sel, 3], ap, atol=1e-15)
+    # the binary32 sampling path follows the same per-axis coordinates
+    assert np.abs(o["rgba32"][sel].astype(np.float64) - o["rgba64"][sel]).max() < 1e-5
+    # the owner bricks of the samples are per-axis floor(x / (B 2^e_a))
+    e = level_shifts(keep_axes, read)
+    want_ids = {vol.brick_id(0, read, *[int(x64[i, a]) >> (5 + e[a]) for a in range(3)]) for i in sel}
+    assert want_ids <= set(o["used_ids"].tolist())
+
+
+@pytest.mark.parametrize("keep_axes,spacing", [([4, 0], (1.0, 1.0, 1.0)), ([4, 4], (1.0, 1.0, 4.0)),
+                                               ([0, 0], (1.0, 1.0, 4.0))])
+def test_anisotropic_step_sequence(keep_axes, spacing):
+    """On the exact +x ray of the lod test, the step after a sample read at
+    level l is 2^s with s the largest exponent such that 2^s times the
+    smallest spacing is at most the smallest physical extent of a level-l
+    voxel (Sec. 6.1's adaptive step), and the owner brick along x follows the
+    level's x extent."""
+    rng = np.random.default_rng(5)
+    v0 = rng.integers(1000, 60000, (8, 8, 64)).astype(np.uint16)
+    lv = synth.mean_levels(v0, 3, keep_axes)
+    mn, mx = synth.leaf_ranges(v0, (8, 8, 8))
+    bricks = []
+    for l in range(3):
+        nz, ny, nx = lv[l].shape
+        bricks += [(0, l, x, y, z) for z in range(-(-nz // 32)) for y in range(-(-ny // 32)) for x in range(-(-nx // 32))]
+    vol = oracle.Volume([lv], spacing, 32, (8, 8, 8), bricks, mn[None].astype(np.int64), mx[None].astype(np.int64),
+                        keep_axes=keep_axes)
+    sp = np.array(spacing)
+    cam = synth.look_at((0.0, 4.25 * sp[1], 3.75 * sp[2]), (1.0, 4.25 * sp[1], 3.75 * sp[2]), (0.0, 0.0, 1.0), 1, 1,
+                        ortho_pixel=1.0)
+    lut = np.zeros((256, 4), np.float32)
+    lut[:, :3] = 1.0
+    lut[:, 3] = np.float32(0.001)
+    tf = synth.TF(0.0, float(np.float32(255.0 / 65535.0)), lut)
+    fr = synth.Frame(1, 1, cam, [tf], 0.5, [0.0, 8.0, 16.0] + [INF] * 13, [0], [2], ert=0.0)
+    o = oracle.render(vol, vol.node_words(), fr)
+    h, i, n = 2166136261, 0, 0
+    while 0.5 * i < 64.0:
+        t = 0.5 * i
+        l = int(t >= 8.0) + int(t >= 16.0)
+        e = level_shifts(keep_axes, l)
+        ext = min(sp[a] * 2 ** e[a] for a in range(3))
+        s = 0
+        while 2 ** (s + 1) * sp.min() <= ext:
+            s += 1
+        bid = (l << 24) | (int(t) >> (5 + e[0]))
+        h = fnv_words(h, [i, 0, l, bid])
+        n += 1
+        i += 1 << s
+    assert int(o["hash"][0]) == h and int(o["n_eval"][0]) == n and int(o["i_end"][0]) == i
