@@ -168,18 +168,28 @@ template <> struct Fmt<2> {
   static __device__ __forceinline__ float to_float(T h) { return __bfloat162float(h); }
 };
 
+// Per-level tables read with a per-lane level index, kept in shared memory:
+// level dims - 1 (clamp bounds) and the per-axis log2 voxel extents.
+struct LevelTabs {
+  float ldimf[kMaxL][3];
+  int lsh[kMaxL][3];
+  int lstep[kMaxL];
+};
+
 template <int EC, int SF>
-__device__ __forceinline__ void tri_coords(const Geometry& g, int l, const float (&x)[3], TriCoords& tc) {
+__device__ __forceinline__ void tri_coords(const Geometry& g, const LevelTabs& lt, int l, const float (&x)[3],
+                                           TriCoords& tc) {
   const int E = EC ? EC : (int)g.edge;  // apron-slot edge, a compile-time constant for 32^3 bricks
   int li[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const float xl = x[k] * pow2f(-l);
+    const int sh = lt.lsh[l][k];        // level-l voxels are 2^sh level-0 voxels long along axis k
+    const float xl = x[k] * pow2f(-sh);
     float u = xl - 0.5f;
-    u = fminf(fmaxf(u, 0.0f), g.ldimf[l][k]);
+    u = fminf(fmaxf(u, 0.0f), lt.ldimf[l][k]);
     const int i0 = (int)u;
     tc.f[k] = u - (float)i0;
-    const int b = (int)(x[k] * pow2f(-(g.blog2 + l)));
+    const int b = (int)(x[k] * pow2f(-(g.blog2 + sh)));
     li[k] = i0 - (b * g.B - 1);
   }
   tc.idx = (li[2] * E + li[1]) * E + li[0];
@@ -207,7 +217,13 @@ __device__ __forceinline__ void tri_load(const Geometry& g, const uint8_t* base,
   }
 }
 
-// Lerps along x, then y, then z (each fma(f, b - a, a)) of loaded corners.
+// b - a per component with one rounding each (as a binary32 subtraction:
+// fma(a, -1, b) rounds the exact difference once).
+__device__ __forceinline__ float2 sub2(float2 b, float2 a) { return __ffma2_rn(a, make_float2(-1.0f, -1.0f), b); }
+
+// Lerps along x, then y, then z (each fma(f, b - a, a)) of loaded corners;
+// the binary32 path runs the x lerps and the y lerps two at a time in packed
+// binary32 operations, each component rounded as its scalar operation.
 template <int BPV, int SF>
 __device__ __forceinline__ float tri_lerp(const uint32_t (&r)[8], const TriCoords& tc) {
   if constexpr (SF != 0) {
@@ -232,32 +248,35 @@ __device__ __forceinline__ float tri_lerp(const uint32_t (&r)[8], const TriCoord
     float v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) v[q] = (float)r[q];
-    const float c00 = fmaf(tc.f[0], v[1] - v[0], v[0]);
-    const float c10 = fmaf(tc.f[0], v[3] - v[2], v[2]);
-    const float c01 = fmaf(tc.f[0], v[5] - v[4], v[4]);
-    const float c11 = fmaf(tc.f[0], v[7] - v[6], v[6]);
-    const float c0 = fmaf(tc.f[1], c10 - c00, c00);
-    const float c1 = fmaf(tc.f[1], c11 - c01, c01);
-    return fmaf(tc.f[2], c1 - c0, c0);
+    const float2 f0 = make_float2(tc.f[0], tc.f[0]), f1 = make_float2(tc.f[1], tc.f[1]);
+    const float2 a0 = make_float2(v[0], v[2]), b0 = make_float2(v[1], v[3]);
+    const float2 a1 = make_float2(v[4], v[6]), b1 = make_float2(v[5], v[7]);
+    const float2 cx0 = __ffma2_rn(f0, sub2(b0, a0), a0);   // (c00, c10)
+    const float2 cx1 = __ffma2_rn(f0, sub2(b1, a1), a1);   // (c01, c11)
+    const float2 ya = make_float2(cx0.x, cx1.x), yb = make_float2(cx0.y, cx1.y);
+    const float2 cy = __ffma2_rn(f1, sub2(yb, ya), ya);    // (c0, c1)
+    return fmaf(tc.f[2], cy.y - cy.x, cy.x);
   }
 }
 
-// TF lookup (linear between the 256 LUT entries) and opacity correction for
-// a step of 2^s (s squarings of 1 - alpha, Sec. 6.1): returns
-// the corrected opacity's complement q and the colour.  tf = (lo, scale).
-__device__ __forceinline__ void shade(const float4* __restrict__ lut, float2 tf, float val, int s, float& q, float& r,
-                                      float& gg, float& b) {  const float t = val - tf.x;
-  float xq = t * tf.y;
+// TF lookup (linear between the 256 LUT entries) at the unclamped TF
+// coordinate xq = (v - lo) * scale, and opacity correction for a step of 2^s
+// (s squarings of 1 - alpha, Sec. 6.1): returns the corrected opacity's
+// complement q and the colour (r, g) and b.  The four component lerps run as
+// two packed binary32 operations, each component rounded as a scalar fma.
+__device__ __forceinline__ void shade(const float4* __restrict__ lut, float xq, int s, float& q, float2& rg,
+                                      float& b) {
   xq = fminf(fmaxf(xq, 0.0f), 255.0f);
   int j = (int)xq;
   j = j > 254 ? 254 : j;
   const float fr = xq - (float)j;
   const float4 L0 = lut[j], L1 = lut[j + 1];
-  r = fmaf(fr, L1.x - L0.x, L0.x);
-  gg = fmaf(fr, L1.y - L0.y, L0.y);
-  b = fmaf(fr, L1.z - L0.z, L0.z);
-  float al = fmaf(fr, L1.w - L0.w, L0.w);
-  al = fminf(fmaxf(al, 0.0f), 1.0f);
+  const float2 ff = make_float2(fr, fr);
+  const float2 lrg = make_float2(L0.x, L0.y), lba = make_float2(L0.z, L0.w);
+  rg = __ffma2_rn(ff, sub2(make_float2(L1.x, L1.y), lrg), lrg);
+  const float2 ba = __ffma2_rn(ff, sub2(make_float2(L1.z, L1.w), lba), lba);
+  b = ba.x;
+  const float al = fminf(fmaxf(ba.y, 0.0f), 1.0f);
   q = 1.0f - al;
   for (int e = 0; e < s; ++e) q = q * q;
 }
@@ -345,6 +364,12 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
   __shared__ unsigned long long s_noff[kMaxDepth + 2];
   __shared__ int s_nn[kMaxDepth + 1][3];
   __shared__ int s_nb[kMaxL][3];
+  __shared__ LevelTabs s_lt;
+  for (int q = threadIdx.x; q < 3 * kMaxL; q += blockDim.x) {
+    s_lt.ldimf[q / 3][q % 3] = g.ldimf[q / 3][q % 3];
+    s_lt.lsh[q / 3][q % 3] = g.lsh[q / 3][q % 3];
+  }
+  for (int q = threadIdx.x; q < kMaxL; q += blockDim.x) s_lt.lstep[q] = g.lstep[q];
   for (int q = threadIdx.x; q <= g.D + 1; q += blockDim.x) s_noff[q] = g.node_off[q];
   for (int q = threadIdx.x; q < 3 * (g.D + 1); q += blockDim.x) s_nn[q / 3][q % 3] = g.nn[q / 3][q % 3];
   for (int q = threadIdx.x; q < 3 * k; q += blockDim.x) s_nb[q / 3][q % 3] = g.nb[q / 3][q % 3];
@@ -365,6 +390,9 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
     if (threadIdx.x == 0) s_base[a.n_views] = (uint32_t)(a.n_rays >> 5);
   }
   __syncthreads();
+  // channels whose TF has a transparent first knot (bit c)
+  uint32_t knot0_clear = 0;
+  for (int c = 0; c < m; ++c) knot0_clear |= (s_lut[c * 256].w <= 0.0f ? 1u : 0u) << c;
 
   const unsigned FULL = 0xFFFFFFFFu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -597,8 +625,9 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
       const bool gbad = (__ballot_sync(FULL, bad) & gmask) != 0;
       // page-table index of this lane's channel at level l (owner brick of the sample)
       auto pt_index = [&](int l) -> uint64_t {
-        const int bsh = g.blog2 + l;
-        const int bx = (int)(sx0 * pow2f(-bsh)), by = (int)(sx1 * pow2f(-bsh)), bz = (int)(sx2 * pow2f(-bsh));
+        const int bx = (int)(sx0 * pow2f(-(g.blog2 + s_lt.lsh[l][0]))),
+                  by = (int)(sx1 * pow2f(-(g.blog2 + s_lt.lsh[l][1]))),
+                  bz = (int)(sx2 * pow2f(-(g.blog2 + s_lt.lsh[l][2])));
         return s_pto[ch * k + l] + ((uint64_t)bz * s_nb[l][1] + by) * s_nb[l][0] + bx;
       };
 
@@ -700,8 +729,9 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
           nc.act = oact;
           nc.n_brick = onb;
           const int esh = g.D - od;
-          nc.one_brick = g.leaf_log2[0] + esh <= g.blog2 + lminu && g.leaf_log2[1] + esh <= g.blog2 + lminu &&
-                         g.leaf_log2[2] + esh <= g.blog2 + lminu;
+          nc.one_brick = g.leaf_log2[0] + esh <= g.blog2 + s_lt.lsh[lminu][0] &&
+                         g.leaf_log2[1] + esh <= g.blog2 + s_lt.lsh[lminu][1] &&
+                         g.leaf_log2[2] + esh <= g.blog2 + s_lt.lsh[lminu][2];
         }
       }
     }
@@ -749,21 +779,26 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
     }
 
     // shade, composite front to back, stop early once transmittance is low
-    const int s = nc.s_sel == 99 ? lminu : nc.s_sel;
-    float col0 = 0.0f, col1 = 0.0f, col2 = 0.0f, trans = 1.0f;
+    // step exponent of the finest level read (or desired): the opacity
+    // correction and the next lattice index use 2^s
+    const int s = s_lt.lstep[nc.s_sel == 99 ? lminu : nc.s_sel];
+    float2 col01 = make_float2(0.0f, 0.0f);
+    float col2 = 0.0f, trans = 1.0f;
     cnt.bs += nc.n_brick;
     cnt.homog += __popc(nc.act) - nc.n_brick;
     n_bs += nc.n_brick;
     // per channel: TF, opacity correction, additive colour (channel order)
     auto add = [&](int c, float val) {
+      const float2 tf = s_tf[c];
+      const float xq = (val - tf.x) * tf.y;
       // a value at or below the window start maps to knot 0; with a
       // transparent knot 0 the channel adds exactly nothing (a' = 0, q = 1)
-      if (!((val - s_tf[c].x) * s_tf[c].y > 0.0f) && s_lut[c * 256].w <= 0.0f) return;
-      float q, cr, cg, cb;
-      shade(s_lut + c * 256, s_tf[c], val, s, q, cr, cg, cb);
+      if (!(xq > 0.0f) && ((knot0_clear >> c) & 1u)) return;
+      float q, cb;
+      float2 rg;
+      shade(s_lut + c * 256, xq, s, q, rg, cb);
       const float ap = 1.0f - q;
-      col0 = fmaf(ap, cr, col0);
-      col1 = fmaf(ap, cg, col1);
+      col01 = __ffma2_rn(make_float2(ap, ap), rg, col01);
       col2 = fmaf(ap, cb, col2);
       trans = trans * q;
     };
@@ -776,9 +811,9 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
           h = fnv_word(h, 0xFFu);
           h = fnv_word(h, 0xFFFFFFFFu);
         } else {
-          const int bsh = g.blog2 + (int)lb;
-          const uint32_t bx = (uint32_t)(x[0] * pow2f(-bsh)), by = (uint32_t)(x[1] * pow2f(-bsh)),
-                         bz = (uint32_t)(x[2] * pow2f(-bsh));
+          const uint32_t bx = (uint32_t)(x[0] * pow2f(-(g.blog2 + s_lt.lsh[lb][0]))),
+                         by = (uint32_t)(x[1] * pow2f(-(g.blog2 + s_lt.lsh[lb][1]))),
+                         bz = (uint32_t)(x[2] * pow2f(-(g.blog2 + s_lt.lsh[lb][2])));
           h = fnv_word(h, lb);
           h = fnv_word(h, ((uint32_t)(c * k + (int)lb) << 24) | (bz << 16) | (by << 8) | bx);
         }
@@ -801,9 +836,9 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
       const bool ha = BPV == 1 && la == kSelHomog, hb = BPV == 1 && lb == kSelHomog;
       if (!ha && (int)la != tl) {  // channels at one level share the corner offset and weights
         tl = (int)la;
-        tri_coords<EC, SF>(g, tl, x, tc);
+        tri_coords<EC, SF>(g, s_lt, tl, x, tc);
       }
-      if (!hb && lb != la) tri_coords<EC, SF>(g, (int)lb, x, tcb);
+      if (!hb && lb != la) tri_coords<EC, SF>(g, s_lt, (int)lb, x, tcb);
       else tcb = tc;
       uint32_t ra[8], rb[8];
       tri_load<BPV, EC, SF>(g, a.cache + (ha ? 0 : (size_t)(sa & kSelMask) * g.slot_pitch), ha ? 0 : tc.idx, ra);
@@ -817,8 +852,8 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
         add(cb, vb);
       }
     }
-    C0 = fmaf(T, col0, C0);
-    C1 = fmaf(T, col1, C1);
+    C0 = fmaf(T, col01.x, C0);
+    C1 = fmaf(T, col01.y, C1);
     C2 = fmaf(T, col2, C2);
     T = T * trans;
     ++n_eval;
