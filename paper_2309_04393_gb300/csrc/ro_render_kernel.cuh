@@ -282,20 +282,30 @@ __device__ __forceinline__ void shade(const float4* __restrict__ lut, float xq, 
 }
 
 // Per-ray cache of the last classification: the final node, the desired
-// levels it was made for and whether every channel may be skipped there.  A
-// sample that lands in the same node with the same desired levels gets the
-// same decisions (the walk, the states, the selected slots and levels),
-// provided the node lies inside one brick of every level a channel may use;
-// requests and usage flags are then already set (the stores are idempotent).
+// levels it was made for (their lod value: the desired levels and the
+// traversal depth are functions of it) and whether every channel may be
+// skipped there.  A sample that lands in the same node with the same desired
+// levels gets the same decisions (the walk, the states, the selected slots
+// and levels), provided the node lies inside one brick of every level a
+// channel may use; requests and usage flags are then already set (the stores
+// are idempotent).
 struct NodeCache {
-  int d;                 // final depth, -1 = empty
+  // d (bits 0-4, 31 = none) | lod (5-8) | all_skip (9) | one_brick (10) |
+  // finest level read (11-15, 31 = none) | channels read from a brick (16-20)
+  uint32_t meta;
   int jn[3];             // node coordinates at depth d
-  uint64_t ldp;          // desired levels (4 bits per channel)
-  int st;                // traversal depth
-  bool all_skip, one_brick;
-  int s_sel;             // finest level read from a brick, 99 = none
   uint32_t act;          // channels with a value at this node (brick or node value)
-  uint32_t n_brick;      // how many of them read a brick
+  __device__ __forceinline__ int d() const { return (meta & 31u) == 31u ? -1 : (int)(meta & 31u); }
+  __device__ __forceinline__ int lod() const { return (int)((meta >> 5) & 15u); }
+  __device__ __forceinline__ bool all_skip() const { return (meta >> 9) & 1u; }
+  __device__ __forceinline__ bool one_brick() const { return (meta >> 10) & 1u; }
+  __device__ __forceinline__ int s_sel() const { return ((meta >> 11) & 31u) == 31u ? 99 : (int)((meta >> 11) & 31u); }
+  __device__ __forceinline__ uint32_t n_brick() const { return (meta >> 16) & 31u; }
+  __device__ __forceinline__ void clear() { meta = 31u; }
+  __device__ __forceinline__ void set(int d, int lod, bool all_skip, bool one_brick, int s_sel, uint32_t n_brick) {
+    meta = (uint32_t)d | ((uint32_t)lod << 5) | ((uint32_t)all_skip << 9) | ((uint32_t)one_brick << 10) |
+           ((uint32_t)(s_sel == 99 ? 31 : s_sel) << 11) | (n_brick << 16);
+  }
 };
 
 // Per-lane selection word (one per channel, in shared memory): bits 31..27
@@ -307,13 +317,13 @@ constexpr uint32_t kSelMask = (1u << 27) - 1u;
 // Per-thread counters of the current tile (a ray's counts stay below 2^28);
 // at every refill the warp adds them to its own 64-bit row in shared memory.
 struct Counters {
-  uint32_t hit, eval, bs, homog, skip, skipped;
+  uint32_t eval, bs, homog;   // rays hit and skips go straight to the warp's shared row
 };
 
 template <int BPV, bool DBG>
-__device__ __forceinline__ void write_pixel(const ViewArgs& V, int px, int py, float C0, float C1, float C2, float T,
+__device__ __forceinline__ void write_pixel(const ViewArgs& V, uint32_t pix, float C0, float C1, float C2, float T,
                                             uint32_t h, uint32_t n_eval, int i, uint32_t n_bs) {
-  const size_t p = (size_t)py * V.W + px;
+  const size_t p = (size_t)(pix >> 16) * V.W + (pix & 0xFFFFu);
   V.image[p] = make_float4(fminf(C0, 1.0f), fminf(C1, 1.0f), fminf(C2, 1.0f), 1.0f - T);
   if constexpr (DBG) {
     if (V.dbg_hash) V.dbg_hash[p] = h;
@@ -375,6 +385,8 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
   for (int q = threadIdx.x; q < 3 * k; q += blockDim.x) s_nb[q / 3][q % 3] = g.nb[q / 3][q % 3];
   // the octree's top depths (those whose words fit kTopWords) in shared memory
   uint32_t* s_top = s_sel + MP * kRenderThreads;
+  // per warp: the last kWalkCache walk results of its tile (see phase 1)
+  uint32_t* s_wc = s_top + kTopWords + (threadIdx.x >> 5) * (kWalkCache * kWalkEntry);
   int top_d = -1;
   while (top_d < g.D && g.node_off[top_d + 2] * MP <= (uint64_t)kTopWords) ++top_d;
   const uint32_t n_top = top_d >= 0 ? (uint32_t)(g.node_off[top_d + 1] * MP) : 0u;
@@ -405,24 +417,28 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
   const unsigned gmask = (MP == 32 ? FULL : ((1u << MP) - 1u)) << (grp * MP);
   const unsigned lt_mask = (1u << lane) - 1u;
 
-  Counters cnt = {0, 0, 0, 0, 0, 0};
+  Counters cnt = {0, 0, 0};
   auto flush = [&]() {
-    const uint32_t vals[6] = {cnt.hit, cnt.eval, cnt.bs, cnt.homog, cnt.skip, cnt.skipped};
+    const uint32_t vals[3] = {cnt.eval, cnt.bs, cnt.homog};
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
+    for (int q = 0; q < 3; ++q) {
       unsigned long long v = vals[q];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-      if (lane == 0) s_red[warp][q] += v;
+      if (lane == 0) s_red[warp][q + 1] += v;
     }
-    cnt = {0, 0, 0, 0, 0, 0};
+    cnt = {0, 0, 0};
   };
   Ray r;
-  int px = 0, py = 0, i = 0, lod = 0;
+  uint32_t pix = 0;    // py << 16 | px
+  int i = 0, lod = 0;
   float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
   uint32_t h = 0, n_eval = 0, n_bs = 0;
   NodeCache nc;
-  nc.d = -1;
+  nc.clear();
+  nc.jn[0] = nc.jn[1] = nc.jn[2] = 0;
+  nc.act = 0;
+  uint32_t wc_next = 0;   // next walk-cache entry to fill (warp-uniform)
   bool active = false, done = false;
   uint32_t cur_tile = 0xFFFFFFFFu, iters = 0;  // current tile and the loop iterations it took
 
@@ -443,6 +459,9 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
         const uint32_t pos = (uint32_t)(base >> 5), w = (uint32_t)lane;
         const uint32_t tile = a.order ? __ldg(a.order + pos) : pos;
         cur_tile = tile;
+        if (lane < kWalkCache) s_wc[lane * kWalkEntry] = 0u;   // a new tile (maybe a new view): forget the walks
+        wc_next = 0;
+        __syncwarp();
         if constexpr (BATCH) {
           // the view owning `tile`: last v with s_base[v] <= tile
           int lo = 0, hi = a.n_views - 1;
@@ -457,8 +476,10 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
           __syncwarp();
         }
         const uint32_t t = tile - V.tile_base;
-        px = (int)((t % V.tiles_x) * (uint32_t)tw + (w & (uint32_t)(tw - 1)));
-        py = (int)((t / V.tiles_x) * (uint32_t)(32 >> twl) + (w >> twl));
+        const int px = (int)((t % V.tiles_x) * (uint32_t)tw + (w & (uint32_t)(tw - 1)));
+        const int py = (int)((t / V.tiles_x) * (uint32_t)(32 >> twl) + (w >> twl));
+        pix = ((uint32_t)py << 16) | (uint32_t)px;
+        bool hit_now = false;
         if (px < V.W && py < V.H) {
           r = make_ray(g, V, px, py);
           i = 0;
@@ -467,14 +488,16 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
           T = 1.0f;
           h = 2166136261u;
           n_eval = n_bs = 0;
-          nc.d = -1;
+          nc.clear();
           if (r.hit) {
             active = true;
-            ++cnt.hit;
+            hit_now = true;
           } else {
-            write_pixel<BPV, DBG>(V, px, py, C0, C1, C2, T, h, n_eval, i, n_bs);
+            write_pixel<BPV, DBG>(V, pix, C0, C1, C2, T, h, n_eval, i, n_bs);
           }
         }
+        const unsigned hits = __ballot_sync(FULL, hit_now);
+        if (lane == 0) s_red[warp][0] += __popc(hits);
       }
     }
     if (__all_sync(FULL, done)) break;
@@ -489,7 +512,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
     if (active) {
       const float t = fmaf((float)i, V.dt, r.t0);
       if (i >= kMaxSamples || !(t < r.t1)) {
-        write_pixel<BPV, DBG>(V, px, py, C0, C1, C2, T, h, n_eval, i, n_bs);
+        write_pixel<BPV, DBG>(V, pix, C0, C1, C2, T, h, n_eval, i, n_bs);
         active = false;
       } else {
         position(g, r, t, x);
@@ -501,22 +524,48 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
         st = V.sdepth[lminu];
 #pragma unroll
         for (int q = 0; q < 3; ++q) L[q] = (int)(x[q] * pow2f(-g.leaf_log2[q]));
-        const bool same_levels = nc.d >= 0 && ldp == nc.ldp && st == nc.st;
+        const int ncd = nc.d();
+        const bool same_levels = ncd >= 0 && lod == nc.lod();
         if (same_levels) {
-          const int sh = g.D - nc.d;
+          const int sh = g.D - ncd;
           same_node = (L[0] >> sh) == nc.jn[0] && (L[1] >> sh) == nc.jn[1] && (L[2] >> sh) == nc.jn[2];
         }
-        need = !(same_node && nc.one_brick);
+        need = !(same_node && nc.one_brick());
+        // a walk another ray of this tile made for the same node and desired
+        // levels gives the same final node, states and selections (the node
+        // lies inside one brick of every usable level): take it instead
+        if (need) {
+#pragma unroll 1
+          for (int e = 0; e < kWalkCache; ++e) {
+            const uint4 hd = *reinterpret_cast<const uint4*>(s_wc + e * kWalkEntry);
+            if (!(hd.x & 1u) || (int)((hd.x >> 6) & 15u) != lod) continue;
+            const int ed = (int)((hd.x >> 1) & 31u), esh = g.D - ed;
+            if ((uint32_t)(L[0] >> esh) != hd.y || (uint32_t)(L[1] >> esh) != hd.z || (uint32_t)(L[2] >> esh) != hd.w)
+              continue;
+            const uint32_t eact = s_wc[e * kWalkEntry + 4];
+            for (uint32_t mm2 = eact; mm2; mm2 &= mm2 - 1u) {
+              const int c = __ffs(mm2) - 1;
+              my_sel[c * stride] = s_wc[e * kWalkEntry + 5 + c];
+            }
+            const int ef = (int)((hd.x >> 11) & 31u);
+            nc.set(ed, lod, ((hd.x >> 10) & 1u) != 0, true, ef == 31 ? 99 : ef, (hd.x >> 16) & 31u);
+            nc.jn[0] = (int)hd.y; nc.jn[1] = (int)hd.z; nc.jn[2] = (int)hd.w;
+            nc.act = eact;
+            need = false;
+            same_node = true;
+            break;
+          }
+        }
         // the walk (Sec. 6.1) resumes below the deepest ancestor shared with the
         // previous sample: those depths were found not all terminal
         const int d0 = V.start_depth < st ? V.start_depth : st;
         dstart = d0;
         if (same_node) {
-          dstart = nc.d;
+          dstart = ncd;
         } else if (same_levels) {
           int dca = 0;
-          for (int q = nc.d; q >= 0; --q) {
-            const int sh = g.D - q, up = nc.d - q;
+          for (int q = ncd; q >= 0; --q) {
+            const int sh = g.D - q, up = ncd - q;
             if ((L[0] >> sh) == (nc.jn[0] >> up) && (L[1] >> sh) == (nc.jn[1] >> up) &&
                 (L[2] >> sh) == (nc.jn[2] >> up)) {
               dca = q;
@@ -549,7 +598,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
                      ldp_hi = __shfl_sync(FULL, (uint32_t)(ldp >> 32), src);
       const uint64_t sldp = ((uint64_t)ldp_hi << 32) | ldp_lo;
       const int sst = __shfl_sync(FULL, st, src), sds = __shfl_sync(FULL, dstart, src),
-                slm = __shfl_sync(FULL, lminu, src);
+                slm = __shfl_sync(FULL, lminu, src), slod = __shfl_sync(FULL, lod, src);
       const bool ssame = __shfl_sync(FULL, (int)same_node, src) != 0;
       const bool cact = gact && ch < m;
       const int ld = cact ? (int)((sldp >> (4 * ch)) & 15) : 0;
@@ -703,6 +752,30 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
         const int other = __shfl_xor_sync(FULL, found, o);
         found = other < found ? other : found;
       }
+      // remember the walk for the tile's other rays when its node lies
+      // inside one brick of every usable level
+      {
+        const int esh = g.D - d;
+        const bool keep = gact && !gbad && g.leaf_log2[0] + esh <= g.blog2 + s_lt.lsh[slm][0] &&
+                          g.leaf_log2[1] + esh <= g.blog2 + s_lt.lsh[slm][1] &&
+                          g.leaf_log2[2] + esh <= g.blog2 + s_lt.lsh[slm][2];
+        const unsigned heads = __ballot_sync(FULL, keep && ch == 0);
+        // at most kWalkCache groups of a pass store, each in its own entry
+        const uint32_t rank = __popc(heads & ((1u << (grp * MP)) - 1u));
+        if (keep && rank < (uint32_t)kWalkCache) {
+          const uint32_t e = (wc_next + rank) % kWalkCache;
+          uint32_t* ent = s_wc + e * kWalkEntry;
+          if (cact) ent[5 + ch] = sel;
+          if (ch == 0) {
+            ent[1] = (uint32_t)jn0; ent[2] = (uint32_t)jn1; ent[3] = (uint32_t)jn2;
+            ent[4] = act;
+            ent[0] = 1u | ((uint32_t)d << 1) | ((uint32_t)slod << 6) | ((uint32_t)all_skip << 10) |
+                     ((uint32_t)(found == 99 ? 31 : found) << 11) | (nbrk << 16);
+          }
+        }
+        wc_next = (wc_next + min(__popc(heads), kWalkCache)) % kWalkCache;
+        __syncwarp();
+      }
       // hand the walk's result to the lanes it was for
       const bool mine = (taken >> lane) & 1u;
       const int from = mine ? __popc(taken & lt_mask) * MP : lane;
@@ -717,21 +790,16 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
       if (mine) {
         if (obad) {
           *a.err = kErrNodeIndex;
-          write_pixel<BPV, DBG>(V, px, py, C0, C1, C2, T, h, n_eval, i, n_bs);
+          write_pixel<BPV, DBG>(V, pix, C0, C1, C2, T, h, n_eval, i, n_bs);
           active = false;
         } else {
-          nc.d = od;
-          nc.jn[0] = oj0; nc.jn[1] = oj1; nc.jn[2] = oj2;
-          nc.ldp = ldp;
-          nc.st = st;
-          nc.all_skip = oskip;
-          nc.s_sel = osel;
-          nc.act = oact;
-          nc.n_brick = onb;
           const int esh = g.D - od;
-          nc.one_brick = g.leaf_log2[0] + esh <= g.blog2 + s_lt.lsh[lminu][0] &&
-                         g.leaf_log2[1] + esh <= g.blog2 + s_lt.lsh[lminu][1] &&
-                         g.leaf_log2[2] + esh <= g.blog2 + s_lt.lsh[lminu][2];
+          const bool ob = g.leaf_log2[0] + esh <= g.blog2 + s_lt.lsh[lminu][0] &&
+                          g.leaf_log2[1] + esh <= g.blog2 + s_lt.lsh[lminu][1] &&
+                          g.leaf_log2[2] + esh <= g.blog2 + s_lt.lsh[lminu][2];
+          nc.set(od, lod, oskip, ob, osel, onb);
+          nc.jn[0] = oj0; nc.jn[1] = oj1; nc.jn[2] = oj2;
+          nc.act = oact;
         }
       }
     }
@@ -739,11 +807,11 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
 
     // ----------------------------------------- phase 3: skip or evaluate
     if (!active) continue;
-    if (nc.all_skip && V.skip) {
+    if (nc.all_skip() && V.skip) {
       // first lattice index whose sample lies outside the node (Algorithm 1):
       // estimate from the node box's exit distance, then correct with the
       // same position arithmetic
-      const int d = nc.d;
+      const int d = nc.d();
       float tb = r.t1;
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
@@ -772,8 +840,8 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
         h = fnv_word(h, (uint32_t)d);
         h = fnv_word(h, (uint32_t)j);
       }
-      ++cnt.skip;
-      cnt.skipped += (uint32_t)(j - i);
+      atomicAdd(&s_red[warp][4], 1ull);
+      atomicAdd(&s_red[warp][5], (unsigned long long)(j - i));
       i = j;
       continue;
     }
@@ -781,12 +849,14 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
     // shade, composite front to back, stop early once transmittance is low
     // step exponent of the finest level read (or desired): the opacity
     // correction and the next lattice index use 2^s
-    const int s = s_lt.lstep[nc.s_sel == 99 ? lminu : nc.s_sel];
+    const int ssel = nc.s_sel();
+    const int s = s_lt.lstep[ssel == 99 ? lminu : ssel];
     float2 col01 = make_float2(0.0f, 0.0f);
     float col2 = 0.0f, trans = 1.0f;
-    cnt.bs += nc.n_brick;
-    cnt.homog += __popc(nc.act) - nc.n_brick;
-    n_bs += nc.n_brick;
+    const uint32_t nbk = nc.n_brick();
+    cnt.bs += nbk;
+    cnt.homog += __popc(nc.act) - nbk;
+    n_bs += nbk;
     // per channel: TF, opacity correction, additive colour (channel order)
     auto add = [&](int c, float val) {
       const float2 tf = s_tf[c];
@@ -859,7 +929,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
     ++n_eval;
     ++cnt.eval;
     if (T < V.ert) {
-      write_pixel<BPV, DBG>(V, px, py, C0, C1, C2, T, h, n_eval, i, n_bs);
+      write_pixel<BPV, DBG>(V, pix, C0, C1, C2, T, h, n_eval, i, n_bs);
       active = false;
       continue;
     }
