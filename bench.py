@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=16)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["cells16", "cells4", "blobs", "views64", "compensator", "leafsweep"],
+    ap.add_argument("--workload", choices=["cells16", "cells4", "blobs", "views64", "compensator", "leafsweep",
+                                           "stream"],
                     default="cells16")
     ap.add_argument("--pairs", type=int, default=200000, help="compensator: coarse/fine training pairs")
     ap.add_argument("--warm-seconds", type=float, default=150.0)
@@ -57,6 +58,8 @@ def parse():
     ap.add_argument("--warm-rounds", type=int, default=12, help="at most this many warm-up rounds over the orbit")
     ap.add_argument("--order", type=int, choices=[0, 1], default=0,
                     help="tile order of ro_render: 0 rows, 1 longest first by the previous frame's costs")
+    ap.add_argument("--overview", action="store_true",
+                    help="stream: the overview orbit (whole slab in view) instead of the close-up one")
     ap.add_argument("--precision", choices=["f32", "f16", "bf16"], default="f32",
                     help="brick sample format: raw values with binary32 lerps, or binary16 / bfloat16 samples")
     return ap.parse_args()
@@ -831,6 +834,143 @@ def run_leafsweep(args, rank, world, local_rank):
     return 0
 
 
+def run_stream(args, rank, world, local_rank):
+    """Out-of-core streaming (Sec. 4's ray-guided request -> upload loop) on
+    the 16-channel 4096x4096x96 procedural slab behind the 8 GiB cache, with
+    level bias 1.0 so that the close-up orbit's working set exceeds the cache
+    and steady frames miss.  A step: enqueue the render of frame f + 1, then
+    on the CPU make the bricks frame f requested (those not already
+    resident) into double-buffered page-locked memory while the GPU renders,
+    upload them with ro_upload_bricks_async (copy on a second stream, scatter
+    after the render), update the octree, read frame f + 1's requests.
+    Reports ms per frame, requests per frame, bricks and bytes streamed per
+    second, the copy engine's H2D rate, and a parity spot check of one frame
+    on the oracle's tile with the GPU's own residency."""
+    import torch
+    from paper_2309_04393_gb300 import loader, ro
+    from synth import recipes
+    torch.cuda.set_device(local_rank)
+    bias = 1.0 if args.lod_bias is None else args.lod_bias
+    scene = recipes.cells_large(arc_deg=args.arc, lod_bias=bias, close_up=not args.overview)
+    frames = scene.frames
+    W, H = frames[0].W, frames[0].H
+    slot_bytes = 34 ** 3 * 2
+    slots = int(args.cache_gib * GIB) // (((slot_bytes + 255) // 256) * 256)
+    max_up = 2048
+    desc = ro.make_desc(scene.dims, scene.spacing, scene.m, scene.value_bits, scene.B, scene.k, scene.leaf, slots,
+                        max_requests=1 << 16, max_upload=max_up, max_meta=1 << 20)
+    ctx = ro.Context(desc)
+    ctx.update_residency_octree(loader.meta_rows(scene.leaf_min, scene.leaf_max))
+    image = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    E = scene.B + 2
+    pinned = torch.empty((2, max_up, E, E, E), dtype=torch.int16, pin_memory=True)
+    bufs = [pinned[j].numpy().view(np.uint16) for j in range(2)]
+    copy_stream = torch.cuda.Stream()
+    resident = set()
+    stats = {"uploaded": 0, "requests": 0, "gen_s": 0.0, "copy_ms": 0.0, "bytes": 0}
+    nbuf = [0]
+
+    def stream_in(ids):
+        """Make and upload the requested bricks not yet resident."""
+        todo = np.array([i for i in ids.tolist() if i not in resident], np.uint32)
+        for q in range(0, todo.size, max_up):
+            chunk = todo[q:q + max_up]
+            buf = bufs[nbuf[0] % 2]
+            nbuf[0] += 1
+            t = time.perf_counter()
+            scene.cells.bricks_mixed(scene.B, decode_ids(chunk, scene.k), out=buf[:chunk.size])
+            stats["gen_s"] += time.perf_counter() - t
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(copy_stream)
+            sl, ev = ctx.upload_bricks_async(chunk, buf, copy_stream)
+            e1.record(copy_stream)
+            copy_events.append((e0, e1))
+            for i in chunk.tolist():
+                resident.add(i)
+            for e in ev.tolist():
+                if e != 0xFFFFFFFF:
+                    resident.discard(e)
+            stats["uploaded"] += int(chunk.size)
+            stats["bytes"] += int(chunk.size) * slot_bytes
+        ctx.update_residency_octree()
+
+    copy_events = []
+    # warm-up: a few steps of the same loop, untimed
+    ro.render_frame(ctx, frames[0], image)
+    ids, _, _ = ctx.read_requests()
+    fi = 1
+    t0 = time.time()
+    for _ in range(max(args.warmup, 3)):
+        ro.render_frame(ctx, frames[fi % len(frames)], image)
+        fi += 1
+        stream_in(ids)
+        ids, _, _ = ctx.read_requests()
+    log(f"  warm-up {time.time() - t0:.1f} s, {len(resident)} bricks resident of {slots} slots")
+    ctx.upload_wait()
+    torch.cuda.synchronize()
+    stats.update(uploaded=0, requests=0, gen_s=0.0, bytes=0)
+    copy_events.clear()
+    render_ev = []
+    clocks = Clocks(local_rank)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ro.render_frame(ctx, frames[fi % len(frames)], image)
+        b.record()
+        render_ev.append((a, b))
+        fi += 1
+        stats["requests"] += int(ids.size)
+        stream_in(ids)
+        ids, _, _ = ctx.read_requests()
+    ctx.upload_wait()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    render_ms = [a.elapsed_time(b) for a, b in render_ev]
+    copy_ms = sum(a.elapsed_time(b) for a, b in copy_events)
+    # counters of one more frame (untimed) and a parity spot check of it on
+    # the oracle's tile, with the page table's residency
+    f = frames[fi % len(frames)]
+    img, dbg = ro.render_frame(ctx, f, image, debug=True)
+    st = ctx.stats()
+    pt = ctx.debug_read(1)
+    req_flags = ctx.debug_read(3)          # every request of the frame (the list is cut at max_requests)
+    ctx.read_requests()
+    check = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        vol = oracle_volume_all_resident(scene)
+        vol.resident[:] = (pt != 0).astype(np.uint8)
+        r = oracle_rate(scene, f, min(args.cpu_seconds, 10.0), seed=3, vol=vol)
+        px = r["px"]
+        g_img = img.cpu().numpy()[px[:, 1], px[:, 0]]
+        g_hash = dbg[0].cpu().numpy().view(np.uint32)[px[:, 1], px[:, 0]]
+        o = r["out"]
+        check = {"tile_pixels": int(len(px)), "hash_equal": bool(np.array_equal(g_hash, o["hash"])),
+                 "rgba32_equal": bool(np.array_equal(g_img, o["rgba32"])),
+                 "oracle_requests_subset": bool(np.all(req_flags[np.nonzero(o["req"])[0]] != 0)),
+                 "max_abs_rgba_vs_f64": float(np.abs(g_img.astype(np.float64) - o["rgba64"]).max())}
+    n = args.steps
+    samples = int(st[1])
+    out = {"metric": "ms per streamed frame", "value": wall / n * 1000.0, "unit": "ms", "n_gpus": world,
+           "steps": n, "warmup": max(args.warmup, 3), "higher_is_better": False, "dtype": "f32",
+           "data": "synthetic (seeded procedural cells, bricks made on request on the host cores)",
+           "config": {"workload": f"stream: cells16 {'overview' if args.overview else 'close-up'} orbit, level bias "
+                                  f"{bias}, 8 GiB cache, 1920x1080", "cache_slots": slots, "lod_bias": bias,
+                      "orbit_arc_deg": args.arc, "max_upload": max_up},
+           "render_ms_avg": float(np.mean(render_ms)),
+           "requests_per_frame": stats["requests"] / n, "bricks_uploaded_per_frame": stats["uploaded"] / n,
+           "bricks_per_s": stats["uploaded"] / wall, "streamed_GB_per_s": stats["bytes"] / wall / 1e9,
+           "h2d_GB_per_s_copy_engine": (stats["bytes"] / (copy_ms / 1000.0) / 1e9) if copy_ms > 0 else None,
+           "host_brick_generation_s_per_frame": stats["gen_s"] / n,
+           "samples_last_frame": samples, "resident_bricks": len(resident),
+           "clocks": clk, "parity_spot_check": check}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -843,8 +983,8 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    run = {"views64": run_views, "compensator": run_compensator, "leafsweep": run_leafsweep}.get(args.workload,
-                                                                                                run_ours)
+    run = {"views64": run_views, "compensator": run_compensator, "leafsweep": run_leafsweep,
+           "stream": run_stream}.get(args.workload, run_ours)
     rc = run(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist

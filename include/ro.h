@@ -167,6 +167,26 @@ ro_status ro_destroy(ro_ctx* ctx);
 ro_status ro_upload_bricks(ro_ctx* ctx, uint32_t n, const uint32_t* brick_ids, const void* voxels,
                            uint32_t* out_slots, uint32_t* out_evicted);
 
+/* ro_upload_bricks with the host-to-device copy on copy_stream (a
+ * cudaStream_t), so that it can run while a render enqueued earlier on the
+ * context's stream is still running (Sec. 4: requested bricks stream in
+ * while the renderer goes on).  voxels must be page-locked host memory
+ * (cudaHostAlloc or registered) and stay unchanged until ro_upload_wait, or
+ * the next upload call, returns.  The copy waits for the previous upload's
+ * scatter (the staging area); the scatter into the cache and the page table
+ * runs on the context's stream after the copy and after everything enqueued
+ * there before this call, so a render never sees a slot change under it.
+ * Slots are chosen as by ro_upload_bricks, from the usage stamps of the last
+ * ro_read_requests; out_slots / out_evicted are filled before returning.
+ * The call itself does not wait for the GPU. */
+ro_status ro_upload_bricks_async(ro_ctx* ctx, uint32_t n, const uint32_t* brick_ids, const void* voxels,
+                                 uint32_t* out_slots, uint32_t* out_evicted, void* copy_stream);
+
+/* Waits (with the context's deadline) until the last asynchronous upload's
+ * copy has landed; its host buffer may then be reused.  RO_OK at once when
+ * none is pending. */
+ro_status ro_upload_wait(ro_ctx* ctx);
+
 /* Leaf metadata entry: raw value range of channel `channel` over leaf
  * `leaf` (x fastest over ceil(dims / leaf_extent) leaves per axis).  The
  * range must cover every level-0 voxel whose trilinear support reaches the

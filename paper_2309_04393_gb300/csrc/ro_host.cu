@@ -193,7 +193,7 @@ void make_layout(const ro_desc* d, const Geometry& g, Layout* L) {
   L->ba_tf = (uint64_t)ro::kMaxViews * sizeof(ro::ViewArgs);
   L->ba_order = align_up(L->ba_tf + (uint64_t)ro::kMaxC * 8, kAlign);
   L->ba_cost = align_up(L->ba_order + (uint64_t)d->max_batch_tiles * 4, kAlign);
-  s.batch = d->max_batch_tiles ? align_up(L->ba_cost + (uint64_t)d->max_batch_tiles * 4, kAlign) : 0;
+  s.batch = d->max_batch_tiles ? align_up(L->ba_cost + (uint64_t)d->max_batch_tiles * ro::kTileParts * 4, kAlign) : 0;
   const uint64_t parts[kParts] = {s.cache, s.page_table, s.octree, s.req_flags, s.node_req_flags, s.used_flags,
                                   s.last_used, s.staging, s.frame, s.lists, s.scratch, s.batch};
   uint64_t tot = 0;
@@ -221,6 +221,10 @@ struct ro_ctx {
   std::vector<uint32_t> brick_of_slot;   // slot -> page-table index or RO_NONE
   std::vector<uint32_t> free_slots;      // descending, pop_back gives the lowest
   std::vector<uint32_t> pending;         // page-table indices changed since the last update
+  std::vector<uint32_t> stamps;          // host copy of last_used (LRU), refreshed by ro_read_requests
+  cudaEvent_t ev_copy = nullptr;         // an async upload's copy into the staging area has landed
+  cudaEvent_t ev_scatter = nullptr;      // the last scatter has read the staging area
+  bool copy_pending = false;
   std::vector<float4> host_lut;
   // batches: device view table / TF ranges / schedule / tile costs in the
   // arena; pinned upload area [views | TF ranges | LUTs]; the captured graph
@@ -259,6 +263,19 @@ ro_status cuda_check(ro_ctx* c, cudaError_t e, const char* where) {
     ro_status _s = (expr);           \
     if (_s != RO_OK) return _s;      \
   } while (0)
+
+// Waits for an event against the context's deadline.
+ro_status wait_event(ro_ctx* c, cudaEvent_t ev, const char* where) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return RO_OK;
+    if (e != cudaErrorNotReady) return cuda_check(c, e, where);
+    const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+    if (ms > (long long)c->timeout_ms) return set_err(c, RO_ERR_TIMEOUT, std::string(where) + ": stream wait timed out");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
 
 ro_status wait_stream(ro_ctx* c, const char* where) {
   RO_TRY(cuda_check(c, cudaEventRecord(c->ev, c->stream), where));
@@ -394,7 +411,10 @@ ro_status ro_create(const ro_desc* desc, void* arena_device, uint64_t arena_byte
   c->free_slots.resize(desc->cache_slots);
   for (uint32_t i = 0; i < desc->cache_slots; ++i) c->free_slots[i] = desc->cache_slots - 1 - i;
   c->host_lut.resize((size_t)ro::kMaxC * 256);
+  c->stamps.assign(desc->cache_slots, 0u);
   cudaError_t e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_copy, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_scatter, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     g_create_error = std::string("cudaEventCreate: ") + cudaGetErrorString(e);
     delete c;
@@ -427,6 +447,8 @@ ro_status ro_destroy(ro_ctx* c) {
   ro_status s = RO_OK;
   if (c->latched == RO_OK) s = wait_stream(c, "ro_destroy");
   if (c->ev) cudaEventDestroy(c->ev);
+  if (c->ev_copy) cudaEventDestroy(c->ev_copy);
+  if (c->ev_scatter) cudaEventDestroy(c->ev_scatter);
   if (c->b_exec) cudaGraphExecDestroy(c->b_exec);
   if (c->b_graph) cudaGraphDestroy(c->b_graph);
   if (c->b_uploaded) cudaEventDestroy(c->b_uploaded);
@@ -474,7 +496,7 @@ ro_status check_ids(ro_ctx* c, uint32_t n, const uint32_t* ids, std::vector<uint
 // scatter kernel writes slots and page-table entries.
 template <class Fill>
 ro_status place_bricks(ro_ctx* c, uint32_t n, const std::vector<uint32_t>& pis, Fill fill, uint32_t* out_slots,
-                       uint32_t* out_evicted, const std::vector<uint32_t>* keep_slots = nullptr) {
+                       uint32_t* out_evicted, const std::vector<uint32_t>* keep_slots = nullptr, bool async = false) {
   // slot choice: keep resident bricks' slots, then free slots, then LRU
   std::vector<uint32_t> slots(n, RO_NONE), evicted(n, RO_NONE);
   std::vector<uint8_t> taken;  // slots assigned in this call
@@ -486,10 +508,9 @@ ro_status place_bricks(ro_ctx* c, uint32_t n, const std::vector<uint32_t>& pis, 
   const uint32_t from_free = std::min<uint32_t>(need, (uint32_t)c->free_slots.size());
   std::vector<uint32_t> lru;
   if (need > from_free) {
-    std::vector<uint32_t> stamps(c->desc.cache_slots);
-    RO_TRY(wait_stream(c, "ro_upload_bricks"));
-    RO_TRY(cuda_check(c, cudaMemcpy(stamps.data(), c->last_used, 4ull * c->desc.cache_slots, cudaMemcpyDeviceToHost),
-                      "ro_upload_bricks: last_used"));
+    // usage stamps as of the last ro_read_requests, fresh bricks stamped at
+    // their upload: no wait for the stream (a render may still be running)
+    const std::vector<uint32_t>& stamps = c->stamps;
     std::vector<uint8_t> keep(c->desc.cache_slots, 0);
     for (uint32_t i = 0; i < n; ++i)
       if (slots[i] != RO_NONE) keep[slots[i]] = 1;
@@ -530,6 +551,7 @@ ro_status place_bricks(ro_ctx* c, uint32_t n, const std::vector<uint32_t>& pis, 
     c->brick_of_slot[sl] = pis[i];
     c->slot_of_brick[pis[i]] = sl;
     c->pending.push_back(pis[i]);
+    c->stamps[sl] = c->frame;
   }
   cudaStream_t st = c->stream;
   RO_TRY(fill(st));
@@ -557,9 +579,13 @@ ro_status place_bricks(ro_ctx* c, uint32_t n, const std::vector<uint32_t>& pis, 
   a.sf = c->g.sf;
   a.bpv = c->g.bpv;
   a.n_el = c->g.edge * c->g.edge * c->g.edge;
+  a.last_used = c->last_used;
+  a.frame = c->frame;
   RO_TRY(cuda_check(c, ro::launch_scatter(a, st), "ro_upload_bricks: scatter"));
+  RO_TRY(cuda_check(c, cudaEventRecord(c->ev_scatter, st), "ro_upload_bricks: event"));
   // the caller's host buffers may be reused once the copies have landed
-  RO_TRY(wait_stream(c, "ro_upload_bricks"));
+  // (an asynchronous upload leaves that wait to ro_upload_wait)
+  if (!async) RO_TRY(wait_stream(c, "ro_upload_bricks"));
   if (out_slots) std::memcpy(out_slots, slots.data(), 4ull * n);
   if (out_evicted) std::memcpy(out_evicted, evicted.data(), 4ull * n);
   return RO_OK;
@@ -578,12 +604,47 @@ ro_status ro_upload_bricks(ro_ctx* c, uint32_t n, const uint32_t* ids, const voi
     return set_err(c, RO_ERR_CAPACITY, "ro_upload_bricks: n exceeds max_upload or cache_slots");
   std::vector<uint32_t> pis;
   RO_TRY(check_ids(c, n, ids, pis, "ro_upload_bricks"));
+  RO_TRY(ro_upload_wait(c));   // a previous asynchronous copy must not race this one
   auto fill = [&](cudaStream_t st) {
     const uint64_t bytes = (uint64_t)c->g.edge * c->g.edge * c->g.edge * c->g.bpv;
     return cuda_check(c, cudaMemcpy2DAsync(c->staging, c->g.slot_pitch, voxels, bytes, bytes, n, cudaMemcpyHostToDevice, st),
                       "ro_upload_bricks: voxels");
   };
   return place_bricks(c, n, pis, fill, out_slots, out_evicted);
+}
+
+ro_status ro_upload_bricks_async(ro_ctx* c, uint32_t n, const uint32_t* ids, const void* voxels, uint32_t* out_slots,
+                                 uint32_t* out_evicted, void* copy_stream) {
+  if (!c) return RO_ERR_INVALID_ARG;
+  if (c->latched != RO_OK) return c->latched;
+  if (n == 0) return RO_OK;
+  if (!ids || !voxels) return set_err(c, RO_ERR_INVALID_ARG, "ro_upload_bricks_async: null pointer");
+  if (n > c->desc.max_upload || n > c->desc.cache_slots)
+    return set_err(c, RO_ERR_CAPACITY, "ro_upload_bricks_async: n exceeds max_upload or cache_slots");
+  std::vector<uint32_t> pis;
+  RO_TRY(check_ids(c, n, ids, pis, "ro_upload_bricks_async"));
+  RO_TRY(ro_upload_wait(c));   // the previous call's host buffer and copy are done with
+  const cudaStream_t cs = static_cast<cudaStream_t>(copy_stream);
+  auto fill = [&](cudaStream_t st) {
+    const uint64_t bytes = (uint64_t)c->g.edge * c->g.edge * c->g.edge * c->g.bpv;
+    // the staging area is free once the previous scatter has read it
+    RO_TRY(cuda_check(c, cudaStreamWaitEvent(cs, c->ev_scatter, 0), "ro_upload_bricks_async: wait scatter"));
+    RO_TRY(cuda_check(c, cudaMemcpy2DAsync(c->staging, c->g.slot_pitch, voxels, bytes, bytes, n, cudaMemcpyHostToDevice, cs),
+                      "ro_upload_bricks_async: voxels"));
+    RO_TRY(cuda_check(c, cudaEventRecord(c->ev_copy, cs), "ro_upload_bricks_async: event"));
+    c->copy_pending = true;
+    return cuda_check(c, cudaStreamWaitEvent(st, c->ev_copy, 0), "ro_upload_bricks_async: wait copy");
+  };
+  return place_bricks(c, n, pis, fill, out_slots, out_evicted, nullptr, true);
+}
+
+ro_status ro_upload_wait(ro_ctx* c) {
+  if (!c) return RO_ERR_INVALID_ARG;
+  if (c->latched != RO_OK) return c->latched;
+  if (!c->copy_pending) return RO_OK;
+  RO_TRY(wait_event(c, c->ev_copy, "ro_upload_wait"));
+  c->copy_pending = false;
+  return RO_OK;
 }
 
 ro_status ro_compensate_bricks(ro_ctx* c, ro_mc* mc, uint32_t n, const uint32_t* ids, uint32_t* out_slots) {
@@ -916,18 +977,6 @@ void fill_common(ro_ctx* c, const ro_tf* tfs, ro::RenderArgs* a) {
   a->work = reinterpret_cast<unsigned long long*>(c->scratch + c->L.sc_work);
 }
 
-// Waits for an event against the context's deadline.
-ro_status wait_event(ro_ctx* c, cudaEvent_t ev, const char* where) {
-  const auto t0 = std::chrono::steady_clock::now();
-  for (;;) {
-    const cudaError_t e = cudaEventQuery(ev);
-    if (e == cudaSuccess) return RO_OK;
-    if (e != cudaErrorNotReady) return cuda_check(c, e, where);
-    const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
-    if (ms > (long long)c->timeout_ms) return set_err(c, RO_ERR_TIMEOUT, std::string(where) + ": stream wait timed out");
-    std::this_thread::sleep_for(std::chrono::microseconds(50));
-  }
-}
 
 }  // namespace
 
@@ -1187,6 +1236,11 @@ ro_status ro_read_requests(ro_ctx* c, uint32_t* ids, uint32_t cap, uint32_t* n, 
   // wait (with the deadline) before any copy into pageable host memory: such
   // a copy would itself block until the stream reaches it
   RO_TRY(wait_stream(c, "ro_read_requests"));
+  // the usage stamps the next uploads choose victims by (only needed once
+  // the cache is full)
+  if (c->free_slots.empty())
+    RO_TRY(cuda_check(c, cudaMemcpyAsync(c->stamps.data(), c->last_used, 4ull * c->desc.cache_slots,
+                                         cudaMemcpyDeviceToHost, st), "ro_read_requests: stamps"));
   uint32_t tot[2] = {0, 0};
   RO_TRY(cuda_check(c, cudaMemcpyAsync(tot, totals, 8, cudaMemcpyDeviceToHost, st), "ro_read_requests: totals"));
   const uint32_t nr = std::min({tot[0], cap, c->desc.max_requests});

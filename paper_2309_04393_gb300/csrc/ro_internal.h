@@ -17,7 +17,9 @@ constexpr int kRenderThreads = 640;   // persistent blocks, one per SM; rays are
 constexpr int kStats = 8;             // per-block counters of the render kernel
 constexpr int kWalkWin = 4;           // octree depths whose node words the walk loads at once
 constexpr int kTopWords = 10240;      // node words of the octree's top depths kept in shared memory (40 KB)
-constexpr int kWalkCache = 8;         // walk results a warp remembers for its tile
+constexpr int kWalkCache = 8;         // walk results a warp remembers (for the same view)
+constexpr int kRefillLanes = 32;      // lanes that take new rays together (32: the whole tile)
+constexpr int kTileParts = 32 / kRefillLanes;   // such bands per 32-pixel tile
 constexpr int kWalkEntry = 24;        // words per remembered walk (header 5 + 16 selections, padded)
 
 // Geometry derived once from the descriptor; copied by value into kernels.
@@ -93,7 +95,7 @@ struct RenderArgs {
   const ViewArgs* views;            // n_views views, tile_base ascending
   int n_views;
   const uint32_t* order;            // schedule position -> tile, or null for the identity
-  uint32_t* tile_cost;              // per tile: loop iterations its warp took (null = not recorded)
+  uint32_t* tile_cost;              // per tile part (tile * kTileParts + part): loop iterations (null = not recorded)
   const float2* tf_dev;             // batch: (lo, scale) per channel in device memory
 };
 
@@ -153,6 +155,8 @@ struct ScatterArgs {
   uint32_t* err;
   int sf, bpv;               // sample format; raw bytes per voxel in the staging area
   uint32_t n_el;             // voxels per brick ((B+2)^3)
+  uint32_t* last_used;       // usage stamps: an inserted brick's slot gets `frame`
+  uint32_t frame;
 };
 
 struct CompactArgs {

@@ -18,16 +18,22 @@ constexpr int kOrderThreads = 1024;
 constexpr int kOrderBuckets = 256;
 
 // One block: histogram of the buckets, offsets from the most expensive
-// bucket down, then every tile placed at its bucket's next position.  The
-// order within a bucket is whatever the shared-memory counters give: any
-// order renders the same images, only the launch's tail changes.
+// bucket down, then every tile placed at its bucket's next position.  A
+// tile's cost is the sum over its parts (the bands of rows warps refill
+// with).  The order within a bucket is whatever the shared-memory counters
+// give: any order renders the same images, only the launch's tail changes.
 __global__ void __launch_bounds__(kOrderThreads) cost_order_kernel(const uint32_t* __restrict__ cost, uint32_t n,
                                                                   uint32_t* __restrict__ order) {
   __shared__ uint32_t s_hist[kOrderBuckets];
   __shared__ uint32_t s_off[kOrderBuckets];
   for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) s_hist[b] = 0;
   __syncthreads();
-  for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) atomicAdd(&s_hist[cost_bucket(__ldg(cost + t))], 1u);
+  auto tile_cost = [&](uint32_t t) {
+    uint32_t c = 0;
+    for (int p = 0; p < kTileParts; ++p) c += __ldg(cost + (size_t)t * kTileParts + p);
+    return c;
+  };
+  for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) atomicAdd(&s_hist[cost_bucket(tile_cost(t))], 1u);
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t run = 0;
@@ -38,7 +44,7 @@ __global__ void __launch_bounds__(kOrderThreads) cost_order_kernel(const uint32_
   }
   __syncthreads();
   for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
-    const uint32_t pos = atomicAdd(&s_off[cost_bucket(__ldg(cost + t))], 1u);
+    const uint32_t pos = atomicAdd(&s_off[cost_bucket(tile_cost(t))], 1u);
     order[pos] = t;
   }
 }

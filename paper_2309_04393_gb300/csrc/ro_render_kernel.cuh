@@ -385,18 +385,20 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
   for (int q = threadIdx.x; q < 3 * k; q += blockDim.x) s_nb[q / 3][q % 3] = g.nb[q / 3][q % 3];
   // the octree's top depths (those whose words fit kTopWords) in shared memory
   uint32_t* s_top = s_sel + MP * kRenderThreads;
-  // per warp: the last kWalkCache walk results of its tile (see phase 1)
+  // per warp: the last kWalkCache walk results (see phase 1), none yet
   uint32_t* s_wc = s_top + kTopWords + (threadIdx.x >> 5) * (kWalkCache * kWalkEntry);
+  if ((threadIdx.x & 31) < kWalkCache) s_wc[(threadIdx.x & 31) * kWalkEntry] = 0u;
   int top_d = -1;
   while (top_d < g.D && g.node_off[top_d + 2] * MP <= (uint64_t)kTopWords) ++top_d;
   const uint32_t n_top = top_d >= 0 ? (uint32_t)(g.node_off[top_d + 1] * MP) : 0u;
   for (uint32_t q = threadIdx.x; q < n_top; q += blockDim.x) s_top[q] = __ldg(a.octree + q);
-  __shared__ unsigned long long s_red[kRenderThreads / 32][kStats];
-  for (int q = threadIdx.x; q < kRenderThreads / 32 * kStats; q += blockDim.x) (&s_red[0][0])[q] = 0;
+  constexpr int kUnits = 32 / kRefillLanes;       // refill units per warp
+  __shared__ unsigned long long s_red[kRenderThreads / 32 * kUnits][kStats];
+  for (int q = threadIdx.x; q < kRenderThreads / 32 * kUnits * kStats; q += blockDim.x) (&s_red[0][0])[q] = 0;
   // batch: first tile of every view (view v owns [s_base[v], s_base[v + 1]))
   // and the current view of each warp
   __shared__ uint32_t s_base[BATCH ? kMaxViews + 1 : 1];
-  __shared__ ViewArgs s_view[BATCH ? kRenderThreads / 32 : 1];
+  __shared__ ViewArgs s_view[BATCH ? kRenderThreads / 32 * kUnits : 1];
   if constexpr (BATCH) {
     for (int q = threadIdx.x; q < a.n_views; q += blockDim.x) s_base[q] = a.views[q].tile_base;
     if (threadIdx.x == 0) s_base[a.n_views] = (uint32_t)(a.n_rays >> 5);
@@ -410,7 +412,13 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int stride = blockDim.x;
   uint32_t* my_sel = s_sel + threadIdx.x;
-  const ViewArgs& V = view_of<BATCH>(a, &s_view[BATCH ? warp : 0]);
+  // a warp refills in units of kRefillLanes lanes: each unit takes the next
+  // kRefillLanes rays of a tile (a band of whole tile rows) once all its
+  // lanes are free, so that its rays stay neighbours
+  const int unit = lane / kRefillLanes, ulane = lane % kRefillLanes;
+  const unsigned umask = (kRefillLanes == 32 ? FULL : ((1u << kRefillLanes) - 1u)) << (unit * kRefillLanes);
+  const int row = warp * kUnits + unit;            // this unit's statistics row / view copy
+  const ViewArgs& V = view_of<BATCH>(a, &s_view[BATCH ? row : 0]);
   const int twl = a.tile_wlog2, tw = 1 << twl;
   constexpr int G = 32 / MP;                       // rays walked per cooperative pass
   const int grp = lane / MP, ch = lane % MP;
@@ -418,14 +426,15 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
   const unsigned lt_mask = (1u << lane) - 1u;
 
   Counters cnt = {0, 0, 0};
+  // adds the unit's counters to its row (all lanes of the unit call it)
   auto flush = [&]() {
     const uint32_t vals[3] = {cnt.eval, cnt.bs, cnt.homog};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       unsigned long long v = vals[q];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-      if (lane == 0) s_red[warp][q + 1] += v;
+      for (int o = kRefillLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(umask, v, o);
+      if (ulane == 0) s_red[row][q + 1] += v;
     }
     cnt = {0, 0, 0};
   };
@@ -440,65 +449,69 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
   nc.act = 0;
   uint32_t wc_next = 0;   // next walk-cache entry to fill (warp-uniform)
   bool active = false, done = false;
-  uint32_t cur_tile = 0xFFFFFFFFu, iters = 0;  // current tile and the loop iterations it took
+  uint32_t cur_tile = 0xFFFFFFFFu, iters = 0;  // current tile part (tile * kUnits + part) and its loop iterations
+  uint32_t vid = 0;                            // the view of the current rays (batch)
 
   for (;;) {
     // ------------------------------------------------------------- refill
     const unsigned busy = __ballot_sync(FULL, active);
-    if (!busy && !done) {
-      flush();
-      if (a.tile_cost && lane == 0 && cur_tile != 0xFFFFFFFFu) a.tile_cost[cur_tile] = iters;
-      iters = 0;
-      unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(a.work, 32ull);
-      base = __shfl_sync(FULL, base, 0);
-      if (base >= a.n_rays) {
-        done = true;
-        cur_tile = 0xFFFFFFFFu;
-      } else {
-        const uint32_t pos = (uint32_t)(base >> 5), w = (uint32_t)lane;
-        const uint32_t tile = a.order ? __ldg(a.order + pos) : pos;
-        cur_tile = tile;
-        if (lane < kWalkCache) s_wc[lane * kWalkEntry] = 0u;   // a new tile (maybe a new view): forget the walks
-        wc_next = 0;
-        __syncwarp();
-        if constexpr (BATCH) {
-          // the view owning `tile`: last v with s_base[v] <= tile
-          int lo = 0, hi = a.n_views - 1;
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_base[mid] <= tile) lo = mid;
-            else hi = mid - 1;
+    const bool unit_free = (busy & umask) == 0 && !done;
+    if (__any_sync(FULL, unit_free)) {
+      if (unit_free) {
+        flush();
+        if (a.tile_cost && ulane == 0 && cur_tile != 0xFFFFFFFFu) a.tile_cost[cur_tile] = iters;
+        iters = 0;
+        unsigned long long base = 0;
+        if (ulane == 0) base = atomicAdd(a.work, (unsigned long long)kRefillLanes);
+        base = __shfl_sync(umask, base, unit * kRefillLanes);
+        if (base >= a.n_rays) {
+          done = true;
+          cur_tile = 0xFFFFFFFFu;
+        } else {
+          const uint32_t pos = (uint32_t)(base >> 5), part = (uint32_t)(base & 31u) / kRefillLanes;
+          const uint32_t w = part * kRefillLanes + (uint32_t)ulane;   // ray of the tile
+          const uint32_t tile = a.order ? __ldg(a.order + pos) : pos;
+          cur_tile = tile * kUnits + part;
+          if constexpr (BATCH) {
+            // the view owning `tile`: last v with s_base[v] <= tile
+            int lo = 0, hi = a.n_views - 1;
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if (s_base[mid] <= tile) lo = mid;
+              else hi = mid - 1;
+            }
+            vid = (uint32_t)lo;
+            const uint4* srcv = reinterpret_cast<const uint4*>(a.views + lo);
+            uint4* dstv = reinterpret_cast<uint4*>(&s_view[row]);
+            for (int q = ulane; q < (int)(sizeof(ViewArgs) / 16); q += kRefillLanes) dstv[q] = __ldg(srcv + q);
+            __syncwarp(umask);
           }
-          const uint4* srcv = reinterpret_cast<const uint4*>(a.views + lo);
-          uint4* dstv = reinterpret_cast<uint4*>(&s_view[warp]);
-          for (int q = lane; q < (int)(sizeof(ViewArgs) / 16); q += 32) dstv[q] = __ldg(srcv + q);
-          __syncwarp();
-        }
-        const uint32_t t = tile - V.tile_base;
-        const int px = (int)((t % V.tiles_x) * (uint32_t)tw + (w & (uint32_t)(tw - 1)));
-        const int py = (int)((t / V.tiles_x) * (uint32_t)(32 >> twl) + (w >> twl));
-        pix = ((uint32_t)py << 16) | (uint32_t)px;
-        bool hit_now = false;
-        if (px < V.W && py < V.H) {
-          r = make_ray(g, V, px, py);
-          i = 0;
-          lod = 0;
-          C0 = C1 = C2 = 0.0f;
-          T = 1.0f;
-          h = 2166136261u;
-          n_eval = n_bs = 0;
-          nc.clear();
-          if (r.hit) {
-            active = true;
-            hit_now = true;
-          } else {
-            write_pixel<BPV, DBG>(V, pix, C0, C1, C2, T, h, n_eval, i, n_bs);
+          const uint32_t t = tile - V.tile_base;
+          const int px = (int)((t % V.tiles_x) * (uint32_t)tw + (w & (uint32_t)(tw - 1)));
+          const int py = (int)((t / V.tiles_x) * (uint32_t)(32 >> twl) + (w >> twl));
+          pix = ((uint32_t)py << 16) | (uint32_t)px;
+          bool hit_now = false;
+          if (px < V.W && py < V.H) {
+            r = make_ray(g, V, px, py);
+            i = 0;
+            lod = 0;
+            C0 = C1 = C2 = 0.0f;
+            T = 1.0f;
+            h = 2166136261u;
+            n_eval = n_bs = 0;
+            nc.clear();
+            if (r.hit) {
+              active = true;
+              hit_now = true;
+            } else {
+              write_pixel<BPV, DBG>(V, pix, C0, C1, C2, T, h, n_eval, i, n_bs);
+            }
           }
+          const unsigned hits = __ballot_sync(umask, hit_now);
+          if (ulane == 0) s_red[row][0] += __popc(hits);
         }
-        const unsigned hits = __ballot_sync(FULL, hit_now);
-        if (lane == 0) s_red[warp][0] += __popc(hits);
       }
+      __syncwarp();
     }
     if (__all_sync(FULL, done)) break;
     ++iters;
@@ -538,7 +551,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
 #pragma unroll 1
           for (int e = 0; e < kWalkCache; ++e) {
             const uint4 hd = *reinterpret_cast<const uint4*>(s_wc + e * kWalkEntry);
-            if (!(hd.x & 1u) || (int)((hd.x >> 6) & 15u) != lod) continue;
+            if (!(hd.x & 1u) || (int)((hd.x >> 6) & 15u) != lod || (hd.x >> 21) != vid) continue;
             const int ed = (int)((hd.x >> 1) & 31u), esh = g.D - ed;
             if ((uint32_t)(L[0] >> esh) != hd.y || (uint32_t)(L[1] >> esh) != hd.z || (uint32_t)(L[2] >> esh) != hd.w)
               continue;
@@ -599,6 +612,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
       const uint64_t sldp = ((uint64_t)ldp_hi << 32) | ldp_lo;
       const int sst = __shfl_sync(FULL, st, src), sds = __shfl_sync(FULL, dstart, src),
                 slm = __shfl_sync(FULL, lminu, src), slod = __shfl_sync(FULL, lod, src);
+      const uint32_t svid = BATCH ? __shfl_sync(FULL, vid, src) : 0u;
       const bool ssame = __shfl_sync(FULL, (int)same_node, src) != 0;
       const bool cact = gact && ch < m;
       const int ld = cact ? (int)((sldp >> (4 * ch)) & 15) : 0;
@@ -770,7 +784,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
             ent[1] = (uint32_t)jn0; ent[2] = (uint32_t)jn1; ent[3] = (uint32_t)jn2;
             ent[4] = act;
             ent[0] = 1u | ((uint32_t)d << 1) | ((uint32_t)slod << 6) | ((uint32_t)all_skip << 10) |
-                     ((uint32_t)(found == 99 ? 31 : found) << 11) | (nbrk << 16);
+                     ((uint32_t)(found == 99 ? 31 : found) << 11) | (nbrk << 16) | (svid << 21);
           }
         }
         wc_next = (wc_next + min(__popc(heads), kWalkCache)) % kWalkCache;
@@ -941,7 +955,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
   __syncthreads();
   if (threadIdx.x < kStats) {
     unsigned long long v = 0;
-    for (int q = 0; q < kRenderThreads / 32; ++q) v += s_red[q][threadIdx.x];
+    for (int q = 0; q < kRenderThreads / 32 * kUnits; ++q) v += s_red[q][threadIdx.x];
     a.block_stats[(size_t)blockIdx.x * kStats + threadIdx.x] = v;
   }
 }

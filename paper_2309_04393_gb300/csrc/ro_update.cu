@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(const __grid_constant__ Sc
       const uint32_t pi = a.ins_index[b];
       if (pi >= a.n_bricks) *a.err = kErrPageIndex;
       else a.pt[pi] = slot + 1;
+      a.last_used[slot] = a.frame;   // a fresh brick counts as used now (LRU)
     }
   } else {
     const uint32_t e = b - a.n_ins;

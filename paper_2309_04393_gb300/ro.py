@@ -24,7 +24,7 @@ STATUS = {0: "RO_OK", 1: "RO_ERR_INVALID_ARG", 2: "RO_ERR_CUDA", 3: "RO_ERR_CAPA
 EXPORTS = ["ro_query_sizes", "ro_create", "ro_destroy", "ro_upload_bricks", "ro_update_residency_octree", "ro_render",
            "ro_read_requests", "ro_get_stats", "ro_debug_read", "ro_brick_index", "ro_set_timeout", "ro_last_error",
            "ro_compact_flags_noalloc", "ro_render_batch", "ro_autotune_batch", "ro_replace_channel",
-           "ro_update_node_metadata"]
+           "ro_update_node_metadata", "ro_upload_bricks_async", "ro_upload_wait"]
 RO_UNKNOWN_DEPTH = 254
 
 
@@ -104,6 +104,8 @@ def load(build_if_missing: bool = True):
     L.ro_create.argtypes = [ctypes.POINTER(Desc), vp, u64, vp, ctypes.POINTER(vp)]
     L.ro_destroy.argtypes = [vp]
     L.ro_upload_bricks.argtypes = [vp, u32, vp, vp, vp, vp]
+    L.ro_upload_bricks_async.argtypes = [vp, u32, vp, vp, vp, vp, vp]
+    L.ro_upload_wait.argtypes = [vp]
     L.ro_update_residency_octree.argtypes = [vp, u32, vp]
     L.ro_update_node_metadata.argtypes = [vp, u32, vp]
     L.ro_render.argtypes = [vp, ctypes.POINTER(Camera), vp, ctypes.POINTER(RenderParams), vp, u32, u32]
@@ -213,6 +215,22 @@ class Context:
         evicted = np.zeros(n, np.uint32)
         self._check(self.L.ro_upload_bricks(self.h, n, _ptr(ids), _ptr(voxels), _ptr(slots), _ptr(evicted)))
         return slots, evicted
+
+    def upload_bricks_async(self, ids, voxels, copy_stream):
+        """ro_upload_bricks_async: voxels a page-locked CPU tensor (or a view
+        of one: a numpy array over pinned memory), kept unchanged until
+        upload_wait(); copy_stream a torch.cuda.Stream."""
+        ids = np.ascontiguousarray(np.asarray(ids, np.uint32))
+        n = ids.size
+        slots = np.zeros(n, np.uint32)
+        evicted = np.zeros(n, np.uint32)
+        ptr = voxels.data_ptr() if hasattr(voxels, "data_ptr") else voxels.ctypes.data
+        self._check(self.L.ro_upload_bricks_async(self.h, n, _ptr(ids), ctypes.c_void_p(ptr), _ptr(slots),
+                                                  _ptr(evicted), ctypes.c_void_p(copy_stream.cuda_stream)))
+        return slots, evicted
+
+    def upload_wait(self):
+        self._check(self.L.ro_upload_wait(self.h))
 
     def update_residency_octree(self, meta=None):
         """meta: (n, 4) uint32 rows (leaf, channel, vmin, vmax) or None."""
