@@ -15,7 +15,7 @@ constexpr int kMaxDepth = 24;   // octree depth bound (2^24 leaves per axis)
 constexpr int kMaxSamples = 1 << 24;  // lattice indices stay exact in binary32
 constexpr int kRenderThreads = 640;   // persistent blocks, one per SM; rays are taken in 8 x 4 pixel tiles
 constexpr int kStats = 8;             // per-block counters of the render kernel
-constexpr int kWalkWin = 4;           // octree depths whose node words the walk loads at once
+constexpr int kWalkWin = 2;           // octree depths whose node words the walk loads at once
 constexpr int kTopWords = 10240;      // node words of the octree's top depths kept in shared memory (40 KB)
 constexpr int kWalkCache = 8;         // walk results a warp remembers (for the same view)
 constexpr int kRefillLanes = 32;      // lanes that take new rays together (32: the whole tile)

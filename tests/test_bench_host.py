@@ -40,10 +40,14 @@ def test_traffic_record_only_for_its_workload():
         workload, image, cache_gib, arc, lod_bias, radius, precision, order = \
             "cells16", None, 8.0, 30.0, None, None, "f32", rec.get("order", 0)
 
-    want = int(rec["dram_read_bytes_per_launch"]) + int(rec["dram_write_bytes_per_launch"])
-    got = bench.recorded_traffic(Args())
+    chan = 3.0e9
+    want = int(round(float(rec["dram_bytes_per_channel_sample"]) * chan))
+    got = bench.recorded_traffic(Args(), chan)
     assert got == (want if current == rec["code_sha256"] else None)
+    # the record's own launch scales back to its own bytes
+    own = (int(rec["dram_read_bytes"]) + int(rec["dram_write_bytes"])) / float(rec["channel_samples"])
+    assert abs(own - float(rec["dram_bytes_per_channel_sample"])) <= 1e-9 * own
     for field, value in (("precision", "f16"), ("image", "960x540"), ("workload", "views64"), ("cache_gib", 1.5)):
         a = Args()
         setattr(a, field, value)
-        assert bench.recorded_traffic(a) is None
+        assert bench.recorded_traffic(a, chan) is None
