@@ -13,7 +13,10 @@ constexpr int kMaxC = 16;       // channels per context (RO_MAX_CHANNELS)
 constexpr int kMaxL = 16;       // levels per context (RO_MAX_LEVELS)
 constexpr int kMaxDepth = 24;   // octree depth bound (2^24 leaves per axis)
 constexpr int kMaxSamples = 1 << 24;  // lattice indices stay exact in binary32
-constexpr int kRenderThreads = 640;   // persistent blocks, one per SM; rays are taken in 8 x 4 pixel tiles
+// threads of a persistent render block (one per SM; rays are taken in 8 x 4
+// pixel tiles): a single-view launch and a batch launch, whose per-warp view
+// copies and view index need more registers
+__host__ __device__ constexpr int render_threads(bool batch) { return batch ? 768 : 896; }
 constexpr int kStats = 8;             // per-block counters of the render kernel
 constexpr int kWalkWin = 2;           // octree depths whose node words the walk loads at once
 constexpr int kTopWords = 10240;      // node words of the octree's top depths kept in shared memory (40 KB)
@@ -206,7 +209,7 @@ cudaError_t launch_pointer_depth(const UpdateArgs& a, cudaStream_t s); // INVALI
 cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
 cudaError_t launch_usage(const UsageArgs& a, cudaStream_t s);
 
-size_t render_smem_bytes(int mp);
+size_t render_smem_bytes(int mp, bool batch);
 
 // Compensator entry points used by ro_compensate_bricks: the batch limit,
 // and the synthesis of n level-0 apron slots (u16 raw values at out_pitch)

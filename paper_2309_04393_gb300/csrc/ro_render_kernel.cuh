@@ -20,6 +20,20 @@ namespace {
 
 enum : int { kEmpty = 0, kHomog = 1, kUnmapped = 2, kBrick = 3, kInvalid = 4 };
 
+// bit budgets of the packed warp shuffles below
+static_assert(kMaxC <= 16, "a channel set fits 16 bits");
+static_assert(kMaxDepth < 31, "depth 31 marks an out-of-range node");
+static_assert(kMaxViews <= (1 << 13), "a view index fits 13 bits");
+
+// 2^23 + v for an integer 0 <= v < 2^23, exactly: v in the significand of 2^23
+__device__ __forceinline__ float biased(uint32_t v) { return __uint_as_float(0x4B000000u | v); }
+
+// floor(x * 2^e) for 0 <= x * 2^e < 2^23 (the product is exact): the sum
+// x * 2^e + 2^23 rounded down is 2^23 + floor(x * 2^e), whose low bits are it
+__device__ __forceinline__ int floor_scaled(float x, float p2) {
+  return __float_as_int(__fmaf_rd(x, p2, 8388608.0f)) - 0x4B000000;
+}
+
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
 
 __device__ __forceinline__ uint32_t fnv_word(uint32_t h, uint32_t w) {
@@ -122,7 +136,7 @@ __device__ __forceinline__ void position(const Geometry& g, const Ray& r, float 
 
 __device__ __forceinline__ void node_coords(const Geometry& g, int d, const float (&x)[3], int (&j)[3]) {
 #pragma unroll
-  for (int k = 0; k < 3; ++k) j[k] = (int)(x[k] * pow2f(-(g.leaf_log2[k] + g.D - d)));
+  for (int k = 0; k < 3; ++k) j[k] = floor_scaled(x[k], pow2f(-(g.leaf_log2[k] + g.D - d)));
 }
 
 // Trilinear sample of a level-l apron slot, in two parts: the
@@ -187,9 +201,10 @@ __device__ __forceinline__ void tri_coords(const Geometry& g, const LevelTabs& l
     const float xl = x[k] * pow2f(-sh);
     float u = xl - 0.5f;
     u = fminf(fmaxf(u, 0.0f), lt.ldimf[l][k]);
-    const int i0 = (int)u;
-    tc.f[k] = u - (float)i0;
-    const int b = (int)(x[k] * pow2f(-(g.blog2 + sh)));
+    const float tu = __fadd_rd(u, 8388608.0f);      // 2^23 + floor(u), u >= 0
+    const int i0 = __float_as_int(tu) - 0x4B000000;
+    tc.f[k] = u - (tu - 8388608.0f);
+    const int b = floor_scaled(x[k], pow2f(-(g.blog2 + sh)));
     li[k] = i0 - (b * g.B - 1);
   }
   tc.idx = (li[2] * E + li[1]) * E + li[0];
@@ -245,14 +260,16 @@ __device__ __forceinline__ float tri_lerp(const uint32_t (&r)[8], const TriCoord
     const typename F::T c = __hfma(f2, __hsub(c1, c0), c0);
     return F::to_float(c) * (BPV == 1 ? 256.0f : 65536.0f);
   } else {
-    float v[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = (float)r[q];
+    // the corners as binary32 values (exact): the lower corners a = A - 2^23
+    // from their biased forms A = 2^23 + a, and the differences b - a = B - A
+    // (exact: both sides are integers below 2^16)
     const float2 f0 = make_float2(tc.f[0], tc.f[0]), f1 = make_float2(tc.f[1], tc.f[1]);
-    const float2 a0 = make_float2(v[0], v[2]), b0 = make_float2(v[1], v[3]);
-    const float2 a1 = make_float2(v[4], v[6]), b1 = make_float2(v[5], v[7]);
-    const float2 cx0 = __ffma2_rn(f0, sub2(b0, a0), a0);   // (c00, c10)
-    const float2 cx1 = __ffma2_rn(f0, sub2(b1, a1), a1);   // (c01, c11)
+    const float2 A0 = make_float2(biased(r[0]), biased(r[2])), B0 = make_float2(biased(r[1]), biased(r[3]));
+    const float2 A1 = make_float2(biased(r[4]), biased(r[6])), B1 = make_float2(biased(r[5]), biased(r[7]));
+    const float2 m23 = make_float2(-8388608.0f, -8388608.0f);
+    const float2 a0 = __fadd2_rn(A0, m23), a1 = __fadd2_rn(A1, m23);
+    const float2 cx0 = __ffma2_rn(f0, sub2(B0, A0), a0);   // (c00, c10)
+    const float2 cx1 = __ffma2_rn(f0, sub2(B1, A1), a1);   // (c01, c11)
     const float2 ya = make_float2(cx0.x, cx1.x), yb = make_float2(cx0.y, cx1.y);
     const float2 cy = __ffma2_rn(f1, sub2(yb, ya), ya);    // (c0, c1)
     return fmaf(tc.f[2], cy.y - cy.x, cy.x);
@@ -267,9 +284,10 @@ __device__ __forceinline__ float tri_lerp(const uint32_t (&r)[8], const TriCoord
 __device__ __forceinline__ void shade(const float4* __restrict__ lut, float xq, int s, float& q, float2& rg,
                                       float& b) {
   xq = fminf(fmaxf(xq, 0.0f), 255.0f);
-  int j = (int)xq;
-  j = j > 254 ? 254 : j;
-  const float fr = xq - (float)j;
+  // j = min(floor(xq), 254) as 2^23 + j: the sum rounded down is exact
+  const float tj = fminf(__fadd_rd(xq, 8388608.0f), 8388862.0f);
+  const int j = __float_as_int(tj) - 0x4B000000;
+  const float fr = xq - (tj - 8388608.0f);
   const float4 L0 = lut[j], L1 = lut[j + 1];
   const float2 ff = make_float2(fr, fr);
   const float2 lrg = make_float2(L0.x, L0.y), lba = make_float2(L0.z, L0.w);
@@ -314,10 +332,11 @@ constexpr uint32_t kSelNone = 0xFFFFFFFFu;
 constexpr uint32_t kSelHomog = 30u;
 constexpr uint32_t kSelMask = (1u << 27) - 1u;
 
-// Per-thread counters of the current tile (a ray's counts stay below 2^28);
-// at every refill the warp adds them to its own 64-bit row in shared memory.
+// Per-thread counters of the current ray (its counts stay below 2^28): the
+// evaluated samples and brick reads are the ray's own n_eval and n_bs; at
+// every refill the unit adds them to its 64-bit row in shared memory.
 struct Counters {
-  uint32_t eval, bs, homog;   // rays hit and skips go straight to the warp's shared row
+  uint32_t homog;   // rays hit and skips go straight to the warp's shared row
 };
 
 template <int BPV, bool DBG>
@@ -352,7 +371,7 @@ __device__ __forceinline__ const ViewArgs& view_of(const RenderArgs& a, const Vi
 }
 
 template <int MP, int BPV, int EC, bool DBG, bool BATCH, int SF>
-__global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_constant__ RenderArgs a) {
+__global__ void __launch_bounds__(render_threads(BATCH), 1) render_kernel(const __grid_constant__ RenderArgs a) {
   extern __shared__ float4 smem[];
   float4* s_lut = smem;
   uint16_t* s_pre = reinterpret_cast<uint16_t*>(s_lut + MP * 256);
@@ -384,21 +403,34 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
   for (int q = threadIdx.x; q < 3 * (g.D + 1); q += blockDim.x) s_nn[q / 3][q % 3] = g.nn[q / 3][q % 3];
   for (int q = threadIdx.x; q < 3 * k; q += blockDim.x) s_nb[q / 3][q % 3] = g.nb[q / 3][q % 3];
   // the octree's top depths (those whose words fit kTopWords) in shared memory
-  uint32_t* s_top = s_sel + MP * kRenderThreads;
+  constexpr int kThreads = render_threads(BATCH);
+  uint32_t* s_top = s_sel + MP * kThreads;
   // per warp: the last kWalkCache walk results (see phase 1), none yet
   uint32_t* s_wc = s_top + kTopWords + (threadIdx.x >> 5) * (kWalkCache * kWalkEntry);
   if ((threadIdx.x & 31) < kWalkCache) s_wc[(threadIdx.x & 31) * kWalkEntry] = 0u;
+  // per thread: its current ray (origin, t0; direction, t1), kept in shared
+  // memory rather than registers
+  float4* s_ray = reinterpret_cast<float4*>(s_top + kTopWords + (kThreads / 32) * kWalkCache * kWalkEntry) +
+                  2 * threadIdx.x;
+  auto ray_get = [&]() {
+    const float4 u = s_ray[0], v = s_ray[1];
+    Ray q;
+    q.o[0] = u.x; q.o[1] = u.y; q.o[2] = u.z; q.t0 = u.w;
+    q.d[0] = v.x; q.d[1] = v.y; q.d[2] = v.z; q.t1 = v.w;
+    q.hit = true;
+    return q;
+  };
   int top_d = -1;
   while (top_d < g.D && g.node_off[top_d + 2] * MP <= (uint64_t)kTopWords) ++top_d;
   const uint32_t n_top = top_d >= 0 ? (uint32_t)(g.node_off[top_d + 1] * MP) : 0u;
   for (uint32_t q = threadIdx.x; q < n_top; q += blockDim.x) s_top[q] = __ldg(a.octree + q);
   constexpr int kUnits = 32 / kRefillLanes;       // refill units per warp
-  __shared__ unsigned long long s_red[kRenderThreads / 32 * kUnits][kStats];
-  for (int q = threadIdx.x; q < kRenderThreads / 32 * kUnits * kStats; q += blockDim.x) (&s_red[0][0])[q] = 0;
+  __shared__ unsigned long long s_red[kThreads / 32 * kUnits][kStats];
+  for (int q = threadIdx.x; q < kThreads / 32 * kUnits * kStats; q += blockDim.x) (&s_red[0][0])[q] = 0;
   // batch: first tile of every view (view v owns [s_base[v], s_base[v + 1]))
   // and the current view of each warp
   __shared__ uint32_t s_base[BATCH ? kMaxViews + 1 : 1];
-  __shared__ ViewArgs s_view[BATCH ? kRenderThreads / 32 * kUnits : 1];
+  __shared__ ViewArgs s_view[BATCH ? kThreads / 32 * kUnits : 1];
   if constexpr (BATCH) {
     for (int q = threadIdx.x; q < a.n_views; q += blockDim.x) s_base[q] = a.views[q].tile_base;
     if (threadIdx.x == 0) s_base[a.n_views] = (uint32_t)(a.n_rays >> 5);
@@ -425,10 +457,12 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
   const unsigned gmask = (MP == 32 ? FULL : ((1u << MP) - 1u)) << (grp * MP);
   const unsigned lt_mask = (1u << lane) - 1u;
 
-  Counters cnt = {0, 0, 0};
-  // adds the unit's counters to its row (all lanes of the unit call it)
+  Counters cnt = {0};
+  uint32_t h = 0, n_eval = 0, n_bs = 0;
+  // adds the unit's counters to its row and clears them (all lanes of the
+  // unit call it; each lane has had one ray since the last refill)
   auto flush = [&]() {
-    const uint32_t vals[3] = {cnt.eval, cnt.bs, cnt.homog};
+    const uint32_t vals[3] = {n_eval, n_bs, cnt.homog};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       unsigned long long v = vals[q];
@@ -436,13 +470,12 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
       for (int o = kRefillLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(umask, v, o);
       if (ulane == 0) s_red[row][q + 1] += v;
     }
-    cnt = {0, 0, 0};
+    cnt = {0};
+    n_eval = n_bs = 0;
   };
-  Ray r;
   uint32_t pix = 0;    // py << 16 | px
   int i = 0, lod = 0;
   float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
-  uint32_t h = 0, n_eval = 0, n_bs = 0;
   NodeCache nc;
   nc.clear();
   nc.jn[0] = nc.jn[1] = nc.jn[2] = 0;
@@ -492,7 +525,9 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
           pix = ((uint32_t)py << 16) | (uint32_t)px;
           bool hit_now = false;
           if (px < V.W && py < V.H) {
-            r = make_ray(g, V, px, py);
+            const Ray r = make_ray(g, V, px, py);
+            s_ray[0] = make_float4(r.o[0], r.o[1], r.o[2], r.t0);
+            s_ray[1] = make_float4(r.d[0], r.d[1], r.d[2], r.t1);
             i = 0;
             lod = 0;
             C0 = C1 = C2 = 0.0f;
@@ -523,6 +558,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
     int lminu = 15, st = 0, dstart = 0;
     bool need = false, same_node = false;
     if (active) {
+      const Ray r = ray_get();
       const float t = fmaf((float)i, V.dt, r.t0);
       if (i >= kMaxSamples || !(t < r.t1)) {
         write_pixel<BPV, DBG>(V, pix, C0, C1, C2, T, h, n_eval, i, n_bs);
@@ -536,7 +572,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
         lminu = V.lminu_tab[lod];
         st = V.sdepth[lminu];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) L[q] = (int)(x[q] * pow2f(-g.leaf_log2[q]));
+        for (int q = 0; q < 3; ++q) L[q] = floor_scaled(x[q], pow2f(-g.leaf_log2[q]));
         const int ncd = nc.d();
         const bool same_levels = ncd >= 0 && lod == nc.lod();
         if (same_levels) {
@@ -549,7 +585,8 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
         // lies inside one brick of every usable level): take it instead
         if (need) {
 #pragma unroll 1
-          for (int e = 0; e < kWalkCache; ++e) {
+          for (int q = 1; q <= kWalkCache; ++q) {
+            const int e = (int)((wc_next + kWalkCache - q) % kWalkCache);   // most recent first
             const uint4 hd = *reinterpret_cast<const uint4*>(s_wc + e * kWalkEntry);
             if (!(hd.x & 1u) || (int)((hd.x >> 6) & 15u) != lod || (hd.x >> 21) != vid) continue;
             const int ed = (int)((hd.x >> 1) & 31u), esh = g.D - ed;
@@ -576,15 +613,13 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
         if (same_node) {
           dstart = ncd;
         } else if (same_levels) {
-          int dca = 0;
-          for (int q = ncd; q >= 0; --q) {
-            const int sh = g.D - q, up = ncd - q;
-            if ((L[0] >> sh) == (nc.jn[0] >> up) && (L[1] >> sh) == (nc.jn[1] >> up) &&
-                (L[2] >> sh) == (nc.jn[2] >> up)) {
-              dca = q;
-              break;
-            }
-          }
+          // deepest shared ancestor: along each axis the node coordinates at
+          // depth ncd agree above their highest differing bit
+          const int sh = g.D - ncd;
+          const uint32_t dx = (uint32_t)((L[0] >> sh) ^ nc.jn[0]) | (uint32_t)((L[1] >> sh) ^ nc.jn[1]) |
+                              (uint32_t)((L[2] >> sh) ^ nc.jn[2]);
+          int dca = dx ? ncd - (32 - __clz((int)dx)) : ncd;
+          dca = dca < 0 ? 0 : dca;
           dstart = dca + 1 > d0 ? dca + 1 : d0;
         }
       }
@@ -610,10 +645,13 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
       const uint32_t ldp_lo = __shfl_sync(FULL, (uint32_t)ldp, src),
                      ldp_hi = __shfl_sync(FULL, (uint32_t)(ldp >> 32), src);
       const uint64_t sldp = ((uint64_t)ldp_hi << 32) | ldp_lo;
-      const int sst = __shfl_sync(FULL, st, src), sds = __shfl_sync(FULL, dstart, src),
-                slm = __shfl_sync(FULL, lminu, src), slod = __shfl_sync(FULL, lod, src);
-      const uint32_t svid = BATCH ? __shfl_sync(FULL, vid, src) : 0u;
-      const bool ssame = __shfl_sync(FULL, (int)same_node, src) != 0;
+      // traversal depth, start depth, finest desired level, lod, same node, view
+      const uint32_t pk = __shfl_sync(FULL, (uint32_t)st | ((uint32_t)dstart << 5) | ((uint32_t)lminu << 10) |
+                                                ((uint32_t)lod << 14) | ((uint32_t)same_node << 18) | (vid << 19), src);
+      const int sst = (int)(pk & 31u), sds = (int)((pk >> 5) & 31u), slm = (int)((pk >> 10) & 15u),
+                slod = (int)((pk >> 14) & 15u);
+      const bool ssame = ((pk >> 18) & 1u) != 0;
+      const uint32_t svid = BATCH ? pk >> 19 : 0u;
       const bool cact = gact && ch < m;
       const int ld = cact ? (int)((sldp >> (4 * ch)) & 15) : 0;
       const uint16_t* pre = s_pre + ch * 257;
@@ -664,10 +702,18 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
           if (dd >= sst || dd >= g.D || (ssame && dd == sds)) stop |= 1u << q;
         }
         stop |= badm;
+        if constexpr (MP > 1) {
+          // over the group's lanes: all terminal (AND), any stop (OR)
+          unsigned tg = 0, sg = 0;
 #pragma unroll
-        for (int o = 1; o < MP; o <<= 1) {
-          tm &= __shfl_xor_sync(FULL, tm, o);
-          stop |= __shfl_xor_sync(FULL, stop, o);
+          for (int q = 0; q < kWalkWin; ++q) {
+            const unsigned bt = __ballot_sync(FULL, (tm >> q) & 1u) & gmask;
+            const unsigned bs = __ballot_sync(FULL, (stop >> q) & 1u) & gmask;
+            tg |= (bt == gmask ? 1u : 0u) << q;
+            sg |= (bs != 0u ? 1u : 0u) << q;
+          }
+          tm = tg;
+          stop = sg;
         }
         const unsigned fin = (tm | stop) & ((1u << kWalkWin) - 1u);
         if (gact && dfin < 0 && fin) {
@@ -688,9 +734,9 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
       const bool gbad = (__ballot_sync(FULL, bad) & gmask) != 0;
       // page-table index of this lane's channel at level l (owner brick of the sample)
       auto pt_index = [&](int l) -> uint64_t {
-        const int bx = (int)(sx0 * pow2f(-(g.blog2 + s_lt.lsh[l][0]))),
-                  by = (int)(sx1 * pow2f(-(g.blog2 + s_lt.lsh[l][1]))),
-                  bz = (int)(sx2 * pow2f(-(g.blog2 + s_lt.lsh[l][2])));
+        const int bx = floor_scaled(sx0, pow2f(-(g.blog2 + s_lt.lsh[l][0]))),
+                  by = floor_scaled(sx1, pow2f(-(g.blog2 + s_lt.lsh[l][1]))),
+                  bz = floor_scaled(sx2, pow2f(-(g.blog2 + s_lt.lsh[l][2])));
         return s_pto[ch * k + l] + ((uint64_t)bz * s_nb[l][1] + by) * s_nb[l][0] + bx;
       };
 
@@ -793,13 +839,18 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
       // hand the walk's result to the lanes it was for
       const bool mine = (taken >> lane) & 1u;
       const int from = mine ? __popc(taken & lt_mask) * MP : lane;
-      const int od = __shfl_sync(FULL, d, from);
       const int oj0 = __shfl_sync(FULL, jn0, from), oj1 = __shfl_sync(FULL, jn1, from),
                 oj2 = __shfl_sync(FULL, jn2, from);
-      const bool oskip = __shfl_sync(FULL, (int)all_skip, from) != 0;
-      const int osel = __shfl_sync(FULL, found, from);
-      const bool obad = __shfl_sync(FULL, (int)gbad, from) != 0;
-      const uint32_t oact = __shfl_sync(FULL, act, from), onb = __shfl_sync(FULL, nbrk, from);
+      // depth (31: a node index out of range), all-skip, finest level read,
+      // brick channels, channel set
+      const uint32_t ow = __shfl_sync(FULL, (uint32_t)(gbad ? 31 : d) | ((uint32_t)all_skip << 5) |
+                                                ((uint32_t)(found == 99 ? 31 : found) << 6) | (nbrk << 11) |
+                                                (act << 16), from);
+      const int od = (int)(ow & 31u);
+      const bool obad = od == 31;
+      const bool oskip = ((ow >> 5) & 1u) != 0;
+      const int osel = ((ow >> 6) & 31u) == 31u ? 99 : (int)((ow >> 6) & 31u);
+      const uint32_t onb = (ow >> 11) & 31u, oact = ow >> 16;
       (void)slm;
       if (mine) {
         if (obad) {
@@ -826,6 +877,7 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
       // estimate from the node box's exit distance, then correct with the
       // same position arithmetic
       const int d = nc.d();
+      const Ray r = ray_get();
       float tb = r.t1;
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
@@ -868,7 +920,6 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
     float2 col01 = make_float2(0.0f, 0.0f);
     float col2 = 0.0f, trans = 1.0f;
     const uint32_t nbk = nc.n_brick();
-    cnt.bs += nbk;
     cnt.homog += __popc(nc.act) - nbk;
     n_bs += nbk;
     // per channel: TF, opacity correction, additive colour (channel order)
@@ -941,7 +992,6 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
     C2 = fmaf(T, col2, C2);
     T = T * trans;
     ++n_eval;
-    ++cnt.eval;
     if (T < V.ert) {
       write_pixel<BPV, DBG>(V, pix, C0, C1, C2, T, h, n_eval, i, n_bs);
       active = false;
@@ -955,26 +1005,27 @@ __global__ void __launch_bounds__(kRenderThreads, 1) render_kernel(const __grid_
   __syncthreads();
   if (threadIdx.x < kStats) {
     unsigned long long v = 0;
-    for (int q = 0; q < kRenderThreads / 32 * kUnits; ++q) v += s_red[q][threadIdx.x];
+    for (int q = 0; q < kThreads / 32 * kUnits; ++q) v += s_red[q][threadIdx.x];
     a.block_stats[(size_t)blockIdx.x * kStats + threadIdx.x] = v;
   }
 }
 
 template <int MP, int BPV, int EC, bool DBG, bool BATCH, int SF>
 cudaError_t launch_one(const RenderArgs& a, cudaStream_t s, int* blocks_out) {
-  const size_t smem = render_smem_bytes(MP);
+  const size_t smem = render_smem_bytes(MP, BATCH);
   auto kern = render_kernel<MP, BPV, EC, DBG, BATCH, SF>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRenderThreads, smem)) != cudaSuccess) return e;
+  constexpr int kThreads = render_threads(BATCH);
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const uint64_t need = (a.n_rays + kRenderThreads - 1) / kRenderThreads;
+  const uint64_t need = (a.n_rays + kThreads - 1) / kThreads;
   int blocks = sms * per_sm;
   if ((uint64_t)blocks > need) blocks = (int)need;
-  kern<<<blocks, kRenderThreads, smem, s>>>(a);
+  kern<<<blocks, kThreads, smem, s>>>(a);
   *blocks_out = blocks;
   return cudaGetLastError();
 }
