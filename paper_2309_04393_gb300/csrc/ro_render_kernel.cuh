@@ -309,7 +309,8 @@ __device__ __forceinline__ void shade(const float4* __restrict__ lut, float xq, 
 // are idempotent).
 struct NodeCache {
   // d (bits 0-4, 31 = none) | lod (5-8) | all_skip (9) | one_brick (10) |
-  // finest level read (11-15, 31 = none) | channels read from a brick (16-20)
+  // finest level read (11-15, 31 = none) | channels read from a brick (16-20) |
+  // step exponent of the finest level read, else of the finest desired (21-25)
   uint32_t meta;
   int jn[3];             // node coordinates at depth d
   uint32_t act;          // channels with a value at this node (brick or node value)
@@ -317,12 +318,13 @@ struct NodeCache {
   __device__ __forceinline__ int lod() const { return (int)((meta >> 5) & 15u); }
   __device__ __forceinline__ bool all_skip() const { return (meta >> 9) & 1u; }
   __device__ __forceinline__ bool one_brick() const { return (meta >> 10) & 1u; }
-  __device__ __forceinline__ int s_sel() const { return ((meta >> 11) & 31u) == 31u ? 99 : (int)((meta >> 11) & 31u); }
   __device__ __forceinline__ uint32_t n_brick() const { return (meta >> 16) & 31u; }
+  __device__ __forceinline__ int step() const { return (int)((meta >> 21) & 31u); }
   __device__ __forceinline__ void clear() { meta = 31u; }
-  __device__ __forceinline__ void set(int d, int lod, bool all_skip, bool one_brick, int s_sel, uint32_t n_brick) {
+  __device__ __forceinline__ void set(int d, int lod, bool all_skip, bool one_brick, int s_sel, uint32_t n_brick,
+                                      int step) {
     meta = (uint32_t)d | ((uint32_t)lod << 5) | ((uint32_t)all_skip << 9) | ((uint32_t)one_brick << 10) |
-           ((uint32_t)(s_sel == 99 ? 31 : s_sel) << 11) | (n_brick << 16);
+           ((uint32_t)(s_sel == 99 ? 31 : s_sel) << 11) | (n_brick << 16) | ((uint32_t)step << 21);
   }
 };
 
@@ -568,9 +570,6 @@ __global__ void __launch_bounds__(render_threads(BATCH), 1) render_kernel(const 
         // lod = #{l in 1..k-1 : t >= lod_t[l]} (Sec. 6.2); t never decreases along
         // a ray and the thresholds are non-decreasing, so the count only grows
         while (lod < k - 1 && t >= V.lod_t[lod + 1]) ++lod;
-        ldp = V.ldp_tab[lod];
-        lminu = V.lminu_tab[lod];
-        st = V.sdepth[lminu];
 #pragma unroll
         for (int q = 0; q < 3; ++q) L[q] = floor_scaled(x[q], pow2f(-g.leaf_log2[q]));
         const int ncd = nc.d();
@@ -580,6 +579,12 @@ __global__ void __launch_bounds__(render_threads(BATCH), 1) render_kernel(const 
           same_node = (L[0] >> sh) == nc.jn[0] && (L[1] >> sh) == nc.jn[1] && (L[2] >> sh) == nc.jn[2];
         }
         need = !(same_node && nc.one_brick());
+        // a new node: the desired levels, their finest and its traversal depth
+        if (need) {
+          ldp = V.ldp_tab[lod];
+          lminu = V.lminu_tab[lod];
+          st = V.sdepth[lminu];
+        }
         // a walk another ray of this tile made for the same node and desired
         // levels gives the same final node, states and selections (the node
         // lies inside one brick of every usable level): take it instead
@@ -598,7 +603,8 @@ __global__ void __launch_bounds__(render_threads(BATCH), 1) render_kernel(const 
               my_sel[c * stride] = s_wc[e * kWalkEntry + 5 + c];
             }
             const int ef = (int)((hd.x >> 11) & 31u);
-            nc.set(ed, lod, ((hd.x >> 10) & 1u) != 0, true, ef == 31 ? 99 : ef, (hd.x >> 16) & 31u);
+            nc.set(ed, lod, ((hd.x >> 10) & 1u) != 0, true, ef == 31 ? 99 : ef, (hd.x >> 16) & 31u,
+                   s_lt.lstep[ef == 31 ? lminu : ef]);
             nc.jn[0] = (int)hd.y; nc.jn[1] = (int)hd.z; nc.jn[2] = (int)hd.w;
             nc.act = eact;
             need = false;
@@ -608,19 +614,21 @@ __global__ void __launch_bounds__(render_threads(BATCH), 1) render_kernel(const 
         }
         // the walk (Sec. 6.1) resumes below the deepest ancestor shared with the
         // previous sample: those depths were found not all terminal
-        const int d0 = V.start_depth < st ? V.start_depth : st;
-        dstart = d0;
-        if (same_node) {
-          dstart = ncd;
-        } else if (same_levels) {
-          // deepest shared ancestor: along each axis the node coordinates at
-          // depth ncd agree above their highest differing bit
-          const int sh = g.D - ncd;
-          const uint32_t dx = (uint32_t)((L[0] >> sh) ^ nc.jn[0]) | (uint32_t)((L[1] >> sh) ^ nc.jn[1]) |
-                              (uint32_t)((L[2] >> sh) ^ nc.jn[2]);
-          int dca = dx ? ncd - (32 - __clz((int)dx)) : ncd;
-          dca = dca < 0 ? 0 : dca;
-          dstart = dca + 1 > d0 ? dca + 1 : d0;
+        if (need) {
+          const int d0 = V.start_depth < st ? V.start_depth : st;
+          dstart = d0;
+          if (same_node) {
+            dstart = ncd;
+          } else if (same_levels) {
+            // deepest shared ancestor: along each axis the node coordinates at
+            // depth ncd agree above their highest differing bit
+            const int sh = g.D - ncd;
+            const uint32_t dx = (uint32_t)((L[0] >> sh) ^ nc.jn[0]) | (uint32_t)((L[1] >> sh) ^ nc.jn[1]) |
+                                (uint32_t)((L[2] >> sh) ^ nc.jn[2]);
+            int dca = dx ? ncd - (32 - __clz((int)dx)) : ncd;
+            dca = dca < 0 ? 0 : dca;
+            dstart = dca + 1 > d0 ? dca + 1 : d0;
+          }
         }
       }
     }
@@ -862,7 +870,7 @@ __global__ void __launch_bounds__(render_threads(BATCH), 1) render_kernel(const 
           const bool ob = g.leaf_log2[0] + esh <= g.blog2 + s_lt.lsh[lminu][0] &&
                           g.leaf_log2[1] + esh <= g.blog2 + s_lt.lsh[lminu][1] &&
                           g.leaf_log2[2] + esh <= g.blog2 + s_lt.lsh[lminu][2];
-          nc.set(od, lod, oskip, ob, osel, onb);
+          nc.set(od, lod, oskip, ob, osel, onb, s_lt.lstep[osel == 99 ? lminu : osel]);
           nc.jn[0] = oj0; nc.jn[1] = oj1; nc.jn[2] = oj2;
           nc.act = oact;
         }
@@ -915,8 +923,7 @@ __global__ void __launch_bounds__(render_threads(BATCH), 1) render_kernel(const 
     // shade, composite front to back, stop early once transmittance is low
     // step exponent of the finest level read (or desired): the opacity
     // correction and the next lattice index use 2^s
-    const int ssel = nc.s_sel();
-    const int s = s_lt.lstep[ssel == 99 ? lminu : ssel];
+    const int s = nc.step();
     float2 col01 = make_float2(0.0f, 0.0f);
     float col2 = 0.0f, trans = 1.0f;
     const uint32_t nbk = nc.n_brick();
