@@ -217,12 +217,11 @@ def code_digest(paths):
 
 
 def recorded_traffic(args, channel_samples):
-    """DRAM bytes of one render launch, scaled from the committed ncu record
-    of a smaller launch of the same kernel (the cells16 slab at 960x540
-    behind a 1.5 GiB cache, captured under the size rule for counter
-    captures) by the channel samples the launch reads: only while the render
-    kernel's code is the code the record was taken from and the workload is
-    the default one; else None."""
+    """DRAM bytes of one render launch from the committed ncu record (a
+    single-pass capture of one steady-state launch of the default workload),
+    as its bytes per channel sample times the channel samples of this launch:
+    only while the render kernel's code is the code the record was taken
+    from and the workload is the default one; else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "render_kernel_cells16_traffic.json")) as fh:
             rec = json.load(fh)
@@ -484,7 +483,7 @@ def run_ours(args, rank, world, local_rank):
                           rays_hit_per_step=hit // len(order), warmup_cache=warm),
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "traffic": recorded_traffic(args, chan / len(order)),
-                        "traffic_note": "scaled from a 960x540 launch's ncu DRAM bytes per channel sample",
+                        "traffic_note": "ncu DRAM bytes per channel sample of a steady-state launch x this launch's channel samples",
                         "peak_source": f"{peak_kind} copy bandwidth",
                         "kernel": "render_kernel (ro_render)",
                         "algorithmic_bytes": f"{fp_bytes} B per channel brick sample (2x2x2 footprint) + 16 B per pixel"},

@@ -14,12 +14,13 @@ constexpr int kMaxL = 16;       // levels per context (RO_MAX_LEVELS)
 constexpr int kMaxDepth = 24;   // octree depth bound (2^24 leaves per axis)
 constexpr int kMaxSamples = 1 << 24;  // lattice indices stay exact in binary32
 // threads of a persistent render block (one per SM; rays are taken in 8 x 4
-// pixel tiles): a single-view launch and a batch launch, whose per-warp view
-// copies and view index need more registers
-__host__ __device__ constexpr int render_threads(bool batch) { return batch ? 768 : 896; }
+// pixel tiles): 1024 for a single-view launch (64 registers a thread), 896
+// for a batch launch, whose per-warp view copies and view index need more
+// registers (72)
+__host__ __device__ constexpr int render_threads(bool batch) { return batch ? 896 : 1024; }
 constexpr int kStats = 8;             // per-block counters of the render kernel
 constexpr int kWalkWin = 2;           // octree depths whose node words the walk loads at once
-constexpr int kTopWords = 10240;      // node words of the octree's top depths kept in shared memory (40 KB)
+constexpr int kTopWords = 1024;       // node words of the octree's top depths kept in shared memory (4 KB)
 constexpr int kWalkCache = 8;         // walk results a warp remembers (for the same view)
 constexpr int kRefillLanes = 32;      // lanes that take new rays together (32: the whole tile)
 constexpr int kTileParts = 32 / kRefillLanes;   // such bands per 32-pixel tile

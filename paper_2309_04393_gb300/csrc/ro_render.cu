@@ -46,7 +46,7 @@ size_t render_smem_bytes(int mp, bool batch) {
   const size_t threads = (size_t)render_threads(batch);
   return (size_t)mp * 256 * sizeof(float4) + (((size_t)mp * 257 * 2 + 15) & ~(size_t)15) +
          (size_t)mp * threads * sizeof(uint32_t) + (size_t)kTopWords * sizeof(uint32_t) +
-         (threads / 32) * kWalkCache * kWalkEntry * sizeof(uint32_t) + 2 * threads * sizeof(float4);
+         (threads / 32) * kWalkCache * kWalkEntry * sizeof(uint32_t) + 3 * threads * sizeof(float4);
 }
 
 cudaError_t launch_render(const RenderArgs& a, bool debug, cudaStream_t s, int* blocks_out) {

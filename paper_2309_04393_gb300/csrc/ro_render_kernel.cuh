@@ -342,10 +342,10 @@ struct Counters {
 };
 
 template <int BPV, bool DBG>
-__device__ __forceinline__ void write_pixel(const ViewArgs& V, uint32_t pix, float C0, float C1, float C2, float T,
+__device__ __forceinline__ void write_pixel(const ViewArgs& V, uint32_t pix, float4 col,
                                             uint32_t h, uint32_t n_eval, int i, uint32_t n_bs) {
   const size_t p = (size_t)(pix >> 16) * V.W + (pix & 0xFFFFu);
-  V.image[p] = make_float4(fminf(C0, 1.0f), fminf(C1, 1.0f), fminf(C2, 1.0f), 1.0f - T);
+  V.image[p] = make_float4(fminf(col.x, 1.0f), fminf(col.y, 1.0f), fminf(col.z, 1.0f), 1.0f - col.w);
   if constexpr (DBG) {
     if (V.dbg_hash) V.dbg_hash[p] = h;
     if (V.dbg_n_eval) V.dbg_n_eval[p] = n_eval;
@@ -410,10 +410,13 @@ __global__ void __launch_bounds__(render_threads(BATCH), 1) render_kernel(const 
   // per warp: the last kWalkCache walk results (see phase 1), none yet
   uint32_t* s_wc = s_top + kTopWords + (threadIdx.x >> 5) * (kWalkCache * kWalkEntry);
   if ((threadIdx.x & 31) < kWalkCache) s_wc[(threadIdx.x & 31) * kWalkEntry] = 0u;
-  // per thread: its current ray (origin, t0; direction, t1), kept in shared
-  // memory rather than registers
+  // per thread: its current ray (origin, t0; direction, t1) and its colour
+  // and transmittance (C0, C1, C2, T), kept in shared memory rather than
+  // registers
   float4* s_ray = reinterpret_cast<float4*>(s_top + kTopWords + (kThreads / 32) * kWalkCache * kWalkEntry) +
                   2 * threadIdx.x;
+  float4* s_col = reinterpret_cast<float4*>(s_top + kTopWords + (kThreads / 32) * kWalkCache * kWalkEntry) +
+                  2 * kThreads + threadIdx.x;
   auto ray_get = [&]() {
     const float4 u = s_ray[0], v = s_ray[1];
     Ray q;
@@ -477,7 +480,6 @@ __global__ void __launch_bounds__(render_threads(BATCH), 1) render_kernel(const 
   };
   uint32_t pix = 0;    // py << 16 | px
   int i = 0, lod = 0;
-  float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
   NodeCache nc;
   nc.clear();
   nc.jn[0] = nc.jn[1] = nc.jn[2] = 0;
@@ -532,8 +534,7 @@ __global__ void __launch_bounds__(render_threads(BATCH), 1) render_kernel(const 
             s_ray[1] = make_float4(r.d[0], r.d[1], r.d[2], r.t1);
             i = 0;
             lod = 0;
-            C0 = C1 = C2 = 0.0f;
-            T = 1.0f;
+            *s_col = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
             h = 2166136261u;
             n_eval = n_bs = 0;
             nc.clear();
@@ -541,7 +542,7 @@ __global__ void __launch_bounds__(render_threads(BATCH), 1) render_kernel(const 
               active = true;
               hit_now = true;
             } else {
-              write_pixel<BPV, DBG>(V, pix, C0, C1, C2, T, h, n_eval, i, n_bs);
+              write_pixel<BPV, DBG>(V, pix, *s_col, h, n_eval, i, n_bs);
             }
           }
           const unsigned hits = __ballot_sync(umask, hit_now);
@@ -563,7 +564,7 @@ __global__ void __launch_bounds__(render_threads(BATCH), 1) render_kernel(const 
       const Ray r = ray_get();
       const float t = fmaf((float)i, V.dt, r.t0);
       if (i >= kMaxSamples || !(t < r.t1)) {
-        write_pixel<BPV, DBG>(V, pix, C0, C1, C2, T, h, n_eval, i, n_bs);
+        write_pixel<BPV, DBG>(V, pix, *s_col, h, n_eval, i, n_bs);
         active = false;
       } else {
         position(g, r, t, x);
@@ -863,7 +864,7 @@ __global__ void __launch_bounds__(render_threads(BATCH), 1) render_kernel(const 
       if (mine) {
         if (obad) {
           *a.err = kErrNodeIndex;
-          write_pixel<BPV, DBG>(V, pix, C0, C1, C2, T, h, n_eval, i, n_bs);
+          write_pixel<BPV, DBG>(V, pix, *s_col, h, n_eval, i, n_bs);
           active = false;
         } else {
           const int esh = g.D - od;
@@ -994,13 +995,15 @@ __global__ void __launch_bounds__(render_threads(BATCH), 1) render_kernel(const 
         add(cb, vb);
       }
     }
-    C0 = fmaf(T, col01.x, C0);
-    C1 = fmaf(T, col01.y, C1);
-    C2 = fmaf(T, col2, C2);
-    T = T * trans;
+    float4 cc = *s_col;                     // (C0, C1, C2, T)
+    cc.x = fmaf(cc.w, col01.x, cc.x);
+    cc.y = fmaf(cc.w, col01.y, cc.y);
+    cc.z = fmaf(cc.w, col2, cc.z);
+    cc.w = cc.w * trans;
+    *s_col = cc;
     ++n_eval;
-    if (T < V.ert) {
-      write_pixel<BPV, DBG>(V, pix, C0, C1, C2, T, h, n_eval, i, n_bs);
+    if (cc.w < V.ert) {
+      write_pixel<BPV, DBG>(V, pix, cc, h, n_eval, i, n_bs);
       active = false;
       continue;
     }
