@@ -10,7 +10,8 @@
 // cores.  A binary32 convolution block computes an 8 x 8 x 4 voxel tile for
 // all output channels from a shared-memory copy of the input tile with its
 // one-voxel halo (zero outside the grid) and of the layer's weights; the
-// tcgen05 convolution marches an 8 x 16 column along z.  An input-gradient
+// tcgen05 convolution marches an 8 x 16 column along z with the three z
+// taps of an input slice in one instruction.  An input-gradient
 // pass is the forward kernel on the spatially flipped, channel-transposed
 // weights.
 #include <cuda_bf16.h>
@@ -230,42 +231,8 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
 }
 
 // ------------------------------------ fifth-generation tensor cores (tcgen05)
-// The 32 -> 32 convolution with tcgen05.mma.  A block owns an 8 (x) by 16 (y)
-// column of output voxels over kZChunk consecutive z slices and marches along
-// z: the weights stay in shared memory for the whole column, the input sits
-// in a ring of four z slices (rounded to bfloat16), and while the matrix
-// instructions of slice z run, the block stores slice z - 1 and loads slice
-// z + 2 of the halo.  Per slice the 128 x 32 binary32 accumulator D (two of
-// them in tensor memory, used in turn) receives, for each of the 27 taps,
-// A_t (128 voxels x 32 input channels) times the tap's weights as two K = 16
-// steps: 54 instructions from one thread, one commit.  Operands use the
-// canonical K-major layout without swizzle: core matrices of 8 rows x 16
-// bytes, 128 bytes apart along K and 256 bytes from one 8-row group to the
-// next.  D's row groups are the 16 y rows of the column (8 voxels along x
-// each), so a tap's y offset moves the operand's start by whole groups and
-// its z offset picks the ring slot; the x offset needs its own copy of each
-// slice, written once for dx = 0, 1, 2.  Waits are bounded: on a timeout
-// the block records an error, stops, waits (bounded) for its instructions
-// in flight and still frees tensor memory.
-constexpr int T5X = 8, T5Y = 16, kZChunk = 17;
-constexpr int H5X = T5X + 2, H5Y = T5Y + 2;
-constexpr int kT5Threads = 256;
-constexpr int kT5TilesX = (EG + T5X - 1) / T5X, kT5TilesY = (EG + T5Y - 1) / T5Y, kT5Chunks = (EG + kZChunk - 1) / kZChunk;
-constexpr int kT5Units = kT5TilesX * kT5TilesY * kT5Chunks;  // columns per grid
-constexpr int kDxBytes = 2 * H5Y * 256;                      // one x-shifted copy: [ks][hy][chunk][row][16 B]
-constexpr int kSlotBytes = 3 * kDxBytes;                     // one z slice: three copies
-constexpr int kRing = 4;
-constexpr int kBBytesTap = 2 * 4 * 256;                      // one tap's B: [ks][co group][chunk][row][16 B]
-constexpr int kT5BBytes = 27 * kBBytesTap;
 constexpr uint32_t kWaitLimit = 1u << 22;
 constexpr uint64_t kWaitNs = 500000000ull;           // half a second
-
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
-  // start >> 4; leading byte offset 128 (next K chunk); stride byte offset
-  // 256 (next 8-row group); descriptor version 1; no swizzle
-  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
-         ((uint64_t)1 << 46);
-}
 
 // gives up after kWaitLimit polls or kWaitNs nanoseconds, whichever comes first
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
@@ -285,24 +252,74 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
-// A z slice of the halo column is kSliceItems 8-channel pieces (32 bytes of
-// binary32 input each), at most kItemsT5 per thread.  t5_fetch reads this
-// thread's pieces of slice gz into registers (zeros outside the grid);
-// t5_store rounds them to bfloat16 and writes them into every x-shifted copy
-// of ring slot `slot` whose 8-voxel rows hold them.  Fetching one step
-// ahead keeps the loads in flight while the matrix instructions run.
-constexpr int kSliceItems = H5Y * H5X * 4;
-constexpr int kItemsT5 = (kSliceItems + kT5Threads - 1) / kT5Threads;
 
-__device__ __forceinline__ void t5_fetch(const float* __restrict__ src, int x0t, int y0t, int gz, int tid,
-                                         float4 (&v)[kItemsT5][2]) {
+// The 32 -> 32 convolution on tcgen05.mma, with the three z taps folded
+// into N.  A block owns an 8 (x) by 16 (y) column of output voxels over
+// kTzChunk consecutive z slices and marches along z: the weights stay in
+// shared memory for the whole column, the input sits in a ring of four z
+// slices (rounded to bfloat16), and while the matrix instructions of input
+// slice s run, the block reads out a finished output slice and stores input
+// slice s + 2 of the halo.  An input slice s contributes to output slices s + 1, s and s - 1 through the
+// taps dz = 0, 1, 2 with the same input rows, so for each of the nine (dy,
+// dx) taps one tcgen05.mma of M = 128 voxels, N = 96 (the three dz taps'
+// 32 output channels side by side) and K = 16 reads the input tile once
+// and adds into three accumulators: 18 instructions per input slice instead
+// of 54 with N = 32, and a third of the operand reads from shared memory.
+// The accumulators are a ring of eight 32-column blocks of tensor memory:
+// output slice zo (relative to the block's first) lives in block
+// (-zo - 1) mod 8, so slices zo, zo - 1, zo - 2 are consecutive columns; at
+// the ring's end the instruction is split in two.  A block is zeroed once
+// its slice has been read out (its last contribution came from input slice
+// zo + 2), five input slices before it is used again.  The input slice is
+// stored once, as rows of 8 channels (16 bytes) in planes of one channel
+// octet: [octet][halo y][halo x][16 B]; an 8-row core-matrix group is a halo
+// row, 160 bytes from the next, so the x offset of a tap moves the operand's
+// start by 16 bytes and the y offset by 160.
+constexpr int TZX = 8, TZY = 16, kTzChunk = 17;
+constexpr int HZX2 = TZX + 2, HZY2 = TZY + 2;
+constexpr int kTzThreads = 256;
+constexpr int kTzTilesX = (EG + TZX - 1) / TZX, kTzTilesY = (EG + TZY - 1) / TZY, kTzChunks = (EG + kTzChunk - 1) / kTzChunk;
+constexpr int kTzUnits = kTzTilesX * kTzTilesY * kTzChunks;  // columns per grid
+constexpr int kTzRowStride = HZX2 * 16;                      // one halo row of 10 voxels: 160 B (SBO)
+constexpr int kTzPlane = HZY2 * kTzRowStride;                // one channel octet of a slice: 2,880 B (LBO)
+constexpr int kTzSlice = 4 * kTzPlane;                       // 11,520 B
+constexpr int kTzRing = 4;                                   // input slices in shared memory
+constexpr int kTzBKs = 12 * 256;                             // B of one (dy, dx) tap and K step: 96 rows
+constexpr int kTzBTap = 2 * kTzBKs;                          // 6,144 B
+constexpr int kTzB = 9 * kTzBTap;                            // 55,296 B
+constexpr int kTzCols = 256;                                 // tensor-memory columns: 8 blocks of 32
+constexpr int kTzSliceItems = HZY2 * HZX2 * 4;               // 8-channel pieces of an input slice
+constexpr int kTzItems = (kTzSliceItems + kTzThreads - 1) / kTzThreads;
+
+__device__ __forceinline__ uint64_t umma_desc_kmajor(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  // start >> 4; leading byte offset (next K chunk); stride byte offset (next
+  // 8-row group); descriptor version 1; no swizzle
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ uint32_t tz_idesc(int n) {
+  // D binary32, A and B bfloat16, both K-major, N, M = 128
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+// D += A B (the accumulator blocks start at zero)
+__device__ __forceinline__ void tz_mma(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t idesc) {
+  asm volatile("{\n .reg .pred p;\n setp.eq.u32 p, 1, 1;\n"
+               " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+               :: "r"(d_tmem), "l"(da), "l"(db), "r"(idesc));
+}
+
+// this thread's 8-channel pieces of input slice gz (zeros outside the grid)
+__device__ __forceinline__ void tz_fetch(const float* __restrict__ src, int x0t, int y0t, int gz, int tid,
+                                         float4 (&v)[kTzItems][2]) {
 #pragma unroll
-  for (int j = 0; j < kItemsT5; ++j) {
-    const int w = tid + j * kT5Threads;
+  for (int j = 0; j < kTzItems; ++j) {
+    const int w = tid + j * kTzThreads;
     v[j][0] = v[j][1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    const int q = w % 4, hx = (w / 4) % H5X, hy = w / (4 * H5X);
+    const int q = w % 4, hx = (w / 4) % HZX2, hy = w / (4 * HZX2);
     const int gx = x0t + hx - 1, gy = y0t + hy - 1;
-    if (w < kSliceItems && gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG) {
+    if (w < kTzSliceItems && gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG) {
       const float4* p4 = reinterpret_cast<const float4*>(src + ((size_t)(gz * EG + gy) * EG + gx) * HID + 8 * q);
       v[j][0] = __ldg(p4);
       v[j][1] = __ldg(p4 + 1);
@@ -310,58 +327,65 @@ __device__ __forceinline__ void t5_fetch(const float* __restrict__ src, int x0t,
   }
 }
 
-__device__ __forceinline__ void t5_store(uint8_t* slot, int tid, const float4 (&v)[kItemsT5][2]) {
+// ... rounded to bfloat16, into the octet planes of a ring slot
+__device__ __forceinline__ void tz_store(uint8_t* slot, int tid, const float4 (&v)[kTzItems][2]) {
 #pragma unroll
-  for (int j = 0; j < kItemsT5; ++j) {
-    const int w = tid + j * kT5Threads;
-    if (w >= kSliceItems) continue;
-    const int q = w % 4, hx = (w / 4) % H5X, hy = w / (4 * H5X);
+  for (int j = 0; j < kTzItems; ++j) {
+    const int w = tid + j * kTzThreads;
+    if (w >= kTzSliceItems) continue;
+    const int q = w % 4, hx = (w / 4) % HZX2, hy = w / (4 * HZX2);
     __nv_bfloat162 h[4] = {__floats2bfloat162_rn(v[j][0].x, v[j][0].y), __floats2bfloat162_rn(v[j][0].z, v[j][0].w),
                            __floats2bfloat162_rn(v[j][1].x, v[j][1].y), __floats2bfloat162_rn(v[j][1].z, v[j][1].w)};
-    const uint4 val = *reinterpret_cast<const uint4*>(h);
-#pragma unroll
-    for (int dx = 0; dx < 3; ++dx) {
-      const int r = hx - dx;                                 // row of the copy that holds this voxel
-      if (r < 0 || r >= T5X) continue;
-      *reinterpret_cast<uint4*>(slot + dx * kDxBytes + ((q >> 1) * H5Y + hy) * 256 + (q & 1) * 128 + r * 16) = val;
-    }
+    *reinterpret_cast<uint4*>(slot + q * kTzPlane + hy * kTzRowStride + hx * 16) = *reinterpret_cast<const uint4*>(h);
   }
 }
 
+// 32 columns of zeros into this warp's 32 lanes of tensor memory
+__device__ __forceinline__ void tz_zero(uint32_t taddr) {
+  const uint32_t z = 0u;
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+               "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" :: "r"(taddr), "r"(z) : "memory");
+}
+
+__device__ __forceinline__ int tz_block(int zo) { return ((-zo - 1) % 8 + 8) % 8; }
+
 template <int EPI>
-__global__ void __launch_bounds__(kT5Threads, 1) conv_tc05_kernel(const float* __restrict__ in,
-                                                                 const __nv_bfloat16* __restrict__ wb,
-                                                                 const float* __restrict__ bias, float* __restrict__ out,
-                                                                 const float* __restrict__ aux, uint32_t* __restrict__ err) {
-  extern __shared__ __align__(128) uint8_t sm5[];
-  uint8_t* s_b = sm5;                                        // 27 taps x kBBytesTap
-  uint8_t* s_a = sm5 + kT5BBytes;                            // kRing slices x kSlotBytes
+__global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __restrict__ in,
+                                                               const __nv_bfloat16* __restrict__ wb,
+                                                               const float* __restrict__ bias, float* __restrict__ out,
+                                                               const float* __restrict__ aux, uint32_t* __restrict__ err) {
+  extern __shared__ __align__(128) uint8_t smz[];
+  uint8_t* s_b = smz;                                        // 9 (dy, dx) taps x kTzBTap
+  uint8_t* s_a = smz + kTzB;                                 // kTzRing input slices x kTzSlice
   __shared__ __align__(8) uint64_t s_mbar[2];
   __shared__ uint32_t s_tmem, s_fail;
   __shared__ float s_bias[HID];
   const int tid = threadIdx.x, warp = tid >> 5;
   const int unit = blockIdx.x, n = blockIdx.y;
-  const int x0t = (unit % kT5TilesX) * T5X, y0t = ((unit / kT5TilesX) % kT5TilesY) * T5Y;
-  const int z0 = (unit / (kT5TilesX * kT5TilesY)) * kZChunk;
-  const int nz = min(kZChunk, EG - z0);                      // output slices of this column
+  const int x0t = (unit % kTzTilesX) * TZX, y0t = ((unit / kTzTilesX) % kTzTilesY) * TZY;
+  const int z0 = (unit / (kTzTilesX * kTzTilesY)) * kTzChunk;
+  const int nz = min(kTzChunk, EG - z0);                     // output slices of this column
   const float* src = in + (size_t)n * NV * HID;
-  // weights wb[tap][co][ci] (64-byte rows) into the canonical layout
-  for (int q = tid; q < 27 * HID * 4; q += kT5Threads) {
+  // weights wb[tap][co][ci] (64-byte rows): tap (dz, dy, dx) goes to the B of
+  // (dy, dx), rows dz * 32 + co, in the canonical K-major layout
+  for (int q = tid; q < 27 * HID * 4; q += kTzThreads) {
     const int t = q / (HID * 4), co = (q / 4) % HID, ch = q % 4;
-    *reinterpret_cast<uint4*>(s_b + t * kBBytesTap + (ch >> 1) * 1024 + (co >> 3) * 256 + (ch & 1) * 128 +
-                              (co & 7) * 16) = __ldg(reinterpret_cast<const uint4*>(wb) + q);
+    const int nrow = (t / 9) * HID + co, c = t % 9;
+    *reinterpret_cast<uint4*>(s_b + c * kTzBTap + (ch >> 1) * kTzBKs + (nrow >> 3) * 256 + (ch & 1) * 128 +
+                              (nrow & 7) * 16) = __ldg(reinterpret_cast<const uint4*>(wb) + q);
   }
   if (tid < HID) s_bias[tid] = EPI == kEpiRelu ? bias[tid] : 0.0f;
-  // input slices z0 - 1, z0, z0 + 1 (ring slots 0, 1, 2)
-  float4 pre[kItemsT5][2];
-  for (int li = 0; li < 3; ++li) {
-    t5_fetch(src, x0t, y0t, z0 - 1 + li, tid, pre);
-    t5_store(s_a + li * kSlotBytes, tid, pre);
+  // input slices 0 and 1 (z0 - 1, z0) into ring slots 0 and 1; slice 2 into
+  // registers, stored in the first step
+  float4 pre[kTzItems][2];
+  for (int li = 0; li < 2; ++li) {
+    tz_fetch(src, x0t, y0t, z0 - 1 + li, tid, pre);
+    tz_store(s_a + li * kTzSlice, tid, pre);
   }
-  t5_fetch(src, x0t, y0t, z0 + 2, tid, pre);                 // input slice 3, stored in the first step
+  tz_fetch(src, x0t, y0t, z0 + 1, tid, pre);
   // this thread's accumulator row (warps 0-3): voxel (ex, ey) of each slice;
   // am holds its mask row (input-gradient pass), fetched a step ahead
-  const int ex = x0t + tid % T5X, ey = y0t + tid / T5X;
+  const int ex = x0t + tid % TZX, ey = y0t + tid / TZX;
   const bool erow = warp < 4 && ex < EG && ey < EG;
   float4 am[HID / 4];
 #pragma unroll
@@ -372,7 +396,8 @@ __global__ void __launch_bounds__(kT5Threads, 1) conv_tc05_kernel(const float* _
     s_fail = 0;
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" :: "r"(smem_u32(&s_tmem)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&s_tmem)), "n"(kTzCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -380,77 +405,95 @@ __global__ void __launch_bounds__(kT5Threads, 1) conv_tc05_kernel(const float* _
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+  if (warp < 4) {                                            // every accumulator block starts at zero
+    for (int b = 0; b < kTzCols / 32; ++b) tz_zero(tmem + lane_base + (uint32_t)(32 * b));
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t a0 = smem_u32(s_a), b0 = smem_u32(s_b);
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(HID >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-  int issued = 0;                                            // slices whose instructions were issued
-  for (int zl = 0; zl <= nz; ++zl) {
-    if (zl < nz && tid == 128) {                             // one thread of the loader warps issues slice zl
-      const uint32_t d_tmem = tmem + (uint32_t)(32 * (zl & 1));
-      for (int t = 0; t < 27; ++t) {
-        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-        const uint32_t a_t = a0 + ((zl + dz) % kRing) * kSlotBytes + dx * kDxBytes + dy * 256;
+  int issued = 0;                                            // input slices whose instructions were issued
+  for (int i = 0; i <= nz + 2; ++i) {
+    if (i <= nz + 1 && tid == 128) {                         // one thread issues input slice i
+      const int bb = tz_block(i);                            // block of output slice i (tap dz = 0)
+      const uint32_t a_s = a0 + (uint32_t)((i % kTzRing) * kTzSlice);
+      for (int c = 0; c < 9; ++c) {
+        const int dy = c / 3, dx = c % 3;
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) {
-          const uint64_t da = umma_desc(a_t + ks * (H5Y * 256));
-          const uint64_t db = umma_desc(b0 + t * kBBytesTap + ks * 1024);
-          const uint32_t acc = (t > 0 || ks > 0) ? 1u : 0u;
-          asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                       :: "r"(d_tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+          const uint64_t da = umma_desc_kmajor(a_s + (uint32_t)(2 * ks * kTzPlane + dy * kTzRowStride + dx * 16),
+                                               kTzPlane, kTzRowStride);
+          const uint32_t bt = b0 + (uint32_t)(c * kTzBTap + ks * kTzBKs);
+          if (bb <= 5) {
+            tz_mma(tmem + (uint32_t)(32 * bb), da, umma_desc_kmajor(bt, 128, 256), tz_idesc(96));
+          } else if (bb == 6) {                              // blocks 6, 7 | 0
+            tz_mma(tmem + 192u, da, umma_desc_kmajor(bt, 128, 256), tz_idesc(64));
+            tz_mma(tmem, da, umma_desc_kmajor(bt + 8 * 256, 128, 256), tz_idesc(32));
+          } else {                                           // block 7 | 0, 1
+            tz_mma(tmem + 224u, da, umma_desc_kmajor(bt, 128, 256), tz_idesc(32));
+            tz_mma(tmem, da, umma_desc_kmajor(bt + 4 * 256, 128, 256), tz_idesc(64));
+          }
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(smem_u32(&s_mbar[zl & 1])) : "memory");
+                   :: "r"(smem_u32(&s_mbar[i & 1])) : "memory");
     }
-    if (zl < nz) issued = zl + 1;
-    if (zl >= 1) {
-      // slice zl - 1 done: store it (warps 0-3: one accumulator row each)
-      const int zp = zl - 1;
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&s_mbar[zp & 1]), (uint32_t)((zp >> 1) & 1)));
+    if (i <= nz + 1) issued = i + 1;
+    if (i >= 1) {
+      // input slice i - 1 done: output slice i - 3 is complete; read it out
+      // (warps 0-3: one accumulator row each), then zero its block
+      const int ip = i - 1, zo = i - 3;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&s_mbar[ip & 1]), (uint32_t)((ip >> 1) & 1)));
       if (!ok) {
         atomicExch(err, 1u);
         s_fail = 1;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (ok && warp < 4) {
-        uint32_t r[32];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * (zp & 1));
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                     "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                       "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                       "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                       "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                       "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                     : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        // accumulator row tid: y row tid / 8 of the column, x tid % 8
-        if (erow) {
-          const size_t v = (size_t)n * NV + (size_t)((z0 + zp) * EG + ey) * EG + ex;
-          float4* o4 = reinterpret_cast<float4*>(out + v * HID);
+        const uint32_t taddr = tmem + lane_base + (uint32_t)(32 * tz_block(zo));
+        if (zo >= 0) {
+          uint32_t r[32];
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                       "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                         "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                         "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                         "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                       : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (erow) {
+            const size_t v = (size_t)n * NV + (size_t)((z0 + zo) * EG + ey) * EG + ex;
+            float4* o4 = reinterpret_cast<float4*>(out + v * HID);
 #pragma unroll
-          for (int c4 = 0; c4 < HID / 4; ++c4) {
-            float o[4];
-            const float mk[4] = {am[c4].x, am[c4].y, am[c4].z, am[c4].w};
+            for (int c4 = 0; c4 < HID / 4; ++c4) {
+              float o[4];
+              const float mk[4] = {am[c4].x, am[c4].y, am[c4].z, am[c4].w};
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float val = __uint_as_float(r[4 * c4 + e]);
-              if constexpr (EPI == kEpiRelu) o[e] = fmaxf(val + s_bias[4 * c4 + e], 0.0f);
-              else o[e] = mk[e] > 0.0f ? val : 0.0f;
+              for (int e = 0; e < 4; ++e) {
+                const float val = __uint_as_float(r[4 * c4 + e]);
+                if constexpr (EPI == kEpiRelu) o[e] = fmaxf(val + s_bias[4 * c4 + e], 0.0f);
+                else o[e] = mk[e] > 0.0f ? val : 0.0f;
+              }
+              o4[c4] = make_float4(o[0], o[1], o[2], o[3]);
             }
-            o4[c4] = make_float4(o[0], o[1], o[2], o[3]);
           }
         }
+        tz_zero(taddr);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       }
     }
-    // slice zl + 2 of the column (input slice li = zl + 3) into the slot
-    // that slice zl - 2 left; every instruction that read it has completed
-    if (zl + 3 <= nz + 1) t5_store(s_a + ((zl + 3) % kRing) * kSlotBytes, tid, pre);
-    if (zl + 4 <= nz + 1) t5_fetch(src, x0t, y0t, z0 + zl + 3, tid, pre);
-    if constexpr (EPI != kEpiRelu) {                         // mask rows of output slice zl, stored next step
-      if (erow && zl < nz) {
+    // input slice i + 2 into the slot input slice i - 2 left (every
+    // instruction that read it has completed); fetch slice i + 3
+    if (i + 2 <= nz + 1) tz_store(s_a + ((i + 2) % kTzRing) * kTzSlice, tid, pre);
+    if (i + 3 <= nz + 1) tz_fetch(src, x0t, y0t, z0 - 1 + i + 3, tid, pre);
+    if constexpr (EPI != kEpiRelu) {                         // mask rows of output slice i - 2, read out next step
+      const int zm = i - 2;
+      if (erow && zm >= 0 && zm < nz) {
         const float4* a4 =
-            reinterpret_cast<const float4*>(aux + ((size_t)n * NV + (size_t)((z0 + zl) * EG + ey) * EG + ex) * HID);
+            reinterpret_cast<const float4*>(aux + ((size_t)n * NV + (size_t)((z0 + zm) * EG + ey) * EG + ex) * HID);
 #pragma unroll
         for (int c4 = 0; c4 < HID / 4; ++c4) am[c4] = __ldg(a4 + c4);
       }
@@ -463,19 +506,19 @@ __global__ void __launch_bounds__(kT5Threads, 1) conv_tc05_kernel(const float* _
   }
   if (s_fail && issued > 0) {
     // a wait gave up: a last bounded wait for the newest commit before freeing
-    const int zp = issued - 1;
-    mbar_wait(smem_u32(&s_mbar[zp & 1]), (uint32_t)((zp >> 1) & 1));
+    const int ip = issued - 1;
+    mbar_wait(smem_u32(&s_mbar[ip & 1]), (uint32_t)((ip >> 1) & 1));
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" :: "r"(tmem));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(kTzCols));
   }
 }
 
-constexpr size_t conv_tc05_smem() { return (size_t)kT5BBytes + (size_t)kRing * kSlotBytes; }
-static_assert(conv_tc05_smem() <= 227 * 1024, "shared memory of the tcgen05 convolution");
+constexpr size_t conv_tz_smem() { return (size_t)kTzB + (size_t)kTzRing * kTzSlice; }
+static_assert(2 * conv_tz_smem() + 2 * 1024 <= 228 * 1024, "two blocks of the z-folded convolution per SM");
 
 __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
@@ -813,11 +856,11 @@ cudaError_t conv(const float* in, const float* w, const float* b, float* out, co
 template <int EPI>
 cudaError_t conv_tc(const float* in, const __nv_bfloat16* wb, const float* b, float* out, const float* aux, uint32_t n,
                     uint32_t* flag, cudaStream_t s) {
-  auto k = conv_tc05_kernel<EPI>;
-  constexpr size_t sm = conv_tc05_smem();
+  auto k = conv_tz_kernel<EPI>;
+  constexpr size_t sm = conv_tz_smem();
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k<<<dim3(kT5Units, n), kT5Threads, sm, s>>>(in, wb, b, out, aux, flag);
+  k<<<dim3(kTzUnits, n), kTzThreads, sm, s>>>(in, wb, b, out, aux, flag);
   return cudaGetLastError();
 }
 
