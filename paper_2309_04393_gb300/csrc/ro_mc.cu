@@ -104,14 +104,25 @@ template <int CIN>
 __device__ __forceinline__ void load_halo(const float* __restrict__ src, float* s_in, int x0t, int y0t, int z0t) {
   constexpr int SC = pad_stride(CIN);
   if constexpr (CIN % 4 == 0) {
-    for (int q = threadIdx.x; q < HZ * HY * HX * (CIN / 4); q += blockDim.x) {
-      const int c4 = q % (CIN / 4), p = q / (CIN / 4);
-      const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
-      const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
-      float4 val = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      if (gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
-        val = __ldg(reinterpret_cast<const float4*>(src + ((size_t)(gz * EG + gy) * EG + gx) * CIN) + c4);
-      *reinterpret_cast<float4*>(s_in + p * SC + 4 * c4) = val;
+    // 16-byte loads, four of them in flight before any is stored
+    constexpr int kItems = HZ * HY * HX * (CIN / 4), kBatch = 4;
+    for (int q0 = threadIdx.x; q0 < kItems; q0 += kBatch * (int)blockDim.x) {
+      float4 val[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int q = q0 + u * (int)blockDim.x;
+        const int c4 = q % (CIN / 4), p = q / (CIN / 4);
+        const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
+        const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
+        val[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (q < kItems && gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
+          val[u] = __ldg(reinterpret_cast<const float4*>(src + ((size_t)(gz * EG + gy) * EG + gx) * CIN) + c4);
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int q = q0 + u * (int)blockDim.x;
+        if (q < kItems) *reinterpret_cast<float4*>(s_in + (q / (CIN / 4)) * SC + 4 * (q % (CIN / 4))) = val[u];
+      }
     }
   } else {
     for (int q = threadIdx.x; q < HZ * HY * HX * CIN; q += blockDim.x) {
@@ -258,8 +269,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 // kTzChunk consecutive z slices and marches along z: the weights stay in
 // shared memory for the whole column, the input sits in a ring of four z
 // slices (rounded to bfloat16), and while the matrix instructions of input
-// slice s run, the block reads out a finished output slice and stores input
-// slice s + 2 of the halo.  An input slice s contributes to output slices s + 1, s and s - 1 through the
+// slices s and s + 1 run, the block reads out output slice s - 2 and stores
+// input slice s + 3 of the halo.  An input slice s contributes to output slices s + 1, s and s - 1 through the
 // taps dz = 0, 1, 2 with the same input rows, so for each of the nine (dy,
 // dx) taps one tcgen05.mma of M = 128 voxels, N = 96 (the three dz taps'
 // 32 output channels side by side) and K = 16 reads the input tile once
@@ -357,7 +368,7 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
   extern __shared__ __align__(128) uint8_t smz[];
   uint8_t* s_b = smz;                                        // 9 (dy, dx) taps x kTzBTap
   uint8_t* s_a = smz + kTzB;                                 // kTzRing input slices x kTzSlice
-  __shared__ __align__(8) uint64_t s_mbar[2];
+  __shared__ __align__(8) uint64_t s_mbar[4];        // input slice j commits to s_mbar[j % 4]
   __shared__ uint32_t s_tmem, s_fail;
   __shared__ float s_bias[HID];
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -375,14 +386,14 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
                               (nrow & 7) * 16) = __ldg(reinterpret_cast<const uint4*>(wb) + q);
   }
   if (tid < HID) s_bias[tid] = EPI == kEpiRelu ? bias[tid] : 0.0f;
-  // input slices 0 and 1 (z0 - 1, z0) into ring slots 0 and 1; slice 2 into
-  // registers, stored in the first step
+  // input slices 0, 1 and 2 (z0 - 1 .. z0 + 1) into ring slots 0-2; slice 3
+  // into registers, stored in the first step
   float4 pre[kTzItems][2];
-  for (int li = 0; li < 2; ++li) {
+  for (int li = 0; li < 3; ++li) {
     tz_fetch(src, x0t, y0t, z0 - 1 + li, tid, pre);
     tz_store(s_a + li * kTzSlice, tid, pre);
   }
-  tz_fetch(src, x0t, y0t, z0 + 1, tid, pre);
+  tz_fetch(src, x0t, y0t, z0 + 2, tid, pre);
   // this thread's accumulator row (warps 0-3): voxel (ex, ey) of each slice;
   // am holds its mask row (input-gradient pass), fetched a step ahead
   const int ex = x0t + tid % TZX, ey = y0t + tid / TZX;
@@ -391,8 +402,7 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
 #pragma unroll
   for (int c4 = 0; c4 < HID / 4; ++c4) am[c4] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&s_mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&s_mbar[1])));
+    for (int q = 0; q < 4; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&s_mbar[q])));
     s_fail = 0;
   }
   if (warp == 0) {
@@ -414,38 +424,43 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t a0 = smem_u32(s_a), b0 = smem_u32(s_b);
-  int issued = 0;                                            // input slices whose instructions were issued
-  for (int i = 0; i <= nz + 2; ++i) {
-    if (i <= nz + 1 && tid == 128) {                         // one thread issues input slice i
-      const int bb = tz_block(i);                            // block of output slice i (tap dz = 0)
-      const uint32_t a_s = a0 + (uint32_t)((i % kTzRing) * kTzSlice);
-      for (int c = 0; c < 9; ++c) {
-        const int dy = c / 3, dx = c % 3;
+  // the matrix instructions of input slice j (one thread), committed to s_mbar[j % 4]
+  auto issue = [&](int j) {
+    const int bb = tz_block(j);                              // block of output slice j (tap dz = 0)
+    const uint32_t a_s = a0 + (uint32_t)((j % kTzRing) * kTzSlice);
+    for (int c = 0; c < 9; ++c) {
+      const int dy = c / 3, dx = c % 3;
 #pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-          const uint64_t da = umma_desc_kmajor(a_s + (uint32_t)(2 * ks * kTzPlane + dy * kTzRowStride + dx * 16),
-                                               kTzPlane, kTzRowStride);
-          const uint32_t bt = b0 + (uint32_t)(c * kTzBTap + ks * kTzBKs);
-          if (bb <= 5) {
-            tz_mma(tmem + (uint32_t)(32 * bb), da, umma_desc_kmajor(bt, 128, 256), tz_idesc(96));
-          } else if (bb == 6) {                              // blocks 6, 7 | 0
-            tz_mma(tmem + 192u, da, umma_desc_kmajor(bt, 128, 256), tz_idesc(64));
-            tz_mma(tmem, da, umma_desc_kmajor(bt + 8 * 256, 128, 256), tz_idesc(32));
-          } else {                                           // block 7 | 0, 1
-            tz_mma(tmem + 224u, da, umma_desc_kmajor(bt, 128, 256), tz_idesc(32));
-            tz_mma(tmem, da, umma_desc_kmajor(bt + 4 * 256, 128, 256), tz_idesc(64));
-          }
+      for (int ks = 0; ks < 2; ++ks) {
+        const uint64_t da = umma_desc_kmajor(a_s + (uint32_t)(2 * ks * kTzPlane + dy * kTzRowStride + dx * 16),
+                                             kTzPlane, kTzRowStride);
+        const uint32_t bt = b0 + (uint32_t)(c * kTzBTap + ks * kTzBKs);
+        if (bb <= 5) {
+          tz_mma(tmem + (uint32_t)(32 * bb), da, umma_desc_kmajor(bt, 128, 256), tz_idesc(96));
+        } else if (bb == 6) {                                // blocks 6, 7 | 0
+          tz_mma(tmem + 192u, da, umma_desc_kmajor(bt, 128, 256), tz_idesc(64));
+          tz_mma(tmem, da, umma_desc_kmajor(bt + 8 * 256, 128, 256), tz_idesc(32));
+        } else {                                             // block 7 | 0, 1
+          tz_mma(tmem + 224u, da, umma_desc_kmajor(bt, 128, 256), tz_idesc(32));
+          tz_mma(tmem, da, umma_desc_kmajor(bt + 4 * 256, 128, 256), tz_idesc(64));
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(smem_u32(&s_mbar[i & 1])) : "memory");
     }
-    if (i <= nz + 1) issued = i + 1;
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(smem_u32(&s_mbar[j & 3])) : "memory");
+  };
+  // input slice i + 1 is issued in step i, while slice i - 1 is awaited:
+  // at most three slices in flight, on three different barriers
+  if (tid == 128) issue(0);
+  int issued = 1;                                            // input slices whose instructions were issued
+  for (int i = 0; i <= nz + 2; ++i) {
+    if (i + 1 <= nz + 1 && tid == 128) issue(i + 1);
+    if (i + 1 <= nz + 1) issued = i + 2;
     if (i >= 1) {
       // input slice i - 1 done: output slice i - 3 is complete; read it out
       // (warps 0-3: one accumulator row each), then zero its block
       const int ip = i - 1, zo = i - 3;
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&s_mbar[ip & 1]), (uint32_t)((ip >> 1) & 1)));
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&s_mbar[ip & 3]), (uint32_t)((ip >> 2) & 1)));
       if (!ok) {
         atomicExch(err, 1u);
         s_fail = 1;
@@ -485,10 +500,10 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       }
     }
-    // input slice i + 2 into the slot input slice i - 2 left (every
-    // instruction that read it has completed); fetch slice i + 3
-    if (i + 2 <= nz + 1) tz_store(s_a + ((i + 2) % kTzRing) * kTzSlice, tid, pre);
-    if (i + 3 <= nz + 1) tz_fetch(src, x0t, y0t, z0 - 1 + i + 3, tid, pre);
+    // input slice i + 3 into the slot input slice i - 1 left (every
+    // instruction that read it has completed); fetch slice i + 4
+    if (i + 3 <= nz + 1) tz_store(s_a + ((i + 3) % kTzRing) * kTzSlice, tid, pre);
+    if (i + 4 <= nz + 1) tz_fetch(src, x0t, y0t, z0 - 1 + i + 4, tid, pre);
     if constexpr (EPI != kEpiRelu) {                         // mask rows of output slice i - 2, read out next step
       const int zm = i - 2;
       if (erow && zm >= 0 && zm < nz) {
@@ -507,7 +522,7 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
   if (s_fail && issued > 0) {
     // a wait gave up: a last bounded wait for the newest commit before freeing
     const int ip = issued - 1;
-    mbar_wait(smem_u32(&s_mbar[ip & 1]), (uint32_t)((ip >> 1) & 1));
+    mbar_wait(smem_u32(&s_mbar[ip & 3]), (uint32_t)((ip >> 2) & 1));
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -532,11 +547,13 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t&
 // (tile position, s) loops over grids s, s + kWgradSplitTc, ...; the input
 // tile (halo) and the gradient tile enter shared memory as bfloat16 rows,
 // and ldmatrix.trans turns the voxel rows into the K dimension of both
-// operands.  Warp w accumulates taps w, w + 8, w + 16, w + 24 and adds its
-// sums once (atomically) at the end.  The bias gradient db[co] = sum over
-// voxels of g[v][co] is summed in binary32 from the same loads.
+// operands.  Warp w of 16 accumulates taps w and w + 16 and adds its sums
+// once (atomically) at the end.  The tiles are loaded with 16-byte reads,
+// four in flight per thread.  The bias gradient db[co] = sum over voxels of
+// g[v][co] is summed in binary32 from the same loads.
 constexpr int kWgradSplitTc = 2;
-__global__ void __launch_bounds__(kConvThreads) wgrad_mma_kernel(const float* __restrict__ in,
+constexpr int kWgWarps = 16, kWgThreads = 32 * kWgWarps;   // two taps a warp
+__global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const float* __restrict__ in,
                                                                 const float* __restrict__ g, int n_grids,
                                                                 float* __restrict__ dW, float* __restrict__ db) {
   extern __shared__ __align__(16) uint8_t smb[];
@@ -547,7 +564,7 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_mma_kernel(const float* __
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g4 = lane >> 2, t4 = lane & 3;
   const int mi = lane >> 3, mr = lane & 7;
-  constexpr int kTapsPerWarp = 4;
+  constexpr int kTapsPerWarp = (27 + kWgWarps - 1) / kWgWarps;
   float acc[kTapsPerWarp][2][4][4];
 #pragma unroll
   for (int j = 0; j < kTapsPerWarp; ++j)
@@ -558,36 +575,63 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_mma_kernel(const float* __
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[j][mt][nt][q] = 0.0f;
   const uint32_t x_base = smem_u32(s_x), g_base = smem_u32(s_g);
-  // kConvThreads is a multiple of HID / 2: a thread's channel pair is fixed
-  static_assert(kConvThreads % (HID / 2) == 0, "channel pair per thread");
-  float2 bsum = make_float2(0.0f, 0.0f);
+  // kWgThreads is a multiple of HID / 4: a thread's four channels are fixed
+  static_assert(kWgThreads % (HID / 4) == 0, "channel quad per thread");
+  float4 bsum = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  // 16-byte loads, kLoadBatch of them in flight before any is stored
+  constexpr int kLoadBatch = 4;
+  constexpr int kHaloItems = HZ * HY * HX * (HID / 4), kTileItems = TZ * TY * TX * (HID / 4);
+  auto store4 = [](uint8_t* row, int c4, float4 v) {
+    __nv_bfloat162 h[2] = {__floats2bfloat162_rn(v.x, v.y), __floats2bfloat162_rn(v.z, v.w)};
+    *reinterpret_cast<uint2*>(row + 8 * c4) = *reinterpret_cast<const uint2*>(h);
+  };
   for (int n = blockIdx.y; n < n_grids; n += kWgradSplitTc) {
     const float* src = in + (size_t)n * NV * HID;
     const float* gs = g + (size_t)n * NV * HID;
     __syncthreads();
-    for (int q = threadIdx.x; q < HZ * HY * HX * (HID / 2); q += blockDim.x) {
-      const int c2 = q % (HID / 2), p = q / (HID / 2);
-      const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
-      const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
-      float2 v = make_float2(0.0f, 0.0f);
-      if (gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
-        v = *reinterpret_cast<const float2*>(src + ((size_t)(gz * EG + gy) * EG + gx) * HID + 2 * c2);
-      *reinterpret_cast<__nv_bfloat162*>(s_x + p * kRowB + 4 * c2) = __floats2bfloat162_rn(v.x, v.y);
+    for (int q0 = threadIdx.x; q0 < kHaloItems; q0 += kLoadBatch * kWgThreads) {
+      float4 v[kLoadBatch];
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int q = q0 + u * kWgThreads;
+        const int c4 = q % (HID / 4), p = q / (HID / 4);
+        const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
+        const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
+        v[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (q < kHaloItems && gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
+          v[u] = __ldg(reinterpret_cast<const float4*>(src + ((size_t)(gz * EG + gy) * EG + gx) * HID) + c4);
+      }
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int q = q0 + u * kWgThreads;
+        if (q < kHaloItems) store4(s_x + (q / (HID / 4)) * kRowB, q % (HID / 4), v[u]);
+      }
     }
-    for (int q = threadIdx.x; q < TZ * TY * TX * (HID / 2); q += blockDim.x) {
-      const int c2 = q % (HID / 2), p = q / (HID / 2);
-      const int gx = x0t + p % TX, gy = y0t + (p / TX) % TY, gz = z0t + p / (TX * TY);
-      float2 v = make_float2(0.0f, 0.0f);                   // voxels outside the grid add nothing
-      if (gx < EG && gy < EG && gz < EG)
-        v = *reinterpret_cast<const float2*>(gs + ((size_t)(gz * EG + gy) * EG + gx) * HID + 2 * c2);
-      bsum.x += v.x;
-      bsum.y += v.y;
-      *reinterpret_cast<__nv_bfloat162*>(s_g + p * kRowB + 4 * c2) = __floats2bfloat162_rn(v.x, v.y);
+    for (int q0 = threadIdx.x; q0 < kTileItems; q0 += kLoadBatch * kWgThreads) {
+      float4 v[kLoadBatch];
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int q = q0 + u * kWgThreads;
+        const int c4 = q % (HID / 4), p = q / (HID / 4);
+        const int gx = x0t + p % TX, gy = y0t + (p / TX) % TY, gz = z0t + p / (TX * TY);
+        v[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);         // voxels outside the grid add nothing
+        if (q < kTileItems && gx < EG && gy < EG && gz < EG)
+          v[u] = __ldg(reinterpret_cast<const float4*>(gs + ((size_t)(gz * EG + gy) * EG + gx) * HID) + c4);
+      }
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int q = q0 + u * kWgThreads;
+        bsum.x += v[u].x;
+        bsum.y += v[u].y;
+        bsum.z += v[u].z;
+        bsum.w += v[u].w;
+        if (q < kTileItems) store4(s_g + (q / (HID / 4)) * kRowB, q % (HID / 4), v[u]);
+      }
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < kTapsPerWarp; ++j) {
-      const int t = warp + 8 * j;
+      const int t = warp + kWgWarps * j;
       if (t >= 27) break;
       const int toff = ((t / 9) * HY + (t / 3) % 3) * HX + t % 3;
       for (int kc = 0; kc < (TZ * TY * TX) / 16; ++kc) {
@@ -614,7 +658,7 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_mma_kernel(const float* __
   }
 #pragma unroll
   for (int j = 0; j < kTapsPerWarp; ++j) {
-    const int t = warp + 8 * j;
+    const int t = warp + kWgWarps * j;
     if (t >= 27) break;
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
@@ -629,19 +673,23 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_mma_kernel(const float* __
         }
       }
   }
-  // bias gradient: the threads of one channel pair, then one add per channel
+  // bias gradient: the threads of one channel quad, then one add per channel
   __syncthreads();
-  float2* s_red = reinterpret_cast<float2*>(smb);
+  float4* s_red = reinterpret_cast<float4*>(smb);
   s_red[threadIdx.x] = bsum;
   __syncthreads();
-  if (threadIdx.x < HID / 2) {
-    float2 t = make_float2(0.0f, 0.0f);
-    for (int q = threadIdx.x; q < kConvThreads; q += HID / 2) {
+  if (threadIdx.x < HID / 4) {
+    float4 t = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int q = threadIdx.x; q < kWgThreads; q += HID / 4) {
       t.x += s_red[q].x;
       t.y += s_red[q].y;
+      t.z += s_red[q].z;
+      t.w += s_red[q].w;
     }
-    atomicAdd(&db[2 * threadIdx.x], t.x);
-    atomicAdd(&db[2 * threadIdx.x + 1], t.y);
+    atomicAdd(&db[4 * threadIdx.x], t.x);
+    atomicAdd(&db[4 * threadIdx.x + 1], t.y);
+    atomicAdd(&db[4 * threadIdx.x + 2], t.z);
+    atomicAdd(&db[4 * threadIdx.x + 3], t.w);
   }
 }
 
@@ -665,11 +713,15 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_kernel(const float* __rest
   float* s_g = sm + HZ * HY * HX * SC;                    // TZ * TY * TX * COUT
   const int tile = blockIdx.x;
   const int x0t = (tile % kTilesX) * TX, y0t = ((tile / kTilesX) % kTilesY) * TY, z0t = (tile / (kTilesX * kTilesY)) * TZ;
-  float acc[PPT][COUT];
+  constexpr bool kQuads = CIN == 1 && COUT % 4 == 0;
+  constexpr int NQ = 27 * (COUT / 4);                     // (tap, output channel quad) pairs
+  static_assert(!kQuads || NQ <= kConvThreads, "a thread per pair");
+  float acc[kQuads ? 1 : PPT][kQuads ? 1 : COUT];
 #pragma unroll
-  for (int j = 0; j < PPT; ++j)
+  for (int j = 0; j < (kQuads ? 1 : PPT); ++j)
 #pragma unroll
-    for (int co = 0; co < COUT; ++co) acc[j][co] = 0.0f;
+    for (int co = 0; co < (kQuads ? 1 : COUT); ++co) acc[j][co] = 0.0f;
+  float4 acc4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   float bacc = 0.0f;
   for (int n = blockIdx.y; n < n_grids; n += kWgradSplit) {
     const float* src = in + (size_t)n * NV * CIN;
@@ -677,14 +729,24 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_kernel(const float* __rest
     __syncthreads();
     load_halo<CIN>(src, s_in, x0t, y0t, z0t);
     if constexpr (COUT % 4 == 0) {
-      for (int q = threadIdx.x; q < TZ * TY * TX * (COUT / 4); q += blockDim.x) {
-        const int c4 = q % (COUT / 4), p = q / (COUT / 4);
-        const int tx = p % TX, ty = (p / TX) % TY, tz = p / (TX * TY);
-        const int gx = x0t + tx, gy = y0t + ty, gz = z0t + tz;
-        float4 val = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // voxels outside the grid add nothing
-        if (gx < EG && gy < EG && gz < EG)
-          val = __ldg(reinterpret_cast<const float4*>(gs + ((size_t)(gz * EG + gy) * EG + gx) * COUT) + c4);
-        reinterpret_cast<float4*>(s_g)[q] = val;
+      // 16-byte loads, four of them in flight before any is stored
+      constexpr int kItems = TZ * TY * TX * (COUT / 4), kBatch = 4;
+      for (int q0 = threadIdx.x; q0 < kItems; q0 += kBatch * kConvThreads) {
+        float4 val[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const int q = q0 + u * kConvThreads;
+          const int c4 = q % (COUT / 4), p = q / (COUT / 4);
+          const int gx = x0t + p % TX, gy = y0t + (p / TX) % TY, gz = z0t + p / (TX * TY);
+          val[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);    // voxels outside the grid add nothing
+          if (q < kItems && gx < EG && gy < EG && gz < EG)
+            val[u] = __ldg(reinterpret_cast<const float4*>(gs + ((size_t)(gz * EG + gy) * EG + gx) * COUT) + c4);
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const int q = q0 + u * kConvThreads;
+          if (q < kItems) reinterpret_cast<float4*>(s_g)[q] = val[u];
+        }
       }
     } else {
       for (int q = threadIdx.x; q < TZ * TY * TX * COUT; q += blockDim.x) {
@@ -697,29 +759,56 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_kernel(const float* __rest
       }
     }
     __syncthreads();
+    if constexpr (kQuads) {
+      // one input channel: a thread per (tap, four output channels)
+      if (threadIdx.x < NQ) {
+        const int t = threadIdx.x / (COUT / 4), c4 = threadIdx.x % (COUT / 4);
+        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+        for (int p = 0; p < TZ * TY * TX; ++p) {
+          const int tx = p % TX, ty = (p / TX) % TY, tz = p / (TX * TY);
+          const float xv = s_in[(((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * SC];
+          const float4 gv = reinterpret_cast<const float4*>(s_g + p * COUT)[c4];
+          acc4.x = fmaf(xv, gv.x, acc4.x);
+          acc4.y = fmaf(xv, gv.y, acc4.y);
+          acc4.z = fmaf(xv, gv.z, acc4.z);
+          acc4.w = fmaf(xv, gv.w, acc4.w);
+        }
+      }
+    } else {
 #pragma unroll
-    for (int j = 0; j < PPT; ++j) {
-      const int pr = threadIdx.x + j * kConvThreads;
-      if (pr >= NP) break;
-      const int t = pr / CIN, ci = pr % CIN;
-      const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-      for (int p = 0; p < TZ * TY * TX; ++p) {
-        const int tx = p % TX, ty = (p / TX) % TY, tz = p / (TX * TY);
-        const float xv = s_in[(((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * SC + ci];
-        const float* gr = s_g + p * COUT;
+      for (int j = 0; j < PPT; ++j) {
+        const int pr = threadIdx.x + j * kConvThreads;
+        if (pr >= NP) break;
+        const int t = pr / CIN, ci = pr % CIN;
+        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+        for (int p = 0; p < TZ * TY * TX; ++p) {
+          const int tx = p % TX, ty = (p / TX) % TY, tz = p / (TX * TY);
+          const float xv = s_in[(((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * SC + ci];
+          const float* gr = s_g + p * COUT;
 #pragma unroll
-        for (int co = 0; co < COUT; ++co) acc[j][co] = fmaf(xv, gr[co], acc[j][co]);
+          for (int co = 0; co < COUT; ++co) acc[j][co] = fmaf(xv, gr[co], acc[j][co]);
+        }
       }
     }
     if (threadIdx.x < COUT)
       for (int p = 0; p < TZ * TY * TX; ++p) bacc += s_g[p * COUT + threadIdx.x];
   }
+  if constexpr (kQuads) {
+    if (threadIdx.x < NQ) {
+      float* d = dW + (threadIdx.x / (COUT / 4)) * COUT + 4 * (threadIdx.x % (COUT / 4));
+      atomicAdd(d, acc4.x);
+      atomicAdd(d + 1, acc4.y);
+      atomicAdd(d + 2, acc4.z);
+      atomicAdd(d + 3, acc4.w);
+    }
+  } else {
 #pragma unroll
-  for (int j = 0; j < PPT; ++j) {
-    const int pr = threadIdx.x + j * kConvThreads;
-    if (pr >= NP) break;
+    for (int j = 0; j < PPT; ++j) {
+      const int pr = threadIdx.x + j * kConvThreads;
+      if (pr >= NP) break;
 #pragma unroll
-    for (int co = 0; co < COUT; ++co) atomicAdd(&dW[pr * COUT + co], acc[j][co]);
+      for (int co = 0; co < COUT; ++co) atomicAdd(&dW[pr * COUT + co], acc[j][co]);
+    }
   }
   if (threadIdx.x < COUT) atomicAdd(&db[threadIdx.x], bacc);
 }
@@ -816,6 +905,13 @@ struct ro_mc {
   float* loss;                        // scratch loss when the caller passes none
   uint32_t* flag;                     // set by a tensor-core wait that gave up (latched)
   uint32_t step = 0;
+  cudaStream_t side = nullptr;        // weight gradients, beside the input gradients
+  cudaEvent_t ev[5] = {};             // fork and join points between the two streams
+  ~ro_mc() {
+    for (cudaEvent_t& x : ev)
+      if (x) cudaEventDestroy(x);
+    if (side) cudaStreamDestroy(side);
+  }
 };
 
 namespace {
@@ -868,7 +964,7 @@ cudaError_t wgrad_tc(const float* in, const float* g, uint32_t n, float* dW, flo
   constexpr size_t sm = wgrad_mma_smem();
   cudaError_t e = cudaFuncSetAttribute(wgrad_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  wgrad_mma_kernel<<<dim3(kTilesX * kTilesY * kTilesZ, kWgradSplitTc), kConvThreads, sm, s>>>(in, g, (int)n, dW, db);
+  wgrad_mma_kernel<<<dim3(kTilesX * kTilesY * kTilesZ, kWgradSplitTc), kWgThreads, sm, s>>>(in, g, (int)n, dW, db);
   return cudaGetLastError();
 }
 
@@ -907,17 +1003,34 @@ cudaError_t mc_backward(ro_mc* m, uint32_t n, const float* x0, const float* targ
     e = cudaGetLastError();
   }
   const float* zero_bias = nullptr;
+  // The weight gradients of a layer and the input gradients through it read
+  // the same output gradient and write different buffers: the weight
+  // gradients run on the side stream.  ga is written again by the layer-2
+  // input gradients, so those wait until the layer-3 weight gradients have
+  // read it; the main stream joins the side stream at the end.
+  cudaStream_t s2 = m->side;
+  auto fork = [&](int k) {
+    cudaError_t r = cudaEventRecord(m->ev[k], s);
+    return r == cudaSuccess ? cudaStreamWaitEvent(s2, m->ev[k], 0) : r;
+  };
   // layer 4 (32 -> 1)
-  if (e == cudaSuccess) e = wgrad<HID, 1>(m->a3, m->g4, n, G + kWOff[3], G + kBOff[3], s);
+  if (e == cudaSuccess) e = fork(0);
+  if (e == cudaSuccess) e = wgrad<HID, 1>(m->a3, m->g4, n, G + kWOff[3], G + kBOff[3], s2);
   if (e == cudaSuccess) e = conv<1, HID, kEpiMask>(m->g4, m->Wt3, zero_bias, m->ga, m->a3, n, s);
   // layer 3 (32 -> 32)
-  if (e == cudaSuccess) e = wgrad_tc(m->a2, m->ga, n, G + kWOff[2], G + kBOff[2], s);
+  if (e == cudaSuccess) e = fork(1);
+  if (e == cudaSuccess) e = wgrad_tc(m->a2, m->ga, n, G + kWOff[2], G + kBOff[2], s2);
+  if (e == cudaSuccess) e = cudaEventRecord(m->ev[2], s2);
   if (e == cudaSuccess) e = conv_tc<kEpiMask>(m->ga, m->wd2, zero_bias, m->gb, m->a2, n, m->flag, s);
   // layer 2 (32 -> 32)
-  if (e == cudaSuccess) e = wgrad_tc(m->a1, m->gb, n, G + kWOff[1], G + kBOff[1], s);
+  if (e == cudaSuccess) e = fork(3);
+  if (e == cudaSuccess) e = wgrad_tc(m->a1, m->gb, n, G + kWOff[1], G + kBOff[1], s2);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->ev[2], 0);
   if (e == cudaSuccess) e = conv_tc<kEpiMask>(m->gb, m->wd1, zero_bias, m->ga, m->a1, n, m->flag, s);
   // layer 1 (1 -> 32)
   if (e == cudaSuccess) e = wgrad<1, HID>(x0, m->ga, n, G + kWOff[0], G + kBOff[0], s);
+  if (e == cudaSuccess) e = cudaEventRecord(m->ev[4], s2);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->ev[4], 0);
   return e;
 }
 
@@ -953,7 +1066,10 @@ ro_status ro_mc_create(const ro_mc_desc* d, void* arena, uint64_t arena_bytes, v
   m->a1 = f(L.a1); m->a2 = f(L.a2); m->a3 = f(L.a3); m->ga = f(L.ga); m->gb = f(L.gb);
   m->g4 = f(L.g4); m->y = f(L.y); m->loss = f(L.loss);
   m->flag = reinterpret_cast<uint32_t*>(b + L.flag);
-  cudaError_t e = cudaMemsetAsync(arena, 0, L.Wt3, m->stream);   // parameters, copies, moments, gradients, flag
+  cudaError_t e = cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking);
+  for (cudaEvent_t& x : m->ev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMemsetAsync(arena, 0, L.Wt3, m->stream);   // parameters, copies, moments, gradients, flag
   if (e == cudaSuccess) e = mc_refresh(m);
   if (e != cudaSuccess) {
     delete m;
@@ -965,7 +1081,9 @@ ro_status ro_mc_create(const ro_mc_desc* d, void* arena, uint64_t arena_bytes, v
 
 ro_status ro_mc_destroy(ro_mc* m) {
   if (!m) return RO_ERR_INVALID_ARG;
-  const cudaError_t e = cudaStreamSynchronize(m->stream);
+  cudaError_t e = cudaStreamSynchronize(m->stream);
+  const cudaError_t e2 = cudaStreamSynchronize(m->side);
+  if (e == cudaSuccess) e = e2;
   delete m;
   return mc_err(e);
 }
