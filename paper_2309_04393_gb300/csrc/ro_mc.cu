@@ -713,14 +713,16 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_kernel(const float* __rest
   float* s_g = sm + HZ * HY * HX * SC;                    // TZ * TY * TX * COUT
   const int tile = blockIdx.x;
   const int x0t = (tile % kTilesX) * TX, y0t = ((tile / kTilesX) % kTilesY) * TY, z0t = (tile / (kTilesX * kTilesY)) * TZ;
-  constexpr bool kQuads = CIN == 1 && COUT % 4 == 0;
-  constexpr int NQ = 27 * (COUT / 4);                     // (tap, output channel quad) pairs
-  static_assert(!kQuads || NQ <= kConvThreads, "a thread per pair");
-  float acc[kQuads ? 1 : PPT][kQuads ? 1 : COUT];
+  constexpr bool kQuads = CIN == 1 && COUT % 4 == 0;     // a thread per (tap, output channel quad)
+  constexpr bool kInQuads = COUT == 1 && CIN % 4 == 0;   // a thread per (tap, input channel quad)
+  constexpr int NQ = 27 * (kQuads ? COUT / 4 : CIN / 4);
+  static_assert(!(kQuads || kInQuads) || NQ <= kConvThreads, "a thread per pair");
+  constexpr bool kPairs = !kQuads && !kInQuads;
+  float acc[kPairs ? PPT : 1][kPairs ? COUT : 1];
 #pragma unroll
-  for (int j = 0; j < (kQuads ? 1 : PPT); ++j)
+  for (int j = 0; j < (kPairs ? PPT : 1); ++j)
 #pragma unroll
-    for (int co = 0; co < (kQuads ? 1 : COUT); ++co) acc[j][co] = 0.0f;
+    for (int co = 0; co < (kPairs ? COUT : 1); ++co) acc[j][co] = 0.0f;
   float4 acc4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   float bacc = 0.0f;
   for (int n = blockIdx.y; n < n_grids; n += kWgradSplit) {
@@ -774,6 +776,22 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_kernel(const float* __rest
           acc4.w = fmaf(xv, gv.w, acc4.w);
         }
       }
+    } else if constexpr (kInQuads) {
+      // one output channel: a thread per (tap, four input channels), 16-byte reads
+      if (threadIdx.x < NQ) {
+        const int t = threadIdx.x / (CIN / 4), c4 = threadIdx.x % (CIN / 4);
+        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+        for (int p = 0; p < TZ * TY * TX; ++p) {
+          const int tx = p % TX, ty = (p / TX) % TY, tz = p / (TX * TY);
+          const float4 xv =
+              *reinterpret_cast<const float4*>(s_in + (((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * SC + 4 * c4);
+          const float gv = s_g[p];
+          acc4.x = fmaf(xv.x, gv, acc4.x);
+          acc4.y = fmaf(xv.y, gv, acc4.y);
+          acc4.z = fmaf(xv.z, gv, acc4.z);
+          acc4.w = fmaf(xv.w, gv, acc4.w);
+        }
+      }
     } else {
 #pragma unroll
       for (int j = 0; j < PPT; ++j) {
@@ -796,6 +814,14 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_kernel(const float* __rest
   if constexpr (kQuads) {
     if (threadIdx.x < NQ) {
       float* d = dW + (threadIdx.x / (COUT / 4)) * COUT + 4 * (threadIdx.x % (COUT / 4));
+      atomicAdd(d, acc4.x);
+      atomicAdd(d + 1, acc4.y);
+      atomicAdd(d + 2, acc4.z);
+      atomicAdd(d + 3, acc4.w);
+    }
+  } else if constexpr (kInQuads) {
+    if (threadIdx.x < NQ) {                              // dW[t][ci][0], four consecutive ci
+      float* d = dW + (threadIdx.x / (CIN / 4)) * CIN + 4 * (threadIdx.x % (CIN / 4));
       atomicAdd(d, acc4.x);
       atomicAdd(d + 1, acc4.y);
       atomicAdd(d + 2, acc4.z);
