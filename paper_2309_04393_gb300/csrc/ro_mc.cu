@@ -47,7 +47,12 @@ static_assert(kBOff[3] + 1 == RO_MC_PARAMS, "parameter layout");
 // (36 floats: eight 16-byte reads of neighbouring voxels cover all banks)
 __host__ __device__ constexpr int pad_stride(int c) { return c > 1 ? (c % 4 == 0 ? c + 4 : c + 1) : 1; }
 
-enum : int { kEpiNone = 0, kEpiRelu = 1, kEpiResidual = 2, kEpiMask = 3 };
+// convolution epilogues: ReLU(sum + bias); the residual y = x0 + sum + bias
+// (one output channel); the gradient passed where the layer's activation is
+// positive
+enum : int { kEpiRelu = 1, kEpiResidual = 2, kEpiMask = 3 };
+
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 // ------------------------------------------------------------- upsample
 // Level-0 voxel X (relative to the child's apron origin) sits at level-1
@@ -98,10 +103,11 @@ __global__ void to_raw_kernel(const float* __restrict__ y, uint8_t* __restrict__
 
 // ---------------------------------------------------------- convolution
 // The HZ x HY x HX input tile with its one-voxel halo (zeros outside the
-// grid) into shared memory at channel stride pad_stride(CIN); 16-byte loads
-// when the channels allow.
-template <int CIN>
+// grid) into shared memory at channel stride pad_stride(CIN), rounded to
+// bfloat16 values when RND; 16-byte loads when the channels allow.
+template <int CIN, bool RND>
 __device__ __forceinline__ void load_halo(const float* __restrict__ src, float* s_in, int x0t, int y0t, int z0t) {
+  auto rnd = [](float v) { return RND ? bf16_round(v) : v; };
   constexpr int SC = pad_stride(CIN);
   if constexpr (CIN % 4 == 0) {
     // 16-byte loads, four of them in flight before any is stored
@@ -121,7 +127,9 @@ __device__ __forceinline__ void load_halo(const float* __restrict__ src, float* 
 #pragma unroll
       for (int u = 0; u < kBatch; ++u) {
         const int q = q0 + u * (int)blockDim.x;
-        if (q < kItems) *reinterpret_cast<float4*>(s_in + (q / (CIN / 4)) * SC + 4 * (q % (CIN / 4))) = val[u];
+        if (q < kItems)
+          *reinterpret_cast<float4*>(s_in + (q / (CIN / 4)) * SC + 4 * (q % (CIN / 4))) =
+              make_float4(rnd(val[u].x), rnd(val[u].y), rnd(val[u].z), rnd(val[u].w));
       }
     }
   } else {
@@ -132,93 +140,9 @@ __device__ __forceinline__ void load_halo(const float* __restrict__ src, float* 
       float val = 0.0f;
       if (gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
         val = src[((size_t)(gz * EG + gy) * EG + gx) * CIN + c];
-      s_in[p * SC + c] = val;
+      s_in[p * SC + c] = rnd(val);
     }
   }
-}
-
-// out[v][co] = epi(sum_tap sum_ci in[v + off(tap)][ci] * w[tap][ci][co] + b[co])
-// aux: the residual x0 (kEpiResidual, COUT = 1) or the activation whose
-// positive entries pass the gradient (kEpiMask).
-template <int CIN, int COUT, int EPI>
-__global__ void __launch_bounds__(kConvThreads) conv_kernel(const float* __restrict__ in, const float* __restrict__ w,
-                                                           const float* __restrict__ bias, float* __restrict__ out,
-                                                           const float* __restrict__ aux) {
-  extern __shared__ float sm[];
-  constexpr int SC = pad_stride(CIN);
-  float* s_in = sm;                              // HZ * HY * HX * SC
-  float* s_w = sm + HZ * HY * HX * SC;           // 27 * CIN * COUT
-  const int tile = blockIdx.x, n = blockIdx.y;
-  const int x0t = (tile % kTilesX) * TX, y0t = ((tile / kTilesX) % kTilesY) * TY, z0t = (tile / (kTilesX * kTilesY)) * TZ;
-  load_halo<CIN>(in + (size_t)n * NV * CIN, s_in, x0t, y0t, z0t);
-  for (int q = threadIdx.x; q < 27 * CIN * COUT; q += blockDim.x) s_w[q] = w[q];
-  __syncthreads();
-  const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
-  const int gx = x0t + tx, gy = y0t + ty, gz = z0t + tz;
-  float acc[COUT];
-#pragma unroll
-  for (int co = 0; co < COUT; ++co) acc[co] = 0.0f;
-  for (int t = 0; t < 27; ++t) {
-    const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-    const float* a = s_in + (((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * SC;
-    const float* wt = s_w + t * CIN * COUT;
-    if constexpr (CIN % 4 == 0 && COUT == 1) {
-      // 16-byte reads of four channels and their four weights
-#pragma unroll
-      for (int c4 = 0; c4 < CIN / 4; ++c4) {
-        const float4 xv = *reinterpret_cast<const float4*>(a + 4 * c4);
-        const float4 wv = *reinterpret_cast<const float4*>(wt + 4 * c4);
-        acc[0] = fmaf(xv.x, wv.x, acc[0]);
-        acc[0] = fmaf(xv.y, wv.y, acc[0]);
-        acc[0] = fmaf(xv.z, wv.z, acc[0]);
-        acc[0] = fmaf(xv.w, wv.w, acc[0]);
-      }
-    } else {
-#pragma unroll 4
-      for (int ci = 0; ci < CIN; ++ci) {
-        const float xv = a[ci];
-        const float* wr = wt + ci * COUT;
-#pragma unroll
-        for (int co = 0; co < COUT; ++co) acc[co] = fmaf(xv, wr[co], acc[co]);
-      }
-    }
-  }
-  if (gx >= EG || gy >= EG || gz >= EG) return;
-  const size_t v = (size_t)n * NV + (size_t)(gz * EG + gy) * EG + gx;
-  if constexpr (COUT % 4 == 0) {
-    // 16-byte stores (and mask reads) of four channels
-#pragma unroll
-    for (int c4 = 0; c4 < COUT / 4; ++c4) {
-      float r[4] = {acc[4 * c4], acc[4 * c4 + 1], acc[4 * c4 + 2], acc[4 * c4 + 3]};
-      float4 m4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      if constexpr (EPI == kEpiMask) m4 = __ldg(reinterpret_cast<const float4*>(aux + v * COUT) + c4);
-      const float mk[4] = {m4.x, m4.y, m4.z, m4.w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int co = 4 * c4 + e;
-        if constexpr (EPI == kEpiRelu) r[e] = fmaxf(r[e] + bias[co], 0.0f);
-        else if constexpr (EPI == kEpiNone) r[e] = r[e] + bias[co];
-        else if constexpr (EPI == kEpiResidual) r[e] = r[e] + bias[co] + aux[v];
-        else r[e] = mk[e] > 0.0f ? r[e] : 0.0f;
-      }
-      reinterpret_cast<float4*>(out + v * COUT)[c4] = make_float4(r[0], r[1], r[2], r[3]);
-    }
-  } else {
-#pragma unroll
-    for (int co = 0; co < COUT; ++co) {
-      float r = acc[co];
-      if constexpr (EPI == kEpiRelu) r = fmaxf(r + bias[co], 0.0f);
-      else if constexpr (EPI == kEpiNone) r = r + bias[co];
-      else if constexpr (EPI == kEpiResidual) r = r + bias[co] + aux[v];
-      else r = aux[v * COUT + co] > 0.0f ? r : 0.0f;
-      out[v * COUT + co] = r;
-    }
-  }
-}
-
-template <int CIN, int COUT>
-constexpr size_t conv_smem() {
-  return (size_t)(HZ * HY * HX * pad_stride(CIN) + 27 * CIN * COUT) * sizeof(float);
 }
 
 // ----------------------------------------- warp-level tensor-core helpers
@@ -293,14 +217,31 @@ constexpr int kTzTilesX = (EG + TZX - 1) / TZX, kTzTilesY = (EG + TZY - 1) / TZY
 constexpr int kTzUnits = kTzTilesX * kTzTilesY * kTzChunks;  // columns per grid
 constexpr int kTzRowStride = HZX2 * 16;                      // one halo row of 10 voxels: 160 B (SBO)
 constexpr int kTzPlane = HZY2 * kTzRowStride;                // one channel octet of a slice: 2,880 B (LBO)
-constexpr int kTzSlice = 4 * kTzPlane;                       // 11,520 B
 constexpr int kTzRing = 4;                                   // input slices in shared memory
-constexpr int kTzBKs = 12 * 256;                             // B of one (dy, dx) tap and K step: 96 rows
-constexpr int kTzBTap = 2 * kTzBKs;                          // 6,144 B
-constexpr int kTzB = 9 * kTzBTap;                            // 55,296 B
-constexpr int kTzCols = 256;                                 // tensor-memory columns: 8 blocks of 32
-constexpr int kTzSliceItems = HZY2 * HZX2 * 4;               // 8-channel pieces of an input slice
-constexpr int kTzItems = (kTzSliceItems + kTzThreads - 1) / kTzThreads;
+
+// Shapes of a z-folded convolution with CIN (1 or 32) input and COUT (1 or
+// 32) output channels.  One input channel is padded to K = 16: its slice is
+// one plane with the value in the first of each row's 8 channels, and the
+// second 8-channel chunk is a plane of zeros.  One output channel is padded
+// to 16 accumulator columns per z tap (N = 48).
+template <int CIN, int COUT>
+struct TzShape {
+  static constexpr int KS = CIN == 1 ? 1 : 2;                // K steps of 16 input channels
+  static constexpr int PLANES = CIN == 1 ? 2 : 4;            // 8-channel planes of an input slice
+  static constexpr int SLICE = PLANES * kTzPlane;            // 5,760 or 11,520 B
+  static constexpr int COUTP = COUT == 1 ? 16 : 32;          // accumulator columns of an output slice
+  static constexpr int NB = 3 * COUTP;                       // B rows of a (dy, dx) tap: the three dz taps
+  static constexpr int BKS = NB / 8 * 256;                   // B of one (dy, dx) tap and K step
+  static constexpr int BTAP = KS * BKS;
+  static constexpr int BBYTES = 9 * BTAP;
+  static constexpr int COLS = 8 * COUTP;                     // tensor-memory columns: 8 blocks
+  static constexpr int ITEMS = HZY2 * HZX2 * (CIN == 1 ? 1 : 4);   // pieces of an input slice
+  static constexpr int PER = (ITEMS + kTzThreads - 1) / kTzThreads;
+  // shared memory; at least 76 KB when a block holds 256 columns of tensor
+  // memory, so that no third block (which could not allocate) is resident
+  static constexpr size_t SMEM_USED = (size_t)BBYTES + (size_t)kTzRing * SLICE;
+  static constexpr size_t SMEM = COLS == 256 && SMEM_USED < 76 * 1024 ? 76 * 1024 : SMEM_USED;
+};
 
 __device__ __forceinline__ uint64_t umma_desc_kmajor(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   // start >> 4; leading byte offset (next K chunk); stride byte offset (next
@@ -321,53 +262,72 @@ __device__ __forceinline__ void tz_mma(uint32_t d_tmem, uint64_t da, uint64_t db
                :: "r"(d_tmem), "l"(da), "l"(db), "r"(idesc));
 }
 
-// this thread's 8-channel pieces of input slice gz (zeros outside the grid)
+// this thread's pieces of input slice gz (zeros outside the grid): 8
+// channels (32 bytes) each for 32 channels, one value for one channel
+template <int CIN>
 __device__ __forceinline__ void tz_fetch(const float* __restrict__ src, int x0t, int y0t, int gz, int tid,
-                                         float4 (&v)[kTzItems][2]) {
+                                         float4 (&v)[TzShape<CIN, 32>::PER][2]) {
+  using S = TzShape<CIN, 32>;
 #pragma unroll
-  for (int j = 0; j < kTzItems; ++j) {
+  for (int j = 0; j < S::PER; ++j) {
     const int w = tid + j * kTzThreads;
     v[j][0] = v[j][1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    const int q = w % 4, hx = (w / 4) % HZX2, hy = w / (4 * HZX2);
+    const int q = CIN == 1 ? 0 : w % 4, p = CIN == 1 ? w : w / 4;
+    const int hx = p % HZX2, hy = p / HZX2;
     const int gx = x0t + hx - 1, gy = y0t + hy - 1;
-    if (w < kTzSliceItems && gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG) {
-      const float4* p4 = reinterpret_cast<const float4*>(src + ((size_t)(gz * EG + gy) * EG + gx) * HID + 8 * q);
-      v[j][0] = __ldg(p4);
-      v[j][1] = __ldg(p4 + 1);
+    if (w < S::ITEMS && gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG) {
+      if constexpr (CIN == 1) {
+        v[j][0].x = __ldg(src + (size_t)(gz * EG + gy) * EG + gx);
+      } else {
+        const float4* p4 = reinterpret_cast<const float4*>(src + ((size_t)(gz * EG + gy) * EG + gx) * HID + 8 * q);
+        v[j][0] = __ldg(p4);
+        v[j][1] = __ldg(p4 + 1);
+      }
     }
   }
 }
 
-// ... rounded to bfloat16, into the octet planes of a ring slot
-__device__ __forceinline__ void tz_store(uint8_t* slot, int tid, const float4 (&v)[kTzItems][2]) {
+// ... rounded to bfloat16, into the octet planes of a ring slot (one
+// channel: the value and seven zeros in plane 0)
+template <int CIN>
+__device__ __forceinline__ void tz_store(uint8_t* slot, int tid, const float4 (&v)[TzShape<CIN, 32>::PER][2]) {
+  using S = TzShape<CIN, 32>;
 #pragma unroll
-  for (int j = 0; j < kTzItems; ++j) {
+  for (int j = 0; j < S::PER; ++j) {
     const int w = tid + j * kTzThreads;
-    if (w >= kTzSliceItems) continue;
-    const int q = w % 4, hx = (w / 4) % HZX2, hy = w / (4 * HZX2);
+    if (w >= S::ITEMS) continue;
+    const int q = CIN == 1 ? 0 : w % 4, p = CIN == 1 ? w : w / 4;
+    const int hx = p % HZX2, hy = p / HZX2;
     __nv_bfloat162 h[4] = {__floats2bfloat162_rn(v[j][0].x, v[j][0].y), __floats2bfloat162_rn(v[j][0].z, v[j][0].w),
                            __floats2bfloat162_rn(v[j][1].x, v[j][1].y), __floats2bfloat162_rn(v[j][1].z, v[j][1].w)};
     *reinterpret_cast<uint4*>(slot + q * kTzPlane + hy * kTzRowStride + hx * 16) = *reinterpret_cast<const uint4*>(h);
   }
 }
 
-// 32 columns of zeros into this warp's 32 lanes of tensor memory
+// NC columns of zeros into this warp's 32 lanes of tensor memory
+template <int NC>
 __device__ __forceinline__ void tz_zero(uint32_t taddr) {
   const uint32_t z = 0u;
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
-               "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" :: "r"(taddr), "r"(z) : "memory");
+  if constexpr (NC == 32)
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+                 "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" :: "r"(taddr), "r"(z) : "memory");
+  else
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};"
+                 :: "r"(taddr), "r"(z) : "memory");
 }
 
 __device__ __forceinline__ int tz_block(int zo) { return ((-zo - 1) % 8 + 8) % 8; }
 
-template <int EPI>
+template <int EPI, int CIN, int COUT>
 __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __restrict__ in,
                                                                const __nv_bfloat16* __restrict__ wb,
                                                                const float* __restrict__ bias, float* __restrict__ out,
                                                                const float* __restrict__ aux, uint32_t* __restrict__ err) {
+  using S = TzShape<CIN, COUT>;
+  constexpr int CP = S::COUTP;
   extern __shared__ __align__(128) uint8_t smz[];
-  uint8_t* s_b = smz;                                        // 9 (dy, dx) taps x kTzBTap
-  uint8_t* s_a = smz + kTzB;                                 // kTzRing input slices x kTzSlice
+  uint8_t* s_b = smz;                                        // 9 (dy, dx) taps x S::BTAP
+  uint8_t* s_a = smz + S::BBYTES;                            // kTzRing input slices x S::SLICE
   __shared__ __align__(8) uint64_t s_mbar[4];        // input slice j commits to s_mbar[j % 4]
   __shared__ uint32_t s_tmem, s_fail;
   __shared__ float s_bias[HID];
@@ -376,38 +336,48 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
   const int x0t = (unit % kTzTilesX) * TZX, y0t = ((unit / kTzTilesX) % kTzTilesY) * TZY;
   const int z0 = (unit / (kTzTilesX * kTzTilesY)) * kTzChunk;
   const int nz = min(kTzChunk, EG - z0);                     // output slices of this column
-  const float* src = in + (size_t)n * NV * HID;
-  // weights wb[tap][co][ci] (64-byte rows): tap (dz, dy, dx) goes to the B of
-  // (dy, dx), rows dz * 32 + co, in the canonical K-major layout
-  for (int q = tid; q < 27 * HID * 4; q += kTzThreads) {
-    const int t = q / (HID * 4), co = (q / 4) % HID, ch = q % 4;
-    const int nrow = (t / 9) * HID + co, c = t % 9;
-    *reinterpret_cast<uint4*>(s_b + c * kTzBTap + (ch >> 1) * kTzBKs + (nrow >> 3) * 256 + (ch & 1) * 128 +
+  const float* src = in + (size_t)n * NV * CIN;
+  // weights wb[tap][co][ci] (CP rows of 32 channels, 64 bytes, per tap): tap
+  // (dz, dy, dx) goes to the B of (dy, dx), rows dz * CP + co, in the
+  // canonical K-major layout; with one input channel only its first K step
+  for (int q = tid; q < 27 * CP * 4; q += kTzThreads) {
+    const int t = q / (CP * 4), co = (q / 4) % CP, ch = q % 4;
+    if (ch >= 2 * S::KS) continue;
+    const int nrow = (t / 9) * CP + co, c = t % 9;
+    *reinterpret_cast<uint4*>(s_b + c * S::BTAP + (ch >> 1) * S::BKS + (nrow >> 3) * 256 + (ch & 1) * 128 +
                               (nrow & 7) * 16) = __ldg(reinterpret_cast<const uint4*>(wb) + q);
   }
-  if (tid < HID) s_bias[tid] = EPI == kEpiRelu ? bias[tid] : 0.0f;
+  if (tid < COUT) s_bias[tid] = EPI == kEpiMask ? 0.0f : bias[tid];
+  if constexpr (CIN == 1) {                                  // the zero chunk of every slot
+    for (int q = tid; q < kTzRing * kTzPlane / 16; q += kTzThreads) {
+      const int slot = q / (kTzPlane / 16), r = q % (kTzPlane / 16);
+      *reinterpret_cast<uint4*>(s_a + slot * S::SLICE + kTzPlane + 16 * r) = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
   // input slices 0, 1 and 2 (z0 - 1 .. z0 + 1) into ring slots 0-2; slice 3
   // into registers, stored in the first step
-  float4 pre[kTzItems][2];
+  float4 pre[S::PER][2];
   for (int li = 0; li < 3; ++li) {
-    tz_fetch(src, x0t, y0t, z0 - 1 + li, tid, pre);
-    tz_store(s_a + li * kTzSlice, tid, pre);
+    tz_fetch<CIN>(src, x0t, y0t, z0 - 1 + li, tid, pre);
+    tz_store<CIN>(s_a + li * S::SLICE, tid, pre);
   }
-  tz_fetch(src, x0t, y0t, z0 + 2, tid, pre);
+  tz_fetch<CIN>(src, x0t, y0t, z0 + 2, tid, pre);
   // this thread's accumulator row (warps 0-3): voxel (ex, ey) of each slice;
-  // am holds its mask row (input-gradient pass), fetched a step ahead
+  // am holds its mask row (input-gradient pass) or residual value, fetched
+  // a step ahead
   const int ex = x0t + tid % TZX, ey = y0t + tid / TZX;
   const bool erow = warp < 4 && ex < EG && ey < EG;
-  float4 am[HID / 4];
+  constexpr int kAux = EPI == kEpiMask ? COUT / 4 : 1;
+  float4 am[kAux];
 #pragma unroll
-  for (int c4 = 0; c4 < HID / 4; ++c4) am[c4] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  for (int c4 = 0; c4 < kAux; ++c4) am[c4] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   if (tid == 0) {
     for (int q = 0; q < 4; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&s_mbar[q])));
     s_fail = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&s_tmem)), "n"(kTzCols));
+                 :: "r"(smem_u32(&s_tmem)), "n"(S::COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -417,7 +387,7 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
   const uint32_t tmem = s_tmem;
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   if (warp < 4) {                                            // every accumulator block starts at zero
-    for (int b = 0; b < kTzCols / 32; ++b) tz_zero(tmem + lane_base + (uint32_t)(32 * b));
+    for (int b = 0; b < 8; ++b) tz_zero<CP>(tmem + lane_base + (uint32_t)(CP * b));
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -427,22 +397,22 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
   // the matrix instructions of input slice j (one thread), committed to s_mbar[j % 4]
   auto issue = [&](int j) {
     const int bb = tz_block(j);                              // block of output slice j (tap dz = 0)
-    const uint32_t a_s = a0 + (uint32_t)((j % kTzRing) * kTzSlice);
+    const uint32_t a_s = a0 + (uint32_t)((j % kTzRing) * S::SLICE);
     for (int c = 0; c < 9; ++c) {
       const int dy = c / 3, dx = c % 3;
 #pragma unroll
-      for (int ks = 0; ks < 2; ++ks) {
+      for (int ks = 0; ks < S::KS; ++ks) {
         const uint64_t da = umma_desc_kmajor(a_s + (uint32_t)(2 * ks * kTzPlane + dy * kTzRowStride + dx * 16),
                                              kTzPlane, kTzRowStride);
-        const uint32_t bt = b0 + (uint32_t)(c * kTzBTap + ks * kTzBKs);
+        const uint32_t bt = b0 + (uint32_t)(c * S::BTAP + ks * S::BKS);
         if (bb <= 5) {
-          tz_mma(tmem + (uint32_t)(32 * bb), da, umma_desc_kmajor(bt, 128, 256), tz_idesc(96));
+          tz_mma(tmem + (uint32_t)(CP * bb), da, umma_desc_kmajor(bt, 128, 256), tz_idesc(3 * CP));
         } else if (bb == 6) {                                // blocks 6, 7 | 0
-          tz_mma(tmem + 192u, da, umma_desc_kmajor(bt, 128, 256), tz_idesc(64));
-          tz_mma(tmem, da, umma_desc_kmajor(bt + 8 * 256, 128, 256), tz_idesc(32));
+          tz_mma(tmem + (uint32_t)(6 * CP), da, umma_desc_kmajor(bt, 128, 256), tz_idesc(2 * CP));
+          tz_mma(tmem, da, umma_desc_kmajor(bt + (2 * CP / 8) * 256, 128, 256), tz_idesc(CP));
         } else {                                             // block 7 | 0, 1
-          tz_mma(tmem + 224u, da, umma_desc_kmajor(bt, 128, 256), tz_idesc(32));
-          tz_mma(tmem, da, umma_desc_kmajor(bt + 4 * 256, 128, 256), tz_idesc(64));
+          tz_mma(tmem + (uint32_t)(7 * CP), da, umma_desc_kmajor(bt, 128, 256), tz_idesc(CP));
+          tz_mma(tmem, da, umma_desc_kmajor(bt + (CP / 8) * 256, 128, 256), tz_idesc(2 * CP));
         }
       }
     }
@@ -467,50 +437,66 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (ok && warp < 4) {
-        const uint32_t taddr = tmem + lane_base + (uint32_t)(32 * tz_block(zo));
+        const uint32_t taddr = tmem + lane_base + (uint32_t)(CP * tz_block(zo));
         if (zo >= 0) {
-          uint32_t r[32];
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                       "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                         "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                         "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                         "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                       : "r"(taddr));
+          uint32_t r[CP];
+          if constexpr (CP == 32)
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                           "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                           "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                           "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                         : "r"(taddr));
+          else
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                           "=r"(r[14]), "=r"(r[15])
+                         : "r"(taddr));
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
           if (erow) {
             const size_t v = (size_t)n * NV + (size_t)((z0 + zo) * EG + ey) * EG + ex;
-            float4* o4 = reinterpret_cast<float4*>(out + v * HID);
+            if constexpr (COUT == 1) {                       // y = x0 + f(x0): column 0, bias, residual
+              out[v] = __uint_as_float(r[0]) + s_bias[0] + am[0].x;
+            } else {
+              float4* o4 = reinterpret_cast<float4*>(out + v * HID);
 #pragma unroll
-            for (int c4 = 0; c4 < HID / 4; ++c4) {
-              float o[4];
-              const float mk[4] = {am[c4].x, am[c4].y, am[c4].z, am[c4].w};
+              for (int c4 = 0; c4 < HID / 4; ++c4) {
+                float o[4];
+                const float4 m4 = am[EPI == kEpiMask ? c4 : 0];
+                const float mk[4] = {m4.x, m4.y, m4.z, m4.w};
 #pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const float val = __uint_as_float(r[4 * c4 + e]);
-                if constexpr (EPI == kEpiRelu) o[e] = fmaxf(val + s_bias[4 * c4 + e], 0.0f);
-                else o[e] = mk[e] > 0.0f ? val : 0.0f;
+                for (int e = 0; e < 4; ++e) {
+                  const float val = __uint_as_float(r[4 * c4 + e]);
+                  if constexpr (EPI == kEpiRelu) o[e] = fmaxf(val + s_bias[4 * c4 + e], 0.0f);
+                  else o[e] = mk[e] > 0.0f ? val : 0.0f;
+                }
+                o4[c4] = make_float4(o[0], o[1], o[2], o[3]);
               }
-              o4[c4] = make_float4(o[0], o[1], o[2], o[3]);
             }
           }
         }
-        tz_zero(taddr);
+        tz_zero<CP>(taddr);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       }
     }
     // input slice i + 3 into the slot input slice i - 1 left (every
     // instruction that read it has completed); fetch slice i + 4
-    if (i + 3 <= nz + 1) tz_store(s_a + ((i + 3) % kTzRing) * kTzSlice, tid, pre);
-    if (i + 4 <= nz + 1) tz_fetch(src, x0t, y0t, z0 - 1 + i + 4, tid, pre);
-    if constexpr (EPI != kEpiRelu) {                         // mask rows of output slice i - 2, read out next step
+    if (i + 3 <= nz + 1) tz_store<CIN>(s_a + ((i + 3) % kTzRing) * S::SLICE, tid, pre);
+    if (i + 4 <= nz + 1) tz_fetch<CIN>(src, x0t, y0t, z0 - 1 + i + 4, tid, pre);
+    if constexpr (EPI != kEpiRelu) {                         // mask rows / residual of output slice i - 2
       const int zm = i - 2;
       if (erow && zm >= 0 && zm < nz) {
-        const float4* a4 =
-            reinterpret_cast<const float4*>(aux + ((size_t)n * NV + (size_t)((z0 + zm) * EG + ey) * EG + ex) * HID);
+        const size_t v = (size_t)n * NV + (size_t)((z0 + zm) * EG + ey) * EG + ex;
+        if constexpr (EPI == kEpiMask) {
+          const float4* a4 = reinterpret_cast<const float4*>(aux + v * COUT);
 #pragma unroll
-        for (int c4 = 0; c4 < HID / 4; ++c4) am[c4] = __ldg(a4 + c4);
+          for (int c4 = 0; c4 < kAux; ++c4) am[c4] = __ldg(a4 + c4);
+        } else {
+          am[0].x = __ldg(aux + v);
+        }
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -528,12 +514,13 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(kTzCols));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(S::COLS));
   }
 }
 
-constexpr size_t conv_tz_smem() { return (size_t)kTzB + (size_t)kTzRing * kTzSlice; }
-static_assert(2 * conv_tz_smem() + 2 * 1024 <= 228 * 1024, "two blocks of the z-folded convolution per SM");
+static_assert(2 * TzShape<32, 32>::SMEM + 2 * 1024 <= 228 * 1024, "two blocks of the z-folded convolution per SM");
+static_assert(3 * TzShape<1, 32>::SMEM > 227 * 1024 && 3 * TzShape<32, 32>::SMEM > 227 * 1024,
+              "at most two blocks of 256 tensor-memory columns per SM");
 
 __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
@@ -699,9 +686,11 @@ constexpr size_t wgrad_mma_smem() { return (size_t)(HZ * HY * HX + TZ * TY * TX)
 // dW[tap][ci][co] += sum_v in[v + off(tap)][ci] * g[v][co] and db[co] +=
 // sum_v g[v][co] over one tile position of the grids blockIdx.y,
 // blockIdx.y + kWgradSplit, ...; each block owns one tile position and one
-// share of the grids and adds its sums once (atomically) at the end.
+// share of the grids and adds its sums once (atomically) at the end.  RIN /
+// RG: the input / the gradient enters the products rounded to bfloat16, as
+// in the tensor-core passes of the same layer (the bias sum is unrounded).
 constexpr int kWgradSplit = 4;
-template <int CIN, int COUT>
+template <int CIN, int COUT, bool RIN, bool RG>
 __global__ void __launch_bounds__(kConvThreads) wgrad_kernel(const float* __restrict__ in, const float* __restrict__ g,
                                                             int n_grids, float* __restrict__ dW,
                                                             float* __restrict__ db) {
@@ -729,7 +718,7 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_kernel(const float* __rest
     const float* src = in + (size_t)n * NV * CIN;
     const float* gs = g + (size_t)n * NV * COUT;
     __syncthreads();
-    load_halo<CIN>(src, s_in, x0t, y0t, z0t);
+    load_halo<CIN, RIN>(src, s_in, x0t, y0t, z0t);
     if constexpr (COUT % 4 == 0) {
       // 16-byte loads, four of them in flight before any is stored
       constexpr int kItems = TZ * TY * TX * (COUT / 4), kBatch = 4;
@@ -769,7 +758,8 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_kernel(const float* __rest
         for (int p = 0; p < TZ * TY * TX; ++p) {
           const int tx = p % TX, ty = (p / TX) % TY, tz = p / (TX * TY);
           const float xv = s_in[(((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * SC];
-          const float4 gv = reinterpret_cast<const float4*>(s_g + p * COUT)[c4];
+          float4 gv = reinterpret_cast<const float4*>(s_g + p * COUT)[c4];
+          if constexpr (RG) gv = make_float4(bf16_round(gv.x), bf16_round(gv.y), bf16_round(gv.z), bf16_round(gv.w));
           acc4.x = fmaf(xv, gv.x, acc4.x);
           acc4.y = fmaf(xv, gv.y, acc4.y);
           acc4.z = fmaf(xv, gv.z, acc4.z);
@@ -785,7 +775,7 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_kernel(const float* __rest
           const int tx = p % TX, ty = (p / TX) % TY, tz = p / (TX * TY);
           const float4 xv =
               *reinterpret_cast<const float4*>(s_in + (((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * SC + 4 * c4);
-          const float gv = s_g[p];
+          const float gv = RG ? bf16_round(s_g[p]) : s_g[p];
           acc4.x = fmaf(xv.x, gv, acc4.x);
           acc4.y = fmaf(xv.y, gv, acc4.y);
           acc4.z = fmaf(xv.z, gv, acc4.z);
@@ -804,7 +794,7 @@ __global__ void __launch_bounds__(kConvThreads) wgrad_kernel(const float* __rest
           const float xv = s_in[(((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * SC + ci];
           const float* gr = s_g + p * COUT;
 #pragma unroll
-          for (int co = 0; co < COUT; ++co) acc[j][co] = fmaf(xv, gr[co], acc[j][co]);
+          for (int co = 0; co < COUT; ++co) acc[j][co] = fmaf(xv, RG ? bf16_round(gr[co]) : gr[co], acc[j][co]);
         }
       }
     }
@@ -868,13 +858,14 @@ __global__ void loss_kernel(const float* __restrict__ y, const float* __restrict
 
 // ------------------------------------------------------------ parameters
 // The effective weights: each W rounded to bfloat16 (nearest even), biases
-// as they are.  Layer 3 (32 -> 1) also gets its binary32 input-gradient
-// weights wt3[26 - tap][co][ci] = W[tap][ci][co]; the tensor-core layers 1
-// and 2 get bfloat16 rows: forward wf[tap][co][ci] and input gradient
-// wd[26 - tap][ci][co] (= W[tap][ci][co]).
-__global__ void refresh_kernel(const float* __restrict__ P, float* __restrict__ Pq, float* __restrict__ Wt3,
+// as they are, and the bfloat16 rows of the tensor-core convolutions:
+// forward wf[tap][co][ci] and input gradient wd[26 - tap][ci][co] (=
+// W[tap][ci][co]), rows of 32 input channels; layer 0 has one real input
+// channel per row, layer 3 one real output row of 16 per tap.
+__global__ void refresh_kernel(const float* __restrict__ P, float* __restrict__ Pq, __nv_bfloat16* __restrict__ wf0,
                                __nv_bfloat16* __restrict__ wf1, __nv_bfloat16* __restrict__ wf2,
-                               __nv_bfloat16* __restrict__ wd1, __nv_bfloat16* __restrict__ wd2) {
+                               __nv_bfloat16* __restrict__ wf3, __nv_bfloat16* __restrict__ wd1,
+                               __nv_bfloat16* __restrict__ wd2, __nv_bfloat16* __restrict__ wd3) {
   const int woff[4] = {kWOff[0], kWOff[1], kWOff[2], kWOff[3]}, boff[4] = {kBOff[0], kBOff[1], kBOff[2], kBOff[3]};
   const int cin[4] = {kCin[0], kCin[1], kCin[2], kCin[3]}, cout[4] = {kCout[0], kCout[1], kCout[2], kCout[3]};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < RO_MC_PARAMS; i += gridDim.x * blockDim.x) {
@@ -883,14 +874,17 @@ __global__ void refresh_kernel(const float* __restrict__ P, float* __restrict__ 
     const bool is_w = i < boff[layer];
     const float q = is_w ? __bfloat162float(__float2bfloat16_rn(P[i])) : P[i];
     Pq[i] = q;
-    if (is_w && layer > 0) {
+    if (is_w) {
       const int ci_n = cin[layer], co_n = cout[layer];
       const int r = i - woff[layer];
       const int t = r / (ci_n * co_n), ci = (r / co_n) % ci_n, co = r % co_n;
-      if (layer == 3) {
-        Wt3[((26 - t) * co_n + co) * ci_n + ci] = q;
+      const __nv_bfloat16 h = __float2bfloat16_rn(q);
+      if (layer == 0) {                     // 1 -> 32: rows of 32 input channels, the first one real
+        wf0[(t * HID + co) * HID] = h;
+      } else if (layer == 3) {              // 32 -> 1: row 0 of 16 per tap; input gradient 1 -> 32
+        wf3[(t * 16) * HID + ci] = h;
+        wd3[((26 - t) * HID + ci) * HID] = h;
       } else {
-        const __nv_bfloat16 h = __float2bfloat16_rn(q);
         (layer == 1 ? wf1 : wf2)[(t * co_n + co) * ci_n + ci] = h;
         (layer == 1 ? wd1 : wd2)[((26 - t) * ci_n + ci) * co_n + co] = h;
       }
@@ -923,8 +917,9 @@ struct ro_mc {
   ro_mc_desc desc;
   cudaStream_t stream = nullptr;
   float *P, *Pq, *M, *V, *G;          // parameters, effective copy, Adam moments, gradients
-  float* Wt3;                         // binary32 input-gradient weights of layer 3
-  __nv_bfloat16 *wf1, *wf2, *wd1, *wd2;  // tensor-core rows of layers 1 and 2 (forward, input gradient)
+  // tensor-core rows of the layers: forward wf0..wf3, input gradient wd1..wd3
+  // (layers 0 and 3 padded: one real input channel, one real output row)
+  __nv_bfloat16 *wf0, *wf1, *wf2, *wf3, *wd1, *wd2, *wd3;
   float *a1, *a2, *a3;                // hidden activations (after ReLU), n * NV * 32
   float *ga, *gb;                     // hidden gradients, n * NV * 32
   float *g4, *y;                      // output gradient and output, n * NV
@@ -946,7 +941,7 @@ constexpr uint64_t kMcAlign = 256;
 uint64_t mc_align(uint64_t v) { return (v + kMcAlign - 1) / kMcAlign * kMcAlign; }
 
 struct McLayout {
-  uint64_t P, Pq, M, V, G, flag, Wt3, wf1, wf2, wd1, wd2, a1, a2, a3, ga, gb, g4, y, loss, total;
+  uint64_t P, Pq, M, V, G, flag, wf0, wf1, wf2, wf3, wd1, wd2, wd3, wend, a1, a2, a3, ga, gb, g4, y, loss, total;
 };
 
 McLayout mc_layout(uint32_t nb) {
@@ -955,31 +950,21 @@ McLayout mc_layout(uint32_t nb) {
   auto take = [&](uint64_t bytes) { const uint64_t at = o; o = mc_align(o + bytes); return at; };
   const uint64_t pb = (uint64_t)RO_MC_PARAMS * 4, hid = (uint64_t)nb * NV * HID * 4, one = (uint64_t)nb * NV * 4;
   L.P = take(pb); L.Pq = take(pb); L.M = take(pb); L.V = take(pb); L.G = take(pb); L.flag = take(4);
-  L.Wt3 = take(27ull * HID * 4);
-  L.wf1 = take(27ull * HID * HID * 2); L.wf2 = take(27ull * HID * HID * 2);
-  L.wd1 = take(27ull * HID * HID * 2); L.wd2 = take(27ull * HID * HID * 2);
+  L.wf0 = take(27ull * HID * HID * 2); L.wf1 = take(27ull * HID * HID * 2); L.wf2 = take(27ull * HID * HID * 2);
+  L.wf3 = take(27ull * 16 * HID * 2);
+  L.wd1 = take(27ull * HID * HID * 2); L.wd2 = take(27ull * HID * HID * 2); L.wd3 = take(27ull * HID * HID * 2);
+  L.wend = o;
   L.a1 = take(hid); L.a2 = take(hid); L.a3 = take(hid); L.ga = take(hid); L.gb = take(hid);
   L.g4 = take(one); L.y = take(one); L.loss = take(4);
   L.total = o;
   return L;
 }
 
-template <int CIN, int COUT, int EPI>
-cudaError_t conv(const float* in, const float* w, const float* b, float* out, const float* aux, uint32_t n,
-                 cudaStream_t s) {
-  auto k = conv_kernel<CIN, COUT, EPI>;
-  constexpr size_t sm = conv_smem<CIN, COUT>();
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  k<<<dim3(kTilesX * kTilesY * kTilesZ, n), kConvThreads, sm, s>>>(in, w, b, out, aux);
-  return cudaGetLastError();
-}
-
-template <int EPI>
+template <int EPI, int CIN, int COUT>
 cudaError_t conv_tc(const float* in, const __nv_bfloat16* wb, const float* b, float* out, const float* aux, uint32_t n,
                     uint32_t* flag, cudaStream_t s) {
-  auto k = conv_tz_kernel<EPI>;
-  constexpr size_t sm = conv_tz_smem();
+  auto k = conv_tz_kernel<EPI, CIN, COUT>;
+  constexpr size_t sm = TzShape<CIN, COUT>::SMEM;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k<<<dim3(kTzUnits, n), kTzThreads, sm, s>>>(in, wb, b, out, aux, flag);
@@ -994,9 +979,9 @@ cudaError_t wgrad_tc(const float* in, const float* g, uint32_t n, float* dW, flo
   return cudaGetLastError();
 }
 
-template <int CIN, int COUT>
+template <int CIN, int COUT, bool RIN, bool RG>
 cudaError_t wgrad(const float* in, const float* g, uint32_t n, float* dW, float* db, cudaStream_t s) {
-  auto k = wgrad_kernel<CIN, COUT>;
+  auto k = wgrad_kernel<CIN, COUT, RIN, RG>;
   constexpr size_t sm = wgrad_smem<CIN, COUT>();
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -1010,10 +995,10 @@ ro_status mc_err(cudaError_t e) { return e == cudaSuccess ? RO_OK : RO_ERR_CUDA;
 cudaError_t mc_forward(ro_mc* m, uint32_t n, const float* x0, float* y) {
   cudaStream_t s = m->stream;
   const float* Pq = m->Pq;
-  cudaError_t e = conv<1, HID, kEpiRelu>(x0, Pq + kWOff[0], Pq + kBOff[0], m->a1, nullptr, n, s);
-  if (e == cudaSuccess) e = conv_tc<kEpiRelu>(m->a1, m->wf1, Pq + kBOff[1], m->a2, nullptr, n, m->flag, s);
-  if (e == cudaSuccess) e = conv_tc<kEpiRelu>(m->a2, m->wf2, Pq + kBOff[2], m->a3, nullptr, n, m->flag, s);
-  if (e == cudaSuccess) e = conv<HID, 1, kEpiResidual>(m->a3, Pq + kWOff[3], Pq + kBOff[3], y, x0, n, s);
+  cudaError_t e = conv_tc<kEpiRelu, 1, HID>(x0, m->wf0, Pq + kBOff[0], m->a1, nullptr, n, m->flag, s);
+  if (e == cudaSuccess) e = conv_tc<kEpiRelu, HID, HID>(m->a1, m->wf1, Pq + kBOff[1], m->a2, nullptr, n, m->flag, s);
+  if (e == cudaSuccess) e = conv_tc<kEpiRelu, HID, HID>(m->a2, m->wf2, Pq + kBOff[2], m->a3, nullptr, n, m->flag, s);
+  if (e == cudaSuccess) e = conv_tc<kEpiResidual, HID, 1>(m->a3, m->wf3, Pq + kBOff[3], y, x0, n, m->flag, s);
   return e;
 }
 
@@ -1041,27 +1026,27 @@ cudaError_t mc_backward(ro_mc* m, uint32_t n, const float* x0, const float* targ
   };
   // layer 4 (32 -> 1)
   if (e == cudaSuccess) e = fork(0);
-  if (e == cudaSuccess) e = wgrad<HID, 1>(m->a3, m->g4, n, G + kWOff[3], G + kBOff[3], s2);
-  if (e == cudaSuccess) e = conv<1, HID, kEpiMask>(m->g4, m->Wt3, zero_bias, m->ga, m->a3, n, s);
+  if (e == cudaSuccess) e = wgrad<HID, 1, true, true>(m->a3, m->g4, n, G + kWOff[3], G + kBOff[3], s2);
+  if (e == cudaSuccess) e = conv_tc<kEpiMask, 1, HID>(m->g4, m->wd3, zero_bias, m->ga, m->a3, n, m->flag, s);
   // layer 3 (32 -> 32)
   if (e == cudaSuccess) e = fork(1);
   if (e == cudaSuccess) e = wgrad_tc(m->a2, m->ga, n, G + kWOff[2], G + kBOff[2], s2);
   if (e == cudaSuccess) e = cudaEventRecord(m->ev[2], s2);
-  if (e == cudaSuccess) e = conv_tc<kEpiMask>(m->ga, m->wd2, zero_bias, m->gb, m->a2, n, m->flag, s);
+  if (e == cudaSuccess) e = conv_tc<kEpiMask, HID, HID>(m->ga, m->wd2, zero_bias, m->gb, m->a2, n, m->flag, s);
   // layer 2 (32 -> 32)
   if (e == cudaSuccess) e = fork(3);
   if (e == cudaSuccess) e = wgrad_tc(m->a1, m->gb, n, G + kWOff[1], G + kBOff[1], s2);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->ev[2], 0);
-  if (e == cudaSuccess) e = conv_tc<kEpiMask>(m->gb, m->wd1, zero_bias, m->ga, m->a1, n, m->flag, s);
+  if (e == cudaSuccess) e = conv_tc<kEpiMask, HID, HID>(m->gb, m->wd1, zero_bias, m->ga, m->a1, n, m->flag, s);
   // layer 1 (1 -> 32)
-  if (e == cudaSuccess) e = wgrad<1, HID>(x0, m->ga, n, G + kWOff[0], G + kBOff[0], s);
+  if (e == cudaSuccess) e = wgrad<1, HID, true, false>(x0, m->ga, n, G + kWOff[0], G + kBOff[0], s);
   if (e == cudaSuccess) e = cudaEventRecord(m->ev[4], s2);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->ev[4], 0);
   return e;
 }
 
 cudaError_t mc_refresh(ro_mc* m) {
-  refresh_kernel<<<64, 256, 0, m->stream>>>(m->P, m->Pq, m->Wt3, m->wf1, m->wf2, m->wd1, m->wd2);
+  refresh_kernel<<<64, 256, 0, m->stream>>>(m->P, m->Pq, m->wf0, m->wf1, m->wf2, m->wf3, m->wd1, m->wd2, m->wd3);
   return cudaGetLastError();
 }
 
@@ -1086,16 +1071,18 @@ ro_status ro_mc_create(const ro_mc_desc* d, void* arena, uint64_t arena_bytes, v
   uint8_t* b = static_cast<uint8_t*>(arena);
   auto f = [&](uint64_t off) { return reinterpret_cast<float*>(b + off); };
   m->P = f(L.P); m->Pq = f(L.Pq); m->M = f(L.M); m->V = f(L.V); m->G = f(L.G);
-  m->Wt3 = f(L.Wt3);
   auto h = [&](uint64_t off) { return reinterpret_cast<__nv_bfloat16*>(b + off); };
-  m->wf1 = h(L.wf1); m->wf2 = h(L.wf2); m->wd1 = h(L.wd1); m->wd2 = h(L.wd2);
+  m->wf0 = h(L.wf0); m->wf1 = h(L.wf1); m->wf2 = h(L.wf2); m->wf3 = h(L.wf3);
+  m->wd1 = h(L.wd1); m->wd2 = h(L.wd2); m->wd3 = h(L.wd3);
   m->a1 = f(L.a1); m->a2 = f(L.a2); m->a3 = f(L.a3); m->ga = f(L.ga); m->gb = f(L.gb);
   m->g4 = f(L.g4); m->y = f(L.y); m->loss = f(L.loss);
   m->flag = reinterpret_cast<uint32_t*>(b + L.flag);
   cudaError_t e = cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking);
   for (cudaEvent_t& x : m->ev)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaMemsetAsync(arena, 0, L.Wt3, m->stream);   // parameters, copies, moments, gradients, flag
+  // parameters, copies, moments, gradients, flag and the tensor-core rows
+  // (whose padding stays zero)
+  if (e == cudaSuccess) e = cudaMemsetAsync(arena, 0, L.wend, m->stream);
   if (e == cudaSuccess) e = mc_refresh(m);
   if (e != cudaSuccess) {
     delete m;

@@ -50,28 +50,31 @@ def test_forward_and_gradients_match_oracle(mc):
                  for W, b in params])
     x0f = x0.astype(np.float32).astype(np.float64)
     for k in range(2):
-        want, _ = omc.forward(q, x0f[k], bf16_inputs=(1, 2))
+        want, _ = omc.forward(q, x0f[k], bf16_inputs=(0, 1, 2, 3))
         err = np.abs(y[k] - want)
         # binary32 sums agree to ~1e-7; where an activation lies within a
         # binary32 step of a bfloat16 rounding boundary the two sides round
         # it one bfloat16 step apart, which moves the 27 neighbours of the
-        # next layer by about |w| * |a| * 2^-8 and spreads from there.  The
-        # oracle with binary32-sized noise (2^-23) on the layer inputs gives
-        # median 0, 99 % 2.3e-4, 99.9 % 4.8e-4, max 9.2e-4 on these inputs:
-        # the bounds below sit about 2x above that
+        # next layer by about |w| * |a| * 2^-8 and spreads from there (the
+        # last layer's input is rounded too, so a flip there reaches y
+        # directly).  The oracle against itself with binary32-sized noise
+        # (2^-23) on every layer input gives median 0, 99 % 3.8e-4, 99.9 %
+        # 1.0e-3, max 2.5e-3 on these inputs (and 99 % 4.7e-4, max 3.6e-3 on
+        # the 32-grid test's): the bounds below sit about 2x above that
         assert np.median(err) <= 1e-6
-        assert np.quantile(err, 0.99) <= 5e-4
-        assert err.max() <= 3e-3 * max(1.0, np.abs(want).max())
+        assert np.quantile(err, 0.99) <= 1e-3
+        assert err.max() <= 7.5e-3 * max(1.0, np.abs(want).max())
     g, loss = m.gradients(tx, tt)
     g = g.cpu().numpy()
     tf = target.astype(np.float32).astype(np.float64)
     # the oracle's loss over both grids: the mean of the per-grid means
-    losses, grads = zip(*[omc.loss_and_grads(q, x0f[k], tf[k], bf16_inputs=(1, 2)) for k in range(2)])
+    losses, grads = zip(*[omc.loss_and_grads(q, x0f[k], tf[k], bf16_inputs=(0, 1, 2, 3)) for k in range(2)])
     want_loss = sum(losses) / 2
     assert abs(float(loss.item()) - want_loss) <= 1e-4 * want_loss
     # the oracle mirrors the GPU's rounding of the output gradients entering
-    # the two 32 -> 32 layers' tensor-core products to bfloat16
-    losses, grads = zip(*[omc.loss_and_grads(q, x0f[k], tf[k], bf16_inputs=(1, 2), bf16_grads=(1, 2))
+    # the last three layers' tensor-core products (and the binary32 weight
+    # gradients of the last layer, which round as its input gradients do)
+    losses, grads = zip(*[omc.loss_and_grads(q, x0f[k], tf[k], bf16_inputs=(0, 1, 2, 3), bf16_grads=(1, 2, 3))
                           for k in range(2)])
     want = [(sum(gr[i][0] for gr in grads) / 2, sum(gr[i][1] for gr in grads) / 2) for i in range(4)]
     got = mcmod.unflatten(g.astype(np.float64))
@@ -197,12 +200,12 @@ def test_full_batch_matches_oracle_samples_and_per_grid_gradients(mc):
                      for W, b in params])
         x0f = x0.astype(np.float32).astype(np.float64)
         for k in (0, 17, n - 1):
-            want, _ = omc.forward(q, x0f[k], bf16_inputs=(1, 2))
+            want, _ = omc.forward(q, x0f[k], bf16_inputs=(0, 1, 2, 3))
             err = np.abs(y[k] - want)
             # bounds of the two-grid forward test (bfloat16 rounding flips)
             assert np.median(err) <= 1e-6
-            assert np.quantile(err, 0.99) <= 5e-4
-            assert err.max() <= 3e-3 * max(1.0, np.abs(want).max())
+            assert np.quantile(err, 0.99) <= 1e-3
+            assert err.max() <= 7.5e-3 * max(1.0, np.abs(want).max())
         g, loss = big.gradients(tx, tt)
         g = g.cpu().numpy().astype(np.float64)
         mean_g = np.zeros_like(g)
