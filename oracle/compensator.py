@@ -15,12 +15,11 @@ network   y = x0 + f(x0): f is four 3x3x3 convolutions with zero padding
           the first three.  Weight layout W[tap, ci, co], tap = (dz * 3 +
           dy) * 3 + dx; activations channels-last [z, y, x, c].
 loss      mean squared error against the true level-0 apron slot (scaled).
-precision the GPU runs every layer's forward pass and the input
-          gradients of the last three on the tensor cores with bfloat16
-          inputs (binary32 sums); forward(..., bf16_inputs=(0, 1, 2, 3))
+precision the GPU runs every product on the tensor cores with bfloat16
+          operands (binary32 sums); forward(..., bf16_inputs=(0, 1, 2, 3))
           mirrors that rounding of the layer inputs, and
-          loss_and_grads(..., bf16_grads=(1, 2, 3)) the rounding of the
-          output gradients that enter those layers' weight- and input-
+          loss_and_grads(..., bf16_grads=(0, 1, 2, 3)) the rounding of the
+          output gradients that enter the layers' weight- and input-
           gradient products (their bias gradients sum the unrounded values).
 adam      one step of Adam (Kingma and Ba, 2015, Algorithm 1): exponential
           moving averages of the gradient and its square, both divided by

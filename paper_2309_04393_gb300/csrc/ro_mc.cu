@@ -4,16 +4,15 @@
 //
 // Activations are channels-last binary32 grids of 34^3 voxels.  The weights
 // take part as bfloat16 values (the parameters are rounded once per update
-// into an effective binary32 copy); every sum is binary32.  The two 32 -> 32
-// layers (forward, input gradient and weight gradient) run on the tensor
-// cores with their inputs rounded to bfloat16; the rest on the binary32
-// cores.  A binary32 convolution block computes an 8 x 8 x 4 voxel tile for
-// all output channels from a shared-memory copy of the input tile with its
-// one-voxel halo (zero outside the grid) and of the layer's weights; the
-// tcgen05 convolution marches an 8 x 16 column along z with the three z
-// taps of an input slice in one instruction.  An input-gradient
-// pass is the forward kernel on the spatially flipped, channel-transposed
-// weights.
+// into an effective binary32 copy); every sum is binary32.  Every product
+// runs on the tensor cores with its operands rounded to bfloat16: the
+// convolutions (each layer's forward pass, the last three layers' input
+// gradients) on tcgen05, marching an 8 x 16 column along z with the three z
+// taps of an input slice in one instruction; the weight gradients on
+// mma.sync over 8 x 8 x 4 voxel tiles with their one-voxel halo (zero
+// outside the grid).  The single-channel side of the first and last layers
+// is padded with zeros.  An input-gradient pass is the forward kernel on the
+// spatially flipped, channel-transposed weights.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -30,9 +29,8 @@ namespace {
 constexpr int EG = RO_MC_EDGE;        // grid edge
 constexpr int NV = RO_MC_VOXELS;      // voxels per grid
 constexpr int HID = 32;               // hidden channels
-constexpr int TX = 8, TY = 8, TZ = 4; // output tile of one block
+constexpr int TX = 8, TY = 8, TZ = 4; // voxel tile of one weight-gradient block
 constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
-constexpr int kConvThreads = TX * TY * TZ;
 constexpr int kTilesX = (EG + TX - 1) / TX, kTilesY = (EG + TY - 1) / TY, kTilesZ = (EG + TZ - 1) / TZ;
 
 // layer shapes and offsets of W and b in the parameter vector
@@ -42,17 +40,10 @@ constexpr int kWOff[4] = {0, 896, 28576, 56256};        // W of layer i
 constexpr int kBOff[4] = {864, 28544, 56224, 57120};    // b of layer i (after W)
 static_assert(kBOff[3] + 1 == RO_MC_PARAMS, "parameter layout");
 
-// channel stride of a shared-memory tile: padded so that neighbouring
-// voxels fall in different banks; a multiple of 4 for 16-byte accesses
-// (36 floats: eight 16-byte reads of neighbouring voxels cover all banks)
-__host__ __device__ constexpr int pad_stride(int c) { return c > 1 ? (c % 4 == 0 ? c + 4 : c + 1) : 1; }
-
 // convolution epilogues: ReLU(sum + bias); the residual y = x0 + sum + bias
 // (one output channel); the gradient passed where the layer's activation is
 // positive
 enum : int { kEpiRelu = 1, kEpiResidual = 2, kEpiMask = 3 };
-
-__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 // ------------------------------------------------------------- upsample
 // Level-0 voxel X (relative to the child's apron origin) sits at level-1
@@ -98,50 +89,6 @@ __global__ void to_raw_kernel(const float* __restrict__ y, uint8_t* __restrict__
   for (int v = threadIdx.x; v < NV; v += blockDim.x) {
     const float r = rintf(y[(size_t)n * NV + v] * 65536.0f);
     o[v] = (uint16_t)fminf(fmaxf(r, 0.0f), 65535.0f);
-  }
-}
-
-// ---------------------------------------------------------- convolution
-// The HZ x HY x HX input tile with its one-voxel halo (zeros outside the
-// grid) into shared memory at channel stride pad_stride(CIN), rounded to
-// bfloat16 values when RND; 16-byte loads when the channels allow.
-template <int CIN, bool RND>
-__device__ __forceinline__ void load_halo(const float* __restrict__ src, float* s_in, int x0t, int y0t, int z0t) {
-  auto rnd = [](float v) { return RND ? bf16_round(v) : v; };
-  constexpr int SC = pad_stride(CIN);
-  if constexpr (CIN % 4 == 0) {
-    // 16-byte loads, four of them in flight before any is stored
-    constexpr int kItems = HZ * HY * HX * (CIN / 4), kBatch = 4;
-    for (int q0 = threadIdx.x; q0 < kItems; q0 += kBatch * (int)blockDim.x) {
-      float4 val[kBatch];
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        const int q = q0 + u * (int)blockDim.x;
-        const int c4 = q % (CIN / 4), p = q / (CIN / 4);
-        const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
-        const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
-        val[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (q < kItems && gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
-          val[u] = __ldg(reinterpret_cast<const float4*>(src + ((size_t)(gz * EG + gy) * EG + gx) * CIN) + c4);
-      }
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        const int q = q0 + u * (int)blockDim.x;
-        if (q < kItems)
-          *reinterpret_cast<float4*>(s_in + (q / (CIN / 4)) * SC + 4 * (q % (CIN / 4))) =
-              make_float4(rnd(val[u].x), rnd(val[u].y), rnd(val[u].z), rnd(val[u].w));
-      }
-    }
-  } else {
-    for (int q = threadIdx.x; q < HZ * HY * HX * CIN; q += blockDim.x) {
-      const int c = q % CIN, p = q / CIN;
-      const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
-      const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
-      float val = 0.0f;
-      if (gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
-        val = src[((size_t)(gz * EG + gy) * EG + gx) * CIN + c];
-      s_in[p * SC + c] = rnd(val);
-    }
   }
 }
 
@@ -540,9 +487,13 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t&
 // g[v][co] is summed in binary32 from the same loads.
 constexpr int kWgradSplitTc = 2;
 constexpr int kWgWarps = 16, kWgThreads = 32 * kWgWarps;   // two taps a warp
+template <int CIN, int COUT>
 __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const float* __restrict__ in,
                                                                 const float* __restrict__ g, int n_grids,
                                                                 float* __restrict__ dW, float* __restrict__ db) {
+  // a single channel takes channel 0 of rows that are zero elsewhere: one
+  // 16-channel m tile (input) or one 8-channel n tile (gradient)
+  constexpr int MT = CIN == 1 ? 1 : 2, NT = COUT == 1 ? 1 : 4;
   extern __shared__ __align__(16) uint8_t smb[];
   uint8_t* s_x = smb;                                       // HZ * HY * HX rows (input, halo)
   uint8_t* s_g = smb + HZ * HY * HX * kRowB;                // TZ * TY * TX rows (gradient)
@@ -552,46 +503,58 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const float* _
   const int g4 = lane >> 2, t4 = lane & 3;
   const int mi = lane >> 3, mr = lane & 7;
   constexpr int kTapsPerWarp = (27 + kWgWarps - 1) / kWgWarps;
-  float acc[kTapsPerWarp][2][4][4];
+  float acc[kTapsPerWarp][MT][NT][4];
 #pragma unroll
   for (int j = 0; j < kTapsPerWarp; ++j)
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+    for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt)
+      for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[j][mt][nt][q] = 0.0f;
   const uint32_t x_base = smem_u32(s_x), g_base = smem_u32(s_g);
+  if constexpr (CIN == 1 || COUT == 1) {                    // the rows' other channels stay zero
+    for (int q = threadIdx.x; q < (HZ * HY * HX + TZ * TY * TX) * kRowB / 16; q += kWgThreads)
+      reinterpret_cast<uint4*>(smb)[q] = make_uint4(0u, 0u, 0u, 0u);
+  }
   // kWgThreads is a multiple of HID / 4: a thread's four channels are fixed
   static_assert(kWgThreads % (HID / 4) == 0, "channel quad per thread");
   float4 bsum = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  // 16-byte loads, kLoadBatch of them in flight before any is stored
+  // 16-byte loads (one value for a single channel), kLoadBatch of them in
+  // flight before any is stored
   constexpr int kLoadBatch = 4;
-  constexpr int kHaloItems = HZ * HY * HX * (HID / 4), kTileItems = TZ * TY * TX * (HID / 4);
+  constexpr int kHaloItems = HZ * HY * HX * (CIN == 1 ? 1 : HID / 4);
+  constexpr int kTileItems = TZ * TY * TX * (COUT == 1 ? 1 : HID / 4);
   auto store4 = [](uint8_t* row, int c4, float4 v) {
     __nv_bfloat162 h[2] = {__floats2bfloat162_rn(v.x, v.y), __floats2bfloat162_rn(v.z, v.w)};
     *reinterpret_cast<uint2*>(row + 8 * c4) = *reinterpret_cast<const uint2*>(h);
   };
+  auto store1 = [](uint8_t* row, float v) { *reinterpret_cast<__nv_bfloat16*>(row) = __float2bfloat16_rn(v); };
   for (int n = blockIdx.y; n < n_grids; n += kWgradSplitTc) {
-    const float* src = in + (size_t)n * NV * HID;
-    const float* gs = g + (size_t)n * NV * HID;
+    const float* src = in + (size_t)n * NV * CIN;
+    const float* gs = g + (size_t)n * NV * COUT;
     __syncthreads();
     for (int q0 = threadIdx.x; q0 < kHaloItems; q0 += kLoadBatch * kWgThreads) {
       float4 v[kLoadBatch];
 #pragma unroll
       for (int u = 0; u < kLoadBatch; ++u) {
         const int q = q0 + u * kWgThreads;
-        const int c4 = q % (HID / 4), p = q / (HID / 4);
+        const int c4 = CIN == 1 ? 0 : q % (HID / 4), p = CIN == 1 ? q : q / (HID / 4);
         const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
         const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
         v[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (q < kHaloItems && gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG)
-          v[u] = __ldg(reinterpret_cast<const float4*>(src + ((size_t)(gz * EG + gy) * EG + gx) * HID) + c4);
+        if (q < kHaloItems && gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG) {
+          const size_t vox = (size_t)(gz * EG + gy) * EG + gx;
+          if constexpr (CIN == 1) v[u].x = __ldg(src + vox);
+          else v[u] = __ldg(reinterpret_cast<const float4*>(src + vox * HID) + c4);
+        }
       }
 #pragma unroll
       for (int u = 0; u < kLoadBatch; ++u) {
         const int q = q0 + u * kWgThreads;
-        if (q < kHaloItems) store4(s_x + (q / (HID / 4)) * kRowB, q % (HID / 4), v[u]);
+        if (q >= kHaloItems) continue;
+        if constexpr (CIN == 1) store1(s_x + q * kRowB, v[u].x);
+        else store4(s_x + (q / (HID / 4)) * kRowB, q % (HID / 4), v[u]);
       }
     }
     for (int q0 = threadIdx.x; q0 < kTileItems; q0 += kLoadBatch * kWgThreads) {
@@ -599,11 +562,14 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const float* _
 #pragma unroll
       for (int u = 0; u < kLoadBatch; ++u) {
         const int q = q0 + u * kWgThreads;
-        const int c4 = q % (HID / 4), p = q / (HID / 4);
+        const int c4 = COUT == 1 ? 0 : q % (HID / 4), p = COUT == 1 ? q : q / (HID / 4);
         const int gx = x0t + p % TX, gy = y0t + (p / TX) % TY, gz = z0t + p / (TX * TY);
         v[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);         // voxels outside the grid add nothing
-        if (q < kTileItems && gx < EG && gy < EG && gz < EG)
-          v[u] = __ldg(reinterpret_cast<const float4*>(gs + ((size_t)(gz * EG + gy) * EG + gx) * HID) + c4);
+        if (q < kTileItems && gx < EG && gy < EG && gz < EG) {
+          const size_t vox = (size_t)(gz * EG + gy) * EG + gx;
+          if constexpr (COUT == 1) v[u].x = __ldg(gs + vox);
+          else v[u] = __ldg(reinterpret_cast<const float4*>(gs + vox * HID) + c4);
+        }
       }
 #pragma unroll
       for (int u = 0; u < kLoadBatch; ++u) {
@@ -612,7 +578,9 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const float* _
         bsum.y += v[u].y;
         bsum.z += v[u].z;
         bsum.w += v[u].w;
-        if (q < kTileItems) store4(s_g + (q / (HID / 4)) * kRowB, q % (HID / 4), v[u]);
+        if (q >= kTileItems) continue;
+        if constexpr (COUT == 1) store1(s_g + q * kRowB, v[u].x);
+        else store4(s_g + (q / (HID / 4)) * kRowB, q % (HID / 4), v[u]);
       }
     }
     __syncthreads();
@@ -625,20 +593,20 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const float* _
         // A (input channels x voxels): voxel row r + 8 (i >> 1), channels 8 (i & 1) (+16 per m tile)
         const int pa = 16 * kc + mr + 8 * (mi >> 1);
         const int pos = ((pa / (TX * TY)) * HY + (pa / TX) % TY) * HX + pa % TX + toff;
-        uint32_t a[2][4], b[4][2];
+        uint32_t a[MT][4], b[4][2];
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
+        for (int mt = 0; mt < MT; ++mt)
           ldsm_x4_t(x_base + pos * kRowB + 16 * (mi & 1) + 32 * mt, a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
         // B (voxels x output channels): voxel row r + 8 (i & 1), channels 8 (i >> 1) + 16 nj
         const int pb = 16 * kc + mr + 8 * (mi & 1);
 #pragma unroll
-        for (int nj = 0; nj < 2; ++nj)
+        for (int nj = 0; nj < (NT + 1) / 2; ++nj)
           ldsm_x4_t(g_base + pb * kRowB + 16 * (mi >> 1) + 32 * nj, b[2 * nj][0], b[2 * nj][1], b[2 * nj + 1][0],
                     b[2 * nj + 1][1]);
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
+        for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-          for (int nt = 0; nt < 4; ++nt)
+          for (int nt = 0; nt < NT; ++nt)
             mma_bf16(acc[j][mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b[nt][0], b[nt][1]);
       }
     }
@@ -648,24 +616,32 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const float* _
     const int t = warp + kWgWarps * j;
     if (t >= 27) break;
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+    for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int ci = 16 * mt + g4 + 8 * h;
+        if (ci >= CIN) continue;
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
+        for (int nt = 0; nt < NT; ++nt) {
           const int co = 8 * nt + 2 * t4;
-          atomicAdd(&dW[(t * HID + ci) * HID + co], acc[j][mt][nt][2 * h]);
-          atomicAdd(&dW[(t * HID + ci) * HID + co + 1], acc[j][mt][nt][2 * h + 1]);
+          if (co < COUT) atomicAdd(&dW[(t * CIN + ci) * COUT + co], acc[j][mt][nt][2 * h]);
+          if (co + 1 < COUT) atomicAdd(&dW[(t * CIN + ci) * COUT + co + 1], acc[j][mt][nt][2 * h + 1]);
         }
       }
   }
-  // bias gradient: the threads of one channel quad, then one add per channel
+  // bias gradient: the threads of one channel quad (of the one channel),
+  // then one add per channel
   __syncthreads();
   float4* s_red = reinterpret_cast<float4*>(smb);
   s_red[threadIdx.x] = bsum;
   __syncthreads();
-  if (threadIdx.x < HID / 4) {
+  if constexpr (COUT == 1) {
+    if (threadIdx.x == 0) {
+      float t = 0.0f;
+      for (int q = 0; q < kWgThreads; ++q) t += s_red[q].x;
+      atomicAdd(&db[0], t);
+    }
+  } else if (threadIdx.x < HID / 4) {
     float4 t = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     for (int q = threadIdx.x; q < kWgThreads; q += HID / 4) {
       t.x += s_red[q].x;
@@ -683,156 +659,6 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const float* _
 constexpr size_t wgrad_mma_smem() { return (size_t)(HZ * HY * HX + TZ * TY * TX) * kRowB; }
 
 // ------------------------------------------------------ weight gradients
-// dW[tap][ci][co] += sum_v in[v + off(tap)][ci] * g[v][co] and db[co] +=
-// sum_v g[v][co] over one tile position of the grids blockIdx.y,
-// blockIdx.y + kWgradSplit, ...; each block owns one tile position and one
-// share of the grids and adds its sums once (atomically) at the end.  RIN /
-// RG: the input / the gradient enters the products rounded to bfloat16, as
-// in the tensor-core passes of the same layer (the bias sum is unrounded).
-constexpr int kWgradSplit = 4;
-template <int CIN, int COUT, bool RIN, bool RG>
-__global__ void __launch_bounds__(kConvThreads) wgrad_kernel(const float* __restrict__ in, const float* __restrict__ g,
-                                                            int n_grids, float* __restrict__ dW,
-                                                            float* __restrict__ db) {
-  extern __shared__ float sm[];
-  constexpr int SC = pad_stride(CIN);
-  constexpr int NP = 27 * CIN;                            // (tap, ci) pairs
-  constexpr int PPT = (NP + kConvThreads - 1) / kConvThreads;
-  float* s_in = sm;                                       // HZ * HY * HX * SC
-  float* s_g = sm + HZ * HY * HX * SC;                    // TZ * TY * TX * COUT
-  const int tile = blockIdx.x;
-  const int x0t = (tile % kTilesX) * TX, y0t = ((tile / kTilesX) % kTilesY) * TY, z0t = (tile / (kTilesX * kTilesY)) * TZ;
-  constexpr bool kQuads = CIN == 1 && COUT % 4 == 0;     // a thread per (tap, output channel quad)
-  constexpr bool kInQuads = COUT == 1 && CIN % 4 == 0;   // a thread per (tap, input channel quad)
-  constexpr int NQ = 27 * (kQuads ? COUT / 4 : CIN / 4);
-  static_assert(!(kQuads || kInQuads) || NQ <= kConvThreads, "a thread per pair");
-  constexpr bool kPairs = !kQuads && !kInQuads;
-  float acc[kPairs ? PPT : 1][kPairs ? COUT : 1];
-#pragma unroll
-  for (int j = 0; j < (kPairs ? PPT : 1); ++j)
-#pragma unroll
-    for (int co = 0; co < (kPairs ? COUT : 1); ++co) acc[j][co] = 0.0f;
-  float4 acc4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  float bacc = 0.0f;
-  for (int n = blockIdx.y; n < n_grids; n += kWgradSplit) {
-    const float* src = in + (size_t)n * NV * CIN;
-    const float* gs = g + (size_t)n * NV * COUT;
-    __syncthreads();
-    load_halo<CIN, RIN>(src, s_in, x0t, y0t, z0t);
-    if constexpr (COUT % 4 == 0) {
-      // 16-byte loads, four of them in flight before any is stored
-      constexpr int kItems = TZ * TY * TX * (COUT / 4), kBatch = 4;
-      for (int q0 = threadIdx.x; q0 < kItems; q0 += kBatch * kConvThreads) {
-        float4 val[kBatch];
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-          const int q = q0 + u * kConvThreads;
-          const int c4 = q % (COUT / 4), p = q / (COUT / 4);
-          const int gx = x0t + p % TX, gy = y0t + (p / TX) % TY, gz = z0t + p / (TX * TY);
-          val[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);    // voxels outside the grid add nothing
-          if (q < kItems && gx < EG && gy < EG && gz < EG)
-            val[u] = __ldg(reinterpret_cast<const float4*>(gs + ((size_t)(gz * EG + gy) * EG + gx) * COUT) + c4);
-        }
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-          const int q = q0 + u * kConvThreads;
-          if (q < kItems) reinterpret_cast<float4*>(s_g)[q] = val[u];
-        }
-      }
-    } else {
-      for (int q = threadIdx.x; q < TZ * TY * TX * COUT; q += blockDim.x) {
-        const int c = q % COUT, p = q / COUT;
-        const int tx = p % TX, ty = (p / TX) % TY, tz = p / (TX * TY);
-        const int gx = x0t + tx, gy = y0t + ty, gz = z0t + tz;
-        float val = 0.0f;                                 // voxels outside the grid add nothing
-        if (gx < EG && gy < EG && gz < EG) val = gs[((size_t)(gz * EG + gy) * EG + gx) * COUT + c];
-        s_g[q] = val;
-      }
-    }
-    __syncthreads();
-    if constexpr (kQuads) {
-      // one input channel: a thread per (tap, four output channels)
-      if (threadIdx.x < NQ) {
-        const int t = threadIdx.x / (COUT / 4), c4 = threadIdx.x % (COUT / 4);
-        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-        for (int p = 0; p < TZ * TY * TX; ++p) {
-          const int tx = p % TX, ty = (p / TX) % TY, tz = p / (TX * TY);
-          const float xv = s_in[(((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * SC];
-          float4 gv = reinterpret_cast<const float4*>(s_g + p * COUT)[c4];
-          if constexpr (RG) gv = make_float4(bf16_round(gv.x), bf16_round(gv.y), bf16_round(gv.z), bf16_round(gv.w));
-          acc4.x = fmaf(xv, gv.x, acc4.x);
-          acc4.y = fmaf(xv, gv.y, acc4.y);
-          acc4.z = fmaf(xv, gv.z, acc4.z);
-          acc4.w = fmaf(xv, gv.w, acc4.w);
-        }
-      }
-    } else if constexpr (kInQuads) {
-      // one output channel: a thread per (tap, four input channels), 16-byte reads
-      if (threadIdx.x < NQ) {
-        const int t = threadIdx.x / (CIN / 4), c4 = threadIdx.x % (CIN / 4);
-        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-        for (int p = 0; p < TZ * TY * TX; ++p) {
-          const int tx = p % TX, ty = (p / TX) % TY, tz = p / (TX * TY);
-          const float4 xv =
-              *reinterpret_cast<const float4*>(s_in + (((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * SC + 4 * c4);
-          const float gv = RG ? bf16_round(s_g[p]) : s_g[p];
-          acc4.x = fmaf(xv.x, gv, acc4.x);
-          acc4.y = fmaf(xv.y, gv, acc4.y);
-          acc4.z = fmaf(xv.z, gv, acc4.z);
-          acc4.w = fmaf(xv.w, gv, acc4.w);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < PPT; ++j) {
-        const int pr = threadIdx.x + j * kConvThreads;
-        if (pr >= NP) break;
-        const int t = pr / CIN, ci = pr % CIN;
-        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-        for (int p = 0; p < TZ * TY * TX; ++p) {
-          const int tx = p % TX, ty = (p / TX) % TY, tz = p / (TX * TY);
-          const float xv = s_in[(((tz + dz) * HY + (ty + dy)) * HX + (tx + dx)) * SC + ci];
-          const float* gr = s_g + p * COUT;
-#pragma unroll
-          for (int co = 0; co < COUT; ++co) acc[j][co] = fmaf(xv, RG ? bf16_round(gr[co]) : gr[co], acc[j][co]);
-        }
-      }
-    }
-    if (threadIdx.x < COUT)
-      for (int p = 0; p < TZ * TY * TX; ++p) bacc += s_g[p * COUT + threadIdx.x];
-  }
-  if constexpr (kQuads) {
-    if (threadIdx.x < NQ) {
-      float* d = dW + (threadIdx.x / (COUT / 4)) * COUT + 4 * (threadIdx.x % (COUT / 4));
-      atomicAdd(d, acc4.x);
-      atomicAdd(d + 1, acc4.y);
-      atomicAdd(d + 2, acc4.z);
-      atomicAdd(d + 3, acc4.w);
-    }
-  } else if constexpr (kInQuads) {
-    if (threadIdx.x < NQ) {                              // dW[t][ci][0], four consecutive ci
-      float* d = dW + (threadIdx.x / (CIN / 4)) * CIN + 4 * (threadIdx.x % (CIN / 4));
-      atomicAdd(d, acc4.x);
-      atomicAdd(d + 1, acc4.y);
-      atomicAdd(d + 2, acc4.z);
-      atomicAdd(d + 3, acc4.w);
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < PPT; ++j) {
-      const int pr = threadIdx.x + j * kConvThreads;
-      if (pr >= NP) break;
-#pragma unroll
-      for (int co = 0; co < COUT; ++co) atomicAdd(&dW[pr * COUT + co], acc[j][co]);
-    }
-  }
-  if (threadIdx.x < COUT) atomicAdd(&db[threadIdx.x], bacc);
-}
-
-template <int CIN, int COUT>
-constexpr size_t wgrad_smem() {
-  return (size_t)(HZ * HY * HX * pad_stride(CIN) + TZ * TY * TX * COUT) * sizeof(float);
-}
 
 // ----------------------------------------------------------------- loss
 // g[v] = 2 (y[v] - t[v]) / N over the N voxels of all grids; loss += sum of
@@ -971,23 +797,16 @@ cudaError_t conv_tc(const float* in, const __nv_bfloat16* wb, const float* b, fl
   return cudaGetLastError();
 }
 
+template <int CIN, int COUT>
 cudaError_t wgrad_tc(const float* in, const float* g, uint32_t n, float* dW, float* db, cudaStream_t s) {
   constexpr size_t sm = wgrad_mma_smem();
-  cudaError_t e = cudaFuncSetAttribute(wgrad_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  auto k = wgrad_mma_kernel<CIN, COUT>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  wgrad_mma_kernel<<<dim3(kTilesX * kTilesY * kTilesZ, kWgradSplitTc), kWgThreads, sm, s>>>(in, g, (int)n, dW, db);
+  k<<<dim3(kTilesX * kTilesY * kTilesZ, kWgradSplitTc), kWgThreads, sm, s>>>(in, g, (int)n, dW, db);
   return cudaGetLastError();
 }
 
-template <int CIN, int COUT, bool RIN, bool RG>
-cudaError_t wgrad(const float* in, const float* g, uint32_t n, float* dW, float* db, cudaStream_t s) {
-  auto k = wgrad_kernel<CIN, COUT, RIN, RG>;
-  constexpr size_t sm = wgrad_smem<CIN, COUT>();
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  k<<<dim3(kTilesX * kTilesY * kTilesZ, kWgradSplit), kConvThreads, sm, s>>>(in, g, (int)n, dW, db);
-  return cudaGetLastError();
-}
 
 ro_status mc_err(cudaError_t e) { return e == cudaSuccess ? RO_OK : RO_ERR_CUDA; }
 
@@ -1026,20 +845,20 @@ cudaError_t mc_backward(ro_mc* m, uint32_t n, const float* x0, const float* targ
   };
   // layer 4 (32 -> 1)
   if (e == cudaSuccess) e = fork(0);
-  if (e == cudaSuccess) e = wgrad<HID, 1, true, true>(m->a3, m->g4, n, G + kWOff[3], G + kBOff[3], s2);
+  if (e == cudaSuccess) e = wgrad_tc<HID, 1>(m->a3, m->g4, n, G + kWOff[3], G + kBOff[3], s2);
   if (e == cudaSuccess) e = conv_tc<kEpiMask, 1, HID>(m->g4, m->wd3, zero_bias, m->ga, m->a3, n, m->flag, s);
   // layer 3 (32 -> 32)
   if (e == cudaSuccess) e = fork(1);
-  if (e == cudaSuccess) e = wgrad_tc(m->a2, m->ga, n, G + kWOff[2], G + kBOff[2], s2);
+  if (e == cudaSuccess) e = wgrad_tc<HID, HID>(m->a2, m->ga, n, G + kWOff[2], G + kBOff[2], s2);
   if (e == cudaSuccess) e = cudaEventRecord(m->ev[2], s2);
   if (e == cudaSuccess) e = conv_tc<kEpiMask, HID, HID>(m->ga, m->wd2, zero_bias, m->gb, m->a2, n, m->flag, s);
   // layer 2 (32 -> 32)
   if (e == cudaSuccess) e = fork(3);
-  if (e == cudaSuccess) e = wgrad_tc(m->a1, m->gb, n, G + kWOff[1], G + kBOff[1], s2);
+  if (e == cudaSuccess) e = wgrad_tc<HID, HID>(m->a1, m->gb, n, G + kWOff[1], G + kBOff[1], s2);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->ev[2], 0);
   if (e == cudaSuccess) e = conv_tc<kEpiMask, HID, HID>(m->gb, m->wd1, zero_bias, m->ga, m->a1, n, m->flag, s);
   // layer 1 (1 -> 32)
-  if (e == cudaSuccess) e = wgrad<1, HID, true, false>(x0, m->ga, n, G + kWOff[0], G + kBOff[0], s);
+  if (e == cudaSuccess) e = wgrad_tc<1, HID>(x0, m->ga, n, G + kWOff[0], G + kBOff[0], s);
   if (e == cudaSuccess) e = cudaEventRecord(m->ev[4], s2);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->ev[4], 0);
   return e;

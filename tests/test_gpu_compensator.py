@@ -72,9 +72,8 @@ def test_forward_and_gradients_match_oracle(mc):
     want_loss = sum(losses) / 2
     assert abs(float(loss.item()) - want_loss) <= 1e-4 * want_loss
     # the oracle mirrors the GPU's rounding of the output gradients entering
-    # the last three layers' tensor-core products (and the binary32 weight
-    # gradients of the last layer, which round as its input gradients do)
-    losses, grads = zip(*[omc.loss_and_grads(q, x0f[k], tf[k], bf16_inputs=(0, 1, 2, 3), bf16_grads=(1, 2, 3))
+    # every layer's tensor-core weight- and input-gradient products
+    losses, grads = zip(*[omc.loss_and_grads(q, x0f[k], tf[k], bf16_inputs=(0, 1, 2, 3), bf16_grads=(0, 1, 2, 3))
                           for k in range(2)])
     want = [(sum(gr[i][0] for gr in grads) / 2, sum(gr[i][1] for gr in grads) / 2) for i in range(4)]
     got = mcmod.unflatten(g.astype(np.float64))
