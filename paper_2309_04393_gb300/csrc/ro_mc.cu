@@ -152,18 +152,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 // (-zo - 1) mod 8, so slices zo, zo - 1, zo - 2 are consecutive columns; at
 // the ring's end the instruction is split in two.  A block is zeroed once
 // its slice has been read out (its last contribution came from input slice
-// zo + 2), five input slices before it is used again.  The input slice is
-// stored once, as rows of 8 channels (16 bytes) in planes of one channel
-// octet: [octet][halo y][halo x][16 B]; an 8-row core-matrix group is a halo
-// row, 160 bytes from the next, so the x offset of a tap moves the operand's
-// start by 16 bytes and the y offset by 160.
-constexpr int TZX = 8, TZY = 16, kTzChunk = 17;
-constexpr int HZX2 = TZX + 2, HZY2 = TZY + 2;
+// zo + 2), five input slices before it is used again.  The x-y plane is
+// flattened with its one-voxel halo, 36 voxels a row (voxel (x, y) at
+// f = (y + 1) 36 + x + 1), and a block's 128 accumulator rows are a run of
+// 128 consecutive f (ten runs cover the 34 x 34 outputs; rows that fall on
+// the halo columns or past the last output are computed and not stored).
+// The input run the taps reach, 128 + 2 x 37 voxels, is stored once per
+// slice as rows of 8 channels (16 bytes) in planes of one channel octet:
+// core matrices are 8 consecutive rows (128 bytes apart), and the tap
+// (dy, dx) moves the operand's start by (36 dy + dx) rows.
+constexpr int kTzChunk = 17;                                 // output z slices of a block
 constexpr int kTzThreads = 256;
-constexpr int kTzTilesX = (EG + TZX - 1) / TZX, kTzTilesY = (EG + TZY - 1) / TZY, kTzChunks = (EG + kTzChunk - 1) / kTzChunk;
-constexpr int kTzUnits = kTzTilesX * kTzTilesY * kTzChunks;  // columns per grid
-constexpr int kTzRowStride = HZX2 * 16;                      // one halo row of 10 voxels: 160 B (SBO)
-constexpr int kTzPlane = HZY2 * kTzRowStride;                // one channel octet of a slice: 2,880 B (LBO)
+constexpr int kTzPadW = EG + 2;                              // 36: a halo row of the flattened plane
+constexpr int kTzMTiles = (EG * kTzPadW - 2 + 127) / 128;    // 128-row runs covering the outputs: 10
+constexpr int kTzRows = 128 + 2 * (kTzPadW + 1);             // input rows a run's taps reach: 202
+constexpr int kTzChunks = (EG + kTzChunk - 1) / kTzChunk;
+constexpr int kTzUnits = kTzMTiles * kTzChunks;              // blocks per grid
+constexpr int kTzPlane = kTzRows * 16;                       // one channel octet of a slice: 3,232 B (LBO)
 constexpr int kTzRing = 4;                                   // input slices in shared memory
 
 // Shapes of a z-folded convolution with CIN (1 or 32) input and COUT (1 or
@@ -182,7 +187,7 @@ struct TzShape {
   static constexpr int BTAP = KS * BKS;
   static constexpr int BBYTES = 9 * BTAP;
   static constexpr int COLS = 8 * COUTP;                     // tensor-memory columns: 8 blocks
-  static constexpr int ITEMS = HZY2 * HZX2 * (CIN == 1 ? 1 : 4);   // pieces of an input slice
+  static constexpr int ITEMS = kTzRows * (CIN == 1 ? 1 : 4);       // pieces of an input slice
   static constexpr int PER = (ITEMS + kTzThreads - 1) / kTzThreads;
   // shared memory; at least 76 KB when a block holds 256 columns of tensor
   // memory, so that no third block (which could not allocate) is resident
@@ -209,19 +214,20 @@ __device__ __forceinline__ void tz_mma(uint32_t d_tmem, uint64_t da, uint64_t db
                :: "r"(d_tmem), "l"(da), "l"(db), "r"(idesc));
 }
 
-// this thread's pieces of input slice gz (zeros outside the grid): 8
-// channels (32 bytes) each for 32 channels, one value for one channel
+// this thread's pieces of input slice gz, flattened rows f0 .. f0 + 201
+// (zeros outside the grid): 8 channels (32 bytes) each for 32 channels, one
+// value for one channel
 template <int CIN>
-__device__ __forceinline__ void tz_fetch(const float* __restrict__ src, int x0t, int y0t, int gz, int tid,
+__device__ __forceinline__ void tz_fetch(const float* __restrict__ src, int f0, int gz, int tid,
                                          float4 (&v)[TzShape<CIN, 32>::PER][2]) {
   using S = TzShape<CIN, 32>;
 #pragma unroll
   for (int j = 0; j < S::PER; ++j) {
     const int w = tid + j * kTzThreads;
     v[j][0] = v[j][1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    const int q = CIN == 1 ? 0 : w % 4, p = CIN == 1 ? w : w / 4;
-    const int hx = p % HZX2, hy = p / HZX2;
-    const int gx = x0t + hx - 1, gy = y0t + hy - 1;
+    const int q = CIN == 1 ? 0 : w % 4, l = CIN == 1 ? w : w / 4;
+    const int f = f0 + l;
+    const int gx = f % kTzPadW - 1, gy = f / kTzPadW - 1;
     if (w < S::ITEMS && gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG) {
       if constexpr (CIN == 1) {
         v[j][0].x = __ldg(src + (size_t)(gz * EG + gy) * EG + gx);
@@ -243,11 +249,10 @@ __device__ __forceinline__ void tz_store(uint8_t* slot, int tid, const float4 (&
   for (int j = 0; j < S::PER; ++j) {
     const int w = tid + j * kTzThreads;
     if (w >= S::ITEMS) continue;
-    const int q = CIN == 1 ? 0 : w % 4, p = CIN == 1 ? w : w / 4;
-    const int hx = p % HZX2, hy = p / HZX2;
+    const int q = CIN == 1 ? 0 : w % 4, l = CIN == 1 ? w : w / 4;
     __nv_bfloat162 h[4] = {__floats2bfloat162_rn(v[j][0].x, v[j][0].y), __floats2bfloat162_rn(v[j][0].z, v[j][0].w),
                            __floats2bfloat162_rn(v[j][1].x, v[j][1].y), __floats2bfloat162_rn(v[j][1].z, v[j][1].w)};
-    *reinterpret_cast<uint4*>(slot + q * kTzPlane + hy * kTzRowStride + hx * 16) = *reinterpret_cast<const uint4*>(h);
+    *reinterpret_cast<uint4*>(slot + q * kTzPlane + l * 16) = *reinterpret_cast<const uint4*>(h);
   }
 }
 
@@ -280,8 +285,8 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
   __shared__ float s_bias[HID];
   const int tid = threadIdx.x, warp = tid >> 5;
   const int unit = blockIdx.x, n = blockIdx.y;
-  const int x0t = (unit % kTzTilesX) * TZX, y0t = ((unit / kTzTilesX) % kTzTilesY) * TZY;
-  const int z0 = (unit / (kTzTilesX * kTzTilesY)) * kTzChunk;
+  const int f0 = (unit % kTzMTiles) * 128;                   // first input row; outputs from f0 + 37
+  const int z0 = (unit / kTzMTiles) * kTzChunk;
   const int nz = min(kTzChunk, EG - z0);                     // output slices of this column
   const float* src = in + (size_t)n * NV * CIN;
   // weights wb[tap][co][ci] (CP rows of 32 channels, 64 bytes, per tap): tap
@@ -305,15 +310,16 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
   // into registers, stored in the first step
   float4 pre[S::PER][2];
   for (int li = 0; li < 3; ++li) {
-    tz_fetch<CIN>(src, x0t, y0t, z0 - 1 + li, tid, pre);
+    tz_fetch<CIN>(src, f0, z0 - 1 + li, tid, pre);
     tz_store<CIN>(s_a + li * S::SLICE, tid, pre);
   }
-  tz_fetch<CIN>(src, x0t, y0t, z0 + 2, tid, pre);
-  // this thread's accumulator row (warps 0-3): voxel (ex, ey) of each slice;
-  // am holds its mask row (input-gradient pass) or residual value, fetched
-  // a step ahead
-  const int ex = x0t + tid % TZX, ey = y0t + tid / TZX;
-  const bool erow = warp < 4 && ex < EG && ey < EG;
+  tz_fetch<CIN>(src, f0, z0 + 2, tid, pre);
+  // this thread's accumulator row (warps 0-3): voxel (ex, ey) of each slice
+  // (halo columns and rows past the plane are not stored); am holds its mask
+  // row (input-gradient pass) or residual value, fetched a step ahead
+  const int fr = f0 + kTzPadW + 1 + tid;
+  const int ex = fr % kTzPadW - 1, ey = fr / kTzPadW - 1;
+  const bool erow = warp < 4 && ex >= 0 && ex < EG && ey < EG;
   constexpr int kAux = EPI == kEpiMask ? COUT / 4 : 1;
   float4 am[kAux];
 #pragma unroll
@@ -349,8 +355,8 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
       const int dy = c / 3, dx = c % 3;
 #pragma unroll
       for (int ks = 0; ks < S::KS; ++ks) {
-        const uint64_t da = umma_desc_kmajor(a_s + (uint32_t)(2 * ks * kTzPlane + dy * kTzRowStride + dx * 16),
-                                             kTzPlane, kTzRowStride);
+        const uint64_t da = umma_desc_kmajor(a_s + (uint32_t)(2 * ks * kTzPlane + (dy * kTzPadW + dx) * 16),
+                                             kTzPlane, 128);
         const uint32_t bt = b0 + (uint32_t)(c * S::BTAP + ks * S::BKS);
         if (bb <= 5) {
           tz_mma(tmem + (uint32_t)(CP * bb), da, umma_desc_kmajor(bt, 128, 256), tz_idesc(3 * CP));
@@ -432,7 +438,7 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
     // input slice i + 3 into the slot input slice i - 1 left (every
     // instruction that read it has completed); fetch slice i + 4
     if (i + 3 <= nz + 1) tz_store<CIN>(s_a + ((i + 3) % kTzRing) * S::SLICE, tid, pre);
-    if (i + 4 <= nz + 1) tz_fetch<CIN>(src, x0t, y0t, z0 - 1 + i + 4, tid, pre);
+    if (i + 4 <= nz + 1) tz_fetch<CIN>(src, f0, z0 - 1 + i + 4, tid, pre);
     if constexpr (EPI != kEpiRelu) {                         // mask rows / residual of output slice i - 2
       const int zm = i - 2;
       if (erow && zm >= 0 && zm < nz) {
