@@ -17,7 +17,9 @@
  *
  * Conventions as in ro.h: every call returns an ro_status; device memory is
  * the caller's (one arena of ro_mc_query_bytes bytes); work is enqueued on
- * the stream given at creation; grids are device arrays, x fastest.
+ * the stream given at creation (a training step runs its weight gradients
+ * on an internal second stream that forks from and joins back into that
+ * stream within the call); grids are device arrays, x fastest.
  * Gradients are summed with atomic adds, so their last bits depend on the
  * order blocks finish.
  */
@@ -48,8 +50,9 @@ typedef struct {
 ro_status ro_mc_query_bytes(const ro_mc_desc* desc, uint64_t* bytes);
 
 /* Creates a compensator over the caller's arena (256-byte aligned, at
- * least ro_mc_query_bytes bytes) on `stream` (a cudaStream_t).  Parameters
- * start at zero: set them with ro_mc_set_params. */
+ * least ro_mc_query_bytes bytes) on `stream` (a cudaStream_t), with one
+ * internal stream and five events of its own (freed by ro_mc_destroy).
+ * Parameters start at zero: set them with ro_mc_set_params. */
 ro_status ro_mc_create(const ro_mc_desc* desc, void* arena_device, uint64_t arena_bytes, void* stream, ro_mc** out);
 
 /* Waits for the stream and frees the host-side state. */

@@ -753,7 +753,7 @@ struct ro_mc {
   // (layers 0 and 3 padded: one real input channel, one real output row)
   __nv_bfloat16 *wf0, *wf1, *wf2, *wf3, *wd1, *wd2, *wd3;
   float *a1, *a2, *a3;                // hidden activations (after ReLU), n * NV * 32
-  float *ga, *gb;                     // hidden gradients, n * NV * 32
+  float *ga, *gb, *gc;                // hidden gradients, n * NV * 32
   float *g4, *y;                      // output gradient and output, n * NV
   float* loss;                        // scratch loss when the caller passes none
   uint32_t* flag;                     // set by a tensor-core wait that gave up (latched)
@@ -773,7 +773,8 @@ constexpr uint64_t kMcAlign = 256;
 uint64_t mc_align(uint64_t v) { return (v + kMcAlign - 1) / kMcAlign * kMcAlign; }
 
 struct McLayout {
-  uint64_t P, Pq, M, V, G, flag, wf0, wf1, wf2, wf3, wd1, wd2, wd3, wend, a1, a2, a3, ga, gb, g4, y, loss, total;
+  uint64_t P, Pq, M, V, G, flag, wf0, wf1, wf2, wf3, wd1, wd2, wd3, wend, a1, a2, a3, ga, gb, gc, g4, y, loss,
+      total;
 };
 
 McLayout mc_layout(uint32_t nb) {
@@ -786,7 +787,7 @@ McLayout mc_layout(uint32_t nb) {
   L.wf3 = take(27ull * 16 * HID * 2);
   L.wd1 = take(27ull * HID * HID * 2); L.wd2 = take(27ull * HID * HID * 2); L.wd3 = take(27ull * HID * HID * 2);
   L.wend = o;
-  L.a1 = take(hid); L.a2 = take(hid); L.a3 = take(hid); L.ga = take(hid); L.gb = take(hid);
+  L.a1 = take(hid); L.a2 = take(hid); L.a3 = take(hid); L.ga = take(hid); L.gb = take(hid); L.gc = take(hid);
   L.g4 = take(one); L.y = take(one); L.loss = take(4);
   L.total = o;
   return L;
@@ -841,9 +842,9 @@ cudaError_t mc_backward(ro_mc* m, uint32_t n, const float* x0, const float* targ
   const float* zero_bias = nullptr;
   // The weight gradients of a layer and the input gradients through it read
   // the same output gradient and write different buffers: the weight
-  // gradients run on the side stream.  ga is written again by the layer-2
-  // input gradients, so those wait until the layer-3 weight gradients have
-  // read it; the main stream joins the side stream at the end.
+  // gradients run on the side stream.  Each output gradient has a buffer of
+  // its own (ga, gb, gc), so neither stream waits for the other until the
+  // main stream joins the side stream at the end.
   cudaStream_t s2 = m->side;
   auto fork = [&](int k) {
     cudaError_t r = cudaEventRecord(m->ev[k], s);
@@ -856,15 +857,13 @@ cudaError_t mc_backward(ro_mc* m, uint32_t n, const float* x0, const float* targ
   // layer 3 (32 -> 32)
   if (e == cudaSuccess) e = fork(1);
   if (e == cudaSuccess) e = wgrad_tc<HID, HID>(m->a2, m->ga, n, G + kWOff[2], G + kBOff[2], s2);
-  if (e == cudaSuccess) e = cudaEventRecord(m->ev[2], s2);
   if (e == cudaSuccess) e = conv_tc<kEpiMask, HID, HID>(m->ga, m->wd2, zero_bias, m->gb, m->a2, n, m->flag, s);
   // layer 2 (32 -> 32)
   if (e == cudaSuccess) e = fork(3);
   if (e == cudaSuccess) e = wgrad_tc<HID, HID>(m->a1, m->gb, n, G + kWOff[1], G + kBOff[1], s2);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->ev[2], 0);
-  if (e == cudaSuccess) e = conv_tc<kEpiMask, HID, HID>(m->gb, m->wd1, zero_bias, m->ga, m->a1, n, m->flag, s);
+  if (e == cudaSuccess) e = conv_tc<kEpiMask, HID, HID>(m->gb, m->wd1, zero_bias, m->gc, m->a1, n, m->flag, s);
   // layer 1 (1 -> 32)
-  if (e == cudaSuccess) e = wgrad_tc<1, HID>(x0, m->ga, n, G + kWOff[0], G + kBOff[0], s);
+  if (e == cudaSuccess) e = wgrad_tc<1, HID>(x0, m->gc, n, G + kWOff[0], G + kBOff[0], s);
   if (e == cudaSuccess) e = cudaEventRecord(m->ev[4], s2);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->ev[4], 0);
   return e;
@@ -899,7 +898,7 @@ ro_status ro_mc_create(const ro_mc_desc* d, void* arena, uint64_t arena_bytes, v
   auto h = [&](uint64_t off) { return reinterpret_cast<__nv_bfloat16*>(b + off); };
   m->wf0 = h(L.wf0); m->wf1 = h(L.wf1); m->wf2 = h(L.wf2); m->wf3 = h(L.wf3);
   m->wd1 = h(L.wd1); m->wd2 = h(L.wd2); m->wd3 = h(L.wd3);
-  m->a1 = f(L.a1); m->a2 = f(L.a2); m->a3 = f(L.a3); m->ga = f(L.ga); m->gb = f(L.gb);
+  m->a1 = f(L.a1); m->a2 = f(L.a2); m->a3 = f(L.a3); m->ga = f(L.ga); m->gb = f(L.gb); m->gc = f(L.gc);
   m->g4 = f(L.g4); m->y = f(L.y); m->loss = f(L.loss);
   m->flag = reinterpret_cast<uint32_t*>(b + L.flag);
   cudaError_t e = cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking);
