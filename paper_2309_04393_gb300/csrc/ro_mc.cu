@@ -55,7 +55,7 @@ __global__ void upsample_kernel(const uint8_t* __restrict__ base, size_t pitch, 
   const uint16_t* s = reinterpret_cast<const uint16_t*>(base + (slot_of ? (size_t)slot_of[n] : (size_t)n) * pitch);
   const uint32_t o = octants[n];
   const int oc[3] = {(int)(o & 1u), (int)((o >> 1) & 1u), (int)((o >> 2) & 1u)};
-  for (int v = threadIdx.x; v < NV; v += blockDim.x) {
+  for (int v = blockIdx.y * blockDim.x + threadIdx.x; v < NV; v += gridDim.y * blockDim.x) {
     const int X[3] = {v % EG, (v / EG) % EG, v / (EG * EG)};
     int i0[3];
     float f[3];
@@ -82,11 +82,15 @@ __global__ void upsample_kernel(const uint8_t* __restrict__ base, size_t pitch, 
   }
 }
 
+// blocks per grid of the voxel-wise kernels (upsample, to_raw): a batch of
+// 32 grids gives 256 blocks
+constexpr int kGridBlocks = 8;
+
 // y (scaled) -> raw u16 values, nearest, clamped to [0, 65535], at out_pitch
 __global__ void to_raw_kernel(const float* __restrict__ y, uint8_t* __restrict__ out, size_t out_pitch) {
   const int n = blockIdx.x;
   uint16_t* o = reinterpret_cast<uint16_t*>(out + (size_t)n * out_pitch);
-  for (int v = threadIdx.x; v < NV; v += blockDim.x) {
+  for (int v = blockIdx.y * blockDim.x + threadIdx.x; v < NV; v += gridDim.y * blockDim.x) {
     const float r = rintf(y[(size_t)n * NV + v] * 65536.0f);
     o[v] = (uint16_t)fminf(fmaxf(r, 0.0f), 65535.0f);
   }
@@ -948,8 +952,8 @@ ro_status ro_mc_get_params(ro_mc* m, float* host) {
 
 ro_status ro_mc_upsample(ro_mc* m, uint32_t n, const uint16_t* slots, const uint32_t* octants, float* x0) {
   if (!m || !slots || !octants || !x0 || n < 1 || n > m->desc.max_batch) return RO_ERR_INVALID_ARG;
-  upsample_kernel<<<n, 256, 0, m->stream>>>(reinterpret_cast<const uint8_t*>(slots), (size_t)NV * 2, nullptr, octants,
-                                             x0);
+  upsample_kernel<<<dim3(n, kGridBlocks), 256, 0, m->stream>>>(reinterpret_cast<const uint8_t*>(slots), (size_t)NV * 2,
+                                                                nullptr, octants, x0);
   return mc_err(cudaGetLastError());
 }
 
@@ -1014,11 +1018,11 @@ cudaError_t mc_synthesize(::ro_mc* m, uint32_t n, const uint8_t* cache, uint32_t
   if (!m || n < 1 || n > m->desc.max_batch) return cudaErrorInvalidValue;
   cudaStream_t keep = m->stream;
   m->stream = s;
-  upsample_kernel<<<n, 256, 0, s>>>(cache, pitch, parent_slots, octants, m->g4);
+  upsample_kernel<<<dim3(n, kGridBlocks), 256, 0, s>>>(cache, pitch, parent_slots, octants, m->g4);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = mc_forward(m, n, m->g4, m->y);
   if (e == cudaSuccess) {
-    to_raw_kernel<<<n, 256, 0, s>>>(m->y, out, out_pitch);
+    to_raw_kernel<<<dim3(n, kGridBlocks), 256, 0, s>>>(m->y, out, out_pitch);
     e = cudaGetLastError();
   }
   m->stream = keep;
