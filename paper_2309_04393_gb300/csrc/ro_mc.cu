@@ -221,8 +221,10 @@ __device__ __forceinline__ void tz_mma(uint32_t d_tmem, uint64_t da, uint64_t db
 // this thread's pieces of input slice gz, flattened rows f0 .. f0 + 201
 // (zeros outside the grid): 8 channels (32 bytes) each for 32 channels, one
 // value for one channel
-template <int CIN>
-__device__ __forceinline__ void tz_fetch(const float* __restrict__ src, int f0, int gz, int tid,
+// (INBF: the input is stored as bfloat16 values, 16 bytes per 8 channels,
+// kept as they are)
+template <int CIN, bool INBF>
+__device__ __forceinline__ void tz_fetch(const void* __restrict__ src_v, int f0, int gz, int tid,
                                          float4 (&v)[TzShape<CIN, 32>::PER][2]) {
   using S = TzShape<CIN, 32>;
 #pragma unroll
@@ -233,10 +235,13 @@ __device__ __forceinline__ void tz_fetch(const float* __restrict__ src, int f0, 
     const int f = f0 + l;
     const int gx = f % kTzPadW - 1, gy = f / kTzPadW - 1;
     if (w < S::ITEMS && gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG) {
+      const size_t vox = (size_t)(gz * EG + gy) * EG + gx;
       if constexpr (CIN == 1) {
-        v[j][0].x = __ldg(src + (size_t)(gz * EG + gy) * EG + gx);
+        v[j][0].x = __ldg(static_cast<const float*>(src_v) + vox);
+      } else if constexpr (INBF) {
+        v[j][0] = __ldg(reinterpret_cast<const float4*>(static_cast<const __nv_bfloat16*>(src_v) + vox * HID + 8 * q));
       } else {
-        const float4* p4 = reinterpret_cast<const float4*>(src + ((size_t)(gz * EG + gy) * EG + gx) * HID + 8 * q);
+        const float4* p4 = reinterpret_cast<const float4*>(static_cast<const float*>(src_v) + vox * HID + 8 * q);
         v[j][0] = __ldg(p4);
         v[j][1] = __ldg(p4 + 1);
       }
@@ -246,7 +251,7 @@ __device__ __forceinline__ void tz_fetch(const float* __restrict__ src, int f0, 
 
 // ... rounded to bfloat16, into the octet planes of a ring slot (one
 // channel: the value and seven zeros in plane 0)
-template <int CIN>
+template <int CIN, bool INBF>
 __device__ __forceinline__ void tz_store(uint8_t* slot, int tid, const float4 (&v)[TzShape<CIN, 32>::PER][2]) {
   using S = TzShape<CIN, 32>;
 #pragma unroll
@@ -254,9 +259,13 @@ __device__ __forceinline__ void tz_store(uint8_t* slot, int tid, const float4 (&
     const int w = tid + j * kTzThreads;
     if (w >= S::ITEMS) continue;
     const int q = CIN == 1 ? 0 : w % 4, l = CIN == 1 ? w : w / 4;
-    __nv_bfloat162 h[4] = {__floats2bfloat162_rn(v[j][0].x, v[j][0].y), __floats2bfloat162_rn(v[j][0].z, v[j][0].w),
-                           __floats2bfloat162_rn(v[j][1].x, v[j][1].y), __floats2bfloat162_rn(v[j][1].z, v[j][1].w)};
-    *reinterpret_cast<uint4*>(slot + q * kTzPlane + l * 16) = *reinterpret_cast<const uint4*>(h);
+    if constexpr (INBF) {
+      *reinterpret_cast<float4*>(slot + q * kTzPlane + l * 16) = v[j][0];
+    } else {
+      __nv_bfloat162 h[4] = {__floats2bfloat162_rn(v[j][0].x, v[j][0].y), __floats2bfloat162_rn(v[j][0].z, v[j][0].w),
+                             __floats2bfloat162_rn(v[j][1].x, v[j][1].y), __floats2bfloat162_rn(v[j][1].z, v[j][1].w)};
+      *reinterpret_cast<uint4*>(slot + q * kTzPlane + l * 16) = *reinterpret_cast<const uint4*>(h);
+    }
   }
 }
 
@@ -274,11 +283,14 @@ __device__ __forceinline__ void tz_zero(uint32_t taddr) {
 
 __device__ __forceinline__ int tz_block(int zo) { return ((-zo - 1) % 8 + 8) % 8; }
 
-template <int EPI, int CIN, int COUT>
-__global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __restrict__ in,
+// in: binary32, or bfloat16 when INBF (the hidden activations); out: the
+// hidden activations as bfloat16 (ReLU epilogue), else binary32; aux: the
+// activations (bfloat16) whose sign masks the gradient, or x0 (binary32)
+template <int EPI, int CIN, int COUT, bool INBF>
+__global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const void* __restrict__ in,
                                                                const __nv_bfloat16* __restrict__ wb,
-                                                               const float* __restrict__ bias, float* __restrict__ out,
-                                                               const float* __restrict__ aux, uint32_t* __restrict__ err) {
+                                                               const float* __restrict__ bias, void* __restrict__ out,
+                                                               const void* __restrict__ aux, uint32_t* __restrict__ err) {
   using S = TzShape<CIN, COUT>;
   constexpr int CP = S::COUTP;
   extern __shared__ __align__(128) uint8_t smz[];
@@ -292,7 +304,7 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
   const int f0 = (unit % kTzMTiles) * 128;                   // first input row; outputs from f0 + 37
   const int z0 = (unit / kTzMTiles) * kTzChunk;
   const int nz = min(kTzChunk, EG - z0);                     // output slices of this column
-  const float* src = in + (size_t)n * NV * CIN;
+  const void* src = static_cast<const uint8_t*>(in) + (size_t)n * NV * CIN * (INBF ? 2 : 4);
   // weights wb[tap][co][ci] (CP rows of 32 channels, 64 bytes, per tap): tap
   // (dz, dy, dx) goes to the B of (dy, dx), rows dz * CP + co, in the
   // canonical K-major layout; with one input channel only its first K step
@@ -314,20 +326,20 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
   // into registers, stored in the first step
   float4 pre[S::PER][2];
   for (int li = 0; li < 3; ++li) {
-    tz_fetch<CIN>(src, f0, z0 - 1 + li, tid, pre);
-    tz_store<CIN>(s_a + li * S::SLICE, tid, pre);
+    tz_fetch<CIN, INBF>(src, f0, z0 - 1 + li, tid, pre);
+    tz_store<CIN, INBF>(s_a + li * S::SLICE, tid, pre);
   }
-  tz_fetch<CIN>(src, f0, z0 + 2, tid, pre);
+  tz_fetch<CIN, INBF>(src, f0, z0 + 2, tid, pre);
   // this thread's accumulator row (warps 0-3): voxel (ex, ey) of each slice
   // (halo columns and rows past the plane are not stored); am holds its mask
   // row (input-gradient pass) or residual value, fetched a step ahead
   const int fr = f0 + kTzPadW + 1 + tid;
   const int ex = fr % kTzPadW - 1, ey = fr / kTzPadW - 1;
   const bool erow = warp < 4 && ex >= 0 && ex < EG && ey < EG;
-  constexpr int kAux = EPI == kEpiMask ? COUT / 4 : 1;
-  float4 am[kAux];
+  constexpr int kAux = EPI == kEpiMask ? COUT / 8 : 1;       // 8 bfloat16 mask values, or x0
+  uint4 am[kAux];
 #pragma unroll
-  for (int c4 = 0; c4 < kAux; ++c4) am[c4] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  for (int c8 = 0; c8 < kAux; ++c8) am[c8] = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
     for (int q = 0; q < 4; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&s_mbar[q])));
     s_fail = 0;
@@ -416,19 +428,32 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
           if (erow) {
             const size_t v = (size_t)n * NV + (size_t)((z0 + zo) * EG + ey) * EG + ex;
             if constexpr (COUT == 1) {                       // y = x0 + f(x0): column 0, bias, residual
-              out[v] = __uint_as_float(r[0]) + s_bias[0] + am[0].x;
-            } else {
-              float4* o4 = reinterpret_cast<float4*>(out + v * HID);
+              static_cast<float*>(out)[v] = __uint_as_float(r[0]) + s_bias[0] + __uint_as_float(am[0].x);
+            } else if constexpr (EPI == kEpiRelu) {          // the activation, stored as bfloat16
+              uint4* o8 = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out) + v * HID);
 #pragma unroll
-              for (int c4 = 0; c4 < HID / 4; ++c4) {
-                float o[4];
-                const float4 m4 = am[EPI == kEpiMask ? c4 : 0];
-                const float mk[4] = {m4.x, m4.y, m4.z, m4.w};
+              for (int c8 = 0; c8 < HID / 8; ++c8) {
+                uint32_t h[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                  const float val = __uint_as_float(r[4 * c4 + e]);
-                  if constexpr (EPI == kEpiRelu) o[e] = fmaxf(val + s_bias[4 * c4 + e], 0.0f);
-                  else o[e] = mk[e] > 0.0f ? val : 0.0f;
+                  const float lo = fmaxf(__uint_as_float(r[8 * c8 + 2 * e]) + s_bias[8 * c8 + 2 * e], 0.0f);
+                  const float hi = fmaxf(__uint_as_float(r[8 * c8 + 2 * e + 1]) + s_bias[8 * c8 + 2 * e + 1], 0.0f);
+                  const __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
+                  h[e] = *reinterpret_cast<const uint32_t*>(&b2);
+                }
+                o8[c8] = make_uint4(h[0], h[1], h[2], h[3]);
+              }
+            } else {                                         // gradient where the activation is positive
+              float4* o4 = reinterpret_cast<float4*>(static_cast<float*>(out) + v * HID);
+#pragma unroll
+              for (int c4 = 0; c4 < HID / 4; ++c4) {
+                const uint32_t mw[2] = {(&am[c4 / 2].x)[2 * (c4 % 2)], (&am[c4 / 2].x)[2 * (c4 % 2) + 1]};
+                float o[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  const uint32_t hbits = (mw[e / 2] >> (16 * (e % 2))) & 0xFFFFu;
+                  const float mk = __uint_as_float(hbits << 16);         // the bfloat16 value, exactly
+                  o[e] = mk > 0.0f ? __uint_as_float(r[4 * c4 + e]) : 0.0f;
                 }
                 o4[c4] = make_float4(o[0], o[1], o[2], o[3]);
               }
@@ -441,18 +466,18 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const float* __r
     }
     // input slice i + 3 into the slot input slice i - 1 left (every
     // instruction that read it has completed); fetch slice i + 4
-    if (i + 3 <= nz + 1) tz_store<CIN>(s_a + ((i + 3) % kTzRing) * S::SLICE, tid, pre);
-    if (i + 4 <= nz + 1) tz_fetch<CIN>(src, f0, z0 - 1 + i + 4, tid, pre);
+    if (i + 3 <= nz + 1) tz_store<CIN, INBF>(s_a + ((i + 3) % kTzRing) * S::SLICE, tid, pre);
+    if (i + 4 <= nz + 1) tz_fetch<CIN, INBF>(src, f0, z0 - 1 + i + 4, tid, pre);
     if constexpr (EPI != kEpiRelu) {                         // mask rows / residual of output slice i - 2
       const int zm = i - 2;
       if (erow && zm >= 0 && zm < nz) {
         const size_t v = (size_t)n * NV + (size_t)((z0 + zm) * EG + ey) * EG + ex;
         if constexpr (EPI == kEpiMask) {
-          const float4* a4 = reinterpret_cast<const float4*>(aux + v * COUT);
+          const uint4* a8 = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(aux) + v * COUT);
 #pragma unroll
-          for (int c4 = 0; c4 < kAux; ++c4) am[c4] = __ldg(a4 + c4);
+          for (int c8 = 0; c8 < kAux; ++c8) am[c8] = __ldg(a8 + c8);
         } else {
-          am[0].x = __ldg(aux + v);
+          am[0].x = __float_as_uint(__ldg(static_cast<const float*>(aux) + v));
         }
       }
     }
@@ -494,11 +519,12 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t&
 // operands.  Warp w of 16 accumulates taps w and w + 16 and adds its sums
 // once (atomically) at the end.  The tiles are loaded with 16-byte reads,
 // four in flight per thread.  The bias gradient db[co] = sum over voxels of
-// g[v][co] is summed in binary32 from the same loads.
+// g[v][co] is summed in binary32 from the same loads.  A bfloat16 input
+// (INBF: the hidden activations) is copied into the rows as it is.
 constexpr int kWgradSplitTc = 2;
 constexpr int kWgWarps = 16, kWgThreads = 32 * kWgWarps;   // two taps a warp
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const float* __restrict__ in,
+template <int CIN, int COUT, bool INBF>
+__global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __restrict__ in,
                                                                 const float* __restrict__ g, int n_grids,
                                                                 float* __restrict__ dW, float* __restrict__ db) {
   // a single channel takes channel 0 of rows that are zero elsewhere: one
@@ -533,7 +559,9 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const float* _
   // 16-byte loads (one value for a single channel), kLoadBatch of them in
   // flight before any is stored
   constexpr int kLoadBatch = 4;
-  constexpr int kHaloItems = HZ * HY * HX * (CIN == 1 ? 1 : HID / 4);
+  static_assert(!INBF || CIN == HID, "bfloat16 input rows hold all 32 channels");
+  constexpr int kInQ = INBF ? HID / 8 : HID / 4;            // 16-byte pieces of an input row
+  constexpr int kHaloItems = HZ * HY * HX * (CIN == 1 ? 1 : kInQ);
   constexpr int kTileItems = TZ * TY * TX * (COUT == 1 ? 1 : HID / 4);
   auto store4 = [](uint8_t* row, int c4, float4 v) {
     __nv_bfloat162 h[2] = {__floats2bfloat162_rn(v.x, v.y), __floats2bfloat162_rn(v.z, v.w)};
@@ -541,7 +569,7 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const float* _
   };
   auto store1 = [](uint8_t* row, float v) { *reinterpret_cast<__nv_bfloat16*>(row) = __float2bfloat16_rn(v); };
   for (int n = blockIdx.y; n < n_grids; n += kWgradSplitTc) {
-    const float* src = in + (size_t)n * NV * CIN;
+    const uint8_t* src = static_cast<const uint8_t*>(in) + (size_t)n * NV * CIN * (INBF ? 2 : 4);
     const float* gs = g + (size_t)n * NV * COUT;
     __syncthreads();
     for (int q0 = threadIdx.x; q0 < kHaloItems; q0 += kLoadBatch * kWgThreads) {
@@ -549,14 +577,15 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const float* _
 #pragma unroll
       for (int u = 0; u < kLoadBatch; ++u) {
         const int q = q0 + u * kWgThreads;
-        const int c4 = CIN == 1 ? 0 : q % (HID / 4), p = CIN == 1 ? q : q / (HID / 4);
+        const int c4 = CIN == 1 ? 0 : q % kInQ, p = CIN == 1 ? q : q / kInQ;
         const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
         const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
         v[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (q < kHaloItems && gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG) {
           const size_t vox = (size_t)(gz * EG + gy) * EG + gx;
-          if constexpr (CIN == 1) v[u].x = __ldg(src + vox);
-          else v[u] = __ldg(reinterpret_cast<const float4*>(src + vox * HID) + c4);
+          if constexpr (CIN == 1) v[u].x = __ldg(reinterpret_cast<const float*>(src) + vox);
+          else if constexpr (INBF) v[u] = __ldg(reinterpret_cast<const float4*>(src + vox * HID * 2) + c4);
+          else v[u] = __ldg(reinterpret_cast<const float4*>(src + vox * HID * 4) + c4);
         }
       }
 #pragma unroll
@@ -564,7 +593,8 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const float* _
         const int q = q0 + u * kWgThreads;
         if (q >= kHaloItems) continue;
         if constexpr (CIN == 1) store1(s_x + q * kRowB, v[u].x);
-        else store4(s_x + (q / (HID / 4)) * kRowB, q % (HID / 4), v[u]);
+        else if constexpr (INBF) *reinterpret_cast<float4*>(s_x + (q / kInQ) * kRowB + 16 * (q % kInQ)) = v[u];
+        else store4(s_x + (q / kInQ) * kRowB, q % kInQ, v[u]);
       }
     }
     for (int q0 = threadIdx.x; q0 < kTileItems; q0 += kLoadBatch * kWgThreads) {
@@ -756,7 +786,7 @@ struct ro_mc {
   // tensor-core rows of the layers: forward wf0..wf3, input gradient wd1..wd3
   // (layers 0 and 3 padded: one real input channel, one real output row)
   __nv_bfloat16 *wf0, *wf1, *wf2, *wf3, *wd1, *wd2, *wd3;
-  float *a1, *a2, *a3;                // hidden activations (after ReLU), n * NV * 32
+  __nv_bfloat16 *a1, *a2, *a3;        // hidden activations (after ReLU), n * NV * 32, bfloat16
   float *ga, *gb, *gc;                // hidden gradients, n * NV * 32
   float *g4, *y;                      // output gradient and output, n * NV
   float* loss;                        // scratch loss when the caller passes none
@@ -785,22 +815,22 @@ McLayout mc_layout(uint32_t nb) {
   McLayout L{};
   uint64_t o = 0;
   auto take = [&](uint64_t bytes) { const uint64_t at = o; o = mc_align(o + bytes); return at; };
-  const uint64_t pb = (uint64_t)RO_MC_PARAMS * 4, hid = (uint64_t)nb * NV * HID * 4, one = (uint64_t)nb * NV * 4;
+  const uint64_t pb = (uint64_t)RO_MC_PARAMS * 4, hid = (uint64_t)nb * NV * HID * 4, act = (uint64_t)nb * NV * HID * 2, one = (uint64_t)nb * NV * 4;
   L.P = take(pb); L.Pq = take(pb); L.M = take(pb); L.V = take(pb); L.G = take(pb); L.flag = take(4);
   L.wf0 = take(27ull * HID * HID * 2); L.wf1 = take(27ull * HID * HID * 2); L.wf2 = take(27ull * HID * HID * 2);
   L.wf3 = take(27ull * 16 * HID * 2);
   L.wd1 = take(27ull * HID * HID * 2); L.wd2 = take(27ull * HID * HID * 2); L.wd3 = take(27ull * HID * HID * 2);
   L.wend = o;
-  L.a1 = take(hid); L.a2 = take(hid); L.a3 = take(hid); L.ga = take(hid); L.gb = take(hid); L.gc = take(hid);
+  L.a1 = take(act); L.a2 = take(act); L.a3 = take(act); L.ga = take(hid); L.gb = take(hid); L.gc = take(hid);
   L.g4 = take(one); L.y = take(one); L.loss = take(4);
   L.total = o;
   return L;
 }
 
-template <int EPI, int CIN, int COUT>
-cudaError_t conv_tc(const float* in, const __nv_bfloat16* wb, const float* b, float* out, const float* aux, uint32_t n,
+template <int EPI, int CIN, int COUT, bool INBF>
+cudaError_t conv_tc(const void* in, const __nv_bfloat16* wb, const float* b, void* out, const void* aux, uint32_t n,
                     uint32_t* flag, cudaStream_t s) {
-  auto k = conv_tz_kernel<EPI, CIN, COUT>;
+  auto k = conv_tz_kernel<EPI, CIN, COUT, INBF>;
   constexpr size_t sm = TzShape<CIN, COUT>::SMEM;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -808,10 +838,10 @@ cudaError_t conv_tc(const float* in, const __nv_bfloat16* wb, const float* b, fl
   return cudaGetLastError();
 }
 
-template <int CIN, int COUT>
-cudaError_t wgrad_tc(const float* in, const float* g, uint32_t n, float* dW, float* db, cudaStream_t s) {
+template <int CIN, int COUT, bool INBF>
+cudaError_t wgrad_tc(const void* in, const float* g, uint32_t n, float* dW, float* db, cudaStream_t s) {
   constexpr size_t sm = wgrad_mma_smem();
-  auto k = wgrad_mma_kernel<CIN, COUT>;
+  auto k = wgrad_mma_kernel<CIN, COUT, INBF>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k<<<dim3(kTilesX * kTilesY * kTilesZ, kWgradSplitTc), kWgThreads, sm, s>>>(in, g, (int)n, dW, db);
@@ -825,10 +855,10 @@ ro_status mc_err(cudaError_t e) { return e == cudaSuccess ? RO_OK : RO_ERR_CUDA;
 cudaError_t mc_forward(ro_mc* m, uint32_t n, const float* x0, float* y) {
   cudaStream_t s = m->stream;
   const float* Pq = m->Pq;
-  cudaError_t e = conv_tc<kEpiRelu, 1, HID>(x0, m->wf0, Pq + kBOff[0], m->a1, nullptr, n, m->flag, s);
-  if (e == cudaSuccess) e = conv_tc<kEpiRelu, HID, HID>(m->a1, m->wf1, Pq + kBOff[1], m->a2, nullptr, n, m->flag, s);
-  if (e == cudaSuccess) e = conv_tc<kEpiRelu, HID, HID>(m->a2, m->wf2, Pq + kBOff[2], m->a3, nullptr, n, m->flag, s);
-  if (e == cudaSuccess) e = conv_tc<kEpiResidual, HID, 1>(m->a3, m->wf3, Pq + kBOff[3], y, x0, n, m->flag, s);
+  cudaError_t e = conv_tc<kEpiRelu, 1, HID, false>(x0, m->wf0, Pq + kBOff[0], m->a1, nullptr, n, m->flag, s);
+  if (e == cudaSuccess) e = conv_tc<kEpiRelu, HID, HID, true>(m->a1, m->wf1, Pq + kBOff[1], m->a2, nullptr, n, m->flag, s);
+  if (e == cudaSuccess) e = conv_tc<kEpiRelu, HID, HID, true>(m->a2, m->wf2, Pq + kBOff[2], m->a3, nullptr, n, m->flag, s);
+  if (e == cudaSuccess) e = conv_tc<kEpiResidual, HID, 1, true>(m->a3, m->wf3, Pq + kBOff[3], y, x0, n, m->flag, s);
   return e;
 }
 
@@ -856,18 +886,18 @@ cudaError_t mc_backward(ro_mc* m, uint32_t n, const float* x0, const float* targ
   };
   // layer 4 (32 -> 1)
   if (e == cudaSuccess) e = fork(0);
-  if (e == cudaSuccess) e = wgrad_tc<HID, 1>(m->a3, m->g4, n, G + kWOff[3], G + kBOff[3], s2);
-  if (e == cudaSuccess) e = conv_tc<kEpiMask, 1, HID>(m->g4, m->wd3, zero_bias, m->ga, m->a3, n, m->flag, s);
+  if (e == cudaSuccess) e = wgrad_tc<HID, 1, true>(m->a3, m->g4, n, G + kWOff[3], G + kBOff[3], s2);
+  if (e == cudaSuccess) e = conv_tc<kEpiMask, 1, HID, false>(m->g4, m->wd3, zero_bias, m->ga, m->a3, n, m->flag, s);
   // layer 3 (32 -> 32)
   if (e == cudaSuccess) e = fork(1);
-  if (e == cudaSuccess) e = wgrad_tc<HID, HID>(m->a2, m->ga, n, G + kWOff[2], G + kBOff[2], s2);
-  if (e == cudaSuccess) e = conv_tc<kEpiMask, HID, HID>(m->ga, m->wd2, zero_bias, m->gb, m->a2, n, m->flag, s);
+  if (e == cudaSuccess) e = wgrad_tc<HID, HID, true>(m->a2, m->ga, n, G + kWOff[2], G + kBOff[2], s2);
+  if (e == cudaSuccess) e = conv_tc<kEpiMask, HID, HID, false>(m->ga, m->wd2, zero_bias, m->gb, m->a2, n, m->flag, s);
   // layer 2 (32 -> 32)
   if (e == cudaSuccess) e = fork(3);
-  if (e == cudaSuccess) e = wgrad_tc<HID, HID>(m->a1, m->gb, n, G + kWOff[1], G + kBOff[1], s2);
-  if (e == cudaSuccess) e = conv_tc<kEpiMask, HID, HID>(m->gb, m->wd1, zero_bias, m->gc, m->a1, n, m->flag, s);
+  if (e == cudaSuccess) e = wgrad_tc<HID, HID, true>(m->a1, m->gb, n, G + kWOff[1], G + kBOff[1], s2);
+  if (e == cudaSuccess) e = conv_tc<kEpiMask, HID, HID, false>(m->gb, m->wd1, zero_bias, m->gc, m->a1, n, m->flag, s);
   // layer 1 (1 -> 32)
-  if (e == cudaSuccess) e = wgrad_tc<1, HID>(x0, m->gc, n, G + kWOff[0], G + kBOff[0], s);
+  if (e == cudaSuccess) e = wgrad_tc<1, HID, false>(x0, m->gc, n, G + kWOff[0], G + kBOff[0], s);
   if (e == cudaSuccess) e = cudaEventRecord(m->ev[4], s2);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->ev[4], 0);
   return e;
@@ -902,7 +932,7 @@ ro_status ro_mc_create(const ro_mc_desc* d, void* arena, uint64_t arena_bytes, v
   auto h = [&](uint64_t off) { return reinterpret_cast<__nv_bfloat16*>(b + off); };
   m->wf0 = h(L.wf0); m->wf1 = h(L.wf1); m->wf2 = h(L.wf2); m->wf3 = h(L.wf3);
   m->wd1 = h(L.wd1); m->wd2 = h(L.wd2); m->wd3 = h(L.wd3);
-  m->a1 = f(L.a1); m->a2 = f(L.a2); m->a3 = f(L.a3); m->ga = f(L.ga); m->gb = f(L.gb); m->gc = f(L.gc);
+  m->a1 = h(L.a1); m->a2 = h(L.a2); m->a3 = h(L.a3); m->ga = f(L.ga); m->gb = f(L.gb); m->gc = f(L.gc);
   m->g4 = f(L.g4); m->y = f(L.y); m->loss = f(L.loss);
   m->flag = reinterpret_cast<uint32_t*>(b + L.flag);
   cudaError_t e = cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking);
