@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 #include <new>
 #include <string>
@@ -140,12 +141,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 
 
 // The 32 -> 32 convolution on tcgen05.mma, with the three z taps folded
-// into N.  A block owns an 8 (x) by 16 (y) column of output voxels over
-// kTzChunk consecutive z slices and marches along z: the weights stay in
-// shared memory for the whole column, the input sits in a ring of four z
-// slices (rounded to bfloat16), and while the matrix instructions of input
-// slices s and s + 1 run, the block reads out output slice s - 2 and stores
-// input slice s + 3 of the halo.  An input slice s contributes to output slices s + 1, s and s - 1 through the
+// into N.  The output slices of all columns (grid, 128-voxel run of the
+// x-y plane, z) form one list, and a persistent block takes an equal
+// contiguous share of it (two blocks per SM), so that no wave of blocks
+// runs part-empty; within a column it marches along z: the weights stay in
+// shared memory for the block's whole share, the input sits in a ring of
+// four z slices (rounded to bfloat16), and while the matrix instructions
+// of input slices s and s + 1 run, the block reads out output slice s - 2
+// and stores input slice s + 3 of the halo.  A share that crosses into the
+// next column starts a new march there (two more halo slices).  An input slice s contributes to output slices s + 1, s and s - 1 through the
 // taps dz = 0, 1, 2 with the same input rows, so for each of the nine (dy,
 // dx) taps one tcgen05.mma of M = 128 voxels, N = 96 (the three dz taps'
 // 32 output channels side by side) and K = 16 reads the input tile once
@@ -165,13 +169,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 // slice as rows of 8 channels (16 bytes) in planes of one channel octet:
 // core matrices are 8 consecutive rows (128 bytes apart), and the tap
 // (dy, dx) moves the operand's start by (36 dy + dx) rows.
-constexpr int kTzChunk = 17;                                 // output z slices of a block
 constexpr int kTzThreads = 256;
 constexpr int kTzPadW = EG + 2;                              // 36: a halo row of the flattened plane
 constexpr int kTzMTiles = (EG * kTzPadW - 2 + 127) / 128;    // 128-row runs covering the outputs: 10
 constexpr int kTzRows = 128 + 2 * (kTzPadW + 1);             // input rows a run's taps reach: 202
-constexpr int kTzChunks = (EG + kTzChunk - 1) / kTzChunk;
-constexpr int kTzUnits = kTzMTiles * kTzChunks;              // blocks per grid
+constexpr int kTzMinShare = 4;                               // output slices a block takes at least
+constexpr int kTzBlocksPerSm = 2;                            // resident blocks of the convolution per SM
 constexpr int kTzPlane = kTzRows * 16;                       // one channel octet of a slice: 3,232 B (LBO)
 constexpr int kTzRing = 4;                                   // input slices in shared memory
 
@@ -287,10 +290,11 @@ __device__ __forceinline__ int tz_block(int zo) { return ((-zo - 1) % 8 + 8) % 8
 // hidden activations as bfloat16 (ReLU epilogue), else binary32; aux: the
 // activations (bfloat16) whose sign masks the gradient, or x0 (binary32)
 template <int EPI, int CIN, int COUT, bool INBF>
-__global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const void* __restrict__ in,
+__global__ void __launch_bounds__(kTzThreads, kTzBlocksPerSm) conv_tz_kernel(const void* __restrict__ in,
                                                                const __nv_bfloat16* __restrict__ wb,
                                                                const float* __restrict__ bias, void* __restrict__ out,
-                                                               const void* __restrict__ aux, uint32_t* __restrict__ err) {
+                                                               const void* __restrict__ aux, uint32_t n_grids,
+                                                               uint32_t* __restrict__ err) {
   using S = TzShape<CIN, COUT>;
   constexpr int CP = S::COUTP;
   extern __shared__ __align__(128) uint8_t smz[];
@@ -300,11 +304,10 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const void* __re
   __shared__ uint32_t s_tmem, s_fail;
   __shared__ float s_bias[HID];
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int unit = blockIdx.x, n = blockIdx.y;
-  const int f0 = (unit % kTzMTiles) * 128;                   // first input row; outputs from f0 + 37
-  const int z0 = (unit / kTzMTiles) * kTzChunk;
-  const int nz = min(kTzChunk, EG - z0);                     // output slices of this column
-  const void* src = static_cast<const uint8_t*>(in) + (size_t)n * NV * CIN * (INBF ? 2 : 4);
+  // this block's share of the output slices (column-major: z fastest)
+  const uint32_t total = n_grids * (uint32_t)(kTzMTiles * EG);
+  const uint32_t w_begin = (uint32_t)((uint64_t)blockIdx.x * total / gridDim.x);
+  const uint32_t w_end = (uint32_t)((uint64_t)(blockIdx.x + 1) * total / gridDim.x);
   // weights wb[tap][co][ci] (CP rows of 32 channels, 64 bytes, per tap): tap
   // (dz, dy, dx) goes to the B of (dy, dx), rows dz * CP + co, in the
   // canonical K-major layout; with one input channel only its first K step
@@ -322,24 +325,6 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const void* __re
       *reinterpret_cast<uint4*>(s_a + slot * S::SLICE + kTzPlane + 16 * r) = make_uint4(0u, 0u, 0u, 0u);
     }
   }
-  // input slices 0, 1 and 2 (z0 - 1 .. z0 + 1) into ring slots 0-2; slice 3
-  // into registers, stored in the first step
-  float4 pre[S::PER][2];
-  for (int li = 0; li < 3; ++li) {
-    tz_fetch<CIN, INBF>(src, f0, z0 - 1 + li, tid, pre);
-    tz_store<CIN, INBF>(s_a + li * S::SLICE, tid, pre);
-  }
-  tz_fetch<CIN, INBF>(src, f0, z0 + 2, tid, pre);
-  // this thread's accumulator row (warps 0-3): voxel (ex, ey) of each slice
-  // (halo columns and rows past the plane are not stored); am holds its mask
-  // row (input-gradient pass) or residual value, fetched a step ahead
-  const int fr = f0 + kTzPadW + 1 + tid;
-  const int ex = fr % kTzPadW - 1, ey = fr / kTzPadW - 1;
-  const bool erow = warp < 4 && ex >= 0 && ex < EG && ey < EG;
-  constexpr int kAux = EPI == kEpiMask ? COUT / 8 : 1;       // 8 bfloat16 mask values, or x0
-  uint4 am[kAux];
-#pragma unroll
-  for (int c8 = 0; c8 < kAux; ++c8) am[c8] = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
     for (int q = 0; q < 4; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&s_mbar[q])));
     s_fail = 0;
@@ -349,21 +334,17 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const void* __re
                  :: "r"(smem_u32(&s_tmem)), "n"(S::COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-  if (warp < 4) {                                            // every accumulator block starts at zero
-    for (int b = 0; b < 8; ++b) tz_zero<CP>(tmem + lane_base + (uint32_t)(CP * b));
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t a0 = smem_u32(s_a), b0 = smem_u32(s_b);
-  // the matrix instructions of input slice j (one thread), committed to s_mbar[j % 4]
+  constexpr int kAux = EPI == kEpiMask ? COUT / 8 : 1;       // 8 bfloat16 mask values, or x0
+  int jb = 0;        // input slices issued by the earlier marches: the barriers' phases run on
+  int issued = 0;    // input slices issued in all
+  // the matrix instructions of input slice j of the current march (one
+  // thread), committed to s_mbar[(jb + j) % 4]
   auto issue = [&](int j) {
     const int bb = tz_block(j);                              // block of output slice j (tap dz = 0)
     const uint32_t a_s = a0 + (uint32_t)((j % kTzRing) * S::SLICE);
@@ -386,105 +367,143 @@ __global__ void __launch_bounds__(kTzThreads, 2) conv_tz_kernel(const void* __re
       }
     }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                 :: "r"(smem_u32(&s_mbar[j & 3])) : "memory");
+                 :: "r"(smem_u32(&s_mbar[(jb + j) & 3])) : "memory");
   };
-  // input slice i + 1 is issued in step i, while slice i - 1 is awaited:
-  // at most three slices in flight, on three different barriers
-  if (tid == 128) issue(0);
-  int issued = 1;                                            // input slices whose instructions were issued
-  for (int i = 0; i <= nz + 2; ++i) {
-    if (i + 1 <= nz + 1 && tid == 128) issue(i + 1);
-    if (i + 1 <= nz + 1) issued = i + 2;
-    if (i >= 1) {
-      // input slice i - 1 done: output slice i - 3 is complete; read it out
-      // (warps 0-3: one accumulator row each), then zero its block
-      const int ip = i - 1, zo = i - 3;
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&s_mbar[ip & 3]), (uint32_t)((ip >> 2) & 1)));
-      if (!ok) {
-        atomicExch(err, 1u);
-        s_fail = 1;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (ok && warp < 4) {
-        const uint32_t taddr = tmem + lane_base + (uint32_t)(CP * tz_block(zo));
-        if (zo >= 0) {
-          uint32_t r[CP];
-          if constexpr (CP == 32)
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                           "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-                           "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-                           "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                         : "r"(taddr));
-          else
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                           "=r"(r[14]), "=r"(r[15])
-                         : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (erow) {
-            const size_t v = (size_t)n * NV + (size_t)((z0 + zo) * EG + ey) * EG + ex;
-            if constexpr (COUT == 1) {                       // y = x0 + f(x0): column 0, bias, residual
-              static_cast<float*>(out)[v] = __uint_as_float(r[0]) + s_bias[0] + __uint_as_float(am[0].x);
-            } else if constexpr (EPI == kEpiRelu) {          // the activation, stored as bfloat16
-              uint4* o8 = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out) + v * HID);
-#pragma unroll
-              for (int c8 = 0; c8 < HID / 8; ++c8) {
-                uint32_t h[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                  const float lo = fmaxf(__uint_as_float(r[8 * c8 + 2 * e]) + s_bias[8 * c8 + 2 * e], 0.0f);
-                  const float hi = fmaxf(__uint_as_float(r[8 * c8 + 2 * e + 1]) + s_bias[8 * c8 + 2 * e + 1], 0.0f);
-                  const __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
-                  h[e] = *reinterpret_cast<const uint32_t*>(&b2);
-                }
-                o8[c8] = make_uint4(h[0], h[1], h[2], h[3]);
-              }
-            } else {                                         // gradient where the activation is positive
-              float4* o4 = reinterpret_cast<float4*>(static_cast<float*>(out) + v * HID);
-#pragma unroll
-              for (int c4 = 0; c4 < HID / 4; ++c4) {
-                const uint32_t mw[2] = {(&am[c4 / 2].x)[2 * (c4 % 2)], (&am[c4 / 2].x)[2 * (c4 % 2) + 1]};
-                float o[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                  const uint32_t hbits = (mw[e / 2] >> (16 * (e % 2))) & 0xFFFFu;
-                  const float mk = __uint_as_float(hbits << 16);         // the bfloat16 value, exactly
-                  o[e] = mk > 0.0f ? __uint_as_float(r[4 * c4 + e]) : 0.0f;
-                }
-                o4[c4] = make_float4(o[0], o[1], o[2], o[3]);
-              }
-            }
-          }
-        }
-        tz_zero<CP>(taddr);
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-      }
+  for (uint32_t w = w_begin; w < w_end;) {
+    // a march: output slices z0 .. z0 + nz - 1 of column col (grid n, run f0)
+    const uint32_t col = w / EG;
+    const int z0 = (int)(w % EG);
+    const int nz = (int)min((uint32_t)(EG - z0), w_end - w);
+    w += (uint32_t)nz;
+    const int n = (int)(col / kTzMTiles);
+    const int f0 = (int)(col % kTzMTiles) * 128;             // first input row; outputs from f0 + 37
+    const void* src = static_cast<const uint8_t*>(in) + (size_t)n * NV * CIN * (INBF ? 2 : 4);
+    // input slices 0, 1 and 2 (z0 - 1 .. z0 + 1) into ring slots 0-2; slice 3
+    // into registers, stored in the first step (every instruction of the
+    // previous march has completed: its last slice was awaited)
+    float4 pre[S::PER][2];
+    for (int li = 0; li < 3; ++li) {
+      tz_fetch<CIN, INBF>(src, f0, z0 - 1 + li, tid, pre);
+      tz_store<CIN, INBF>(s_a + li * S::SLICE, tid, pre);
     }
-    // input slice i + 3 into the slot input slice i - 1 left (every
-    // instruction that read it has completed); fetch slice i + 4
-    if (i + 3 <= nz + 1) tz_store<CIN, INBF>(s_a + ((i + 3) % kTzRing) * S::SLICE, tid, pre);
-    if (i + 4 <= nz + 1) tz_fetch<CIN, INBF>(src, f0, z0 - 1 + i + 4, tid, pre);
-    if constexpr (EPI != kEpiRelu) {                         // mask rows / residual of output slice i - 2
-      const int zm = i - 2;
-      if (erow && zm >= 0 && zm < nz) {
-        const size_t v = (size_t)n * NV + (size_t)((z0 + zm) * EG + ey) * EG + ex;
-        if constexpr (EPI == kEpiMask) {
-          const uint4* a8 = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(aux) + v * COUT);
+    tz_fetch<CIN, INBF>(src, f0, z0 + 2, tid, pre);
+    // this thread's accumulator row (warps 0-3): voxel (ex, ey) of each slice
+    // (halo columns and rows past the plane are not stored); am holds its mask
+    // row (input-gradient pass) or residual value, fetched a step ahead
+    const int fr = f0 + kTzPadW + 1 + tid;
+    const int ex = fr % kTzPadW - 1, ey = fr / kTzPadW - 1;
+    const bool erow = warp < 4 && ex >= 0 && ex < EG && ey < EG;
+    uint4 am[kAux];
 #pragma unroll
-          for (int c8 = 0; c8 < kAux; ++c8) am[c8] = __ldg(a8 + c8);
-        } else {
-          am[0].x = __float_as_uint(__ldg(static_cast<const float*>(aux) + v));
-        }
-      }
+    for (int c8 = 0; c8 < kAux; ++c8) am[c8] = make_uint4(0u, 0u, 0u, 0u);
+    if (warp < 4) {                                          // every accumulator block starts at zero
+      for (int b = 0; b < 8; ++b) tz_zero<CP>(tmem + lane_base + (uint32_t)(CP * b));
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // input slice i + 1 is issued in step i, while slice i - 1 is awaited:
+    // at most three slices in flight, on three different barriers
+    if (tid == 128) issue(0);
+    issued = jb + 1;
+    for (int i = 0; i <= nz + 2; ++i) {
+      if (i + 1 <= nz + 1 && tid == 128) issue(i + 1);
+      if (i + 1 <= nz + 1) issued = jb + i + 2;
+      if (i >= 1) {
+        // input slice i - 1 done: output slice i - 3 is complete; read it out
+        // (warps 0-3: one accumulator row each), then zero its block
+        const int ip = i - 1, zo = i - 3, ipg = jb + ip;
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&s_mbar[ipg & 3]), (uint32_t)((ipg >> 2) & 1)));
+        if (!ok) {
+          atomicExch(err, 1u);
+          s_fail = 1;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok && warp < 4) {
+          const uint32_t taddr = tmem + lane_base + (uint32_t)(CP * tz_block(zo));
+          if (zo >= 0) {
+            uint32_t r[CP];
+            if constexpr (CP == 32)
+              asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                           "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                           : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                             "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                             "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                             "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                             "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                           : "r"(taddr));
+            else
+              asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                           : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                             "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                             "=r"(r[14]), "=r"(r[15])
+                           : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (erow) {
+              const size_t v = (size_t)n * NV + (size_t)((z0 + zo) * EG + ey) * EG + ex;
+              if constexpr (COUT == 1) {                       // y = x0 + f(x0): column 0, bias, residual
+                static_cast<float*>(out)[v] = __uint_as_float(r[0]) + s_bias[0] + __uint_as_float(am[0].x);
+              } else if constexpr (EPI == kEpiRelu) {          // the activation, stored as bfloat16
+                uint4* o8 = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out) + v * HID);
+#pragma unroll
+                for (int c8 = 0; c8 < HID / 8; ++c8) {
+                  uint32_t h[4];
+#pragma unroll
+                  for (int e = 0; e < 4; ++e) {
+                    const float lo = fmaxf(__uint_as_float(r[8 * c8 + 2 * e]) + s_bias[8 * c8 + 2 * e], 0.0f);
+                    const float hi = fmaxf(__uint_as_float(r[8 * c8 + 2 * e + 1]) + s_bias[8 * c8 + 2 * e + 1], 0.0f);
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
+                    h[e] = *reinterpret_cast<const uint32_t*>(&b2);
+                  }
+                  o8[c8] = make_uint4(h[0], h[1], h[2], h[3]);
+                }
+              } else {                                         // gradient where the activation is positive
+                float4* o4 = reinterpret_cast<float4*>(static_cast<float*>(out) + v * HID);
+#pragma unroll
+                for (int c4 = 0; c4 < HID / 4; ++c4) {
+                  const uint32_t mw[2] = {(&am[c4 / 2].x)[2 * (c4 % 2)], (&am[c4 / 2].x)[2 * (c4 % 2) + 1]};
+                  float o[4];
+#pragma unroll
+                  for (int e = 0; e < 4; ++e) {
+                    const uint32_t hbits = (mw[e / 2] >> (16 * (e % 2))) & 0xFFFFu;
+                    const float mk = __uint_as_float(hbits << 16);         // the bfloat16 value, exactly
+                    o[e] = mk > 0.0f ? __uint_as_float(r[4 * c4 + e]) : 0.0f;
+                  }
+                  o4[c4] = make_float4(o[0], o[1], o[2], o[3]);
+                }
+              }
+            }
+          }
+          tz_zero<CP>(taddr);
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+      }
+      // input slice i + 3 into the slot input slice i - 1 left (every
+      // instruction that read it has completed); fetch slice i + 4
+      if (i + 3 <= nz + 1) tz_store<CIN, INBF>(s_a + ((i + 3) % kTzRing) * S::SLICE, tid, pre);
+      if (i + 4 <= nz + 1) tz_fetch<CIN, INBF>(src, f0, z0 - 1 + i + 4, tid, pre);
+      if constexpr (EPI != kEpiRelu) {                         // mask rows / residual of output slice i - 2
+        const int zm = i - 2;
+        if (erow && zm >= 0 && zm < nz) {
+          const size_t v = (size_t)n * NV + (size_t)((z0 + zm) * EG + ey) * EG + ex;
+          if constexpr (EPI == kEpiMask) {
+            const uint4* a8 = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(aux) + v * COUT);
+#pragma unroll
+            for (int c8 = 0; c8 < kAux; ++c8) am[c8] = __ldg(a8 + c8);
+          } else {
+            am[0].x = __float_as_uint(__ldg(static_cast<const float*>(aux) + v));
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (s_fail) break;
+    }
+    jb += nz + 2;
     if (s_fail) break;
   }
   if (s_fail && issued > 0) {
@@ -834,7 +853,19 @@ cudaError_t conv_tc(const void* in, const __nv_bfloat16* wb, const float* b, voi
   constexpr size_t sm = TzShape<CIN, COUT>::SMEM;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k<<<dim3(kTzUnits, n), kTzThreads, sm, s>>>(in, wb, b, out, aux, flag);
+  // persistent: two blocks per SM (the shared memory and tensor memory of
+  // a block are sized for two; the carveout gives the SM's shared memory to
+  // them), each at least kTzMinShare output slices.  Blocks never wait for
+  // one another, so a block that finds no room simply starts later.
+  e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const uint32_t total = n * (uint32_t)(kTzMTiles * EG);
+  const uint32_t blocks = std::min((uint32_t)(kTzBlocksPerSm * sms), (total + kTzMinShare - 1) / kTzMinShare);
+  k<<<blocks, kTzThreads, sm, s>>>(in, wb, b, out, aux, n, flag);
   return cudaGetLastError();
 }
 
