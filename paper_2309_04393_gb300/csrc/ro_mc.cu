@@ -158,9 +158,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 // The accumulators are a ring of eight 32-column blocks of tensor memory:
 // output slice zo (relative to the block's first) lives in block
 // (-zo - 1) mod 8, so slices zo, zo - 1, zo - 2 are consecutive columns; at
-// the ring's end the instruction is split in two.  A block is zeroed once
-// its slice has been read out (its last contribution came from input slice
-// zo + 2), five input slices before it is used again.  The x-y plane is
+// the ring's end the instruction is split in two.  The first product
+// of an output slice (input slice zo, tap (0, 0, 0), first K step)
+// overwrites its block, so a block needs no zeroing after its slice has
+// been read out.  The x-y plane is
 // flattened with its one-voxel halo, 36 voxels a row (voxel (x, y) at
 // f = (y + 1) 36 + x + 1), and a block's 128 accumulator rows are a run of
 // 128 consecutive f (ten runs cover the 34 x 34 outputs; rows that fall on
@@ -214,11 +215,11 @@ __device__ __forceinline__ uint32_t tz_idesc(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
-// D += A B (the accumulator blocks start at zero)
-__device__ __forceinline__ void tz_mma(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t idesc) {
-  asm volatile("{\n .reg .pred p;\n setp.eq.u32 p, 1, 1;\n"
+// D = A B (acc == 0) or D += A B
+__device__ __forceinline__ void tz_mma(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc = 1u) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-               :: "r"(d_tmem), "l"(da), "l"(db), "r"(idesc));
+               :: "r"(d_tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
 // this thread's pieces of input slice gz, flattened rows f0 .. f0 + 201
@@ -270,18 +271,6 @@ __device__ __forceinline__ void tz_store(uint8_t* slot, int tid, const float4 (&
       *reinterpret_cast<uint4*>(slot + q * kTzPlane + l * 16) = *reinterpret_cast<const uint4*>(h);
     }
   }
-}
-
-// NC columns of zeros into this warp's 32 lanes of tensor memory
-template <int NC>
-__device__ __forceinline__ void tz_zero(uint32_t taddr) {
-  const uint32_t z = 0u;
-  if constexpr (NC == 32)
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
-                 "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" :: "r"(taddr), "r"(z) : "memory");
-  else
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};"
-                 :: "r"(taddr), "r"(z) : "memory");
 }
 
 __device__ __forceinline__ int tz_block(int zo) { return ((-zo - 1) % 8 + 8) % 8; }
@@ -355,7 +344,19 @@ __global__ void __launch_bounds__(kTzThreads, kTzBlocksPerSm) conv_tz_kernel(con
         const uint64_t da = umma_desc_kmajor(a_s + (uint32_t)(2 * ks * kTzPlane + (dy * kTzPadW + dx) * 16),
                                              kTzPlane, 128);
         const uint32_t bt = b0 + (uint32_t)(c * S::BTAP + ks * S::BKS);
-        if (bb <= 5) {
+        if (c == 0 && ks == 0) {
+          // output slice j's first product overwrites its block (whatever
+          // it held: the slice read out eight slices before, or nothing);
+          // the dz = 1, 2 columns add to output slices j - 1 and j - 2
+          const uint64_t db1 = umma_desc_kmajor(bt + (CP / 8) * 256, 128, 256);
+          tz_mma(tmem + (uint32_t)(CP * bb), da, umma_desc_kmajor(bt, 128, 256), tz_idesc(CP), 0u);
+          if (bb == 6) {                                     // blocks 7 | 0
+            tz_mma(tmem + (uint32_t)(7 * CP), da, db1, tz_idesc(CP));
+            tz_mma(tmem, da, umma_desc_kmajor(bt + (2 * CP / 8) * 256, 128, 256), tz_idesc(CP));
+          } else {                                           // blocks bb + 1, bb + 2 (mod 8), adjacent
+            tz_mma(tmem + (uint32_t)(CP * ((bb + 1) & 7)), da, db1, tz_idesc(2 * CP));
+          }
+        } else if (bb <= 5) {
           tz_mma(tmem + (uint32_t)(CP * bb), da, umma_desc_kmajor(bt, 128, 256), tz_idesc(3 * CP));
         } else if (bb == 6) {                                // blocks 6, 7 | 0
           tz_mma(tmem + (uint32_t)(6 * CP), da, umma_desc_kmajor(bt, 128, 256), tz_idesc(2 * CP));
@@ -396,10 +397,6 @@ __global__ void __launch_bounds__(kTzThreads, kTzBlocksPerSm) conv_tz_kernel(con
     uint4 am[kAux];
 #pragma unroll
     for (int c8 = 0; c8 < kAux; ++c8) am[c8] = make_uint4(0u, 0u, 0u, 0u);
-    if (warp < 4) {                                          // every accumulator block starts at zero
-      for (int b = 0; b < 8; ++b) tz_zero<CP>(tmem + lane_base + (uint32_t)(CP * b));
-      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -413,7 +410,7 @@ __global__ void __launch_bounds__(kTzThreads, kTzBlocksPerSm) conv_tz_kernel(con
       if (i + 1 <= nz + 1) issued = jb + i + 2;
       if (i >= 1) {
         // input slice i - 1 done: output slice i - 3 is complete; read it out
-        // (warps 0-3: one accumulator row each), then zero its block
+        // (warps 0-3: one accumulator row each)
         const int ip = i - 1, zo = i - 3, ipg = jb + ip;
         const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&s_mbar[ipg & 3]), (uint32_t)((ipg >> 2) & 1)));
         if (!ok) {
@@ -476,8 +473,6 @@ __global__ void __launch_bounds__(kTzThreads, kTzBlocksPerSm) conv_tz_kernel(con
               }
             }
           }
-          tz_zero<CP>(taddr);
-          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         }
       }
       // input slice i + 3 into the slot input slice i - 1 left (every
