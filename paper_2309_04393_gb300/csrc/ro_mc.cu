@@ -195,8 +195,6 @@ struct TzShape {
   static constexpr int BTAP = KS * BKS;
   static constexpr int BBYTES = 9 * BTAP;
   static constexpr int COLS = 8 * COUTP;                     // tensor-memory columns: 8 blocks
-  static constexpr int ITEMS = kTzRows * (CIN == 1 ? 1 : 4);       // pieces of an input slice
-  static constexpr int PER = (ITEMS + kTzThreads - 1) / kTzThreads;
   // shared memory; at least 76 KB when a block holds 256 columns of tensor
   // memory, so that no third block (which could not allocate) is resident
   static constexpr size_t SMEM_USED = (size_t)BBYTES + (size_t)kTzRing * SLICE;
@@ -226,19 +224,23 @@ __device__ __forceinline__ void tz_mma(uint32_t d_tmem, uint64_t da, uint64_t db
 // (zeros outside the grid): 8 channels (32 bytes) each for 32 channels, one
 // value for one channel
 // (INBF: the input is stored as bfloat16 values, 16 bytes per 8 channels,
-// kept as they are)
-template <int CIN, bool INBF>
+// kept as they are); the slice is shared by NT threads, tid < NT
+template <int CIN>
+__host__ __device__ constexpr int tz_items() { return kTzRows * (CIN == 1 ? 1 : 4); }   // pieces of an input slice
+template <int CIN, int NT>
+__host__ __device__ constexpr int tz_per() { return (tz_items<CIN>() + NT - 1) / NT; }
+template <int CIN, bool INBF, int NT>
 __device__ __forceinline__ void tz_fetch(const void* __restrict__ src_v, int f0, int gz, int tid,
-                                         float4 (&v)[TzShape<CIN, 32>::PER][2]) {
+                                         float4 (&v)[tz_per<CIN, NT>()][2]) {
   using S = TzShape<CIN, 32>;
 #pragma unroll
-  for (int j = 0; j < S::PER; ++j) {
-    const int w = tid + j * kTzThreads;
+  for (int j = 0; j < tz_per<CIN, NT>(); ++j) {
+    const int w = tid + j * NT;
     v[j][0] = v[j][1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     const int q = CIN == 1 ? 0 : w % 4, l = CIN == 1 ? w : w / 4;
     const int f = f0 + l;
     const int gx = f % kTzPadW - 1, gy = f / kTzPadW - 1;
-    if (w < S::ITEMS && gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG) {
+    if (w < tz_items<CIN>() && gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG) {
       const size_t vox = (size_t)(gz * EG + gy) * EG + gx;
       if constexpr (CIN == 1) {
         v[j][0].x = __ldg(static_cast<const float*>(src_v) + vox);
@@ -255,13 +257,13 @@ __device__ __forceinline__ void tz_fetch(const void* __restrict__ src_v, int f0,
 
 // ... rounded to bfloat16, into the octet planes of a ring slot (one
 // channel: the value and seven zeros in plane 0)
-template <int CIN, bool INBF>
-__device__ __forceinline__ void tz_store(uint8_t* slot, int tid, const float4 (&v)[TzShape<CIN, 32>::PER][2]) {
+template <int CIN, bool INBF, int NT>
+__device__ __forceinline__ void tz_store(uint8_t* slot, int tid, const float4 (&v)[tz_per<CIN, NT>()][2]) {
   using S = TzShape<CIN, 32>;
 #pragma unroll
-  for (int j = 0; j < S::PER; ++j) {
-    const int w = tid + j * kTzThreads;
-    if (w >= S::ITEMS) continue;
+  for (int j = 0; j < tz_per<CIN, NT>(); ++j) {
+    const int w = tid + j * NT;
+    if (w >= tz_items<CIN>()) continue;
     const int q = CIN == 1 ? 0 : w % 4, l = CIN == 1 ? w : w / 4;
     if constexpr (INBF) {
       *reinterpret_cast<float4*>(slot + q * kTzPlane + l * 16) = v[j][0];
@@ -271,6 +273,24 @@ __device__ __forceinline__ void tz_store(uint8_t* slot, int tid, const float4 (&
       *reinterpret_cast<uint4*>(slot + q * kTzPlane + l * 16) = *reinterpret_cast<const uint4*>(h);
     }
   }
+}
+
+// the 32-channel bfloat16 input slice gz, flattened rows f0 .. f0 + 201,
+// copied into the octet planes of a ring slot without passing through
+// registers (16-byte cp.async; pieces outside the grid are filled with
+// zeros: source size 0), committed as one group
+__device__ __forceinline__ void tz_copy_async(uint8_t* slot, const void* __restrict__ src_v, int f0, int gz, int tid) {
+  const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(src_v);
+  for (int w = tid; w < tz_items<HID>(); w += kTzThreads) {
+    const int q = w % 4, l = w / 4;
+    const int f = f0 + l;
+    const int gx = f % kTzPadW - 1, gy = f / kTzPadW - 1;
+    const bool in = gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG;
+    const __nv_bfloat16* g = in ? src + ((size_t)(gz * EG + gy) * EG + gx) * HID + 8 * q : src;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                 :: "r"(smem_u32(slot + q * kTzPlane + l * 16)), "l"(g), "r"(in ? 16 : 0) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 __device__ __forceinline__ int tz_block(int zo) { return ((-zo - 1) % 8 + 8) % 8; }
@@ -330,6 +350,8 @@ __global__ void __launch_bounds__(kTzThreads, kTzBlocksPerSm) conv_tz_kernel(con
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   const uint32_t a0 = smem_u32(s_a), b0 = smem_u32(s_b);
   constexpr int kAux = EPI == kEpiMask ? COUT / 8 : 1;       // 8 bfloat16 mask values, or x0
+  constexpr int kLd = kTzThreads;                          // threads staging an input slice
+  const int issuer = 128;                                    // the thread issuing the matrix instructions
   int jb = 0;        // input slices issued by the earlier marches: the barriers' phases run on
   int issued = 0;    // input slices issued in all
   // the matrix instructions of input slice j of the current march (one
@@ -382,12 +404,19 @@ __global__ void __launch_bounds__(kTzThreads, kTzBlocksPerSm) conv_tz_kernel(con
     // input slices 0, 1 and 2 (z0 - 1 .. z0 + 1) into ring slots 0-2; slice 3
     // into registers, stored in the first step (every instruction of the
     // previous march has completed: its last slice was awaited)
-    float4 pre[S::PER][2];
-    for (int li = 0; li < 3; ++li) {
-      tz_fetch<CIN, INBF>(src, f0, z0 - 1 + li, tid, pre);
-      tz_store<CIN, INBF>(s_a + li * S::SLICE, tid, pre);
+    // (bfloat16 input: slices 0-2 copied asynchronously, and slice i + 3
+    // in step i, each its own group of copies)
+    float4 pre[INBF ? 1 : tz_per<CIN, kLd>()][2];
+    if constexpr (INBF) {
+      for (int li = 0; li < 3; ++li) tz_copy_async(s_a + li * S::SLICE, src, f0, z0 - 1 + li, tid);
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    } else {
+      for (int li = 0; li < 3; ++li) {
+        tz_fetch<CIN, INBF, kLd>(src, f0, z0 - 1 + li, tid, pre);
+        tz_store<CIN, INBF, kLd>(s_a + li * S::SLICE, tid, pre);
+      }
+      tz_fetch<CIN, INBF, kLd>(src, f0, z0 + 2, tid, pre);
     }
-    tz_fetch<CIN, INBF>(src, f0, z0 + 2, tid, pre);
     // this thread's accumulator row (warps 0-3): voxel (ex, ey) of each slice
     // (halo columns and rows past the plane are not stored); am holds its mask
     // row (input-gradient pass) or residual value, fetched a step ahead
@@ -403,10 +432,10 @@ __global__ void __launch_bounds__(kTzThreads, kTzBlocksPerSm) conv_tz_kernel(con
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // input slice i + 1 is issued in step i, while slice i - 1 is awaited:
     // at most three slices in flight, on three different barriers
-    if (tid == 128) issue(0);
+    if (tid == issuer) issue(0);
     issued = jb + 1;
     for (int i = 0; i <= nz + 2; ++i) {
-      if (i + 1 <= nz + 1 && tid == 128) issue(i + 1);
+      if (i + 1 <= nz + 1 && tid == issuer) issue(i + 1);
       if (i + 1 <= nz + 1) issued = jb + i + 2;
       if (i >= 1) {
         // input slice i - 1 done: output slice i - 3 is complete; read it out
@@ -477,8 +506,17 @@ __global__ void __launch_bounds__(kTzThreads, kTzBlocksPerSm) conv_tz_kernel(con
       }
       // input slice i + 3 into the slot input slice i - 1 left (every
       // instruction that read it has completed); fetch slice i + 4
-      if (i + 3 <= nz + 1) tz_store<CIN, INBF>(s_a + ((i + 3) % kTzRing) * S::SLICE, tid, pre);
-      if (i + 4 <= nz + 1) tz_fetch<CIN, INBF>(src, f0, z0 - 1 + i + 4, tid, pre);
+      if constexpr (INBF) {
+        // slice i + 3 copied into that slot (a group, empty past the
+        // march's end); slice i + 2, needed by the next step's
+        // instructions, has arrived once at most one group is pending
+        if (i + 3 <= nz + 1) tz_copy_async(s_a + ((i + 3) % kTzRing) * S::SLICE, src, f0, z0 - 1 + i + 3, tid);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      } else {
+        if (i + 3 <= nz + 1) tz_store<CIN, INBF, kLd>(s_a + ((i + 3) % kTzRing) * S::SLICE, tid, pre);
+        if (i + 4 <= nz + 1) tz_fetch<CIN, INBF, kLd>(src, f0, z0 - 1 + i + 4, tid, pre);
+      }
       if constexpr (EPI != kEpiRelu) {                         // mask rows / residual of output slice i - 2
         const int zm = i - 2;
         if (erow && zm >= 0 && zm < nz) {
@@ -498,6 +536,7 @@ __global__ void __launch_bounds__(kTzThreads, kTzBlocksPerSm) conv_tz_kernel(con
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (s_fail) break;
     }
+    if constexpr (INBF) asm volatile("cp.async.wait_group 0;" ::: "memory");
     jb += nz + 2;
     if (s_fail) break;
   }
