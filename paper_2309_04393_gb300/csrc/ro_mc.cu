@@ -570,12 +570,13 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t&
 // tile (halo) and the gradient tile enter shared memory as bfloat16 rows,
 // and ldmatrix.trans turns the voxel rows into the K dimension of both
 // operands.  Warp w of 16 accumulates taps w and w + 16 and adds its sums
-// once (atomically) at the end.  The tiles are loaded with 16-byte reads,
-// four in flight per thread.  The bias gradient db[co] = sum over voxels of
-// g[v][co] is summed in binary32 from the same loads.  A bfloat16 input
-// (INBF: the hidden activations) is copied into the rows as it is; with it
-// the 32 -> 32 kernel keeps two buffers and copies the next grid's tiles
-// with cp.async while the products of this grid run.
+// once (atomically) at the end.  The block keeps two buffers and copies
+// the tiles of its next grid with cp.async while the products of this grid
+// run: a bfloat16 input (INBF: the hidden activations) straight into its
+// rows, a binary32 input (the one-channel grid) and the binary32 gradient
+// tile into staging areas that are rounded into the rows at the start of
+// their step.  The bias gradient db[co] = sum over voxels of g[v][co] is
+// summed in binary32 from the staging area.
 constexpr int kWgradSplitTc = 2;
 constexpr int kWgWarps = 16, kWgThreads = 32 * kWgWarps;   // two taps a warp
 template <int CIN, int COUT, bool INBF>
@@ -585,10 +586,7 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
   // a single channel takes channel 0 of rows that are zero elsewhere: one
   // 16-channel m tile (input) or one 8-channel n tile (gradient)
   constexpr int MT = CIN == 1 ? 1 : 2, NT = COUT == 1 ? 1 : 4;
-  constexpr bool PIPE = INBF && CIN == HID && COUT == HID;     // double-buffered, copied with cp.async
   extern __shared__ __align__(16) uint8_t smb[];
-  uint8_t* s_x = smb;                                       // HZ * HY * HX rows (input, halo)
-  uint8_t* s_g = smb + HZ * HY * HX * kRowB;                // TZ * TY * TX rows (gradient)
   const int tile = blockIdx.x;
   const int x0t = (tile % kTilesX) * TX, y0t = ((tile / kTilesX) % kTilesY) * TY, z0t = (tile / (kTilesX * kTilesY)) * TZ;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -604,66 +602,83 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
       for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[j][mt][nt][q] = 0.0f;
-  const uint32_t x_base = smem_u32(s_x), g_base = smem_u32(s_g);
+  // two buffers of rows; binary32 staging areas for the gradient tile and
+  // the one-channel input
+  static_assert(INBF ? CIN == HID : CIN == 1, "the input is the bfloat16 activations or the one-channel grid");
+  constexpr int kXB = HZ * HY * HX * kRowB, kGB = TZ * TY * TX * kRowB;
+  float* s_f = reinterpret_cast<float*>(smb + 2 * (kXB + kGB));      // TZ * TY * TX voxels x COUT
+  float* s_h = s_f + TZ * TY * TX * COUT;                            // HZ * HY * HX voxels (one channel)
   if constexpr (CIN == 1 || COUT == 1) {                    // the rows' other channels stay zero
-    for (int q = threadIdx.x; q < (HZ * HY * HX + TZ * TY * TX) * kRowB / 16; q += kWgThreads)
+    for (int q = threadIdx.x; q < 2 * (kXB + kGB) / 16; q += kWgThreads)
       reinterpret_cast<uint4*>(smb)[q] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
   }
   // kWgThreads is a multiple of HID / 4: a thread's four channels are fixed
   static_assert(kWgThreads % (HID / 4) == 0, "channel quad per thread");
   float4 bsum = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  // 16-byte loads (one value for a single channel), kLoadBatch of them in
-  // flight before any is stored
-  constexpr int kLoadBatch = 4;
-  static_assert(!INBF || CIN == HID, "bfloat16 input rows hold all 32 channels");
-  constexpr int kInQ = INBF ? HID / 8 : HID / 4;            // 16-byte pieces of an input row
-  constexpr int kHaloItems = HZ * HY * HX * (CIN == 1 ? 1 : kInQ);
-  constexpr int kTileItems = TZ * TY * TX * (COUT == 1 ? 1 : HID / 4);
   auto store4 = [](uint8_t* row, int c4, float4 v) {
     __nv_bfloat162 h[2] = {__floats2bfloat162_rn(v.x, v.y), __floats2bfloat162_rn(v.z, v.w)};
     *reinterpret_cast<uint2*>(row + 8 * c4) = *reinterpret_cast<const uint2*>(h);
   };
   auto store1 = [](uint8_t* row, float v) { *reinterpret_cast<__nv_bfloat16*>(row) = __float2bfloat16_rn(v); };
-  // the products of one grid's tiles: warp w, taps w and w + 16
+  // the products of one grid's tiles: warp w, taps w and w + 16; with a
+  // single channel on either side the two taps share the B fragments of
+  // each group of 16 voxels (for the 32 -> 32 layers a warp runs its taps
+  // one after the other: measured faster there)
   auto compute = [&](uint32_t xb, uint32_t gb) {
+    auto tap_pos = [](int t) { return ((t / 9) * HY + (t / 3) % 3) * HX + t % 3; };
+    auto load_b = [&](int kc, uint32_t (&b)[4][2]) {
+      // B (voxels x output channels): voxel row r + 8 (i & 1), channels 8 (i >> 1) + 16 nj
+      const int pb = 16 * kc + mr + 8 * (mi & 1);
 #pragma unroll
-    for (int j = 0; j < kTapsPerWarp; ++j) {
-      const int t = warp + kWgWarps * j;
-      if (t >= 27) break;
-      const int toff = ((t / 9) * HY + (t / 3) % 3) * HX + t % 3;
+      for (int nj = 0; nj < (NT + 1) / 2; ++nj)
+        ldsm_x4_t(gb + pb * kRowB + 16 * (mi >> 1) + 32 * nj, b[2 * nj][0], b[2 * nj][1], b[2 * nj + 1][0],
+                  b[2 * nj + 1][1]);
+    };
+    auto tap_kc = [&](int j, int t, int kc, const uint32_t (&b)[4][2]) {
+      // A (input channels x voxels): voxel row r + 8 (i >> 1), channels 8 (i & 1) (+16 per m tile)
+      const int pa = 16 * kc + mr + 8 * (mi >> 1);
+      const int pos = ((pa / (TX * TY)) * HY + (pa / TX) % TY) * HX + pa % TX + tap_pos(t);
+      uint32_t a[MT][4];
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt)
+        ldsm_x4_t(xb + pos * kRowB + 16 * (mi & 1) + 32 * mt, a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+          mma_bf16(acc[j][mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b[nt][0], b[nt][1]);
+    };
+    if constexpr (CIN == HID && COUT == HID) {
+#pragma unroll
+      for (int j = 0; j < kTapsPerWarp; ++j) {
+        const int t = warp + kWgWarps * j;
+        if (t >= 27) break;
+        for (int kc = 0; kc < (TZ * TY * TX) / 16; ++kc) {
+          uint32_t b[4][2];
+          load_b(kc, b);
+          tap_kc(j, t, kc, b);
+        }
+      }
+    } else {
       for (int kc = 0; kc < (TZ * TY * TX) / 16; ++kc) {
-        // A (input channels x voxels): voxel row r + 8 (i >> 1), channels 8 (i & 1) (+16 per m tile)
-        const int pa = 16 * kc + mr + 8 * (mi >> 1);
-        const int pos = ((pa / (TX * TY)) * HY + (pa / TX) % TY) * HX + pa % TX + toff;
-        uint32_t a[MT][4], b[4][2];
+        uint32_t b[4][2];
+        load_b(kc, b);
 #pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-          ldsm_x4_t(xb + pos * kRowB + 16 * (mi & 1) + 32 * mt, a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
-        // B (voxels x output channels): voxel row r + 8 (i & 1), channels 8 (i >> 1) + 16 nj
-        const int pb = 16 * kc + mr + 8 * (mi & 1);
-#pragma unroll
-        for (int nj = 0; nj < (NT + 1) / 2; ++nj)
-          ldsm_x4_t(gb + pb * kRowB + 16 * (mi >> 1) + 32 * nj, b[2 * nj][0], b[2 * nj][1], b[2 * nj + 1][0],
-                    b[2 * nj + 1][1]);
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-          for (int nt = 0; nt < NT; ++nt)
-            mma_bf16(acc[j][mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b[nt][0], b[nt][1]);
+        for (int j = 0; j < kTapsPerWarp; ++j) {
+          const int t = warp + kWgWarps * j;
+          if (t < 27) tap_kc(j, t, kc, b);                   // warp-uniform
+        }
       }
     }
   };
-  if constexpr (PIPE) {
-    // two buffers: the tiles of the block's next grid are copied while this
-    // grid's products run; the binary32 gradient tile lands in a staging
-    // area and is rounded into its rows (and summed for the bias gradient)
-    // at the start of its step
-    constexpr int kXB = HZ * HY * HX * kRowB, kGB = TZ * TY * TX * kRowB;
-    float* s_f = reinterpret_cast<float*>(smb + 2 * (kXB + kGB));      // TZ * TY * TX rows of 32 floats
-    auto copy = [&](int n, int buf) {
+  // grid n's tiles into buffer buf with cp.async, one group: the bfloat16
+  // input straight into its rows, the binary32 input and gradient into
+  // their staging areas (zero-filled outside the grid: source size 0)
+  auto copy = [&](int n, int buf) {
+    uint8_t* sx = smb + buf * (kXB + kGB);
+    if constexpr (INBF) {
       const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(in) + (size_t)n * NV * HID;
-      const float* gs = g + (size_t)n * NV * HID;
-      uint8_t* sx = smb + buf * (kXB + kGB);
       for (int q = threadIdx.x; q < HZ * HY * HX * (HID / 8); q += kWgThreads) {
         const int c8 = q % (HID / 8), p = q / (HID / 8);
         const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
@@ -673,22 +688,49 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
                      :: "r"(smem_u32(sx + p * kRowB + 16 * c8)), "l"(sp), "r"(ok ? 16 : 0) : "memory");
       }
-      for (int q = threadIdx.x; q < TZ * TY * TX * (HID / 4); q += kWgThreads) {
-        const int c4 = q % (HID / 4), p = q / (HID / 4);
-        const int gx = x0t + p % TX, gy = y0t + (p / TX) % TY, gz = z0t + p / (TX * TY);
-        const bool ok = gx < EG && gy < EG && gz < EG;        // voxels outside the grid add nothing
-        const float* sp = ok ? gs + ((size_t)(gz * EG + gy) * EG + gx) * HID + 4 * c4 : gs;
+    } else {
+      const float* src = static_cast<const float*>(in) + (size_t)n * NV;
+      for (int p = threadIdx.x; p < HZ * HY * HX; p += kWgThreads) {
+        const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
+        const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
+        const bool ok = gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG;
+        const float* sp = ok ? src + (size_t)(gz * EG + gy) * EG + gx : src;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
+                     :: "r"(smem_u32(s_h + p)), "l"(sp), "r"(ok ? 4 : 0) : "memory");
+      }
+    }
+    const float* gs = g + (size_t)n * NV * COUT;
+    for (int q = threadIdx.x; q < TZ * TY * TX * (COUT == 1 ? 1 : HID / 4); q += kWgThreads) {
+      const int c4 = COUT == 1 ? 0 : q % (HID / 4), p = COUT == 1 ? q : q / (HID / 4);
+      const int gx = x0t + p % TX, gy = y0t + (p / TX) % TY, gz = z0t + p / (TX * TY);
+      const bool ok = gx < EG && gy < EG && gz < EG;        // voxels outside the grid add nothing
+      const float* sp = ok ? gs + ((size_t)(gz * EG + gy) * EG + gx) * COUT + 4 * c4 : gs;
+      if constexpr (COUT == 1)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
+                     :: "r"(smem_u32(s_f + p)), "l"(sp), "r"(ok ? 4 : 0) : "memory");
+      else
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
                      :: "r"(smem_u32(s_f + p * HID + 4 * c4)), "l"(sp), "r"(ok ? 16 : 0) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // the next grid's tiles are copied while this grid's products run; the
+  // staging areas are rounded into bfloat16 rows (the gradient also summed
+  // for the bias gradient) at the start of each step
+  int buf = 0;
+  if (blockIdx.y < (unsigned)n_grids) copy((int)blockIdx.y, 0);
+  for (int n = blockIdx.y; n < n_grids; n += kWgradSplitTc) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();                                         // this grid's tiles are in; the other buffer is free
+    uint8_t* sx = smb + buf * (kXB + kGB);
+    uint8_t* sg = sx + kXB;
+    if constexpr (COUT == 1) {
+      for (int p = threadIdx.x; p < TZ * TY * TX; p += kWgThreads) {
+        const float v = s_f[p];
+        bsum.x += v;
+        store1(sg + p * kRowB, v);
       }
-      asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    int buf = 0;
-    if (blockIdx.y < (unsigned)n_grids) copy((int)blockIdx.y, 0);
-    for (int n = blockIdx.y; n < n_grids; n += kWgradSplitTc) {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-      __syncthreads();                                       // this grid's tiles are in; the other buffer is free
-      uint8_t* sg = smb + buf * (kXB + kGB) + kXB;
+    } else {
       for (int q = threadIdx.x; q < TZ * TY * TX * (HID / 4); q += kWgThreads) {
         const float4 v = *reinterpret_cast<const float4*>(s_f + 4 * q);
         bsum.x += v.x;
@@ -697,70 +739,13 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
         bsum.w += v.w;
         store4(sg + (q / (HID / 4)) * kRowB, q % (HID / 4), v);
       }
-      __syncthreads();                                       // rows rounded; the staging area is free
-      if (n + kWgradSplitTc < n_grids) copy(n + kWgradSplitTc, buf ^ 1);
-      compute(smem_u32(smb + buf * (kXB + kGB)), smem_u32(sg));
-      buf ^= 1;
     }
-  } else {
-    for (int n = blockIdx.y; n < n_grids; n += kWgradSplitTc) {
-      const uint8_t* src = static_cast<const uint8_t*>(in) + (size_t)n * NV * CIN * (INBF ? 2 : 4);
-      const float* gs = g + (size_t)n * NV * COUT;
-      __syncthreads();
-      for (int q0 = threadIdx.x; q0 < kHaloItems; q0 += kLoadBatch * kWgThreads) {
-        float4 v[kLoadBatch];
-#pragma unroll
-        for (int u = 0; u < kLoadBatch; ++u) {
-          const int q = q0 + u * kWgThreads;
-          const int c4 = CIN == 1 ? 0 : q % kInQ, p = CIN == 1 ? q : q / kInQ;
-          const int hx = p % HX, hy = (p / HX) % HY, hz = p / (HX * HY);
-          const int gx = x0t + hx - 1, gy = y0t + hy - 1, gz = z0t + hz - 1;
-          v[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-          if (q < kHaloItems && gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG) {
-            const size_t vox = (size_t)(gz * EG + gy) * EG + gx;
-            if constexpr (CIN == 1) v[u].x = __ldg(reinterpret_cast<const float*>(src) + vox);
-            else if constexpr (INBF) v[u] = __ldg(reinterpret_cast<const float4*>(src + vox * HID * 2) + c4);
-            else v[u] = __ldg(reinterpret_cast<const float4*>(src + vox * HID * 4) + c4);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kLoadBatch; ++u) {
-          const int q = q0 + u * kWgThreads;
-          if (q >= kHaloItems) continue;
-          if constexpr (CIN == 1) store1(s_x + q * kRowB, v[u].x);
-          else if constexpr (INBF) *reinterpret_cast<float4*>(s_x + (q / kInQ) * kRowB + 16 * (q % kInQ)) = v[u];
-          else store4(s_x + (q / kInQ) * kRowB, q % kInQ, v[u]);
-        }
-      }
-      for (int q0 = threadIdx.x; q0 < kTileItems; q0 += kLoadBatch * kWgThreads) {
-        float4 v[kLoadBatch];
-#pragma unroll
-        for (int u = 0; u < kLoadBatch; ++u) {
-          const int q = q0 + u * kWgThreads;
-          const int c4 = COUT == 1 ? 0 : q % (HID / 4), p = COUT == 1 ? q : q / (HID / 4);
-          const int gx = x0t + p % TX, gy = y0t + (p / TX) % TY, gz = z0t + p / (TX * TY);
-          v[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);         // voxels outside the grid add nothing
-          if (q < kTileItems && gx < EG && gy < EG && gz < EG) {
-            const size_t vox = (size_t)(gz * EG + gy) * EG + gx;
-            if constexpr (COUT == 1) v[u].x = __ldg(gs + vox);
-            else v[u] = __ldg(reinterpret_cast<const float4*>(gs + vox * HID) + c4);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kLoadBatch; ++u) {
-          const int q = q0 + u * kWgThreads;
-          bsum.x += v[u].x;
-          bsum.y += v[u].y;
-          bsum.z += v[u].z;
-          bsum.w += v[u].w;
-          if (q >= kTileItems) continue;
-          if constexpr (COUT == 1) store1(s_g + q * kRowB, v[u].x);
-          else store4(s_g + (q / (HID / 4)) * kRowB, q % (HID / 4), v[u]);
-        }
-      }
-      __syncthreads();
-      compute(x_base, g_base);
-    }
+    if constexpr (CIN == 1)
+      for (int p = threadIdx.x; p < HZ * HY * HX; p += kWgThreads) store1(sx + p * kRowB, s_h[p]);
+    __syncthreads();                                         // rows rounded; the staging areas are free
+    if (n + kWgradSplitTc < n_grids) copy(n + kWgradSplitTc, buf ^ 1);
+    compute(smem_u32(sx), smem_u32(sg));
+    buf ^= 1;
   }
 #pragma unroll
   for (int j = 0; j < kTapsPerWarp; ++j) {
@@ -807,9 +792,11 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
   }
 }
 
-// one buffer of rows, or two and the binary32 staging area of the gradient tile
-constexpr size_t wgrad_mma_smem(bool pipe) {
-  return (size_t)(HZ * HY * HX + TZ * TY * TX) * kRowB * (pipe ? 2 : 1) + (pipe ? (size_t)TZ * TY * TX * HID * 4 : 0);
+// two buffers of rows and the binary32 staging areas
+template <int CIN, int COUT>
+constexpr size_t wgrad_mma_smem() {
+  return (size_t)(HZ * HY * HX + TZ * TY * TX) * kRowB * 2 + (size_t)TZ * TY * TX * COUT * 4 +
+         (CIN == 1 ? (size_t)HZ * HY * HX * 4 : 0);
 }
 
 // ------------------------------------------------------ weight gradients
@@ -966,7 +953,7 @@ cudaError_t conv_tc(const void* in, const __nv_bfloat16* wb, const float* b, voi
 
 template <int CIN, int COUT, bool INBF>
 cudaError_t wgrad_tc(const void* in, const float* g, uint32_t n, float* dW, float* db, cudaStream_t s) {
-  constexpr size_t sm = wgrad_mma_smem(INBF && CIN == HID && COUT == HID);
+  constexpr size_t sm = wgrad_mma_smem<CIN, COUT>();
   auto k = wgrad_mma_kernel<CIN, COUT, INBF>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
