@@ -295,15 +295,18 @@ __device__ __forceinline__ void tz_copy_async(uint8_t* slot, const void* __restr
 
 __device__ __forceinline__ int tz_block(int zo) { return ((-zo - 1) % 8 + 8) % 8; }
 
-// in: binary32, or bfloat16 when INBF (the hidden activations); out: the
-// hidden activations as bfloat16 (ReLU epilogue), else binary32; aux: the
-// activations (bfloat16) whose sign masks the gradient, or x0 (binary32)
+// in: binary32, or bfloat16 when INBF (the hidden activations and
+// gradients); out: bfloat16 (the hidden activations, ReLU epilogue, and
+// the hidden gradients, mask epilogue), or binary32 (the output y); aux:
+// the activations (bfloat16) whose sign masks the gradient, or x0
+// (binary32); db (mask epilogue): the bias gradient, += the sum over
+// voxels of the binary32 gradient before it is rounded
 template <int EPI, int CIN, int COUT, bool INBF>
 __global__ void __launch_bounds__(kTzThreads, kTzBlocksPerSm) conv_tz_kernel(const void* __restrict__ in,
                                                                const __nv_bfloat16* __restrict__ wb,
                                                                const float* __restrict__ bias, void* __restrict__ out,
                                                                const void* __restrict__ aux, uint32_t n_grids,
-                                                               uint32_t* __restrict__ err) {
+                                                               float* __restrict__ db, uint32_t* __restrict__ err) {
   using S = TzShape<CIN, COUT>;
   constexpr int CP = S::COUTP;
   extern __shared__ __align__(128) uint8_t smz[];
@@ -350,6 +353,10 @@ __global__ void __launch_bounds__(kTzThreads, kTzBlocksPerSm) conv_tz_kernel(con
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   const uint32_t a0 = smem_u32(s_a), b0 = smem_u32(s_b);
   constexpr int kAux = EPI == kEpiMask ? COUT / 8 : 1;       // 8 bfloat16 mask values, or x0
+  static_assert(EPI != kEpiMask || COUT == HID, "the mask epilogue writes 32-channel gradients");
+  float bacc[EPI == kEpiMask ? COUT : 1];                    // this row's gradient sums (bias gradient)
+#pragma unroll
+  for (int c = 0; c < (EPI == kEpiMask ? COUT : 1); ++c) bacc[c] = 0.0f;
   constexpr int kLd = kTzThreads;                          // threads staging an input slice
   const int issuer = 128;                                    // the thread issuing the matrix instructions
   int jb = 0;        // input slices issued by the earlier marches: the barriers' phases run on
@@ -485,19 +492,24 @@ __global__ void __launch_bounds__(kTzThreads, kTzBlocksPerSm) conv_tz_kernel(con
                   }
                   o8[c8] = make_uint4(h[0], h[1], h[2], h[3]);
                 }
-              } else {                                         // gradient where the activation is positive
-                float4* o4 = reinterpret_cast<float4*>(static_cast<float*>(out) + v * HID);
+              } else {                                         // gradient where the activation is positive:
+                // summed in binary32 for the bias gradient, stored as bfloat16
+                uint4* o8 = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out) + v * HID);
 #pragma unroll
-                for (int c4 = 0; c4 < HID / 4; ++c4) {
-                  const uint32_t mw[2] = {(&am[c4 / 2].x)[2 * (c4 % 2)], (&am[c4 / 2].x)[2 * (c4 % 2) + 1]};
-                  float o[4];
+                for (int c8 = 0; c8 < HID / 8; ++c8) {
+                  uint32_t h[4];
 #pragma unroll
                   for (int e = 0; e < 4; ++e) {
-                    const uint32_t hbits = (mw[e / 2] >> (16 * (e % 2))) & 0xFFFFu;
-                    const float mk = __uint_as_float(hbits << 16);         // the bfloat16 value, exactly
-                    o[e] = mk > 0.0f ? __uint_as_float(r[4 * c4 + e]) : 0.0f;
+                    const uint32_t mw = (&am[c8].x)[e];      // mask values of channels 8 c8 + 2 e, + 1
+                    const int c = 8 * c8 + 2 * e;
+                    const float lo = __uint_as_float(mw << 16) > 0.0f ? __uint_as_float(r[c]) : 0.0f;
+                    const float hi = __uint_as_float(mw & 0xFFFF0000u) > 0.0f ? __uint_as_float(r[c + 1]) : 0.0f;
+                    bacc[c] += lo;
+                    bacc[c + 1] += hi;
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
+                    h[e] = *reinterpret_cast<const uint32_t*>(&b2);
                   }
-                  o4[c4] = make_float4(o[0], o[1], o[2], o[3]);
+                  o8[c8] = make_uint4(h[0], h[1], h[2], h[3]);
                 }
               }
             }
@@ -545,6 +557,22 @@ __global__ void __launch_bounds__(kTzThreads, kTzBlocksPerSm) conv_tz_kernel(con
     const int ip = issued - 1;
     mbar_wait(smem_u32(&s_mbar[ip & 3]), (uint32_t)((ip >> 2) & 1));
   }
+  if constexpr (EPI == kEpiMask) {
+    // the bias gradient: the readout rows' sums through shared memory (the
+    // ring, no longer read), then one add per channel and block
+    __syncthreads();
+    float* s_red = reinterpret_cast<float*>(s_a);            // COUT x 128 floats
+    if (warp < 4) {
+#pragma unroll
+      for (int c = 0; c < COUT; ++c) s_red[c * 128 + tid] = bacc[c];
+    }
+    __syncthreads();
+    if (tid < COUT && db != nullptr && !s_fail) {
+      float t = 0.0f;
+      for (int q = 0; q < 128; ++q) t += s_red[tid * 128 + q];
+      atomicAdd(db + tid, t);
+    }
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
@@ -581,7 +609,7 @@ constexpr int kWgradSplitTc = 2;
 constexpr int kWgWarps = 16, kWgThreads = 32 * kWgWarps;   // two taps a warp
 template <int CIN, int COUT, bool INBF>
 __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __restrict__ in,
-                                                                const float* __restrict__ g, int n_grids,
+                                                                const void* __restrict__ g, int n_grids,
                                                                 float* __restrict__ dW, float* __restrict__ db) {
   // a single channel takes channel 0 of rows that are zero elsewhere: one
   // 16-channel m tile (input) or one 8-channel n tile (gradient)
@@ -606,20 +634,18 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
   // the one-channel input
   static_assert(INBF ? CIN == HID : CIN == 1, "the input is the bfloat16 activations or the one-channel grid");
   constexpr int kXB = HZ * HY * HX * kRowB, kGB = TZ * TY * TX * kRowB;
-  float* s_f = reinterpret_cast<float*>(smb + 2 * (kXB + kGB));      // TZ * TY * TX voxels x COUT
-  float* s_h = s_f + TZ * TY * TX * COUT;                            // HZ * HY * HX voxels (one channel)
+  // the 32-channel gradient is bfloat16 (copied into its rows as it is,
+  // its bias gradient summed where it was made); the one-channel gradient
+  // is binary32 (staged, rounded, summed here)
+  constexpr bool GBF = COUT == HID;
+  float* s_f = reinterpret_cast<float*>(smb + 2 * (kXB + kGB));      // TZ * TY * TX voxels (one channel)
+  float* s_h = s_f + (GBF ? 0 : TZ * TY * TX);                       // HZ * HY * HX voxels (one channel)
   if constexpr (CIN == 1 || COUT == 1) {                    // the rows' other channels stay zero
     for (int q = threadIdx.x; q < 2 * (kXB + kGB) / 16; q += kWgThreads)
       reinterpret_cast<uint4*>(smb)[q] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
   }
-  // kWgThreads is a multiple of HID / 4: a thread's four channels are fixed
-  static_assert(kWgThreads % (HID / 4) == 0, "channel quad per thread");
   float4 bsum = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  auto store4 = [](uint8_t* row, int c4, float4 v) {
-    __nv_bfloat162 h[2] = {__floats2bfloat162_rn(v.x, v.y), __floats2bfloat162_rn(v.z, v.w)};
-    *reinterpret_cast<uint2*>(row + 8 * c4) = *reinterpret_cast<const uint2*>(h);
-  };
   auto store1 = [](uint8_t* row, float v) { *reinterpret_cast<__nv_bfloat16*>(row) = __float2bfloat16_rn(v); };
   // the products of one grid's tiles: warp w, taps w and w + 16; with a
   // single channel on either side the two taps share the B fragments of
@@ -699,18 +725,22 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
                      :: "r"(smem_u32(s_h + p)), "l"(sp), "r"(ok ? 4 : 0) : "memory");
       }
     }
-    const float* gs = g + (size_t)n * NV * COUT;
-    for (int q = threadIdx.x; q < TZ * TY * TX * (COUT == 1 ? 1 : HID / 4); q += kWgThreads) {
-      const int c4 = COUT == 1 ? 0 : q % (HID / 4), p = COUT == 1 ? q : q / (HID / 4);
+    for (int q = threadIdx.x; q < TZ * TY * TX * (GBF ? HID / 8 : 1); q += kWgThreads) {
+      const int c8 = GBF ? q % (HID / 8) : 0, p = GBF ? q / (HID / 8) : q;
       const int gx = x0t + p % TX, gy = y0t + (p / TX) % TY, gz = z0t + p / (TX * TY);
       const bool ok = gx < EG && gy < EG && gz < EG;        // voxels outside the grid add nothing
-      const float* sp = ok ? gs + ((size_t)(gz * EG + gy) * EG + gx) * COUT + 4 * c4 : gs;
-      if constexpr (COUT == 1)
+      const size_t vox = (size_t)(gz * EG + gy) * EG + gx;
+      if constexpr (GBF) {
+        const __nv_bfloat16* gs = static_cast<const __nv_bfloat16*>(g) + (size_t)n * NV * HID;
+        const __nv_bfloat16* sp = ok ? gs + vox * HID + 8 * c8 : gs;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                     :: "r"(smem_u32(sx + kXB + p * kRowB + 16 * c8)), "l"(sp), "r"(ok ? 16 : 0) : "memory");
+      } else {
+        const float* gs = static_cast<const float*>(g) + (size_t)n * NV;
+        const float* sp = ok ? gs + vox : gs;
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
                      :: "r"(smem_u32(s_f + p)), "l"(sp), "r"(ok ? 4 : 0) : "memory");
-      else
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
-                     :: "r"(smem_u32(s_f + p * HID + 4 * c4)), "l"(sp), "r"(ok ? 16 : 0) : "memory");
+      }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
@@ -724,25 +754,18 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
     __syncthreads();                                         // this grid's tiles are in; the other buffer is free
     uint8_t* sx = smb + buf * (kXB + kGB);
     uint8_t* sg = sx + kXB;
-    if constexpr (COUT == 1) {
-      for (int p = threadIdx.x; p < TZ * TY * TX; p += kWgThreads) {
-        const float v = s_f[p];
-        bsum.x += v;
-        store1(sg + p * kRowB, v);
+    if constexpr (!GBF || CIN == 1) {
+      if constexpr (!GBF) {
+        for (int p = threadIdx.x; p < TZ * TY * TX; p += kWgThreads) {
+          const float v = s_f[p];
+          bsum.x += v;
+          store1(sg + p * kRowB, v);
+        }
       }
-    } else {
-      for (int q = threadIdx.x; q < TZ * TY * TX * (HID / 4); q += kWgThreads) {
-        const float4 v = *reinterpret_cast<const float4*>(s_f + 4 * q);
-        bsum.x += v.x;
-        bsum.y += v.y;
-        bsum.z += v.z;
-        bsum.w += v.w;
-        store4(sg + (q / (HID / 4)) * kRowB, q % (HID / 4), v);
-      }
+      if constexpr (CIN == 1)
+        for (int p = threadIdx.x; p < HZ * HY * HX; p += kWgThreads) store1(sx + p * kRowB, s_h[p]);
+      __syncthreads();                                       // rows rounded; the staging areas are free
     }
-    if constexpr (CIN == 1)
-      for (int p = threadIdx.x; p < HZ * HY * HX; p += kWgThreads) store1(sx + p * kRowB, s_h[p]);
-    __syncthreads();                                         // rows rounded; the staging areas are free
     if (n + kWgradSplitTc < n_grids) copy(n + kWgradSplitTc, buf ^ 1);
     compute(smem_u32(sx), smem_u32(sg));
     buf ^= 1;
@@ -765,37 +788,26 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
         }
       }
   }
-  // bias gradient: the threads of one channel quad (of the one channel),
-  // then one add per channel
-  __syncthreads();
-  float4* s_red = reinterpret_cast<float4*>(smb);
-  s_red[threadIdx.x] = bsum;
-  __syncthreads();
-  if constexpr (COUT == 1) {
+  // bias gradient of the one output channel: the threads' sums, then one
+  // add per block (a 32-channel gradient's bias gradient is summed by the
+  // input-gradient pass that makes it)
+  if constexpr (!GBF) {
+    __syncthreads();
+    float* s_red = reinterpret_cast<float*>(smb);
+    s_red[threadIdx.x] = bsum.x;
+    __syncthreads();
     if (threadIdx.x == 0) {
       float t = 0.0f;
-      for (int q = 0; q < kWgThreads; ++q) t += s_red[q].x;
+      for (int q = 0; q < kWgThreads; ++q) t += s_red[q];
       atomicAdd(&db[0], t);
     }
-  } else if (threadIdx.x < HID / 4) {
-    float4 t = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    for (int q = threadIdx.x; q < kWgThreads; q += HID / 4) {
-      t.x += s_red[q].x;
-      t.y += s_red[q].y;
-      t.z += s_red[q].z;
-      t.w += s_red[q].w;
-    }
-    atomicAdd(&db[4 * threadIdx.x], t.x);
-    atomicAdd(&db[4 * threadIdx.x + 1], t.y);
-    atomicAdd(&db[4 * threadIdx.x + 2], t.z);
-    atomicAdd(&db[4 * threadIdx.x + 3], t.w);
   }
 }
 
-// two buffers of rows and the binary32 staging areas
+// two buffers of rows and the binary32 staging areas of the one-channel sides
 template <int CIN, int COUT>
 constexpr size_t wgrad_mma_smem() {
-  return (size_t)(HZ * HY * HX + TZ * TY * TX) * kRowB * 2 + (size_t)TZ * TY * TX * COUT * 4 +
+  return (size_t)(HZ * HY * HX + TZ * TY * TX) * kRowB * 2 + (COUT == 1 ? (size_t)TZ * TY * TX * 4 : 0) +
          (CIN == 1 ? (size_t)HZ * HY * HX * 4 : 0);
 }
 
@@ -888,7 +900,7 @@ struct ro_mc {
   // (layers 0 and 3 padded: one real input channel, one real output row)
   __nv_bfloat16 *wf0, *wf1, *wf2, *wf3, *wd1, *wd2, *wd3;
   __nv_bfloat16 *a1, *a2, *a3;        // hidden activations (after ReLU), n * NV * 32, bfloat16
-  float *ga, *gb, *gc;                // hidden gradients, n * NV * 32
+  __nv_bfloat16 *ga, *gb, *gc;        // hidden gradients, n * NV * 32, bfloat16
   float *g4, *y;                      // output gradient and output, n * NV
   float* loss;                        // scratch loss when the caller passes none
   uint32_t* flag;                     // set by a tensor-core wait that gave up (latched)
@@ -916,13 +928,13 @@ McLayout mc_layout(uint32_t nb) {
   McLayout L{};
   uint64_t o = 0;
   auto take = [&](uint64_t bytes) { const uint64_t at = o; o = mc_align(o + bytes); return at; };
-  const uint64_t pb = (uint64_t)RO_MC_PARAMS * 4, hid = (uint64_t)nb * NV * HID * 4, act = (uint64_t)nb * NV * HID * 2, one = (uint64_t)nb * NV * 4;
+  const uint64_t pb = (uint64_t)RO_MC_PARAMS * 4, act = (uint64_t)nb * NV * HID * 2, one = (uint64_t)nb * NV * 4;
   L.P = take(pb); L.Pq = take(pb); L.M = take(pb); L.V = take(pb); L.G = take(pb); L.flag = take(4);
   L.wf0 = take(27ull * HID * HID * 2); L.wf1 = take(27ull * HID * HID * 2); L.wf2 = take(27ull * HID * HID * 2);
   L.wf3 = take(27ull * 16 * HID * 2);
   L.wd1 = take(27ull * HID * HID * 2); L.wd2 = take(27ull * HID * HID * 2); L.wd3 = take(27ull * HID * HID * 2);
   L.wend = o;
-  L.a1 = take(act); L.a2 = take(act); L.a3 = take(act); L.ga = take(hid); L.gb = take(hid); L.gc = take(hid);
+  L.a1 = take(act); L.a2 = take(act); L.a3 = take(act); L.ga = take(act); L.gb = take(act); L.gc = take(act);
   L.g4 = take(one); L.y = take(one); L.loss = take(4);
   L.total = o;
   return L;
@@ -930,7 +942,7 @@ McLayout mc_layout(uint32_t nb) {
 
 template <int EPI, int CIN, int COUT, bool INBF>
 cudaError_t conv_tc(const void* in, const __nv_bfloat16* wb, const float* b, void* out, const void* aux, uint32_t n,
-                    uint32_t* flag, cudaStream_t s) {
+                    uint32_t* flag, cudaStream_t s, float* db = nullptr) {
   auto k = conv_tz_kernel<EPI, CIN, COUT, INBF>;
   constexpr size_t sm = TzShape<CIN, COUT>::SMEM;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -947,12 +959,12 @@ cudaError_t conv_tc(const void* in, const __nv_bfloat16* wb, const float* b, voi
   if (e != cudaSuccess) return e;
   const uint32_t total = n * (uint32_t)(kTzMTiles * EG);
   const uint32_t blocks = std::min((uint32_t)(kTzBlocksPerSm * sms), (total + kTzMinShare - 1) / kTzMinShare);
-  k<<<blocks, kTzThreads, sm, s>>>(in, wb, b, out, aux, n, flag);
+  k<<<blocks, kTzThreads, sm, s>>>(in, wb, b, out, aux, n, db, flag);
   return cudaGetLastError();
 }
 
 template <int CIN, int COUT, bool INBF>
-cudaError_t wgrad_tc(const void* in, const float* g, uint32_t n, float* dW, float* db, cudaStream_t s) {
+cudaError_t wgrad_tc(const void* in, const void* g, uint32_t n, float* dW, float* db, cudaStream_t s) {
   constexpr size_t sm = wgrad_mma_smem<CIN, COUT>();
   auto k = wgrad_mma_kernel<CIN, COUT, INBF>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1000,15 +1012,18 @@ cudaError_t mc_backward(ro_mc* m, uint32_t n, const float* x0, const float* targ
   // layer 4 (32 -> 1)
   if (e == cudaSuccess) e = fork(0);
   if (e == cudaSuccess) e = wgrad_tc<HID, 1, true>(m->a3, m->g4, n, G + kWOff[3], G + kBOff[3], s2);
-  if (e == cudaSuccess) e = conv_tc<kEpiMask, 1, HID, false>(m->g4, m->wd3, zero_bias, m->ga, m->a3, n, m->flag, s);
+  if (e == cudaSuccess)
+    e = conv_tc<kEpiMask, 1, HID, false>(m->g4, m->wd3, zero_bias, m->ga, m->a3, n, m->flag, s, G + kBOff[2]);
   // layer 3 (32 -> 32)
   if (e == cudaSuccess) e = fork(1);
   if (e == cudaSuccess) e = wgrad_tc<HID, HID, true>(m->a2, m->ga, n, G + kWOff[2], G + kBOff[2], s2);
-  if (e == cudaSuccess) e = conv_tc<kEpiMask, HID, HID, false>(m->ga, m->wd2, zero_bias, m->gb, m->a2, n, m->flag, s);
+  if (e == cudaSuccess)
+    e = conv_tc<kEpiMask, HID, HID, true>(m->ga, m->wd2, zero_bias, m->gb, m->a2, n, m->flag, s, G + kBOff[1]);
   // layer 2 (32 -> 32)
   if (e == cudaSuccess) e = fork(3);
   if (e == cudaSuccess) e = wgrad_tc<HID, HID, true>(m->a1, m->gb, n, G + kWOff[1], G + kBOff[1], s2);
-  if (e == cudaSuccess) e = conv_tc<kEpiMask, HID, HID, false>(m->gb, m->wd1, zero_bias, m->gc, m->a1, n, m->flag, s);
+  if (e == cudaSuccess)
+    e = conv_tc<kEpiMask, HID, HID, true>(m->gb, m->wd1, zero_bias, m->gc, m->a1, n, m->flag, s, G + kBOff[0]);
   // layer 1 (1 -> 32)
   if (e == cudaSuccess) e = wgrad_tc<1, HID, false>(x0, m->gc, n, G + kWOff[0], G + kBOff[0], s);
   if (e == cudaSuccess) e = cudaEventRecord(m->ev[4], s2);
@@ -1045,7 +1060,7 @@ ro_status ro_mc_create(const ro_mc_desc* d, void* arena, uint64_t arena_bytes, v
   auto h = [&](uint64_t off) { return reinterpret_cast<__nv_bfloat16*>(b + off); };
   m->wf0 = h(L.wf0); m->wf1 = h(L.wf1); m->wf2 = h(L.wf2); m->wf3 = h(L.wf3);
   m->wd1 = h(L.wd1); m->wd2 = h(L.wd2); m->wd3 = h(L.wd3);
-  m->a1 = h(L.a1); m->a2 = h(L.a2); m->a3 = h(L.a3); m->ga = f(L.ga); m->gb = f(L.gb); m->gc = f(L.gc);
+  m->a1 = h(L.a1); m->a2 = h(L.a2); m->a3 = h(L.a3); m->ga = h(L.ga); m->gb = h(L.gb); m->gc = h(L.gc);
   m->g4 = f(L.g4); m->y = f(L.y); m->loss = f(L.loss);
   m->flag = reinterpret_cast<uint32_t*>(b + L.flag);
   cudaError_t e = cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking);

@@ -71,11 +71,11 @@ def test_compensator_header_exports_and_host_checks_without_gpu():
     for n in (1, 2, 3):
         assert L.ro_mc_query_bytes(ctypes.byref(mc.McDesc(n)), ctypes.byref(size)) == 0
         per.append(size.value)
-    # a grid adds three 32-channel activations (bfloat16), three 32-channel
-    # gradient buffers, the output gradient and the output (binary32, 34^3
+    # a grid adds three 32-channel activations and three 32-channel gradient
+    # buffers (bfloat16), the output gradient and the output (binary32, 34^3
     # voxels); each of the eight regions is rounded up to 256 bytes, so the
     # step differs from that by less than 8 x 256
-    grid = 3 * mc.VOXELS * 32 * 2 + 3 * mc.VOXELS * 32 * 4 + 2 * mc.VOXELS * 4
+    grid = 6 * mc.VOXELS * 32 * 2 + 2 * mc.VOXELS * 4
     for a, b in ((per[0], per[1]), (per[1], per[2])):
         assert abs((b - a) - grid) < 8 * 256
     assert all(p % 256 == 0 for p in per)
