@@ -604,7 +604,12 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t&
 // rows, a binary32 input (the one-channel grid) and the binary32 gradient
 // tile into staging areas that are rounded into the rows at the start of
 // their step.  The bias gradient db[co] = sum over voxels of g[v][co] is
-// summed in binary32 from the staging area.
+// summed in binary32 from the staging area.  With one input channel the
+// taps take the M dimension instead: dW[t][co] = sum over voxels of
+// x[v + off(t)] g[v][co], M = 27 taps (32 rows), N = 32 channels, K =
+// voxels; warp w takes voxels 16 w .. 16 w + 15 of the tile, builds its A
+// fragments from the bfloat16 halo values, and the warps' sums are added
+// through shared memory at the end.
 constexpr int kWgradSplitTc = 2;
 constexpr int kWgWarps = 16, kWgThreads = 32 * kWgWarps;   // two taps a warp
 template <int CIN, int COUT, bool INBF>
@@ -698,6 +703,46 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
       }
     }
   };
+  // one input channel: the taps as M (see above); acc[mt][0][nt] holds
+  // taps 16 mt + g4 (+ 8) and channels 8 nt + 2 t4 (+ 1) of this warp's
+  // 16 voxels
+  auto compute_taps = [&](const uint16_t* xh, uint32_t gb) {
+    static_assert(CIN != 1 || (kWgWarps * 16 == TZ * TY * TX && MT == 1 && kTapsPerWarp == 2), "a 16-voxel chunk per warp");
+    const int kc = warp;
+    uint32_t b[4][2];
+    {
+      const int pb = 16 * kc + mr + 8 * (mi & 1);
+#pragma unroll
+      for (int nj = 0; nj < (NT + 1) / 2; ++nj)
+        ldsm_x4_t(gb + pb * kRowB + 16 * (mi >> 1) + 32 * nj, b[2 * nj][0], b[2 * nj][1], b[2 * nj + 1][0],
+                  b[2 * nj + 1][1]);
+    }
+    // halo index of tile voxels 16 kc + 2 t4 + {0, 1, 8, 9} (tap (0, 0, 0) at offset 0)
+    int hp[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int pv = 16 * kc + 2 * t4 + (q & 1) + 8 * (q >> 1);
+      hp[q] = ((pv / (TX * TY)) * HY + (pv / TX) % TY) * HX + pv % TX;
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      uint32_t a[4];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {                          // rows (taps) 16 mt + g4 and + 8
+        const int t = 16 * mt + g4 + 8 * h;
+        const int toff = ((t / 9) * HY + (t / 3) % 3) * HX + t % 3;
+        uint32_t lo = 0u, hi = 0u;
+        if (t < 27) {
+          lo = (uint32_t)xh[hp[0] + toff] | ((uint32_t)xh[hp[1] + toff] << 16);
+          hi = (uint32_t)xh[hp[2] + toff] | ((uint32_t)xh[hp[3] + toff] << 16);
+        }
+        a[h] = lo;                                           // k 2 t4, 2 t4 + 1
+        a[2 + h] = hi;                                       // k 2 t4 + 8, 2 t4 + 9
+      }
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][0][nt], a[0], a[1], a[2], a[3], b[nt][0], b[nt][1]);
+    }
+  };
   // grid n's tiles into buffer buf with cp.async, one group: the bfloat16
   // input straight into its rows, the binary32 input and gradient into
   // their staging areas (zero-filled outside the grid: source size 0)
@@ -762,14 +807,38 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
           store1(sg + p * kRowB, v);
         }
       }
-      if constexpr (CIN == 1)
-        for (int p = threadIdx.x; p < HZ * HY * HX; p += kWgThreads) store1(sx + p * kRowB, s_h[p]);
-      __syncthreads();                                       // rows rounded; the staging areas are free
+      if constexpr (CIN == 1)                                // the halo as an array of bfloat16 values
+        for (int p = threadIdx.x; p < HZ * HY * HX; p += kWgThreads)
+          reinterpret_cast<__nv_bfloat16*>(sx)[p] = __float2bfloat16_rn(s_h[p]);
+      __syncthreads();                                       // rounded; the staging areas are free
     }
     if (n + kWgradSplitTc < n_grids) copy(n + kWgradSplitTc, buf ^ 1);
-    compute(smem_u32(sx), smem_u32(sg));
+    if constexpr (CIN == 1) compute_taps(reinterpret_cast<const uint16_t*>(sx), smem_u32(sg));
+    else compute(smem_u32(sx), smem_u32(sg));
     buf ^= 1;
   }
+  if constexpr (CIN == 1) {
+    // the warps' sums (acc[mt][0][nt]: taps 16 mt + g4 (+ 8), channels
+    // 8 nt + 2 t4 (+ 1)) added through shared memory, one add per weight
+    __syncthreads();
+    float* s_red = reinterpret_cast<float*>(smb);            // kWgWarps x 32 taps x 32 channels
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          const int t = 16 * mt + g4 + 8 * h, co = 8 * nt + 2 * t4;
+          s_red[(warp * 32 + t) * 32 + co] = acc[mt][0][nt][2 * h];
+          s_red[(warp * 32 + t) * 32 + co + 1] = acc[mt][0][nt][2 * h + 1];
+        }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 27 * COUT; e += kWgThreads) {
+      float t = 0.0f;
+      for (int w = 0; w < kWgWarps; ++w) t += s_red[w * 32 * 32 + e];
+      atomicAdd(&dW[e], t);                                  // dW[t][0][co] at t * COUT + co
+    }
+  } else {
 #pragma unroll
   for (int j = 0; j < kTapsPerWarp; ++j) {
     const int t = warp + kWgWarps * j;
@@ -787,6 +856,7 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
           if (co + 1 < COUT) atomicAdd(&dW[(t * CIN + ci) * COUT + co + 1], acc[j][mt][nt][2 * h + 1]);
         }
       }
+  }
   }
   // bias gradient of the one output channel: the threads' sums, then one
   // add per block (a 32-channel gradient's bias gradient is summed by the
