@@ -609,7 +609,12 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t&
 // x[v + off(t)] g[v][co], M = 27 taps (32 rows), N = 32 channels, K =
 // voxels; warp w takes voxels 16 w .. 16 w + 15 of the tile, builds its A
 // fragments from the bfloat16 halo values, and the warps' sums are added
-// through shared memory at the end.
+// through shared memory at the end.  With one output channel the taps
+// take the N dimension: dW[t][ci] = sum over halo voxels u of x[u][ci]
+// g[u - off(t)] (zero where u - off(t) leaves the tile), M = 32 channels,
+// N = 27 taps (32 columns), K = the 600 halo voxels; warp w takes chunks
+// w, w + 16, w + 32 of 16 halo voxels and builds its B fragments from the
+// bfloat16 gradient values of the tile.
 constexpr int kWgradSplitTc = 2;
 constexpr int kWgWarps = 16, kWgThreads = 32 * kWgWarps;   // two taps a warp
 template <int CIN, int COUT, bool INBF>
@@ -627,6 +632,14 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
   const int mi = lane >> 3, mr = lane & 7;
   constexpr int kTapsPerWarp = (27 + kWgWarps - 1) / kWgWarps;
   float acc[kTapsPerWarp][MT][NT][4];
+  constexpr bool TAPS_N = CIN == HID && COUT == 1;           // one output channel: the taps as N
+  float accn[TAPS_N ? 2 : 1][4][4];                          // [mt][tap n tile][fragment]
+#pragma unroll
+  for (int mt = 0; mt < (TAPS_N ? 2 : 1); ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) accn[mt][nt][q] = 0.0f;
 #pragma unroll
   for (int j = 0; j < kTapsPerWarp; ++j)
 #pragma unroll
@@ -743,6 +756,42 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
       for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][0][nt], a[0], a[1], a[2], a[3], b[nt][0], b[nt][1]);
     }
   };
+  // one output channel: the taps as N (see above); accn[mt][nt] holds
+  // channels 16 mt + g4 (+ 8) and taps 8 nt + 2 t4 (+ 1)
+  auto compute_taps_n = [&](uint32_t xb, const uint16_t* gv) {
+    constexpr int kChunks = (HZ * HY * HX + 15) / 16;        // 38; rows past the halo meet zero B values
+    for (int kc = warp; kc < kChunks; kc += kWgWarps) {
+      uint32_t a[2][4];
+      const int pa = 16 * kc + mr + 8 * (mi >> 1);
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+        ldsm_x4_t(xb + pa * kRowB + 16 * (mi & 1) + 32 * mt, a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+      // halo coordinates of u = 16 kc + 2 t4 + {0, 1, 8, 9}
+      int hx[4], hy[4], hz[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int u = 16 * kc + 2 * t4 + (q & 1) + 8 * (q >> 1);
+        hx[q] = u % HX;
+        hy[q] = (u / HX) % HY;
+        hz[q] = u / (HX * HY);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int t = 8 * nt + g4;                           // this lane's tap (B column)
+        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+        uint32_t bv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int vx = hx[q] - dx, vy = hy[q] - dy, vz = hz[q] - dz;
+          const bool in = t < 27 && vx >= 0 && vx < TX && vy >= 0 && vy < TY && vz >= 0 && vz < TZ;
+          bv[q] = in ? (uint32_t)gv[(vz * TY + vy) * TX + vx] : 0u;
+        }
+        const uint32_t b0 = bv[0] | (bv[1] << 16), b1 = bv[2] | (bv[3] << 16);
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) mma_bf16(accn[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+      }
+    }
+  };
   // grid n's tiles into buffer buf with cp.async, one group: the bfloat16
   // input straight into its rows, the binary32 input and gradient into
   // their staging areas (zero-filled outside the grid: source size 0)
@@ -800,11 +849,11 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
     uint8_t* sx = smb + buf * (kXB + kGB);
     uint8_t* sg = sx + kXB;
     if constexpr (!GBF || CIN == 1) {
-      if constexpr (!GBF) {
+      if constexpr (!GBF) {                                  // one channel: a compact bfloat16 array
         for (int p = threadIdx.x; p < TZ * TY * TX; p += kWgThreads) {
           const float v = s_f[p];
           bsum.x += v;
-          store1(sg + p * kRowB, v);
+          reinterpret_cast<__nv_bfloat16*>(sg)[p] = __float2bfloat16_rn(v);
         }
       }
       if constexpr (CIN == 1)                                // the halo as an array of bfloat16 values
@@ -814,6 +863,7 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
     }
     if (n + kWgradSplitTc < n_grids) copy(n + kWgradSplitTc, buf ^ 1);
     if constexpr (CIN == 1) compute_taps(reinterpret_cast<const uint16_t*>(sx), smem_u32(sg));
+    else if constexpr (TAPS_N) compute_taps_n(smem_u32(sx), reinterpret_cast<const uint16_t*>(sg));
     else compute(smem_u32(sx), smem_u32(sg));
     buf ^= 1;
   }
@@ -837,6 +887,27 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
       float t = 0.0f;
       for (int w = 0; w < kWgWarps; ++w) t += s_red[w * 32 * 32 + e];
       atomicAdd(&dW[e], t);                                  // dW[t][0][co] at t * COUT + co
+    }
+  } else if constexpr (TAPS_N) {
+    // the warps' sums (accn[mt][nt]: channels 16 mt + g4 (+ 8), taps
+    // 8 nt + 2 t4 (+ 1)) added through shared memory, one add per weight
+    __syncthreads();
+    float* s_red = reinterpret_cast<float*>(smb);            // kWgWarps x 32 taps x 32 channels
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          const int ci = 16 * mt + g4 + 8 * h, t = 8 * nt + 2 * t4;
+          s_red[(warp * 32 + t) * 32 + ci] = accn[mt][nt][2 * h];
+          s_red[(warp * 32 + t + 1) * 32 + ci] = accn[mt][nt][2 * h + 1];
+        }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 27 * CIN; e += kWgThreads) {
+      float t = 0.0f;
+      for (int w = 0; w < kWgWarps; ++w) t += s_red[w * 32 * 32 + e];
+      atomicAdd(&dW[e], t);                                  // dW[t][ci][0] at t * CIN + ci
     }
   } else {
 #pragma unroll
