@@ -598,9 +598,9 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t&
 // tile (halo) and the gradient tile enter shared memory as bfloat16 rows,
 // and ldmatrix.trans turns the voxel rows into the K dimension of both
 // operands.  Warp w of 16 accumulates taps w and w + 16 and adds its sums
-// once (atomically) at the end.  The block keeps two buffers and copies
-// the tiles of its next grid with cp.async while the products of this grid
-// run: a bfloat16 input (INBF: the hidden activations) straight into its
+// once (atomically) at the end.  The block keeps three buffers and copies
+// the tiles of its next two grids with cp.async while the products of this
+// grid run: a bfloat16 input (INBF: the hidden activations) straight into its
 // rows, a binary32 input (the one-channel grid) and the binary32 gradient
 // tile into staging areas that are rounded into the rows at the start of
 // their step.  The bias gradient db[co] = sum over voxels of g[v][co] is
@@ -617,6 +617,7 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t&
 // bfloat16 gradient values of the tile.
 constexpr int kWgradSplitTc = 2;
 constexpr int kWgWarps = 16, kWgThreads = 32 * kWgWarps;   // two taps a warp
+constexpr int kWgBufs = 3;                                  // tile buffers: two grids in flight
 template <int CIN, int COUT, bool INBF>
 __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __restrict__ in,
                                                                 const void* __restrict__ g, int n_grids,
@@ -648,18 +649,19 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
       for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[j][mt][nt][q] = 0.0f;
-  // two buffers of rows; binary32 staging areas for the gradient tile and
-  // the one-channel input
+  // kWgBufs buffers of rows, each with binary32 staging areas for the
+  // one-channel gradient tile and the one-channel input
   static_assert(INBF ? CIN == HID : CIN == 1, "the input is the bfloat16 activations or the one-channel grid");
   constexpr int kXB = HZ * HY * HX * kRowB, kGB = TZ * TY * TX * kRowB;
   // the 32-channel gradient is bfloat16 (copied into its rows as it is,
   // its bias gradient summed where it was made); the one-channel gradient
   // is binary32 (staged, rounded, summed here)
   constexpr bool GBF = COUT == HID;
-  float* s_f = reinterpret_cast<float*>(smb + 2 * (kXB + kGB));      // TZ * TY * TX voxels (one channel)
-  float* s_h = s_f + (GBF ? 0 : TZ * TY * TX);                       // HZ * HY * HX voxels (one channel)
-  if constexpr (CIN == 1 || COUT == 1) {                    // the rows' other channels stay zero
-    for (int q = threadIdx.x; q < 2 * (kXB + kGB) / 16; q += kWgThreads)
+  constexpr int kSF = GBF ? 0 : TZ * TY * TX, kSH = CIN == 1 ? HZ * HY * HX : 0;   // staging floats a buffer
+  float* s_f = reinterpret_cast<float*>(smb + kWgBufs * (kXB + kGB));  // [buffer] TZ * TY * TX voxels (one channel)
+  float* s_h = s_f + kWgBufs * kSF;                                    // [buffer] HZ * HY * HX voxels (one channel)
+  if constexpr (CIN == 1 || COUT == 1) {                    // bytes no copy writes are zero (finite)
+    for (int q = threadIdx.x; q < kWgBufs * (kXB + kGB) / 16; q += kWgThreads)
       reinterpret_cast<uint4*>(smb)[q] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
   }
@@ -816,7 +818,7 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
         const bool ok = gx >= 0 && gx < EG && gy >= 0 && gy < EG && gz >= 0 && gz < EG;
         const float* sp = ok ? src + (size_t)(gz * EG + gy) * EG + gx : src;
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
-                     :: "r"(smem_u32(s_h + p)), "l"(sp), "r"(ok ? 4 : 0) : "memory");
+                     :: "r"(smem_u32(s_h + buf * kSH + p)), "l"(sp), "r"(ok ? 4 : 0) : "memory");
       }
     }
     for (int q = threadIdx.x; q < TZ * TY * TX * (GBF ? HID / 8 : 1); q += kWgThreads) {
@@ -833,40 +835,50 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
         const float* gs = static_cast<const float*>(g) + (size_t)n * NV;
         const float* sp = ok ? gs + vox : gs;
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
-                     :: "r"(smem_u32(s_f + p)), "l"(sp), "r"(ok ? 4 : 0) : "memory");
+                     :: "r"(smem_u32(s_f + buf * kSF + p)), "l"(sp), "r"(ok ? 4 : 0) : "memory");
       }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  // the next grid's tiles are copied while this grid's products run; the
-  // staging areas are rounded into bfloat16 rows (the gradient also summed
-  // for the bias gradient) at the start of each step
+  // the tiles of the block's next kWgBufs - 1 grids are in flight while
+  // this grid's products run (one group of copies per step, empty past
+  // the last grid); the staging areas are rounded into bfloat16 (the
+  // gradient also summed for the bias gradient) at the start of a step
+  for (int k = 0; k < kWgBufs - 1; ++k) {
+    const int nk = (int)blockIdx.y + k * kWgradSplitTc;
+    if (nk < n_grids) copy(nk, k);
+    else asm volatile("cp.async.commit_group;" ::: "memory");
+  }
   int buf = 0;
-  if (blockIdx.y < (unsigned)n_grids) copy((int)blockIdx.y, 0);
   for (int n = blockIdx.y; n < n_grids; n += kWgradSplitTc) {
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();                                         // this grid's tiles are in; the other buffer is free
+    asm volatile("cp.async.wait_group %0;" :: "n"(kWgBufs - 2) : "memory");   // this grid's group is done
+    __syncthreads();                                         // its tiles are in; the buffer of the last step is free
     uint8_t* sx = smb + buf * (kXB + kGB);
     uint8_t* sg = sx + kXB;
     if constexpr (!GBF || CIN == 1) {
       if constexpr (!GBF) {                                  // one channel: a compact bfloat16 array
         for (int p = threadIdx.x; p < TZ * TY * TX; p += kWgThreads) {
-          const float v = s_f[p];
+          const float v = s_f[buf * kSF + p];
           bsum.x += v;
           reinterpret_cast<__nv_bfloat16*>(sg)[p] = __float2bfloat16_rn(v);
         }
       }
       if constexpr (CIN == 1)                                // the halo as an array of bfloat16 values
         for (int p = threadIdx.x; p < HZ * HY * HX; p += kWgThreads)
-          reinterpret_cast<__nv_bfloat16*>(sx)[p] = __float2bfloat16_rn(s_h[p]);
-      __syncthreads();                                       // rounded; the staging areas are free
+          reinterpret_cast<__nv_bfloat16*>(sx)[p] = __float2bfloat16_rn(s_h[buf * kSH + p]);
+      __syncthreads();                                       // rounded
     }
-    if (n + kWgradSplitTc < n_grids) copy(n + kWgradSplitTc, buf ^ 1);
+    {
+      const int nn = n + (kWgBufs - 1) * kWgradSplitTc, nb = (buf + kWgBufs - 1) % kWgBufs;
+      if (nn < n_grids) copy(nn, nb);
+      else asm volatile("cp.async.commit_group;" ::: "memory");
+    }
     if constexpr (CIN == 1) compute_taps(reinterpret_cast<const uint16_t*>(sx), smem_u32(sg));
     else if constexpr (TAPS_N) compute_taps_n(smem_u32(sx), reinterpret_cast<const uint16_t*>(sg));
     else compute(smem_u32(sx), smem_u32(sg));
-    buf ^= 1;
+    buf = (buf + 1) % kWgBufs;
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");     // (only empty groups remain)
   if constexpr (CIN == 1) {
     // the warps' sums (acc[mt][0][nt]: taps 16 mt + g4 (+ 8), channels
     // 8 nt + 2 t4 (+ 1)) added through shared memory, one add per weight
@@ -945,12 +957,14 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_mma_kernel(const void* __
   }
 }
 
-// two buffers of rows and the binary32 staging areas of the one-channel sides
+// kWgBufs buffers of rows and the binary32 staging areas of the one-channel sides
 template <int CIN, int COUT>
 constexpr size_t wgrad_mma_smem() {
-  return (size_t)(HZ * HY * HX + TZ * TY * TX) * kRowB * 2 + (COUT == 1 ? (size_t)TZ * TY * TX * 4 : 0) +
-         (CIN == 1 ? (size_t)HZ * HY * HX * 4 : 0);
+  return ((size_t)(HZ * HY * HX + TZ * TY * TX) * kRowB + (COUT == 1 ? (size_t)TZ * TY * TX * 4 : 0) +
+          (CIN == 1 ? (size_t)HZ * HY * HX * 4 : 0)) * kWgBufs;
 }
+static_assert(wgrad_mma_smem<1, HID>() <= 227 * 1024 && wgrad_mma_smem<HID, 1>() <= 227 * 1024 &&
+              wgrad_mma_smem<HID, HID>() <= 227 * 1024, "weight-gradient buffers fit a block's shared memory");
 
 // ------------------------------------------------------ weight gradients
 
