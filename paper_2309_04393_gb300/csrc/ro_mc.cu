@@ -444,6 +444,21 @@ __global__ void __launch_bounds__(kTzThreads, kTzBlocksPerSm) conv_tz_kernel(con
     for (int i = 0; i <= nz + 2; ++i) {
       if (i + 1 <= nz + 1 && tid == issuer) issue(i + 1);
       if (i + 1 <= nz + 1) issued = jb + i + 2;
+      // input slice i + 3 into the slot input slice i - 1 leaves (every
+      // instruction that read it has completed), before the readout so that
+      // its copies are in flight meanwhile; fetch slice i + 4
+      auto stage = [&]() {
+        if constexpr (INBF) {
+          // slice i + 3 copied into that slot (a group, empty past the
+          // march's end)
+          if (i + 3 <= nz + 1) tz_copy_async(s_a + ((i + 3) % kTzRing) * S::SLICE, src, f0, z0 - 1 + i + 3, tid);
+          else asm volatile("cp.async.commit_group;" ::: "memory");
+        } else {
+          if (i + 3 <= nz + 1) tz_store<CIN, INBF, kLd>(s_a + ((i + 3) % kTzRing) * S::SLICE, tid, pre);
+          if (i + 4 <= nz + 1) tz_fetch<CIN, INBF, kLd>(src, f0, z0 - 1 + i + 4, tid, pre);
+        }
+      };
+      if (i == 0) stage();
       if (i >= 1) {
         // input slice i - 1 done: output slice i - 3 is complete; read it out
         // (warps 0-3: one accumulator row each)
@@ -454,6 +469,7 @@ __global__ void __launch_bounds__(kTzThreads, kTzBlocksPerSm) conv_tz_kernel(con
           s_fail = 1;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        stage();
         if (ok && warp < 4) {
           const uint32_t taddr = tmem + lane_base + (uint32_t)(CP * tz_block(zo));
           if (zo >= 0) {
@@ -516,19 +532,9 @@ __global__ void __launch_bounds__(kTzThreads, kTzBlocksPerSm) conv_tz_kernel(con
           }
         }
       }
-      // input slice i + 3 into the slot input slice i - 1 left (every
-      // instruction that read it has completed); fetch slice i + 4
-      if constexpr (INBF) {
-        // slice i + 3 copied into that slot (a group, empty past the
-        // march's end); slice i + 2, needed by the next step's
-        // instructions, has arrived once at most one group is pending
-        if (i + 3 <= nz + 1) tz_copy_async(s_a + ((i + 3) % kTzRing) * S::SLICE, src, f0, z0 - 1 + i + 3, tid);
-        else asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-      } else {
-        if (i + 3 <= nz + 1) tz_store<CIN, INBF, kLd>(s_a + ((i + 3) % kTzRing) * S::SLICE, tid, pre);
-        if (i + 4 <= nz + 1) tz_fetch<CIN, INBF, kLd>(src, f0, z0 - 1 + i + 4, tid, pre);
-      }
+      // slice i + 2, needed by the next step's instructions, has arrived
+      // once at most one group of copies is pending
+      if constexpr (INBF) asm volatile("cp.async.wait_group 1;" ::: "memory");
       if constexpr (EPI != kEpiRelu) {                         // mask rows / residual of output slice i - 2
         const int zm = i - 2;
         if (erow && zm >= 0 && zm < nz) {
